@@ -1,0 +1,249 @@
+"""Seeded synthetic inputs for the StaRMAP workloads.
+
+This module holds no arithmetic of the method itself: it only defines the
+problem data (domain, grid size, boundary types, CFL number, material fields,
+sources and initial conditions) as plain functions of the physical
+coordinates (x, y).  Both the CUDA path and the FP64 oracle evaluate these
+functions at the staggered grid points they compute on their own.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014): a 64-bit Weyl sequence with
+increment 0x9E3779B97F4A7C15 followed by the variant-13 mixing function; a
+uniform double in [0, 1) takes the top 53 bits.
+
+Workloads (the paper's own test problems stand in for any dataset; none is
+needed):
+
+* ``gaussian_p5``      -- 2D P_5, FP64, 64x64 periodic on [-1,1]^2, sigma_a=0,
+                          sigma_s0=1, isotropic Gaussian R_0^0 (std 0.1),
+                          CFL 0.5, 100 steps (section 6.2 style pulse).
+* ``checkerboard_p13`` -- 2D P_13, FP32, 512x512 on [0,7]^2, extrapolation
+                          boundaries, 7x7 unit blocks, 11 of the 48 outer
+                          blocks absorbing (sigma_a=10), the rest scattering
+                          (sigma_s0=1), unit isotropic source in [3,4]^2,
+                          run to t=3.2 (section 6.3).
+* ``random_p39``       -- 2D P_39, FP32 (and FP64), 1024x1024 periodic on
+                          [-1,1]^2, sigma_a=0, log10 sigma_s0 uniform in
+                          [-1,1] on a 32x32 periodic lattice, bilinearly
+                          interpolated, Gaussian R_0^0 (std 0.1), 200 steps.
+* ``batched``          -- 256 uneven instances (n in 64..512, N in 3..15),
+                          piecewise-constant random media, Gaussian sources.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 stream (published definition, see module docstring)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        return (self.next_u64() >> 11) * (1.0 / (1 << 53))
+
+    def uniforms(self, count: int) -> np.ndarray:
+        return np.array([self.uniform() for _ in range(count)], dtype=np.float64)
+
+    def randint(self, hi: int) -> int:
+        """Uniform integer in [0, hi) by rejection-free scaling (hi small)."""
+        return min(int(self.uniform() * hi), hi - 1)
+
+
+# A field is a function f(t, x, y) -> array, broadcasting over numpy arrays.
+Field = Callable[[float, np.ndarray, np.ndarray], np.ndarray]
+
+
+@dataclasses.dataclass
+class Problem:
+    """Problem data in the spirit of the paper's ``par`` struct (section 5.1)."""
+
+    name: str
+    N: int                                   # moment order
+    ax: Tuple[float, float, float, float]    # xmin, xmax, ymin, ymax
+    n: Tuple[int, int]                       # cells in x and y
+    bc: Tuple[str, str]                      # 'periodic' | 'extrapolation' per axis
+    cn: float = 0.5                          # CFL number
+    precision: str = "fp64"                  # 'fp64' | 'fp32'
+    system: str = "pn2d"                     # 'pn2d' | 'slab'
+    sigma_a: Field = None
+    sigma_s0: Field = None
+    # Optional anisotropic scattering: sigma_sl(l) factor so that
+    # Sigma_sl = sigma_s0 * sigma_sl_factor[l] for l >= 1 (None = isotropic).
+    sigma_sl_factor: Optional[Sequence[float]] = None
+    sources: List[Tuple[int, Field]] = dataclasses.field(default_factory=list)
+    ic: List[Tuple[int, Field]] = dataclasses.field(default_factory=list)
+    time_dependent: bool = False
+    nsteps: Optional[int] = None
+    t_final: Optional[float] = None
+
+
+def _const(v: float) -> Field:
+    return lambda t, x, y: np.full(np.broadcast(x, y).shape, float(v))
+
+
+def gaussian_std(x0: float, y0: float, s: float, mass: float = 1.0) -> Field:
+    """Isotropic 2D normal density with standard deviation s and given mass."""
+    def f(t, x, y):
+        r2 = (np.asarray(x) - x0) ** 2 + (np.asarray(y) - y0) ** 2
+        return mass / (2.0 * math.pi * s * s) * np.exp(-r2 / (2.0 * s * s))
+    return f
+
+
+def gaussian_paper(sigma: float) -> Field:
+    """The paper's Gaussian of section 6.4 with pseudo-time sigma (unit mass)."""
+    def f(t, x, y):
+        r2 = np.asarray(x) ** 2 + np.asarray(y) ** 2
+        return 1.0 / (4.0 * math.pi * sigma) * np.exp(-r2 / (4.0 * sigma))
+    return f
+
+
+# --------------------------------------------------------------------------
+# Workloads
+# --------------------------------------------------------------------------
+
+def gaussian_p5(n: int = 64, nsteps: int = 100, N: int = 5,
+                precision: str = "fp64") -> Problem:
+    return Problem(
+        name=f"gaussian_p{N}_{n}",
+        N=N, ax=(-1.0, 1.0, -1.0, 1.0), n=(n, n),
+        bc=("periodic", "periodic"), cn=0.5, precision=precision,
+        sigma_a=_const(0.0), sigma_s0=_const(1.0),
+        ic=[(0, gaussian_std(0.0, 0.0, 0.1))], nsteps=nsteps)
+
+
+def checkerboard_layout(seed: int = 1211, n_absorbing: int = 11) -> np.ndarray:
+    """7x7 block flags: 1 = absorbing, 0 = scattering, centre block = source.
+
+    The paper's figure with the block layout is not available, so the
+    n_absorbing absorbing blocks are drawn at random among the 48 outer blocks
+    by a seeded partial Fisher-Yates shuffle."""
+    rng = SplitMix64(seed)
+    cells = [(bx, by) for by in range(7) for bx in range(7) if (bx, by) != (3, 3)]
+    for i in range(n_absorbing):
+        j = i + rng.randint(len(cells) - i)
+        cells[i], cells[j] = cells[j], cells[i]
+    flags = np.zeros((7, 7), dtype=np.int32)   # flags[by, bx]
+    for bx, by in cells[:n_absorbing]:
+        flags[by, bx] = 1
+    return flags
+
+
+def _block_index(v, lo, width, count):
+    k = np.floor((np.asarray(v, dtype=np.float64) - lo) / width).astype(np.int64)
+    return np.clip(k, 0, count - 1)
+
+
+def checkerboard_p13(n: int = 512, N: int = 13, t_final: float = 3.2,
+                     seed: int = 1211, precision: str = "fp32") -> Problem:
+    flags = checkerboard_layout(seed)
+
+    def absorbing(x, y):
+        bx = _block_index(x, 0.0, 1.0, 7)
+        by = _block_index(y, 0.0, 1.0, 7)
+        return flags[by, bx] == 1
+
+    def sigma_a(t, x, y):
+        return np.where(absorbing(x, y), 10.0, 0.0)
+
+    def sigma_s0(t, x, y):
+        return np.where(absorbing(x, y), 0.0, 1.0)
+
+    def source(t, x, y):
+        bx = _block_index(x, 0.0, 1.0, 7)
+        by = _block_index(y, 0.0, 1.0, 7)
+        return np.where((bx == 3) & (by == 3), 1.0, 0.0)
+
+    return Problem(
+        name=f"checkerboard_p{N}_{n}", N=N, ax=(0.0, 7.0, 0.0, 7.0), n=(n, n),
+        bc=("extrapolation", "extrapolation"), cn=0.5, precision=precision,
+        sigma_a=sigma_a, sigma_s0=sigma_s0, sources=[(0, source)],
+        ic=[], t_final=t_final)
+
+
+def smooth_log_field(seed: int, lattice: int, lo: float, hi: float,
+                     ax: Tuple[float, float, float, float]) -> Field:
+    """10**v with v iid uniform in [lo, hi] on a periodic lattice x lattice
+    grid of nodes over the domain, bilinearly interpolated (periodic)."""
+    rng = SplitMix64(seed)
+    v = lo + (hi - lo) * rng.uniforms(lattice * lattice).reshape(lattice, lattice)  # v[iy, ix]
+    x0, x1, y0, y1 = ax
+
+    def f(t, x, y):
+        u = (np.asarray(x, dtype=np.float64) - x0) / (x1 - x0) * lattice
+        w = (np.asarray(y, dtype=np.float64) - y0) / (y1 - y0) * lattice
+        iu = np.floor(u)
+        iw = np.floor(w)
+        fu = u - iu
+        fw = w - iw
+        i0 = iu.astype(np.int64) % lattice
+        j0 = iw.astype(np.int64) % lattice
+        i1 = (i0 + 1) % lattice
+        j1 = (j0 + 1) % lattice
+        val = ((1 - fu) * (1 - fw) * v[j0, i0] + fu * (1 - fw) * v[j0, i1]
+               + (1 - fu) * fw * v[j1, i0] + fu * fw * v[j1, i1])
+        return 10.0 ** val
+    return f
+
+
+def random_p39(n: int = 1024, N: int = 39, nsteps: int = 200, seed: int = 2205,
+               precision: str = "fp32") -> Problem:
+    ax = (-1.0, 1.0, -1.0, 1.0)
+    return Problem(
+        name=f"random_p{N}_{n}", N=N, ax=ax, n=(n, n),
+        bc=("periodic", "periodic"), cn=0.5, precision=precision,
+        sigma_a=_const(0.0), sigma_s0=smooth_log_field(seed, 32, -1.0, 1.0, ax),
+        ic=[(0, gaussian_std(0.0, 0.0, 0.1))], nsteps=nsteps)
+
+
+def piecewise_blocks(rng: SplitMix64, blocks: int, lo: float, hi: float,
+                     ax: Tuple[float, float, float, float]) -> Field:
+    """Field constant on a blocks x blocks partition, values iid U[lo, hi]."""
+    vals = lo + (hi - lo) * rng.uniforms(blocks * blocks).reshape(blocks, blocks)
+    x0, x1, y0, y1 = ax
+
+    def f(t, x, y):
+        bx = _block_index(x, x0, (x1 - x0) / blocks, blocks)
+        by = _block_index(y, y0, (y1 - y0) / blocks, blocks)
+        return vals[by, bx]
+    return f
+
+
+def batched_instance(k: int, nsteps: int = 100) -> Problem:
+    """Instance k of the batched workload (seed 12112205 + k)."""
+    rng = SplitMix64(12112205 + k)
+    sizes = list(range(64, 513, 32))
+    n = sizes[rng.randint(len(sizes))]
+    N = [3, 5, 7, 9, 11, 13, 15][rng.randint(7)]
+    bc = ["periodic", "extrapolation"][rng.randint(2)]
+    ax = (0.0, 1.0, 0.0, 1.0)
+    sigma_a = piecewise_blocks(rng, 8, 0.0, 5.0, ax)
+    sigma_s0 = piecewise_blocks(rng, 8, 0.0, 10.0, ax)
+    cx = 0.25 + 0.5 * rng.uniform()
+    cy = 0.25 + 0.5 * rng.uniform()
+    return Problem(
+        name=f"batched_{k}", N=N, ax=ax, n=(n, n), bc=(bc, bc), cn=0.5,
+        precision="fp32", sigma_a=sigma_a, sigma_s0=sigma_s0,
+        sources=[(0, gaussian_std(cx, cy, 0.05))], ic=[], nsteps=nsteps)
+
+
+def fourier_mode_ic(count: int, seed: int):
+    """Random complex amplitudes for a Fourier-mode initial condition."""
+    rng = SplitMix64(seed)
+    re = rng.uniforms(count) * 2 - 1
+    im = rng.uniforms(count) * 2 - 1
+    return re + 1j * im
