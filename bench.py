@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of the StaRMAP step on GB300.
+
+Workload (default): 2D P_39 (820 moments), FP32, 1024x1024 periodic grid on
+[-1,1]^2, sigma_a = 0, log10 sigma_s0 uniform in [-1,1] on a 32x32 lattice
+(seed 2205, bilinear), Gaussian R_0^0 pulse (std 0.1), merged schedule.  The
+state (3.6 GB) is larger than L2 (129 MB), so no flush is needed between
+steps.  A bench step is one full time step dt of every moment at every grid
+point; the metric is moment-cell updates per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--workload random_p39|checkerboard_p13|gaussian_p5] [--kernel auto|gather|tiled]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(weak scaling; the method has no cross-replica exchange), timing is bracketed
+by barriers and the slowest rank's time is used.
+
+--impl reference times the FP64 CPU oracle (the slow restatement of the
+paper used as the parity reference) on a bounded sample of the same workload
+on the host cores, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1211_2205_gb300 import inputs  # noqa: E402
+
+METRIC = "moment-cell updates/s"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+KERNEL_SOURCES = {
+    "gather": ["paper_1211_2205_gb300/csrc/kernels_gather.cu"],
+    "tiled": ["paper_1211_2205_gb300/csrc/tiled.cu", "paper_1211_2205_gb300/csrc/tiled_kernel.cuh"],
+}
+
+
+def workload(name: str):
+    if name == "random_p39":
+        return inputs.random_p39(), "2D P_39 FP32 1024x1024 periodic, smooth random sigma_s0, Gaussian pulse"
+    if name == "checkerboard_p13":
+        return inputs.checkerboard_p13(), "2D P_13 FP32 512x512 checkerboard, extrapolation, source"
+    if name == "gaussian_p5":
+        return inputs.gaussian_p5(), "2D P_5 FP64 64x64 periodic Gaussian"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(local_units: float, local_ms: float, world: int):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([local_units, local_ms], dtype=torch.float64)
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        units = t[0:1].clone()
+        ms = t[1:2].clone()
+        dist.all_reduce(units, op=dist.ReduceOp.SUM)
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+        return float(units.item()), float(ms.item())
+    return local_units, local_ms
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            self.path = os.path.join("/tmp", f"starmap_clocks_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash(kind: str) -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES.get(kind, []):
+        p = os.path.join(ROOT, rel)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kind: str, workload_name: str, pass_name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    try:
+        table = json.load(open(PROFILE_TRAFFIC))
+    except Exception:
+        return None
+    ent = table.get(f"{kind}/{workload_name}/{pass_name}")
+    if not ent or ent.get("kernel_hash") != kernel_hash(kind):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and --impl reference)
+# --------------------------------------------------------------------------
+
+def oracle_sample(problem, cells: int, steps: int):
+    """Time the FP64 oracle on a cells x cells window of the workload with the
+    same spacing and material (periodic wrap at the window edges), `steps`
+    full steps.  Returns (updates/s, description)."""
+    from oracle import pn_oracle as O
+    x0, x1, y0, y1 = problem.ax
+    hx = (x1 - x0) / problem.n[0]
+    hy = (y1 - y0) / problem.n[1]
+    cx = x0 + hx * (problem.n[0] // 2 - cells // 2)
+    cy = y0 + hy * (problem.n[1] // 2 - cells // 2)
+    ax = (cx, cx + cells * hx, cy, cy + cells * hy)
+    Mx, My, order = O.system_matrices(problem.system, problem.N)
+    dt = O.time_step(Mx, problem.ax, problem.n, problem.cn)
+    sub = inputs.Problem(**{**problem.__dict__, "ax": ax, "n": (cells, cells), "bc": ("periodic", "periodic")})
+    s = O.solver_from_problem(sub, dt=dt)
+    s.step()  # materials evaluated in the first step: exclude from timing
+    t0 = time.perf_counter()
+    s.run(steps)
+    el = time.perf_counter() - t0
+    updates = sum(u.size for u in s.U) * steps
+    return updates / el, f"oracle (numpy FP64) on a {cells}x{cells} window of the workload, {steps} steps after 1 untimed", el
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    problem, desc = workload(args.workload)
+    cells = {"random_p39": 48, "checkerboard_p13": 96, "gaussian_p5": 64}[args.workload]
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(problem, cells, 1)
+    el_total = 0.0
+    for _ in range(args.steps):
+        v, sample, el = oracle_sample(problem, cells, 1)
+        vals.append(v)
+        el_total += el
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el_total / max(1, args.steps) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "sample": f"{cells}x{cells} window"},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# native arm
+# --------------------------------------------------------------------------
+
+def algorithmic_pass_bytes(s, parity: int, esize: int) -> int:
+    """State bytes one pass must move: read every input component of the
+    other parity once, read and write every output component once."""
+    total = 0
+    for j in range(s.ncomp):
+        info = s.moment_info(j)
+        pts = info["nx"] * info["ny"]
+        is_odd = info["grid"] in (1, 2)
+        out = is_odd == (parity == 1)
+        total += pts * esize * (2 if out else 1)
+    return total
+
+
+def run_native(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1211_2205_gb300 import capi
+
+    problem, desc = workload(args.workload)
+    esize = 4 if problem.precision == "fp32" else 8
+    stream = torch.cuda.current_stream()
+    s = capi.Stepper.from_problem(problem, schedule="merged", kernel=args.kernel, stream=stream.cuda_stream)
+    updates_per_step = sum(s.moment_info(j)["nx"] * s.moment_info(j)["ny"] for j in range(s.ncomp))
+    state_bytes = s.state_bytes()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    s.step(args.warmup)
+    barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        s.step(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = start.elapsed_time(stop)
+    units, ms_max = aggregate(updates_per_step * args.steps, ms, world)
+    value = units / (ms_max / 1e3)
+
+    # dominant kernel: time each pass type alone with events on the same stream
+    pass_times = {}
+    reps = max(4, min(20, args.steps))
+    for name, parity, which in (("even_full", 0, 1), ("odd_full", 1, 1)):
+        s.run_pass(parity, which)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            s.run_pass(parity, which)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pass_times[name] = a.elapsed_time(b) / reps
+    dom = max(pass_times, key=pass_times.get)
+    dom_parity = 0 if dom.startswith("even") else 1
+    alg_bytes = algorithmic_pass_bytes(s, dom_parity, esize)
+    achieved = alg_bytes / (pass_times[dom] / 1e3) / 1e9
+    pk, pk_kind = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    traffic = measured_traffic(s.kernel, args.workload, dom)
+
+    # end to end through the C ABI with host buffers: upload the full state,
+    # K steps, read back R_0^0
+    host_state = s.get_state()
+    r00_bytes = s.moment_info(0)["nx"] * s.moment_info(0)["ny"] * 8
+    barrier()
+    t0 = time.perf_counter()
+    s.set_state(host_state)
+    s.step(args.steps)
+    r00 = s.moments(0)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_units, e2e_ms = aggregate(updates_per_step * args.steps, e2e_s * 1e3, world)
+    e2e_value = e2e_units / (e2e_ms / 1e3)
+    assert np.isfinite(r00).all()
+
+    clocks = clk.summary()
+    launches = 2 * args.steps + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if esize == 4 else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "N": problem.N, "grid": list(problem.n),
+                   "moments": s.ncomp, "updates_per_step": updates_per_step, "schedule": "merged",
+                   "kernel": s.kernel, "state_bytes": state_bytes,
+                   "l2_flush": "none: state larger than L2", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": f"{s.kernel}:{dom}",
+                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": pass_times[dom],
+                     "pass_ms": pass_times, "peak_kind": f"{pk_kind} hbm_gbs"},
+        "e2e": {"value": e2e_value, "unit": "updates/s",
+                "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": r00_bytes / args.steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cells, nst = {"random_p39": (192, 4), "checkerboard_p13": (256, 8), "gaussian_p5": (64, 100)}[args.workload]
+        v, sample, el = oracle_sample(problem, cells, nst)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="random_p39")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "tiled"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps are required")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

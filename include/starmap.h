@@ -1,0 +1,223 @@
+/*
+ * starmap.h -- C ABI of the GB300 StaRMAP stepper.
+ *
+ * The library advances the 2D spherical-harmonics P_N system (and the slab
+ * P_N system) with the staggered-grid scheme of Seibold & Frank, "StaRMAP --
+ * A Second Order Staggered Grid Method for Spherical Harmonics Moment
+ * Equations of Radiative Transfer" (arXiv:1211.2205):
+ *
+ *   d_t u + Mx d_x u + My d_y u + C u = q              (section 4, eq. hyperbolic_balance_law)
+ *
+ * with the moments stored on four mutually staggered grids G11, G21, G12, G22
+ * (section 4.1, eqs. grid11 and staggered_grids), half-grid central
+ * differences (eq. central_differences), exact integration of the decay
+ * over each sub-step (eq. sub_step_solution) and the Strang composition
+ * S = S^o_1/2 o S^e_1/2 o S^e_1/2 o S^o_1/2 (eq. solution_operator_full_step).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - All functions return an int status: STARMAP_OK (0) or a negative
+ *   STARMAP_E_* code.  Nothing aborts, traps or exits; the message of the last
+ *   failure of a handle is available from starmap_last_error().
+ * - Components j = 0 .. starmap_num_moments()-1 follow the paper's real
+ *   ordering R_0^0, R_1^1, I_1^1, R_2^2, I_2^2, R_2^0, R_3^3, ... (section 3,
+ *   eq. transformation); for the slab system component j is psi_j.
+ * - Grids are numbered 0 = G11, 1 = G21, 2 = G12, 3 = G22.  Grid g has
+ *   nx_g x ny_g points (section 5.2): nx_g = n_x for G11/G12 and
+ *   n_x + 1 - p_x for G21/G22, where p_x = 1 for periodic and 0 for
+ *   extrapolation boundaries (eq. periodicity_flags); likewise in y.
+ *   Point (i, k) of grid g lies at (x0_g + i*dx, y0_g + k*dy), see
+ *   starmap_grid_info().
+ * - Every host array that holds a field on a grid is dense, row-major with
+ *   x fastest: element (i, k) at index k*nx_g + i.  Host arrays are always
+ *   double precision; they are copied in or out (the caller keeps ownership).
+ * - Device memory belongs to the library.  Pointers returned by
+ *   starmap_device_ptr() are borrowed and stay valid until starmap_destroy().
+ * - All work is queued on the handle's CUDA stream (the caller's stream if
+ *   one was given in the config).  Entry points that return host data
+ *   synchronise that stream.
+ */
+#ifndef STARMAP_H
+#define STARMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define STARMAP_OK            0
+#define STARMAP_E_ARG        -1   /* invalid argument, size or index          */
+#define STARMAP_E_CFL        -2   /* time step beyond the stability bound     */
+#define STARMAP_E_NOMEM      -3   /* device or host allocation failed         */
+#define STARMAP_E_CUDA       -4   /* a CUDA runtime call failed               */
+#define STARMAP_E_NONFINITE  -5   /* NaN or Inf found in the state            */
+#define STARMAP_E_TIMEOUT    -6   /* a bounded device wait gave up            */
+#define STARMAP_E_STATE      -7   /* call not valid in the handle's state     */
+#define STARMAP_E_UNSUPPORTED -8  /* configuration not supported by a kernel  */
+
+/* ------------------------------------------------------------------ enums */
+#define STARMAP_PERIODIC       0  /* p = 1 in eq. periodicity_flags */
+#define STARMAP_EXTRAPOLATION  1  /* p = 0: ghost copies, section 4.2 */
+
+#define STARMAP_PN2D  0           /* 2D real P_N system, section 3 */
+#define STARMAP_SLAB  1           /* slab P_N system, eq. PN_slab (My = 0, ny = 1 allowed) */
+
+#define STARMAP_FP64  0
+#define STARMAP_FP32  1
+
+/* Step schedules.  LITERAL: every step is odd half, even pair, odd half
+ * (eq. solution_operator_full_step; the even pair is applied as one fused
+ * pass, algebraically identical to two half-steps with frozen odd data).
+ * MERGED: for time-independent material and sources the odd halves of
+ * consecutive steps are merged into one full odd pass (section 5.8 remark),
+ * O_1/2 (E O)^(n-1) E O_1/2 inside one starmap_step(n) call. */
+#define STARMAP_SCHEDULE_LITERAL 0
+#define STARMAP_SCHEDULE_MERGED  1
+
+/* Kernel selection for the half-step passes. */
+#define STARMAP_KERNEL_AUTO    0  /* tiled kernel where supported, else gather */
+#define STARMAP_KERNEL_GATHER  1  /* one thread per point, CSR loop over moments */
+#define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N, N <= 41) */
+
+typedef struct starmap_s starmap_t;
+
+typedef struct {
+    int    system;      /* STARMAP_PN2D or STARMAP_SLAB                         */
+    int    N;           /* moment order, 1 <= N <= 63                           */
+    double ax[4];       /* domain xmin, xmax, ymin, ymax (par.ax, section 5.1)  */
+    int    n[2];        /* cells n_x, n_y (par.n)                               */
+    int    bc[2];       /* STARMAP_PERIODIC / STARMAP_EXTRAPOLATION per axis    */
+    double cn;          /* CFL number: dt = cn * min(dx, dy) / lambda_max(Mx)   */
+    double dt;          /* if > 0: use this time step instead of cn             */
+    int    precision;   /* STARMAP_FP64 or STARMAP_FP32                         */
+    int    schedule;    /* STARMAP_SCHEDULE_*                                   */
+    int    kernel;      /* STARMAP_KERNEL_*                                     */
+    void*  cuda_stream; /* cudaStream_t to queue work on, or NULL for the
+                           library's own stream                               */
+} starmap_config;
+
+/* Fill *cfg with defaults: 2D P_N, N = 1, [0,1]^2, 16x16 periodic, cn = 0.5,
+ * FP64, literal schedule, auto kernel, library stream. */
+void starmap_config_default(starmap_config* cfg);
+
+/* ----------------------------------------------------------- host math
+ * Pure host functions (no GPU needed).  Moment matrices of section 3: the
+ * complex P_N matrices read off eq. Pncomplex with the recursion
+ * coefficients a..f, transformed by S (eq. transformation), or the slab
+ * matrix of eq. PN_slab.  ncomp = (N+1)(N+2)/2 (2D) or N+1 (slab).
+ *   Mx, My : caller arrays of ncomp*ncomp doubles, row-major (may be NULL)
+ *   grid   : caller array of ncomp ints, grid number 0..3 per component
+ *            (index sets I11, I21, I12, I22 of eq. matrix_conditions,
+ *            placed as in section 5.3) (may be NULL)
+ *   order  : caller array of ncomp ints, moment order l (may be NULL)
+ *   lambda_max : largest |eigenvalue| of Mx (section 5.3) (may be NULL)
+ * Returns STARMAP_E_ARG for N out of range or a too small ncomp_capacity. */
+int starmap_host_matrices(int system, int N, int ncomp_capacity,
+                          double* Mx, double* My, int* grid, int* order,
+                          double* lambda_max);
+
+/* E(c) = (exp(c) - 1)/c, section 5.6 (series for |c| <= 2e-4), applied to
+ * count values in place.  Host function, for tests. */
+int starmap_host_expm1div(double* c, size_t count);
+
+/* ------------------------------------------------------------ lifetime */
+/* Create a stepper: builds the matrices, grid assignment and time step on
+ * the host, allocates the state on the current CUDA device and zeroes it.
+ * Material defaults to vacuum (sigma_a = sigma_s0 = 0), no source.
+ * Errors: E_ARG (bad sizes, N, boundary, precision), E_CFL (cn beyond
+ * 1/sqrt(2) in 2D or 1 in slab, or dt beyond that bound), E_UNSUPPORTED
+ * (kernel choice not available for the configuration), E_NOMEM, E_CUDA.
+ * On failure *out is NULL. */
+int  starmap_create(const starmap_config* cfg, starmap_t** out);
+void starmap_destroy(starmap_t* h);
+const char* starmap_last_error(const starmap_t* h);
+
+/* ------------------------------------------------------------ queries */
+int    starmap_num_moments(const starmap_t* h);
+double starmap_dt(const starmap_t* h);
+double starmap_time(const starmap_t* h);
+long   starmap_steps_done(const starmap_t* h);
+/* Kernel actually used for the passes (STARMAP_KERNEL_GATHER or _TILED). */
+int    starmap_kernel(const starmap_t* h);
+/* Component j: order l, index m (>= 0), is_imag (1 for I_l^m), grid 0..3,
+ * and the size nx x ny of its grid.  Any output pointer may be NULL. */
+int starmap_moment_info(const starmap_t* h, int j, int* l, int* m, int* is_imag,
+                        int* grid, int* nx, int* ny);
+/* Grid g: size and the coordinates of its point (0, 0); point (i, k) is at
+ * (x0 + i*dx, y0 + k*dy).  eq. grid11 / staggered_grids. */
+int starmap_grid_info(const starmap_t* h, int g, int* nx, int* ny,
+                      double* x0, double* y0, double* dx, double* dy);
+
+/* ----------------------------------------------------------- problem data
+ * Material of section 5.7, sampled by the caller at the points of grid g
+ * (nx_g*ny_g doubles each).  The decay of component j is Sigma_a for l = 0
+ * and Sigma_a + Sigma_s0 - Sigma_sl for l >= 1 (section 2).  Calling this
+ * for all four grids defines the medium; grids never set stay vacuum.  The
+ * coefficients exp(-c dt/2) and dt/2 E(-c dt/2) are formed on the host in
+ * FP64 and uploaded.  For time-dependent media call it again (at t + dt/2)
+ * before each starmap_step(h, 1) with the literal schedule. */
+int starmap_set_material(starmap_t* h, int g, const double* sigma_a,
+                         const double* sigma_s0, size_t count);
+/* Anisotropic scattering: Sigma_sl = Sigma_s0 * factor[l] for 1 <= l <= N
+ * (e.g. Henyey-Greenstein g^l).  factor has N+1 entries (factor[0] unused).
+ * NULL restores isotropic scattering (Sigma_sl = 0 for l >= 1).  Takes
+ * effect at the next starmap_set_material() call. */
+int starmap_set_scattering_factors(starmap_t* h, const double* factor, int count);
+/* Source of component j (par.source / par.source_ind), sampled on the grid
+ * of j; count = nx*ny of that grid.  NULL clears it. */
+int starmap_set_source(starmap_t* h, int j, const double* q, size_t count);
+/* Set component j (initial condition, par.ic); count = nx*ny of its grid. */
+int starmap_set_moment(starmap_t* h, int j, const double* u, size_t count);
+/* Set the time t (for starmap_time / advance_to bookkeeping). */
+int starmap_set_time(starmap_t* h, double t);
+
+/* ------------------------------------------------------------ stepping */
+/* Advance nsteps full time steps (eq. solution_operator_full_step) with the
+ * configured schedule.  Asynchronous on the handle's stream. */
+int starmap_step(starmap_t* h, long nsteps);
+/* Run one pass of the step: parity 1 updates the odd components (grids
+ * G21, G12) from the even ones, parity 0 the even components (G11, G22) from
+ * the odd ones; which = 0 applies the half-step coefficients (tau = dt/2),
+ * which = 1 the full-step ones (tau = dt: the fused even pair, or two merged
+ * odd halves).  Time and step count are not advanced.  For profiling and for
+ * callers composing their own schedule of eq. solution_operator_full_step. */
+int starmap_pass(starmap_t* h, int parity, int which);
+/* Step until t_out lies in (t, t + dt] and keep the solution of the last
+ * two time levels; starmap_output() then returns the linear interpolation
+ * (1 - lambda) u(t) + lambda u(t + dt), lambda = (t_out - t)/dt
+ * (section 5.8).  E_ARG if t_out < current time. */
+int starmap_advance_to(starmap_t* h, double t_out);
+int starmap_output(starmap_t* h, int j, double* out, size_t count);
+
+/* ------------------------------------------------------------ read-out */
+/* Copy component j (nx*ny doubles of its grid) to the host. */
+int starmap_moments(starmap_t* h, int j, double* out, size_t count);
+/* FP64 device reductions (precision policy: FP64 only for these):
+ * mass = dx dy sum R_0^0 over G11, l2 = sqrt(dx dy sum_j sum u_j^2)
+ * (discrete L2 norm, eq. discrete_L2_norm), nonfinite = count of NaN/Inf
+ * values.  Any output may be NULL.  Returns E_NONFINITE if nonfinite > 0. */
+int starmap_diagnostics(starmap_t* h, double* mass, double* l2, long* nonfinite);
+/* Device pointer of component j (borrowed), with its row pitch in elements
+ * and the offset of point (0,0) in elements.  Element (i, k) is at
+ * ptr[offset + k*pitch + i]; indices -1 and nx_g / ny_g hold boundary
+ * copies.  Element type is double (FP64) or float (FP32). */
+int starmap_device_ptr(starmap_t* h, int j, void** ptr, long* pitch, long* offset);
+
+/* ------------------------------------------------------ checkpointing */
+/* Size in bytes of a state snapshot: all components in the run's precision
+ * plus time and step count.  get/set copy that snapshot to/from a host
+ * buffer of at least that size. */
+size_t starmap_state_bytes(const starmap_t* h);
+int starmap_get_state(starmap_t* h, void* buf, size_t bytes);
+int starmap_set_state(starmap_t* h, const void* buf, size_t bytes);
+
+/* Wait for all queued work of the handle. */
+int starmap_sync(starmap_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STARMAP_H */

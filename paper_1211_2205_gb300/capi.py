@@ -1,0 +1,342 @@
+"""Thin ctypes binding of the StaRMAP C ABI (include/starmap.h).
+
+Argument marshalling only: every step of the method runs in libstarmap.so.
+If the library has not been built, loading raises RuntimeError: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libstarmap.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "starmap.h")
+
+OK = 0
+E_ARG, E_CFL, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE, E_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7, -8
+PERIODIC, EXTRAPOLATION = 0, 1
+PN2D, SLAB = 0, 1
+FP64, FP32 = 0, 1
+SCHEDULE_LITERAL, SCHEDULE_MERGED = 0, 1
+KERNEL_AUTO, KERNEL_GATHER, KERNEL_TILED = 0, 1, 2
+
+
+class StarmapError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"starmap error {code}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("system", ctypes.c_int),
+        ("N", ctypes.c_int),
+        ("ax", ctypes.c_double * 4),
+        ("n", ctypes.c_int * 2),
+        ("bc", ctypes.c_int * 2),
+        ("cn", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("schedule", ctypes.c_int),
+        ("kernel", ctypes.c_int),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def exported_functions() -> list:
+    """Names of all functions declared in include/starmap.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(starmap_[a-z0-9_]+)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+def lib():
+    """Load libstarmap.so (fails loudly if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libstarmap.so is not built (run __graft_entry__.build()); "
+                           "there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    sig = {
+        "starmap_config_default": (None, [ctypes.POINTER(Config)]),
+        "starmap_host_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _ip, _ip, _dp]),
+        "starmap_host_expm1div": (ctypes.c_int, [_dp, ctypes.c_size_t]),
+        "starmap_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(H)]),
+        "starmap_destroy": (None, [H]),
+        "starmap_last_error": (ctypes.c_char_p, [H]),
+        "starmap_num_moments": (ctypes.c_int, [H]),
+        "starmap_dt": (ctypes.c_double, [H]),
+        "starmap_time": (ctypes.c_double, [H]),
+        "starmap_steps_done": (ctypes.c_long, [H]),
+        "starmap_kernel": (ctypes.c_int, [H]),
+        "starmap_moment_info": (ctypes.c_int, [H, ctypes.c_int, _ip, _ip, _ip, _ip, _ip, _ip]),
+        "starmap_grid_info": (ctypes.c_int, [H, ctypes.c_int, _ip, _ip, _dp, _dp, _dp, _dp]),
+        "starmap_set_material": (ctypes.c_int, [H, ctypes.c_int, _dp, _dp, ctypes.c_size_t]),
+        "starmap_set_scattering_factors": (ctypes.c_int, [H, _dp, ctypes.c_int]),
+        "starmap_set_source": (ctypes.c_int, [H, ctypes.c_int, _dp, ctypes.c_size_t]),
+        "starmap_set_moment": (ctypes.c_int, [H, ctypes.c_int, _dp, ctypes.c_size_t]),
+        "starmap_set_time": (ctypes.c_int, [H, ctypes.c_double]),
+        "starmap_step": (ctypes.c_int, [H, ctypes.c_long]),
+        "starmap_advance_to": (ctypes.c_int, [H, ctypes.c_double]),
+        "starmap_pass": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int]),
+        "starmap_output": (ctypes.c_int, [H, ctypes.c_int, _dp, ctypes.c_size_t]),
+        "starmap_moments": (ctypes.c_int, [H, ctypes.c_int, _dp, ctypes.c_size_t]),
+        "starmap_diagnostics": (ctypes.c_int, [H, _dp, _dp, ctypes.POINTER(ctypes.c_long)]),
+        "starmap_device_ptr": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                              ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
+        "starmap_state_bytes": (ctypes.c_size_t, [H]),
+        "starmap_get_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t]),
+        "starmap_set_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t]),
+        "starmap_sync": (ctypes.c_int, [H]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def host_matrices(system: int, N: int):
+    """Mx, My, grid per component, order per component, lambda_max (host math)."""
+    L = lib()
+    n = (N + 1) * (N + 2) // 2 if system == PN2D else N + 1
+    Mx = np.zeros((n, n))
+    My = np.zeros((n, n))
+    grid = np.zeros(n, dtype=np.int32)
+    order = np.zeros(n, dtype=np.int32)
+    lam = ctypes.c_double()
+    rc = L.starmap_host_matrices(system, N, n, _dptr(Mx), _dptr(My), grid.ctypes.data_as(_ip),
+                                 order.ctypes.data_as(_ip), ctypes.byref(lam))
+    if rc != OK:
+        raise StarmapError(rc, L.starmap_last_error(None).decode())
+    return Mx, My, grid, order, lam.value
+
+
+def host_expm1div(c) -> np.ndarray:
+    L = lib()
+    a = np.ascontiguousarray(np.array(c, dtype=np.float64).ravel())
+    rc = L.starmap_host_expm1div(_dptr(a), a.size)
+    if rc != OK:
+        raise StarmapError(rc, "expm1div")
+    return a
+
+
+class Stepper:
+    """One StaRMAP stepper (a handle of the C ABI)."""
+
+    def __init__(self, N: int, ax, n, bc=("periodic", "periodic"), cn: float = 0.5,
+                 precision: str = "fp64", system: str = "pn2d", schedule: str = "literal",
+                 kernel: str = "auto", dt: float = 0.0, stream: Optional[int] = None):
+        self._L = lib()
+        c = Config()
+        self._L.starmap_config_default(ctypes.byref(c))
+        c.system = {"pn2d": PN2D, "slab": SLAB}[system]
+        c.N = int(N)
+        for i in range(4):
+            c.ax[i] = float(ax[i])
+        c.n[0], c.n[1] = int(n[0]), int(n[1])
+        bmap = {"periodic": PERIODIC, "extrapolation": EXTRAPOLATION}
+        c.bc[0], c.bc[1] = bmap[bc[0]], bmap[bc[1]]
+        c.cn = float(cn)
+        c.dt = float(dt)
+        c.precision = {"fp64": FP64, "fp32": FP32}[precision]
+        c.schedule = {"literal": SCHEDULE_LITERAL, "merged": SCHEDULE_MERGED}[schedule]
+        c.kernel = {"auto": KERNEL_AUTO, "gather": KERNEL_GATHER, "tiled": KERNEL_TILED}[kernel]
+        c.cuda_stream = stream
+        h = ctypes.c_void_p()
+        rc = self._L.starmap_create(ctypes.byref(c), ctypes.byref(h))
+        if rc != OK:
+            raise StarmapError(rc, self._L.starmap_last_error(None).decode())
+        self._h = h
+        self.precision = precision
+        self.config = c
+
+    # -- lifetime -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.starmap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != OK:
+            raise StarmapError(rc, self._L.starmap_last_error(self._h).decode())
+
+    # -- queries --------------------------------------------------------
+    @property
+    def ncomp(self) -> int:
+        return self._L.starmap_num_moments(self._h)
+
+    @property
+    def dt(self) -> float:
+        return self._L.starmap_dt(self._h)
+
+    @property
+    def time(self) -> float:
+        return self._L.starmap_time(self._h)
+
+    @property
+    def steps_done(self) -> int:
+        return self._L.starmap_steps_done(self._h)
+
+    @property
+    def kernel(self) -> str:
+        return {KERNEL_GATHER: "gather", KERNEL_TILED: "tiled"}[self._L.starmap_kernel(self._h)]
+
+    def moment_info(self, j: int):
+        v = [ctypes.c_int() for _ in range(6)]
+        self._check(self._L.starmap_moment_info(self._h, j, *[ctypes.byref(x) for x in v]))
+        l, m, im, g, nx, ny = [x.value for x in v]
+        return dict(l=l, m=m, imag=bool(im), grid=g, nx=nx, ny=ny)
+
+    def grid_info(self, g: int):
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        x0, y0, dx, dy = [ctypes.c_double() for _ in range(4)]
+        self._check(self._L.starmap_grid_info(self._h, g, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(x0),
+                                              ctypes.byref(y0), ctypes.byref(dx), ctypes.byref(dy)))
+        return nx.value, ny.value, x0.value, y0.value, dx.value, dy.value
+
+    def grid_coords(self, g: int) -> Tuple[np.ndarray, np.ndarray]:
+        """(X, Y) arrays of shape (ny, nx) of the points of grid g."""
+        nx, ny, x0, y0, dx, dy = self.grid_info(g)
+        X = x0 + dx * np.arange(nx)
+        Y = y0 + dy * np.arange(ny)
+        return np.meshgrid(X, Y, indexing="xy")
+
+    # -- problem data ---------------------------------------------------
+    def set_material(self, g: int, sigma_a: np.ndarray, sigma_s0: np.ndarray):
+        a = np.ascontiguousarray(sigma_a, dtype=np.float64).ravel()
+        s = np.ascontiguousarray(sigma_s0, dtype=np.float64).ravel()
+        self._check(self._L.starmap_set_material(self._h, g, _dptr(a), _dptr(s), a.size))
+
+    def set_scattering_factors(self, factor):
+        if factor is None:
+            self._check(self._L.starmap_set_scattering_factors(self._h, None, 0))
+        else:
+            f = np.ascontiguousarray(factor, dtype=np.float64)
+            self._check(self._L.starmap_set_scattering_factors(self._h, _dptr(f), f.size))
+
+    def set_source(self, j: int, q: Optional[np.ndarray]):
+        if q is None:
+            self._check(self._L.starmap_set_source(self._h, j, None, 0))
+        else:
+            a = np.ascontiguousarray(q, dtype=np.float64).ravel()
+            self._check(self._L.starmap_set_source(self._h, j, _dptr(a), a.size))
+
+    def set_moment(self, j: int, u: np.ndarray):
+        a = np.ascontiguousarray(u, dtype=np.float64).ravel()
+        self._check(self._L.starmap_set_moment(self._h, j, _dptr(a), a.size))
+
+    def set_time(self, t: float):
+        self._check(self._L.starmap_set_time(self._h, float(t)))
+
+    # -- stepping -------------------------------------------------------
+    def step(self, n: int = 1):
+        self._check(self._L.starmap_step(self._h, int(n)))
+
+    def run_pass(self, parity: int, which: int):
+        self._check(self._L.starmap_pass(self._h, int(parity), int(which)))
+
+    def advance_to(self, t: float):
+        self._check(self._L.starmap_advance_to(self._h, float(t)))
+
+    def output(self, j: int) -> np.ndarray:
+        info = self.moment_info(j)
+        out = np.empty((info["ny"], info["nx"]))
+        self._check(self._L.starmap_output(self._h, j, _dptr(out), out.size))
+        return out
+
+    def sync(self):
+        self._check(self._L.starmap_sync(self._h))
+
+    # -- read-out -------------------------------------------------------
+    def moments(self, j: int) -> np.ndarray:
+        info = self.moment_info(j)
+        out = np.empty((info["ny"], info["nx"]))
+        self._check(self._L.starmap_moments(self._h, j, _dptr(out), out.size))
+        return out
+
+    def diagnostics(self):
+        m, l2 = ctypes.c_double(), ctypes.c_double()
+        bad = ctypes.c_long()
+        rc = self._L.starmap_diagnostics(self._h, ctypes.byref(m), ctypes.byref(l2), ctypes.byref(bad))
+        if rc not in (OK, E_NONFINITE):
+            self._check(rc)
+        return m.value, l2.value, bad.value
+
+    def device_ptr(self, j: int):
+        p = ctypes.c_void_p()
+        pitch, off = ctypes.c_long(), ctypes.c_long()
+        self._check(self._L.starmap_device_ptr(self._h, j, ctypes.byref(p), ctypes.byref(pitch), ctypes.byref(off)))
+        return p.value, pitch.value, off.value
+
+    def state_bytes(self) -> int:
+        return self._L.starmap_state_bytes(self._h)
+
+    def get_state(self) -> bytes:
+        buf = ctypes.create_string_buffer(self.state_bytes())
+        self._check(self._L.starmap_get_state(self._h, buf, len(buf)))
+        return buf.raw
+
+    def set_state(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        self._check(self._L.starmap_set_state(self._h, buf, len(data)))
+
+    # -- convenience: load an input-module Problem ---------------------------
+    @classmethod
+    def from_problem(cls, problem, t_eval: float = 0.0, **over) -> "Stepper":
+        kw = dict(N=problem.N, ax=problem.ax, n=problem.n, bc=problem.bc, cn=problem.cn,
+                  precision=problem.precision, system=problem.system)
+        kw.update(over)
+        s = cls(**kw)
+        s.load_problem(problem, t_eval)
+        return s
+
+    def load_problem(self, problem, t_eval: float = 0.0, ic: bool = True):
+        """Sample material, sources and initial conditions of a Problem at
+        the points of each grid and upload them."""
+        if problem.sigma_sl_factor is not None:
+            self.set_scattering_factors(problem.sigma_sl_factor)
+        for g in range(4):
+            nx, ny, *_ = self.grid_info(g)
+            if nx * ny == 0:
+                continue
+            X, Y = self.grid_coords(g)
+            sa = np.broadcast_to(problem.sigma_a(t_eval, X, Y), X.shape) if problem.sigma_a else np.zeros_like(X)
+            ss = np.broadcast_to(problem.sigma_s0(t_eval, X, Y), X.shape) if problem.sigma_s0 else np.zeros_like(X)
+            self.set_material(g, sa, ss)
+        acc = {}
+        for j, q in problem.sources:
+            X, Y = self.grid_coords(self.moment_info(j)["grid"])
+            acc[j] = acc.get(j, 0.0) + np.broadcast_to(q(t_eval, X, Y), X.shape)
+        for j, q in acc.items():
+            self.set_source(j, q)
+        if ic:
+            for j, f in problem.ic:
+                X, Y = self.grid_coords(self.moment_info(j)["grid"])
+                self.set_moment(j, np.broadcast_to(f(0.0, X, Y), X.shape))

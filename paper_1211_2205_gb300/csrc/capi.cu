@@ -1,0 +1,807 @@
+// C ABI of the StaRMAP stepper: handle lifetime, problem data, schedules,
+// read-out and checkpoints.  See include/starmap.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "host_math.h"
+#include "internal.h"
+#include "tiled.h"
+#include "../../include/starmap.h"
+
+using namespace starmap;
+
+namespace {
+thread_local std::string g_create_error;
+}
+
+struct starmap_s {
+    starmap_config cfg{};
+    SystemMatrices sys;
+    int ncomp = 0;
+    double dx = 0, dy = 0, dt = 0, t = 0;
+    long steps = 0;
+    int p[2] = {1, 1};
+    int nxg[4] = {0, 0, 0, 0}, nyg[4] = {0, 0, 0, 0}, Kg[4] = {0, 0, 0, 0};
+    long pitch = 0, rows = 0;
+    std::vector<int> members[4];          // component ids per grid, by local index
+    size_t esize = 8;
+    bool fp32 = false;
+    void* alloc[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* base[4] = {nullptr, nullptr, nullptr, nullptr};
+    long cstride[4] = {0, 0, 0, 0};
+    size_t grid_bytes[4] = {0, 0, 0, 0};
+    void* coef[4] = {nullptr, nullptr, nullptr, nullptr};
+    int ncls_alloc = 0;
+    int nclasses = 2;
+    std::vector<int> comp_class;
+    std::vector<double> sl_factor;        // empty = isotropic
+    std::vector<double> sig_a[4], sig_s[4];
+    std::vector<int> src_slot;            // per component, -1 if none
+    std::vector<void*> src_dev;           // by slot
+    void* src_ptrs_dev = nullptr;
+    GatherOut* outs_dev = nullptr;
+    void* coefs_dev = nullptr;
+    int tbeg[4] = {0, 0, 0, 0}, tend[4] = {0, 0, 0, 0};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double* partials = nullptr;
+    double* result = nullptr;
+    int red_blocks = 608;
+    void* prev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool have_output = false;
+    double out_lambda = 1.0;
+    bool ghosts_dirty = true;
+    int kernel_used = STARMAP_KERNEL_GATHER;
+    TiledPlan* tiled = nullptr;
+    std::string err;
+};
+
+namespace {
+
+int fail(starmap_t* h, int code, const std::string& msg) {
+    if (h) h->err = msg; else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(starmap_t* h, cudaError_t e, const char* what) {
+    return fail(h, STARMAP_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail(h, e_, what); } while (0)
+
+template <class T>
+GridDev<T> grid_dev(const starmap_t* h, int g) {
+    GridDev<T> d;
+    d.base = (T*)h->base[g];
+    d.cstride = h->cstride[g];
+    d.nx = h->nxg[g];
+    d.ny = h->nyg[g];
+    d.K = h->Kg[g];
+    d.coef = (T*)h->coef[g];
+    return d;
+}
+
+int class_of(const starmap_t* h, int l) {
+    if (h->sl_factor.empty()) return l == 0 ? 0 : 1;
+    return l;
+}
+
+// Build the per-component pass tables (couplings, classes, source slots).
+template <class T>
+int build_tables(starmap_t* h) {
+    std::vector<GatherOut> outs;
+    std::vector<GatherCoef<T>> coefs;
+    const int n = h->ncomp;
+    for (int g = 0; g < 4; ++g) {
+        h->tbeg[g] = (int)outs.size();
+        for (int j : h->members[g]) {
+            GatherOut o{};
+            GatherCoef<T> c{};
+            o.grid = g;
+            o.local = h->sys.moms[j].local;
+            o.cls = h->comp_class[j];
+            o.src = h->src_slot[j];
+            for (int k = 0; k < n; ++k) {
+                double mx = h->sys.Mx[(size_t)j * n + k];
+                double my = h->sys.My[(size_t)j * n + k];
+                if (mx != 0.0) {
+                    if (h->sys.moms[k].grid != (g ^ 1) || o.nxt >= MAXC)
+                        return fail(h, STARMAP_E_UNSUPPORTED, "x-coupling outside the staggered pattern");
+                    o.xin[o.nxt] = h->sys.moms[k].local;
+                    c.cx[o.nxt] = (T)(-mx / h->dx);
+                    ++o.nxt;
+                }
+                if (my != 0.0) {
+                    if (h->sys.moms[k].grid != (g ^ 2) || o.nyt >= MAXC)
+                        return fail(h, STARMAP_E_UNSUPPORTED, "y-coupling outside the staggered pattern");
+                    o.yin[o.nyt] = h->sys.moms[k].local;
+                    c.cy[o.nyt] = (T)(-my / h->dy);
+                    ++o.nyt;
+                }
+            }
+            outs.push_back(o);
+            coefs.push_back(c);
+        }
+        h->tend[g] = (int)outs.size();
+    }
+    if (h->outs_dev) { cudaFree(h->outs_dev); h->outs_dev = nullptr; }
+    if (h->coefs_dev) { cudaFree(h->coefs_dev); h->coefs_dev = nullptr; }
+    CK(cudaMalloc(&h->outs_dev, std::max<size_t>(1, outs.size()) * sizeof(GatherOut)), "cudaMalloc tables");
+    CK(cudaMalloc(&h->coefs_dev, std::max<size_t>(1, coefs.size()) * sizeof(GatherCoef<T>)), "cudaMalloc tables");
+    if (!outs.empty()) {
+        CK(cudaMemcpy(h->outs_dev, outs.data(), outs.size() * sizeof(GatherOut), cudaMemcpyHostToDevice), "upload tables");
+        CK(cudaMemcpy(h->coefs_dev, coefs.data(), coefs.size() * sizeof(GatherCoef<T>), cudaMemcpyHostToDevice), "upload tables");
+    }
+    // source pointer array
+    std::vector<void*> ptrs(h->src_dev.begin(), h->src_dev.end());
+    if (h->src_ptrs_dev) { cudaFree(h->src_ptrs_dev); h->src_ptrs_dev = nullptr; }
+    CK(cudaMalloc(&h->src_ptrs_dev, std::max<size_t>(1, ptrs.size()) * sizeof(void*)), "cudaMalloc sources");
+    if (!ptrs.empty())
+        CK(cudaMemcpy(h->src_ptrs_dev, ptrs.data(), ptrs.size() * sizeof(void*), cudaMemcpyHostToDevice), "upload sources");
+    if (h->tiled) {
+        int rc = tiled_update(h->tiled, h->sys, h->comp_class, h->src_slot, h->src_dev, h->dx, h->dy);
+        if (rc) return fail(h, rc, tiled_error(h->tiled));
+    }
+    return STARMAP_OK;
+}
+
+int rebuild_tables(starmap_t* h) {
+    return h->fp32 ? build_tables<float>(h) : build_tables<double>(h);
+}
+
+// Decay coefficients of grid g from the stored material (section 5.5/5.7):
+// class 0: c = Sigma_a; class l >= 1: c = Sigma_a + Sigma_s0 - Sigma_sl.
+// Stored as a = exp(-c dt/2), b = dt/2 E(-c dt/2), A = exp(-c dt), B = dt E(-c dt).
+template <class T>
+int upload_coefficients(starmap_t* h, int g) {
+    const long plane = (long)h->nxg[g] * h->nyg[g];
+    if (plane == 0) return STARMAP_OK;
+    std::vector<T> buf((size_t)h->nclasses * 4 * plane);
+    const std::vector<double>& sa = h->sig_a[g];
+    const std::vector<double>& ss = h->sig_s[g];
+    const double dt = h->dt;
+    for (int cls = 0; cls < h->nclasses; ++cls) {
+        for (long i = 0; i < plane; ++i) {
+            double c;
+            if (cls == 0) c = sa[i];
+            else if (h->sl_factor.empty()) c = sa[i] + ss[i];
+            else c = sa[i] + ss[i] - ss[i] * h->sl_factor[cls];
+            T* dst = buf.data() + (size_t)cls * 4 * plane + i;
+            dst[0] = (T)std::exp(-c * dt / 2);
+            dst[plane] = (T)(dt / 2 * expm1div(-c * dt / 2));
+            dst[2 * plane] = (T)std::exp(-c * dt);
+            dst[3 * plane] = (T)(dt * expm1div(-c * dt));
+        }
+    }
+    CK(cudaMemcpyAsync(h->coef[g], buf.data(), buf.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream), "upload coefficients");
+    CK(cudaStreamSynchronize(h->stream), "upload coefficients");
+    return STARMAP_OK;
+}
+
+int ensure_coef_alloc(starmap_t* h) {
+    if (h->ncls_alloc >= h->nclasses) return STARMAP_OK;
+    for (int g = 0; g < 4; ++g) {
+        if (h->coef[g]) { cudaFree(h->coef[g]); h->coef[g] = nullptr; }
+        size_t bytes = std::max<size_t>(1, (size_t)h->nclasses * 4 * h->nxg[g] * h->nyg[g]) * h->esize;
+        CK(cudaMalloc(&h->coef[g], bytes), "cudaMalloc coefficients");
+    }
+    h->ncls_alloc = h->nclasses;
+    return STARMAP_OK;
+}
+
+int upload_all_coefficients(starmap_t* h) {
+    int rc = ensure_coef_alloc(h);
+    if (rc) return rc;
+    for (int g = 0; g < 4; ++g) {
+        rc = h->fp32 ? upload_coefficients<float>(h, g) : upload_coefficients<double>(h, g);
+        if (rc) return rc;
+    }
+    return STARMAP_OK;
+}
+
+template <class T>
+int fill_ghosts_all(starmap_t* h) {
+    for (int g = 0; g < 4; ++g) {
+        GhostArgs<T> a;
+        a.g = grid_dev<T>(h, g);
+        a.pitch = h->pitch;
+        a.grid = g;
+        a.p[0] = h->p[0];
+        a.p[1] = h->p[1];
+        a.kbegin = 0;
+        a.kend = h->Kg[g];
+        if (launch_fill_ghosts<T>(a, h->stream)) return cuda_fail(h, cudaGetLastError(), "ghost fill");
+    }
+    h->ghosts_dirty = false;
+    return STARMAP_OK;
+}
+
+// One pass over the output grids of a parity.  odd: grids G21, G12;
+// even: G11, G22.  which: 0 half-step coefficients, 1 full-step.
+template <class T>
+int run_pass(starmap_t* h, bool odd, int which) {
+    if (h->kernel_used == STARMAP_KERNEL_TILED) {
+        int rc = tiled_pass(h->tiled, odd, which, h->stream);
+        if (rc) return fail(h, rc, tiled_error(h->tiled));
+        return STARMAP_OK;
+    }
+    const int gl[2] = {odd ? 1 : 0, odd ? 2 : 3};
+    for (int q = 0; q < 2; ++q) {
+        GatherArgs<T> a;
+        for (int g = 0; g < 4; ++g) a.g[g] = grid_dev<T>(h, g);
+        a.pitch = h->pitch;
+        a.p[0] = h->p[0];
+        a.p[1] = h->p[1];
+        a.out_grid = gl[q];
+        a.begin = h->tbeg[gl[q]];
+        a.end = h->tend[gl[q]];
+        a.which = which;
+        a.outs = h->outs_dev;
+        a.coefs = (const GatherCoef<T>*)h->coefs_dev;
+        a.src = (T* const*)h->src_ptrs_dev;
+        if (launch_gather_pass<T>(a, h->stream)) return cuda_fail(h, cudaGetLastError(), "gather pass");
+    }
+    return STARMAP_OK;
+}
+
+template <class T>
+int do_steps(starmap_t* h, long n) {
+    if (n <= 0) return STARMAP_OK;
+    if (h->ghosts_dirty) { int rc = fill_ghosts_all<T>(h); if (rc) return rc; }
+    int rc;
+    if (h->cfg.schedule == STARMAP_SCHEDULE_MERGED) {
+        if ((rc = run_pass<T>(h, true, 0))) return rc;
+        for (long i = 0; i < n; ++i) {
+            if ((rc = run_pass<T>(h, false, 1))) return rc;
+            if ((rc = run_pass<T>(h, true, i == n - 1 ? 0 : 1))) return rc;
+        }
+    } else {
+        for (long i = 0; i < n; ++i) {
+            if ((rc = run_pass<T>(h, true, 0))) return rc;
+            if ((rc = run_pass<T>(h, false, 1))) return rc;
+            if ((rc = run_pass<T>(h, true, 0))) return rc;
+        }
+    }
+    h->t += n * h->dt;
+    h->steps += n;
+    return STARMAP_OK;
+}
+
+int check_j(starmap_t* h, int j) {
+    if (!h) return STARMAP_E_ARG;
+    if (j < 0 || j >= h->ncomp) return fail(h, STARMAP_E_ARG, "component index out of range");
+    return STARMAP_OK;
+}
+
+size_t comp_points(const starmap_t* h, int j) {
+    int g = h->sys.moms[j].grid;
+    return (size_t)h->nxg[g] * h->nyg[g];
+}
+
+char* comp_ptr(const starmap_t* h, int j, void* const* bases) {
+    const Moment& m = h->sys.moms[j];
+    return (char*)bases[m.grid] + ((size_t)m.local * h->cstride[m.grid] + h->pitch) * h->esize;
+}
+
+// copy component j from a device layout (bases) to a host array in the run's precision
+int download_raw(starmap_t* h, int j, void* const* bases, void* dst) {
+    int g = h->sys.moms[j].grid;
+    CK(cudaMemcpy2DAsync(dst, h->nxg[g] * h->esize, comp_ptr(h, j, bases), h->pitch * h->esize,
+                         h->nxg[g] * h->esize, h->nyg[g], cudaMemcpyDeviceToHost, h->stream), "download");
+    return STARMAP_OK;
+}
+
+int upload_raw(starmap_t* h, int j, const void* src) {
+    int g = h->sys.moms[j].grid;
+    CK(cudaMemcpy2DAsync(comp_ptr(h, j, h->base), h->pitch * h->esize, src, h->nxg[g] * h->esize,
+                         h->nxg[g] * h->esize, h->nyg[g], cudaMemcpyHostToDevice, h->stream), "upload");
+    h->ghosts_dirty = true;
+    return STARMAP_OK;
+}
+
+int download_double(starmap_t* h, int j, void* const* bases, double* out) {
+    size_t np = comp_points(h, j);
+    if (h->fp32) {
+        std::vector<float> tmp(np);
+        int rc = download_raw(h, j, bases, tmp.data());
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(h->stream), "download");
+        for (size_t i = 0; i < np; ++i) out[i] = tmp[i];
+    } else {
+        int rc = download_raw(h, j, bases, out);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(h->stream), "download");
+    }
+    return STARMAP_OK;
+}
+
+void release(starmap_t* h) {
+    for (int g = 0; g < 4; ++g) {
+        if (h->alloc[g]) cudaFree(h->alloc[g]);
+        if (h->coef[g]) cudaFree(h->coef[g]);
+        if (h->prev[g]) cudaFree(h->prev[g]);
+    }
+    for (void* p : h->src_dev) if (p) cudaFree(p);
+    if (h->src_ptrs_dev) cudaFree(h->src_ptrs_dev);
+    if (h->outs_dev) cudaFree(h->outs_dev);
+    if (h->coefs_dev) cudaFree(h->coefs_dev);
+    if (h->partials) cudaFree(h->partials);
+    if (h->result) cudaFree(h->result);
+    if (h->tiled) tiled_destroy(h->tiled);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void starmap_config_default(starmap_config* c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->system = STARMAP_PN2D;
+    c->N = 1;
+    c->ax[0] = 0; c->ax[1] = 1; c->ax[2] = 0; c->ax[3] = 1;
+    c->n[0] = 16; c->n[1] = 16;
+    c->bc[0] = STARMAP_PERIODIC; c->bc[1] = STARMAP_PERIODIC;
+    c->cn = 0.5;
+    c->dt = 0;
+    c->precision = STARMAP_FP64;
+    c->schedule = STARMAP_SCHEDULE_LITERAL;
+    c->kernel = STARMAP_KERNEL_AUTO;
+    c->cuda_stream = nullptr;
+}
+
+int starmap_host_matrices(int system, int N, int cap, double* Mx, double* My, int* grid, int* order,
+                          double* lambda_max) {
+    SystemMatrices s;
+    std::string err;
+    if (!build_system(system, N, s, err)) return fail(nullptr, STARMAP_E_ARG, err);
+    if (cap < s.ncomp) return fail(nullptr, STARMAP_E_ARG, "capacity below the number of components");
+    int n = s.ncomp;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            if (Mx) Mx[(size_t)i * n + j] = s.Mx[(size_t)i * n + j];
+            if (My) My[(size_t)i * n + j] = s.My[(size_t)i * n + j];
+        }
+        if (grid) grid[i] = s.moms[i].grid;
+        if (order) order[i] = s.moms[i].l;
+    }
+    if (lambda_max) *lambda_max = s.lambda_max;
+    return STARMAP_OK;
+}
+
+int starmap_host_expm1div(double* c, size_t count) {
+    if (!c && count) return STARMAP_E_ARG;
+    for (size_t i = 0; i < count; ++i) c[i] = expm1div(c[i]);
+    return STARMAP_OK;
+}
+
+int starmap_create(const starmap_config* cfg, starmap_t** out) {
+    if (!out) return fail(nullptr, STARMAP_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, STARMAP_E_ARG, "cfg is NULL");
+    const starmap_config& c = *cfg;
+    if (c.system != STARMAP_PN2D && c.system != STARMAP_SLAB) return fail(nullptr, STARMAP_E_ARG, "unknown system");
+    if (c.N < 1 || c.N > 63) return fail(nullptr, STARMAP_E_ARG, "N must be in [1, 63]");
+    if (c.n[0] < 1 || c.n[1] < 1 || c.n[0] > (1 << 16) || c.n[1] > (1 << 16))
+        return fail(nullptr, STARMAP_E_ARG, "grid size out of range");
+    if (!(c.ax[1] > c.ax[0]) || !(c.ax[3] > c.ax[2])) return fail(nullptr, STARMAP_E_ARG, "empty domain");
+    for (int d = 0; d < 2; ++d)
+        if (c.bc[d] != STARMAP_PERIODIC && c.bc[d] != STARMAP_EXTRAPOLATION)
+            return fail(nullptr, STARMAP_E_ARG, "unknown boundary condition");
+    if (c.precision != STARMAP_FP64 && c.precision != STARMAP_FP32) return fail(nullptr, STARMAP_E_ARG, "unknown precision");
+    if (c.schedule != STARMAP_SCHEDULE_LITERAL && c.schedule != STARMAP_SCHEDULE_MERGED)
+        return fail(nullptr, STARMAP_E_ARG, "unknown schedule");
+    if (c.kernel < STARMAP_KERNEL_AUTO || c.kernel > STARMAP_KERNEL_TILED) return fail(nullptr, STARMAP_E_ARG, "unknown kernel");
+
+    starmap_t* h = new (std::nothrow) starmap_t();
+    if (!h) return fail(nullptr, STARMAP_E_NOMEM, "host allocation failed");
+    h->cfg = c;
+    std::string err;
+    if (!build_system(c.system, c.N, h->sys, err)) { delete h; return fail(nullptr, STARMAP_E_ARG, err); }
+    h->ncomp = h->sys.ncomp;
+    h->dx = (c.ax[1] - c.ax[0]) / c.n[0];
+    h->dy = (c.ax[3] - c.ax[2]) / c.n[1];
+    for (int d = 0; d < 2; ++d) h->p[d] = c.bc[d] == STARMAP_PERIODIC ? 1 : 0;
+    const double hmin = c.system == STARMAP_SLAB ? h->dx : std::min(h->dx, h->dy);
+    const double bound = c.system == STARMAP_SLAB ? 1.0 : 1.0 / std::sqrt(2.0);
+    if (c.dt > 0) {
+        h->dt = c.dt;
+    } else {
+        if (!(c.cn > 0)) { delete h; return fail(nullptr, STARMAP_E_ARG, "cn must be positive"); }
+        h->dt = c.cn * hmin / h->sys.lambda_max;
+    }
+    if (h->dt * h->sys.lambda_max / hmin > bound * (1 + 1e-12)) {
+        delete h;
+        return fail(nullptr, STARMAP_E_CFL, "time step beyond the CFL bound (cn <= 1/sqrt(2) in 2D, 1 in slab)");
+    }
+    // grids (section 5.2)
+    for (int g = 0; g < 4; ++g) {
+        bool xnode = g & 1, ynode = g & 2;
+        h->nxg[g] = xnode ? c.n[0] + 1 - h->p[0] : c.n[0];
+        h->nyg[g] = ynode ? c.n[1] + 1 - h->p[1] : c.n[1];
+        h->Kg[g] = h->sys.grid_count[g];
+    }
+    for (int j = 0; j < h->ncomp; ++j) h->members[h->sys.moms[j].grid].push_back(j);
+    for (int g = 0; g < 4; ++g)
+        std::sort(h->members[g].begin(), h->members[g].end(),
+                  [&](int a, int b) { return h->sys.moms[a].local < h->sys.moms[b].local; });
+    h->fp32 = c.precision == STARMAP_FP32;
+    h->esize = h->fp32 ? 4 : 8;
+    int nxmax = 0, nymax = 0;
+    for (int g = 0; g < 4; ++g) { nxmax = std::max(nxmax, h->nxg[g]); nymax = std::max(nymax, h->nyg[g]); }
+    h->pitch = ((nxmax + 6 + 31) / 32) * 32;
+    h->rows = nymax + 2;
+    h->comp_class.resize(h->ncomp);
+    h->nclasses = 2;
+    for (int j = 0; j < h->ncomp; ++j) h->comp_class[j] = class_of(h, h->sys.moms[j].l);
+    h->src_slot.assign(h->ncomp, -1);
+    for (int g = 0; g < 4; ++g) {
+        size_t plane = (size_t)h->nxg[g] * h->nyg[g];
+        h->sig_a[g].assign(plane, 0.0);
+        h->sig_s[g].assign(plane, 0.0);
+    }
+    // kernel choice
+    bool tiled_ok = tiled_supported(c.system, c.N, c.precision);
+    if (c.kernel == STARMAP_KERNEL_TILED && !tiled_ok) {
+        delete h;
+        return fail(nullptr, STARMAP_E_UNSUPPORTED, "tiled kernel needs FP32, the 2D P_N system and N <= 41");
+    }
+    h->kernel_used = (c.kernel == STARMAP_KERNEL_TILED || (c.kernel == STARMAP_KERNEL_AUTO && tiled_ok))
+                         ? STARMAP_KERNEL_TILED : STARMAP_KERNEL_GATHER;
+
+    // device resources
+    cudaError_t e;
+    if (c.cuda_stream) { h->stream = (cudaStream_t)c.cuda_stream; h->own_stream = false; }
+    else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { int rc = cuda_fail(nullptr, e, "cudaStreamCreate"); delete h; return rc; }
+        h->own_stream = true;
+    }
+    auto bail = [&](int rc) { if (rc != STARMAP_OK) { std::string m = h->err; release(h); delete h; g_create_error = m; } return rc; };
+    for (int g = 0; g < 4; ++g) {
+        h->cstride[g] = h->rows * h->pitch;
+        size_t elems = LEAD + (size_t)std::max(1, h->Kg[g]) * h->cstride[g] + h->pitch;
+        h->grid_bytes[g] = elems * h->esize;
+        e = cudaMalloc(&h->alloc[g], h->grid_bytes[g]);
+        if (e != cudaSuccess) return bail(fail(h, e == cudaErrorMemoryAllocation ? STARMAP_E_NOMEM : STARMAP_E_CUDA,
+                                                std::string("cudaMalloc state: ") + cudaGetErrorString(e)));
+        e = cudaMemsetAsync(h->alloc[g], 0, h->grid_bytes[g], h->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMemset state"));
+        h->base[g] = (char*)h->alloc[g] + LEAD * h->esize;
+    }
+    e = cudaMalloc(&h->partials, (size_t)h->red_blocks * 3 * sizeof(double));
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc reduction"));
+    e = cudaMalloc(&h->result, 4 * sizeof(double));
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc reduction"));
+    if (h->kernel_used == STARMAP_KERNEL_TILED) {
+        TiledGeometry geo;
+        for (int g = 0; g < 4; ++g) {
+            geo.base[g] = h->base[g]; geo.cstride[g] = h->cstride[g];
+            geo.nx[g] = h->nxg[g]; geo.ny[g] = h->nyg[g]; geo.K[g] = h->Kg[g];
+        }
+        geo.pitch = h->pitch; geo.rows = h->rows; geo.p[0] = h->p[0]; geo.p[1] = h->p[1]; geo.N = c.N;
+        int rc = tiled_create(geo, &h->tiled);
+        if (rc) { std::string m = h->tiled ? tiled_error(h->tiled) : "tiled kernel setup failed"; return bail(fail(h, rc, m)); }
+    }
+    int rc = upload_all_coefficients(h);
+    if (rc) return bail(rc);
+    if (h->tiled) { for (int g = 0; g < 4; ++g) tiled_set_coef(h->tiled, g, h->coef[g], h->nclasses); }
+    rc = rebuild_tables(h);
+    if (rc) return bail(rc);
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "create"));
+    *out = h;
+    return STARMAP_OK;
+}
+
+void starmap_destroy(starmap_t* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+}
+
+const char* starmap_last_error(const starmap_t* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int starmap_num_moments(const starmap_t* h) { return h ? h->ncomp : 0; }
+double starmap_dt(const starmap_t* h) { return h ? h->dt : 0.0; }
+double starmap_time(const starmap_t* h) { return h ? h->t : 0.0; }
+long starmap_steps_done(const starmap_t* h) { return h ? h->steps : 0; }
+int starmap_kernel(const starmap_t* h) { return h ? h->kernel_used : 0; }
+
+int starmap_moment_info(const starmap_t* hc, int j, int* l, int* m, int* is_imag, int* grid, int* nx, int* ny) {
+    starmap_t* h = const_cast<starmap_t*>(hc);
+    int rc = check_j(h, j);
+    if (rc) return rc;
+    const Moment& mo = h->sys.moms[j];
+    if (l) *l = mo.l;
+    if (m) *m = mo.m;
+    if (is_imag) *is_imag = mo.imag ? 1 : 0;
+    if (grid) *grid = mo.grid;
+    if (nx) *nx = h->nxg[mo.grid];
+    if (ny) *ny = h->nyg[mo.grid];
+    return STARMAP_OK;
+}
+
+int starmap_grid_info(const starmap_t* hc, int g, int* nx, int* ny, double* x0, double* y0, double* dx, double* dy) {
+    starmap_t* h = const_cast<starmap_t*>(hc);
+    if (!h) return STARMAP_E_ARG;
+    if (g < 0 || g > 3) return fail(h, STARMAP_E_ARG, "grid index out of range");
+    bool xnode = g & 1, ynode = g & 2;
+    if (nx) *nx = h->nxg[g];
+    if (ny) *ny = h->nyg[g];
+    // eq. grid11 / staggered_grids: cells at (i - 1/2) h, nodes at i h, i from p
+    if (x0) *x0 = h->cfg.ax[0] + (xnode ? h->p[0] * h->dx : 0.5 * h->dx);
+    if (y0) *y0 = h->cfg.ax[2] + (ynode ? h->p[1] * h->dy : 0.5 * h->dy);
+    if (dx) *dx = h->dx;
+    if (dy) *dy = h->dy;
+    return STARMAP_OK;
+}
+
+int starmap_set_material(starmap_t* h, int g, const double* sigma_a, const double* sigma_s0, size_t count) {
+    if (!h) return STARMAP_E_ARG;
+    if (g < 0 || g > 3) return fail(h, STARMAP_E_ARG, "grid index out of range");
+    size_t plane = (size_t)h->nxg[g] * h->nyg[g];
+    if (count != plane) return fail(h, STARMAP_E_ARG, "material size does not match the grid");
+    if (!sigma_a || !sigma_s0) return fail(h, STARMAP_E_ARG, "material array is NULL");
+    for (size_t i = 0; i < plane; ++i) {
+        if (!std::isfinite(sigma_a[i]) || !std::isfinite(sigma_s0[i]))
+            return fail(h, STARMAP_E_NONFINITE, "material contains NaN or Inf");
+    }
+    CK(cudaStreamSynchronize(h->stream), "set_material");
+    h->sig_a[g].assign(sigma_a, sigma_a + plane);
+    h->sig_s[g].assign(sigma_s0, sigma_s0 + plane);
+    int rc = ensure_coef_alloc(h);
+    if (rc) return rc;
+    rc = h->fp32 ? upload_coefficients<float>(h, g) : upload_coefficients<double>(h, g);
+    if (rc) return rc;
+    if (h->tiled) tiled_set_coef(h->tiled, g, h->coef[g], h->nclasses);
+    return STARMAP_OK;
+}
+
+int starmap_set_scattering_factors(starmap_t* h, const double* factor, int count) {
+    if (!h) return STARMAP_E_ARG;
+    CK(cudaStreamSynchronize(h->stream), "set_scattering_factors");
+    if (!factor) {
+        h->sl_factor.clear();
+        h->nclasses = 2;
+    } else {
+        if (count != h->cfg.N + 1) return fail(h, STARMAP_E_ARG, "factor must have N+1 entries");
+        h->sl_factor.assign(factor, factor + count);
+        h->nclasses = h->cfg.N + 1;
+    }
+    for (int j = 0; j < h->ncomp; ++j) h->comp_class[j] = class_of(h, h->sys.moms[j].l);
+    int rc = upload_all_coefficients(h);
+    if (rc) return rc;
+    if (h->tiled) for (int g = 0; g < 4; ++g) tiled_set_coef(h->tiled, g, h->coef[g], h->nclasses);
+    return rebuild_tables(h);
+}
+
+int starmap_set_source(starmap_t* h, int j, const double* q, size_t count) {
+    int rc = check_j(h, j);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream), "set_source");
+    size_t np = comp_points(h, j);
+    if (!q) {
+        if (h->src_slot[j] >= 0) {
+            int s = h->src_slot[j];
+            cudaFree(h->src_dev[s]);
+            h->src_dev[s] = nullptr;
+            h->src_slot[j] = -1;
+            // compact slots
+            std::vector<void*> keep;
+            std::vector<int> remap(h->src_dev.size(), -1);
+            for (size_t i = 0; i < h->src_dev.size(); ++i)
+                if (h->src_dev[i]) { remap[i] = (int)keep.size(); keep.push_back(h->src_dev[i]); }
+            for (int k = 0; k < h->ncomp; ++k) if (h->src_slot[k] >= 0) h->src_slot[k] = remap[h->src_slot[k]];
+            h->src_dev = keep;
+        }
+        return rebuild_tables(h);
+    }
+    if (count != np) return fail(h, STARMAP_E_ARG, "source size does not match the grid of the component");
+    if (h->src_slot[j] < 0) {
+        void* d = nullptr;
+        CK(cudaMalloc(&d, np * h->esize), "cudaMalloc source");
+        h->src_slot[j] = (int)h->src_dev.size();
+        h->src_dev.push_back(d);
+    }
+    void* d = h->src_dev[h->src_slot[j]];
+    if (h->fp32) {
+        std::vector<float> tmp(q, q + np);
+        CK(cudaMemcpy(d, tmp.data(), np * 4, cudaMemcpyHostToDevice), "upload source");
+    } else {
+        CK(cudaMemcpy(d, q, np * 8, cudaMemcpyHostToDevice), "upload source");
+    }
+    return rebuild_tables(h);
+}
+
+int starmap_set_moment(starmap_t* h, int j, const double* u, size_t count) {
+    int rc = check_j(h, j);
+    if (rc) return rc;
+    size_t np = comp_points(h, j);
+    if (!u || count != np) return fail(h, STARMAP_E_ARG, "moment size does not match the grid of the component");
+    if (h->fp32) {
+        std::vector<float> tmp(u, u + np);
+        rc = upload_raw(h, j, tmp.data());
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(h->stream), "set_moment");
+    } else {
+        rc = upload_raw(h, j, u);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(h->stream), "set_moment");
+    }
+    h->have_output = false;
+    return STARMAP_OK;
+}
+
+int starmap_set_time(starmap_t* h, double t) {
+    if (!h) return STARMAP_E_ARG;
+    h->t = t;
+    return STARMAP_OK;
+}
+
+int starmap_step(starmap_t* h, long nsteps) {
+    if (!h) return STARMAP_E_ARG;
+    if (nsteps < 0) return fail(h, STARMAP_E_ARG, "negative step count");
+    h->have_output = false;
+    return h->fp32 ? do_steps<float>(h, nsteps) : do_steps<double>(h, nsteps);
+}
+
+int starmap_pass(starmap_t* h, int parity, int which) {
+    if (!h) return STARMAP_E_ARG;
+    if ((parity != 0 && parity != 1) || (which != 0 && which != 1)) return fail(h, STARMAP_E_ARG, "parity and which must be 0 or 1");
+    h->have_output = false;
+    if (h->fp32) {
+        if (h->ghosts_dirty) { int rc = fill_ghosts_all<float>(h); if (rc) return rc; }
+        return run_pass<float>(h, parity == 1, which);
+    }
+    if (h->ghosts_dirty) { int rc = fill_ghosts_all<double>(h); if (rc) return rc; }
+    return run_pass<double>(h, parity == 1, which);
+}
+
+int starmap_advance_to(starmap_t* h, double t_out) {
+    if (!h) return STARMAP_E_ARG;
+    const double eps = 1e-12 * std::max(1.0, std::fabs(t_out));
+    if (t_out < h->t - eps) return fail(h, STARMAP_E_ARG, "t_out lies before the current time");
+    for (int g = 0; g < 4; ++g) {
+        if (!h->prev[g]) CK(cudaMalloc(&h->prev[g], h->grid_bytes[g]), "cudaMalloc output level");
+    }
+    if (t_out <= h->t + eps) {
+        for (int g = 0; g < 4; ++g)
+            CK(cudaMemcpyAsync(h->prev[g], h->alloc[g], h->grid_bytes[g], cudaMemcpyDeviceToDevice, h->stream), "copy level");
+        h->out_lambda = 1.0;
+        h->have_output = true;
+        return STARMAP_OK;
+    }
+    long n = (long)std::ceil((t_out - h->t) / h->dt - 1e-9);
+    if (n < 1) n = 1;
+    int rc = starmap_step(h, n - 1);
+    if (rc) return rc;
+    if (h->ghosts_dirty) {
+        rc = h->fp32 ? fill_ghosts_all<float>(h) : fill_ghosts_all<double>(h);
+        if (rc) return rc;
+    }
+    for (int g = 0; g < 4; ++g)
+        CK(cudaMemcpyAsync(h->prev[g], h->alloc[g], h->grid_bytes[g], cudaMemcpyDeviceToDevice, h->stream), "copy level");
+    double t0 = h->t;
+    rc = starmap_step(h, 1);
+    if (rc) return rc;
+    h->out_lambda = (t_out - t0) / h->dt;
+    h->have_output = true;
+    return STARMAP_OK;
+}
+
+int starmap_output(starmap_t* h, int j, double* out, size_t count) {
+    int rc = check_j(h, j);
+    if (rc) return rc;
+    if (!h->have_output) return fail(h, STARMAP_E_STATE, "no output level: call starmap_advance_to first");
+    size_t np = comp_points(h, j);
+    if (!out || count != np) return fail(h, STARMAP_E_ARG, "output size does not match the grid of the component");
+    std::vector<double> a(np), b(np);
+    void* prevb[4];
+    for (int g = 0; g < 4; ++g) prevb[g] = h->prev[g] ? (char*)h->prev[g] + LEAD * h->esize : nullptr;
+    if ((rc = download_double(h, j, prevb, a.data()))) return rc;
+    if ((rc = download_double(h, j, h->base, b.data()))) return rc;
+    const double lam = h->out_lambda;
+    for (size_t i = 0; i < np; ++i) out[i] = (1.0 - lam) * a[i] + lam * b[i];
+    return STARMAP_OK;
+}
+
+int starmap_moments(starmap_t* h, int j, double* out, size_t count) {
+    int rc = check_j(h, j);
+    if (rc) return rc;
+    size_t np = comp_points(h, j);
+    if (!out || count != np) return fail(h, STARMAP_E_ARG, "output size does not match the grid of the component");
+    return download_double(h, j, h->base, out);
+}
+
+int starmap_diagnostics(starmap_t* h, double* mass, double* l2, long* nonfinite) {
+    if (!h) return STARMAP_E_ARG;
+    int rc;
+    if (h->fp32) {
+        ReduceArgs<float> a;
+        for (int g = 0; g < 4; ++g) a.g[g] = grid_dev<float>(h, g);
+        a.pitch = h->pitch; a.cell = h->dx * h->dy;
+        rc = launch_reduce<float>(a, h->partials, h->red_blocks, h->result, h->stream);
+    } else {
+        ReduceArgs<double> a;
+        for (int g = 0; g < 4; ++g) a.g[g] = grid_dev<double>(h, g);
+        a.pitch = h->pitch; a.cell = h->dx * h->dy;
+        rc = launch_reduce<double>(a, h->partials, h->red_blocks, h->result, h->stream);
+    }
+    if (rc) return cuda_fail(h, cudaGetLastError(), "reduction");
+    double res[3];
+    CK(cudaMemcpyAsync(res, h->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reduction read-back");
+    CK(cudaStreamSynchronize(h->stream), "reduction");
+    if (mass) *mass = res[0];
+    if (l2) *l2 = res[1];
+    if (nonfinite) *nonfinite = (long)res[2];
+    if (res[2] > 0) return fail(h, STARMAP_E_NONFINITE, "state contains NaN or Inf");
+    return STARMAP_OK;
+}
+
+int starmap_device_ptr(starmap_t* h, int j, void** ptr, long* pitch, long* offset) {
+    int rc = check_j(h, j);
+    if (rc) return rc;
+    const Moment& m = h->sys.moms[j];
+    if (ptr) *ptr = (char*)h->base[m.grid] + (size_t)m.local * h->cstride[m.grid] * h->esize;
+    if (pitch) *pitch = h->pitch;
+    if (offset) *offset = h->pitch;
+    return STARMAP_OK;
+}
+
+size_t starmap_state_bytes(const starmap_t* h) {
+    if (!h) return 0;
+    size_t s = 0;
+    for (int j = 0; j < h->ncomp; ++j) s += comp_points(h, j) * h->esize;
+    return s + 2 * sizeof(double);
+}
+
+int starmap_get_state(starmap_t* h, void* buf, size_t bytes) {
+    if (!h) return STARMAP_E_ARG;
+    if (!buf || bytes < starmap_state_bytes(h)) return fail(h, STARMAP_E_ARG, "state buffer too small");
+    char* p = (char*)buf;
+    for (int j = 0; j < h->ncomp; ++j) {
+        int rc = download_raw(h, j, h->base, p);
+        if (rc) return rc;
+        p += comp_points(h, j) * h->esize;
+    }
+    CK(cudaStreamSynchronize(h->stream), "get_state");
+    double meta[2] = {h->t, (double)h->steps};
+    std::memcpy(p, meta, sizeof(meta));
+    return STARMAP_OK;
+}
+
+int starmap_set_state(starmap_t* h, const void* buf, size_t bytes) {
+    if (!h) return STARMAP_E_ARG;
+    if (!buf || bytes < starmap_state_bytes(h)) return fail(h, STARMAP_E_ARG, "state buffer too small");
+    const char* p = (const char*)buf;
+    for (int j = 0; j < h->ncomp; ++j) {
+        int rc = upload_raw(h, j, p);
+        if (rc) return rc;
+        p += comp_points(h, j) * h->esize;
+    }
+    CK(cudaStreamSynchronize(h->stream), "set_state");
+    double meta[2];
+    std::memcpy(meta, p, sizeof(meta));
+    h->t = meta[0];
+    h->steps = (long)meta[1];
+    h->have_output = false;
+    return STARMAP_OK;
+}
+
+int starmap_sync(starmap_t* h) {
+    if (!h) return STARMAP_E_ARG;
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    return STARMAP_OK;
+}
+
+}  // extern "C"
