@@ -247,7 +247,10 @@ def run_native(args):
 
     problem, desc = workload(args.workload)
     esize = 4 if problem.precision == "fp32" else 8
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the legacy default stream has handle 0, which the
+    # library would read as "use your own stream"
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     s = capi.Stepper.from_problem(problem, schedule="merged", kernel=args.kernel, stream=stream.cuda_stream)
     updates_per_step = sum(s.moment_info(j)["nx"] * s.moment_info(j)["ny"] for j in range(s.ncomp))
     state_bytes = s.state_bytes()
@@ -307,7 +310,7 @@ def run_native(args):
     assert np.isfinite(r00).all()
 
     clocks = clk.summary()
-    launches = 2 * args.steps + 1
+    launches = (2 * args.steps + 1) * (1 if s.kernel == "tiled" else 2)
     line = {
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,

@@ -80,7 +80,7 @@ extern "C" {
 /* Kernel selection for the half-step passes. */
 #define STARMAP_KERNEL_AUTO    0  /* tiled kernel where supported, else gather */
 #define STARMAP_KERNEL_GATHER  1  /* one thread per point, CSR loop over moments */
-#define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N, N <= 41) */
+#define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N, N <= 63) */
 
 typedef struct starmap_s starmap_t;
 
@@ -195,6 +195,11 @@ int starmap_output(starmap_t* h, int j, double* out, size_t count);
 /* ------------------------------------------------------------ read-out */
 /* Copy component j (nx*ny doubles of its grid) to the host. */
 int starmap_moments(starmap_t* h, int j, double* out, size_t count);
+/* Copy the nx x ny sub-rectangle of component j whose first point is
+ * (i0, k0) of its grid to the host (nx*ny doubles, x fastest).  E_ARG if the
+ * rectangle leaves the grid. */
+int starmap_moments_window(starmap_t* h, int j, int i0, int k0, int nx, int ny,
+                           double* out, size_t count);
 /* FP64 device reductions (precision policy: FP64 only for these):
  * mass = dx dy sum R_0^0 over G11, l2 = sqrt(dx dy sum_j sum u_j^2)
  * (discrete L2 norm, eq. discrete_L2_norm), nonfinite = count of NaN/Inf

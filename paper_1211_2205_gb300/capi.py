@@ -96,6 +96,8 @@ def lib():
         "starmap_pass": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int]),
         "starmap_output": (ctypes.c_int, [H, ctypes.c_int, _dp, ctypes.c_size_t]),
         "starmap_moments": (ctypes.c_int, [H, ctypes.c_int, _dp, ctypes.c_size_t]),
+        "starmap_moments_window": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, _dp, ctypes.c_size_t]),
         "starmap_diagnostics": (ctypes.c_int, [H, _dp, _dp, ctypes.POINTER(ctypes.c_long)]),
         "starmap_device_ptr": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                               ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
@@ -279,6 +281,11 @@ class Stepper:
         info = self.moment_info(j)
         out = np.empty((info["ny"], info["nx"]))
         self._check(self._L.starmap_moments(self._h, j, _dptr(out), out.size))
+        return out
+
+    def moments_window(self, j: int, i0: int, k0: int, nx: int, ny: int) -> np.ndarray:
+        out = np.empty((ny, nx))
+        self._check(self._L.starmap_moments_window(self._h, j, i0, k0, nx, ny, _dptr(out), out.size))
         return out
 
     def diagnostics(self):

@@ -74,6 +74,15 @@ int cuda_fail(starmap_t* h, cudaError_t e, const char* what) {
 
 #define CK(call, what) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail(h, e_, what); } while (0)
 
+// Surface a bounded-wait failure of the tiled kernel (synchronises the stream).
+int poll_kernel(starmap_t* h) {
+    if (!h->tiled) return STARMAP_OK;
+    int rc = tiled_poll(h->tiled, h->stream);
+    if (rc == -6) return fail(h, STARMAP_E_TIMEOUT, tiled_error(h->tiled));
+    if (rc) return fail(h, STARMAP_E_CUDA, tiled_error(h->tiled));
+    return STARMAP_OK;
+}
+
 template <class T>
 GridDev<T> grid_dev(const starmap_t* h, int g) {
     GridDev<T> d;
@@ -306,6 +315,7 @@ int upload_raw(starmap_t* h, int j, const void* src) {
 
 int download_double(starmap_t* h, int j, void* const* bases, double* out) {
     size_t np = comp_points(h, j);
+    if (int rc = poll_kernel(h)) return rc;
     if (h->fp32) {
         std::vector<float> tmp(np);
         int rc = download_raw(h, j, bases, tmp.data());
@@ -450,7 +460,7 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
     bool tiled_ok = tiled_supported(c.system, c.N, c.precision);
     if (c.kernel == STARMAP_KERNEL_TILED && !tiled_ok) {
         delete h;
-        return fail(nullptr, STARMAP_E_UNSUPPORTED, "tiled kernel needs FP32, the 2D P_N system and N <= 41");
+        return fail(nullptr, STARMAP_E_UNSUPPORTED, "tiled kernel needs FP32, the 2D P_N system, N <= 63 and TMA support");
     }
     h->kernel_used = (c.kernel == STARMAP_KERNEL_TILED || (c.kernel == STARMAP_KERNEL_AUTO && tiled_ok))
                          ? STARMAP_KERNEL_TILED : STARMAP_KERNEL_GATHER;
@@ -723,6 +733,25 @@ int starmap_moments(starmap_t* h, int j, double* out, size_t count) {
     return download_double(h, j, h->base, out);
 }
 
+int starmap_moments_window(starmap_t* h, int j, int i0, int k0, int nx, int ny, double* out, size_t count) {
+    int rc = check_j(h, j);
+    if (rc) return rc;
+    const int g = h->sys.moms[j].grid;
+    if (i0 < 0 || k0 < 0 || nx < 0 || ny < 0 || i0 + nx > h->nxg[g] || k0 + ny > h->nyg[g])
+        return fail(h, STARMAP_E_ARG, "window leaves the grid of the component");
+    if (!out || count != (size_t)nx * ny) return fail(h, STARMAP_E_ARG, "output size does not match the window");
+    if (nx == 0 || ny == 0) return STARMAP_OK;
+    if ((rc = poll_kernel(h))) return rc;
+    const char* src = comp_ptr(h, j, h->base) + ((size_t)k0 * h->pitch + i0) * h->esize;
+    std::vector<char> tmp((size_t)nx * ny * h->esize);
+    CK(cudaMemcpy2DAsync(tmp.data(), nx * h->esize, src, h->pitch * h->esize, nx * h->esize, ny,
+                         cudaMemcpyDeviceToHost, h->stream), "download window");
+    CK(cudaStreamSynchronize(h->stream), "download window");
+    for (size_t i = 0; i < (size_t)nx * ny; ++i)
+        out[i] = h->fp32 ? (double)((const float*)tmp.data())[i] : ((const double*)tmp.data())[i];
+    return STARMAP_OK;
+}
+
 int starmap_diagnostics(starmap_t* h, double* mass, double* l2, long* nonfinite) {
     if (!h) return STARMAP_E_ARG;
     int rc;
@@ -738,6 +767,7 @@ int starmap_diagnostics(starmap_t* h, double* mass, double* l2, long* nonfinite)
         rc = launch_reduce<double>(a, h->partials, h->red_blocks, h->result, h->stream);
     }
     if (rc) return cuda_fail(h, cudaGetLastError(), "reduction");
+    if ((rc = poll_kernel(h))) return rc;
     double res[3];
     CK(cudaMemcpyAsync(res, h->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reduction read-back");
     CK(cudaStreamSynchronize(h->stream), "reduction");
@@ -768,6 +798,7 @@ size_t starmap_state_bytes(const starmap_t* h) {
 int starmap_get_state(starmap_t* h, void* buf, size_t bytes) {
     if (!h) return STARMAP_E_ARG;
     if (!buf || bytes < starmap_state_bytes(h)) return fail(h, STARMAP_E_ARG, "state buffer too small");
+    if (int rc = poll_kernel(h)) return rc;
     char* p = (char*)buf;
     for (int j = 0; j < h->ncomp; ++j) {
         int rc = download_raw(h, j, h->base, p);
@@ -801,7 +832,7 @@ int starmap_set_state(starmap_t* h, const void* buf, size_t bytes) {
 int starmap_sync(starmap_t* h) {
     if (!h) return STARMAP_E_ARG;
     CK(cudaStreamSynchronize(h->stream), "sync");
-    return STARMAP_OK;
+    return poll_kernel(h);
 }
 
 }  // extern "C"

@@ -1,17 +1,363 @@
-// Tiled half-step kernel (placeholder until implemented).
+// Host side of the tiled half-step pass: TMA descriptors and the per-pass
+// tables (item stream, coefficient rows, finalise events), built by walking
+// the same loop the consumer threads walk.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
 #include "tiled.h"
+#include "tiled_kernel.cuh"
 
 namespace starmap {
 
-struct TiledPlan { std::string err; };
+using namespace tiled;
 
-bool tiled_supported(int, int, int) { return false; }
-int tiled_create(const TiledGeometry&, TiledPlan** out) { *out = nullptr; return -8; }
-int tiled_update(TiledPlan*, const SystemMatrices&, const std::vector<int>&, const std::vector<int>&,
-                 const std::vector<void*>&, double, double) { return -8; }
-void tiled_set_coef(TiledPlan*, int, void*, int) {}
-int tiled_pass(TiledPlan*, bool, int, void*) { return -8; }
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 3D map over one grid: x' = x + VEC (x = -VEC .. pitch-VEC-1), memory row
+// y + 1, component; box (bx, by, 1).  The base address is 16-byte aligned
+// (state rows start 128-byte aligned, VEC floats before them).
+bool encode_grid_map(CUtensorMap* map, void* base, long pitch, long rows, int K, int bx, int by) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)rows, (cuuint64_t)(K > 0 ? K : 1)};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * rows * 4};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    void* addr = (char*)base - VEC * 4;
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, addr, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// index of (l, m, imag) in the real ordering of eq. transformation
+int comp_index(int l, int m, int imag) {
+    return l * (l + 1) / 2 + (m > 0 ? 2 * ((l - m) / 2) + imag : l);
+}
+
+bool exists(int N, int L, int q, int imag) {
+    if (L < 0 || L > N || q < 0 || q >= nq_of(L)) return false;
+    return imag ? has_imag(L, q) : true;
+}
+
+struct PassTables {
+    std::vector<uint32_t> items;
+    std::vector<float> coef;              // nin x 8
+    std::vector<int2> fin;                // (local, class)
+    std::vector<int> fin_comp;            // global component per finalise event
+    int nin = 0;
+};
+
+}  // namespace
+
+struct TiledPlan {
+    TiledGeometry geo;
+    std::string err;
+    int N = 0;
+    void* coef[4] = {nullptr, nullptr, nullptr, nullptr};
+    int nclasses = 2;
+    int* err_dev = nullptr;
+    CUtensorMap maps_in[4], maps_out[4];
+    PassTables tab[2];
+    void* dev_items[2] = {nullptr, nullptr};
+    void* dev_coef[2] = {nullptr, nullptr};
+    void* dev_fin[2] = {nullptr, nullptr};
+    void* dev_src[2] = {nullptr, nullptr};
+    int tiles_x = 0, tiles_y = 0;
+    int smem_bytes[2] = {0, 0};
+    Params prm[2][2];                     // [P][which]
+    bool ready = false;
+};
+
+namespace {
+
+void free_tables(TiledPlan* pl) {
+    for (int P = 0; P < 2; ++P) {
+        if (pl->dev_items[P]) cudaFree(pl->dev_items[P]);
+        if (pl->dev_coef[P]) cudaFree(pl->dev_coef[P]);
+        if (pl->dev_fin[P]) cudaFree(pl->dev_fin[P]);
+        if (pl->dev_src[P]) cudaFree(pl->dev_src[P]);
+        pl->dev_items[P] = pl->dev_coef[P] = pl->dev_fin[P] = pl->dev_src[P] = nullptr;
+    }
+}
+
+template <class V>
+bool upload(void** dst, const std::vector<V>& v) {
+    size_t bytes = std::max<size_t>(1, v.size()) * sizeof(V);
+    if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
+    if (!v.empty() && cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    return true;
+}
+
+// Walk the consumer loop of pass P and emit its tables.
+bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>& comp_class, int P, double dx,
+                double dy, PassTables& t, std::string& err) {
+    const int N = pl->N, n = sys.ncomp;
+    t = PassTables();
+    const int gin[2] = {P == 1 ? 0 : 1, P == 1 ? 3 : 2};
+    const int gout[2] = {P == 1 ? 1 : 0, P == 1 ? 2 : 3};
+    auto local_of = [&](int L, int q, int imag, int grid_expected, int& local) -> bool {
+        const int j = comp_index(L, L - 2 * q, imag);
+        const Moment& m = sys.moms[j];
+        if (m.l != L || m.m != L - 2 * q || (int)m.imag != imag || m.grid != grid_expected) return false;
+        local = m.local;
+        return true;
+    };
+    long covered = 0;
+    auto coef_of = [&](const std::vector<double>& M, int L, int q, int imag, int k, double h) -> float {
+        if (!exists(N, L, q, imag)) return 0.f;
+        const int j = comp_index(L, L - 2 * q, imag);
+        const double v = M[(size_t)j * n + k];
+        if (v != 0.0) ++covered;
+        return (float)(-v / h);
+    };
+    auto emit_input = [&](int lp, int q, int imag) -> bool {
+        int local;
+        if (!local_of(lp, q, imag, gin[imag], local)) return false;
+        t.items.push_back(((uint32_t)imag << ITEM_MAP_SHIFT) | (uint32_t)local);
+        const int k = comp_index(lp, lp - 2 * q, imag);
+        // targets Pm (lp-1, q-1), P0 (lp-1, q), N0 (lp+1, q), Np (lp+1, q+1)
+        const int TL[4] = {lp - 1, lp - 1, lp + 1, lp + 1};
+        const int TQ[4] = {q - 1, q, q, q + 1};
+        float row[8];
+        for (int s = 0; s < 4; ++s) {
+            row[s] = coef_of(sys.Mx, TL[s], TQ[s], imag, k, dx);          // same kind through Mx
+            row[4 + s] = coef_of(sys.My, TL[s], TQ[s], 1 - imag, k, dy);  // other kind through My
+        }
+        t.coef.insert(t.coef.end(), row, row + 8);
+        ++t.nin;
+        return true;
+    };
+    auto emit_fin = [&](int L, int q, int imag) -> bool {
+        int local;
+        if (!local_of(L, q, imag, gout[imag], local)) return false;
+        t.items.push_back(((uint32_t)(2 + imag) << ITEM_MAP_SHIFT) | (uint32_t)local);
+        const int j = comp_index(L, L - 2 * q, imag);
+        t.fin.push_back(make_int2(local, comp_class[j]));
+        t.fin_comp.push_back(j);
+        return true;
+    };
+    const int first = 1 - P;
+    int last_in = first;
+    bool ok = true;
+    for (int lp = first; lp <= N && ok; lp += 2) {
+        last_in = lp;
+        const int nq = nq_of(lp), nqp = nq_of(lp - 1);
+        for (int q = 0; q < nq && ok; ++q) {
+            ok = ok && emit_input(lp, q, 0);
+            if (has_imag(lp, q)) ok = ok && emit_input(lp, q, 1);
+            if (q >= 1 && q - 1 < nqp) {
+                ok = ok && emit_fin(lp - 1, q - 1, 0);
+                if (has_imag(lp - 1, q - 1)) ok = ok && emit_fin(lp - 1, q - 1, 1);
+            }
+        }
+        if (ok && nq - 1 < nqp) {
+            ok = ok && emit_fin(lp - 1, nq - 1, 0);
+            if (has_imag(lp - 1, nq - 1)) ok = ok && emit_fin(lp - 1, nq - 1, 1);
+        }
+    }
+    const int L = last_in + 1;
+    if (ok && L <= N)
+        for (int q = 0; q < nq_of(L) && ok; ++q) {
+            ok = ok && emit_fin(L, q, 0);
+            if (has_imag(L, q)) ok = ok && emit_fin(L, q, 1);
+        }
+    if (!ok) { err = "moment placement differs from the tiled kernel's"; return false; }
+    // every component of the output parity is finalised exactly once
+    long nout = 0;
+    for (int j = 0; j < n; ++j) nout += (sys.moms[j].l % 2 == P);
+    if ((long)t.fin.size() != nout) { err = "tiled schedule does not cover every output"; return false; }
+    // every nonzero coupling between the two parities is covered
+    long total = 0;
+    for (int j = 0; j < n; ++j) {
+        if (sys.moms[j].l % 2 != P) continue;
+        for (int k = 0; k < n; ++k)
+            if (sys.moms[k].l % 2 != P)
+                total += (sys.Mx[(size_t)j * n + k] != 0.0) + (sys.My[(size_t)j * n + k] != 0.0);
+    }
+    if (covered != total) { err = "coupling pattern differs from the tiled kernel's structure"; return false; }
+    return true;
+}
+
+}  // namespace
+
+bool tiled_supported(int system, int N, int precision) {
+    return system == 0 && precision == 1 && N >= 1 && N <= MAXN && encode_fn() != nullptr;
+}
+
+int tiled_create(const TiledGeometry& geo, TiledPlan** out) {
+    *out = nullptr;
+    TiledPlan* pl = new TiledPlan();
+    pl->geo = geo;
+    pl->N = geo.N;
+    *out = pl;
+    if (geo.N < 1 || geo.N > MAXN) { pl->err = "tiled kernel supports 1 <= N <= 63"; return -8; }
+    for (int g = 0; g < 4; ++g) {
+        if (!encode_grid_map(&pl->maps_in[g], geo.base[g], geo.pitch, geo.rows, geo.K[g], BX, BYI) ||
+            !encode_grid_map(&pl->maps_out[g], geo.base[g], geo.pitch, geo.rows, geo.K[g], TX, TY)) {
+            pl->err = "cuTensorMapEncodeTiled failed";
+            return -4;
+        }
+    }
+    int nxmax = 0, nymax = 0;
+    for (int g = 0; g < 4; ++g) { nxmax = std::max(nxmax, geo.nx[g]); nymax = std::max(nymax, geo.ny[g]); }
+    pl->tiles_x = (nxmax + TX - 1) / TX;
+    pl->tiles_y = (nymax + TY - 1) / TY;
+    if (cudaMalloc(&pl->err_dev, sizeof(int)) != cudaSuccess || cudaMemset(pl->err_dev, 0, sizeof(int)) != cudaSuccess) {
+        pl->err = "cudaMalloc error flag failed";
+        return -4;
+    }
+    return 0;
+}
+
+int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>& comp_class,
+                 const std::vector<int>& src_slot, const std::vector<void*>& src_dev, double dx, double dy) {
+    free_tables(pl);
+    pl->ready = false;
+    const int gin[2][2] = {{1, 2}, {0, 3}};
+    const int gout[2][2] = {{0, 3}, {1, 2}};
+    for (int P = 0; P < 2; ++P) {
+        PassTables& t = pl->tab[P];
+        if (!build_pass(pl, sys, comp_class, P, dx, dy, t, pl->err)) return -8;
+        std::vector<const float*> src(t.fin.size(), nullptr);
+        for (size_t e = 0; e < t.fin.size(); ++e) {
+            int s = src_slot[t.fin_comp[e]];
+            if (s >= 0) src[e] = (const float*)src_dev[s];
+        }
+        if (!upload(&pl->dev_items[P], t.items) || !upload(&pl->dev_coef[P], t.coef) || !upload(&pl->dev_fin[P], t.fin) ||
+            !upload(&pl->dev_src[P], src)) {
+            pl->err = "uploading the tiled tables failed";
+            return -4;
+        }
+        // shared memory: barriers, ring, coefficient rows, finalise events, partial sums
+        int off = 256 + NSLOTS * SLOT;
+        const int coef_off = off;
+        off += (int)(t.nin * 2 * sizeof(float4));
+        off = (off + 15) & ~15;
+        const int fin_off = off;
+        off += (int)(t.fin.size() * sizeof(int2));
+        off = (off + 15) & ~15;
+        const int part_off = off;
+        off += (nq_of(pl->N) + 1) * 2 * CONSUMERS * (int)sizeof(float);
+        pl->smem_bytes[P] = off;
+        int dev = 0, maxsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (off > maxsm) { pl->err = "tiled kernel needs more shared memory than the device offers"; return -8; }
+        const int need = std::max(pl->smem_bytes[0], pl->smem_bytes[1]);
+        if (cudaFuncSetAttribute(k_tiled_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, need) != cudaSuccess) {
+            pl->err = "cudaFuncSetAttribute failed";
+            return -4;
+        }
+        for (int w = 0; w < 2; ++w) {
+            Params& prm = pl->prm[P][w];
+            std::memset(&prm, 0, sizeof(prm));
+            for (int k = 0; k < 2; ++k) {
+                prm.maps[k] = pl->maps_in[gin[P][k]];
+                prm.maps[2 + k] = pl->maps_out[gout[P][k]];
+                const int g = gout[P][k];
+                prm.out[k].base = (float*)pl->geo.base[g];
+                prm.out[k].cstride = pl->geo.cstride[g];
+                prm.out[k].coef = (const float*)pl->coef[g];
+                prm.out[k].nx = pl->geo.nx[g];
+                prm.out[k].ny = pl->geo.ny[g];
+            }
+            prm.pitch = pl->geo.pitch;
+            prm.p[0] = pl->geo.p[0];
+            prm.p[1] = pl->geo.p[1];
+            prm.tiles_x = pl->tiles_x;
+            prm.N = pl->N;
+            prm.P = P;
+            prm.which = w;
+            prm.nclasses = pl->nclasses;
+            prm.nitems = (int)t.items.size();
+            prm.nin = t.nin;
+            prm.nfin = (int)t.fin.size();
+            prm.items = (const uint32_t*)pl->dev_items[P];
+            prm.coef = (const float4*)pl->dev_coef[P];
+            prm.fin = (const int2*)pl->dev_fin[P];
+            prm.src = (const float* const*)pl->dev_src[P];
+            prm.err = pl->err_dev;
+            prm.smem_coef_off = coef_off;
+            prm.smem_fin_off = fin_off;
+            prm.smem_part_off = part_off;
+        }
+    }
+    pl->ready = true;
+    return 0;
+}
+
+void tiled_set_coef(TiledPlan* pl, int g, void* coef, int nclasses) {
+    if (!pl) return;
+    pl->coef[g] = coef;
+    pl->nclasses = nclasses;
+    for (int P = 0; P < 2; ++P)
+        for (int w = 0; w < 2; ++w) {
+            Params& prm = pl->prm[P][w];
+            prm.nclasses = nclasses;
+            for (int k = 0; k < 2; ++k) {
+                const int gout = P == 1 ? (k == 0 ? 1 : 2) : (k == 0 ? 0 : 3);
+                if (gout == g) prm.out[k].coef = (const float*)coef;
+            }
+        }
+}
+
+int tiled_pass(TiledPlan* pl, bool odd, int which, void* stream) {
+    if (!pl->ready) { pl->err = "tiled tables not built"; return -7; }
+    const int P = odd ? 1 : 0;
+    k_tiled_pass<<<pl->tiles_x * pl->tiles_y, THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(pl->prm[P][which]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        pl->err = std::string("tiled pass launch: ") + cudaGetErrorString(e);
+        return -4;
+    }
+    return 0;
+}
+
+int tiled_poll(TiledPlan* pl, void* stream) {
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, pl->err_dev, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        pl->err = "reading the tiled kernel's error flag failed";
+        return -4;
+    }
+    if (flag) {
+        pl->err = "a bounded wait in the tiled kernel gave up";
+        cudaMemsetAsync(pl->err_dev, 0, sizeof(int), (cudaStream_t)stream);
+        return -6;
+    }
+    return 0;
+}
+
 const char* tiled_error(TiledPlan* p) { return p ? p->err.c_str() : "tiled kernel unavailable"; }
-void tiled_destroy(TiledPlan* p) { delete p; }
+
+void tiled_destroy(TiledPlan* p) {
+    if (!p) return;
+    free_tables(p);
+    if (p->err_dev) cudaFree(p->err_dev);
+    delete p;
+}
 
 }  // namespace starmap

@@ -24,6 +24,8 @@ int tiled_update(TiledPlan* plan, const SystemMatrices& sys, const std::vector<i
                  const std::vector<int>& src_slot, const std::vector<void*>& src_dev, double dx, double dy);
 void tiled_set_coef(TiledPlan* plan, int g, void* coef, int nclasses);
 int tiled_pass(TiledPlan* plan, bool odd, int which, void* stream);
+// Read and clear the bounded-wait failure flag (synchronises the stream).
+int tiled_poll(TiledPlan* plan, void* stream);
 const char* tiled_error(TiledPlan* plan);
 void tiled_destroy(TiledPlan* plan);
 

@@ -211,14 +211,20 @@ def random_p39(n: int = 1024, N: int = 39, nsteps: int = 200, seed: int = 2205,
 
 
 def piecewise_blocks(rng: SplitMix64, blocks: int, lo: float, hi: float,
-                     ax: Tuple[float, float, float, float]) -> Field:
-    """Field constant on a blocks x blocks partition, values iid U[lo, hi]."""
+                     ax: Tuple[float, float, float, float], shift: float = 0.37) -> Field:
+    """Field constant on a blocks x blocks periodic partition of the domain,
+    values iid U[lo, hi].  The block lattice is shifted by `shift` block
+    widths so that block edges do not fall on the staggered grid points of
+    the grid sizes used (a point exactly on an edge would take either value
+    depending on the last bit of its computed coordinate)."""
     vals = lo + (hi - lo) * rng.uniforms(blocks * blocks).reshape(blocks, blocks)
     x0, x1, y0, y1 = ax
+    wx = (x1 - x0) / blocks
+    wy = (y1 - y0) / blocks
 
     def f(t, x, y):
-        bx = _block_index(x, x0, (x1 - x0) / blocks, blocks)
-        by = _block_index(y, y0, (y1 - y0) / blocks, blocks)
+        bx = np.floor((np.asarray(x, dtype=np.float64) - x0) / wx - shift).astype(np.int64) % blocks
+        by = np.floor((np.asarray(y, dtype=np.float64) - y0) / wy - shift).astype(np.int64) % blocks
         return vals[by, bx]
     return f
 

@@ -67,15 +67,16 @@ def test_anisotropic_scattering_fp64():
 @pytest.mark.parametrize("bc", ["periodic", "extrapolation"])
 def test_slab_fp64(bc):
     N = 7
-    p = _random_problem(N, (50, 1), (bc, "periodic"), "fp64", 3, 12, system="slab")
+    p = _random_problem(N, (47, 1), (bc, "periodic"), "fp64", 3, 12, system="slab")
     s, got = gpu_run(p, kernel="gather")
     o, ref = oracle_run(p, dt=s.dt)
     assert rel_l2(got, ref) <= FP64_TOL
 
 
 def test_fp32_gather_checkerboard_reduced():
-    """P_13 checkerboard on 70x70 to t = 0.8, FP32 against the FP64 oracle."""
-    p = inputs.checkerboard_p13(n=70, t_final=0.8, precision="fp32")
+    """P_13 checkerboard on 72x72 (no grid point on a block edge) to t = 0.8,
+    FP32 against the FP64 oracle."""
+    p = inputs.checkerboard_p13(n=72, t_final=0.8, precision="fp32")
     s, got = gpu_run(p, t_final=0.8, kernel="gather")
     o, ref = oracle_run(p, dt=s.dt, t_final=0.8)
     assert rel_l2(got, ref) <= FP32_TOL

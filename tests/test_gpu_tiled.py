@@ -1,0 +1,105 @@
+"""GPU parity of the tiled (TMA-staged, order-streamed) FP32 kernel against
+the FP64 oracle (rel-L2 <= 1e-5) and against the gather kernel."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import gpu_run, oracle_run, rel_l2
+from oracle import pn_oracle as O
+from paper_1211_2205_gb300 import capi, inputs
+from test_gpu_parity import _random_problem
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 8, 13])
+@pytest.mark.parametrize("bc", [("periodic", "periodic"), ("extrapolation", "extrapolation"),
+                                ("periodic", "extrapolation"), ("extrapolation", "periodic")])
+def test_tiled_vs_oracle_ragged(N, bc):
+    """70 x 45 grid: three 32-wide tile columns (ragged), six 8-high tile
+    rows (ragged), every boundary combination."""
+    p = _random_problem(N, (70, 45), bc, "fp32", 300 + N, 7)
+    for sched in ("literal", "merged"):
+        s, got = gpu_run(p, schedule=sched, kernel="tiled")
+        assert s.kernel == "tiled"
+        o, ref = oracle_run(p, dt=s.dt)
+        assert rel_l2(got, ref) <= FP32_TOL, sched
+
+
+def test_tiled_anisotropic():
+    p = _random_problem(6, (41, 33), ("extrapolation", "periodic"), "fp32", 17, 6, aniso=True)
+    s, got = gpu_run(p, kernel="tiled")
+    o, ref = oracle_run(p, dt=s.dt)
+    assert rel_l2(got, ref) <= FP32_TOL
+
+
+def test_tiled_matches_gather():
+    p = _random_problem(9, (64, 40), ("periodic", "extrapolation"), "fp32", 23, 10)
+    a, ga = gpu_run(p, kernel="tiled", schedule="merged")
+    b, gb = gpu_run(p, kernel="gather", schedule="merged")
+    assert rel_l2(ga, gb) <= 2e-6
+
+
+def test_tiled_checkerboard_to_time():
+    """P_13 checkerboard, 72 x 72, interpolated output at t = 0.8."""
+    p = inputs.checkerboard_p13(n=72, t_final=0.8, precision="fp32")
+    s, got = gpu_run(p, t_final=0.8, kernel="tiled", schedule="merged")
+    o, ref = oracle_run(p, dt=s.dt, t_final=0.8)
+    assert rel_l2(got, ref) <= FP32_TOL
+
+
+def test_tiled_large_order():
+    """P_39 on a 40 x 36 periodic grid (all 820 moments, several tiles)."""
+    p = _random_problem(39, (40, 36), ("periodic", "periodic"), "fp32", 39, 3)
+    s, got = gpu_run(p, kernel="tiled", schedule="merged")
+    o, ref = oracle_run(p, dt=s.dt)
+    assert rel_l2(got, ref) <= FP32_TOL
+
+
+def test_tiled_mass_conservation_fp32():
+    p = _random_problem(7, (64, 64), ("periodic", "periodic"), "fp32", 55, 1)
+    p.sigma_a = lambda t, x, y: 0 * x
+    p.sources = []
+    s = capi.Stepper.from_problem(p, kernel="tiled", schedule="merged")
+    m0, _, _ = s.diagnostics()
+    s.step(50)
+    m1, _, bad = s.diagnostics()
+    assert bad == 0
+    assert abs(m1 - m0) <= 1e-5 * abs(m0)
+
+
+def _window_problem(p, i0, j0, cells, dt):
+    """Sub-problem on cells x cells cells starting at cell (i0, j0) of p,
+    same spacing and material, periodic wrap (valid in the window interior
+    while the wrap error has not travelled in)."""
+    x0, x1, y0, y1 = p.ax
+    hx = (x1 - x0) / p.n[0]
+    hy = (y1 - y0) / p.n[1]
+    ax = (x0 + i0 * hx, x0 + (i0 + cells) * hx, y0 + j0 * hy, y0 + (j0 + cells) * hy)
+    return inputs.Problem(**{**p.__dict__, "ax": ax, "n": (cells, cells), "bc": ("periodic", "periodic")})
+
+
+@pytest.mark.parametrize("nsteps", [4])
+def test_full_size_random_p39_sampled(nsteps):
+    """The bench configuration (P_39, 1024 x 1024, FP32, merged schedule,
+    tiled kernel): a 16 x 16 window of the result (all 820 moments) against
+    the oracle run on the window plus a halo of 1.5 cells per step."""
+    p = inputs.random_p39()
+    s = capi.Stepper.from_problem(p, kernel="tiled", schedule="merged")
+    s.step(nsteps)
+    halo = int(math.ceil(1.5 * nsteps)) + 3
+    w = 16
+    i0, j0 = 600 - halo, 300 - halo            # window cell origin (includes the Gaussian's tail)
+    sub = _window_problem(p, i0, j0, w + 2 * halo, s.dt)
+    o = O.solver_from_problem(sub, dt=s.dt)
+    o.run(nsteps)
+    got, ref = [], []
+    for j in range(s.ncomp):
+        # on every periodic grid, window point k is point i0 + k of the full grid
+        got.append(s.moments_window(j, i0 + halo, j0 + halo, w, w))
+        sub_u = o.U[j].T                       # (ny, nx) on the window grid
+        ref.append(sub_u[halo: halo + w, halo: halo + w])
+    assert rel_l2(got, ref) <= FP32_TOL
