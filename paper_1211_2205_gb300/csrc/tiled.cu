@@ -63,8 +63,8 @@ bool exists(int N, int L, int q, int imag) {
 }
 
 struct PassTables {
-    std::vector<uint32_t> items;
-    std::vector<float> coef;              // nin x 8
+    std::vector<int4> stages;             // slot components: in R, in I, out R, out I (-1 absent)
+    std::vector<float> coef;              // nin x 16 (each coefficient twice, for f32x2)
     std::vector<int2> fin;                // (local, class)
     std::vector<int> fin_comp;            // global component per finalise event
     int nin = 0;
@@ -81,7 +81,7 @@ struct TiledPlan {
     int* err_dev = nullptr;
     CUtensorMap maps_in[4], maps_out[4];
     PassTables tab[2];
-    void* dev_items[2] = {nullptr, nullptr};
+    void* dev_stages[2] = {nullptr, nullptr};
     void* dev_coef[2] = {nullptr, nullptr};
     void* dev_fin[2] = {nullptr, nullptr};
     void* dev_src[2] = {nullptr, nullptr};
@@ -95,11 +95,11 @@ namespace {
 
 void free_tables(TiledPlan* pl) {
     for (int P = 0; P < 2; ++P) {
-        if (pl->dev_items[P]) cudaFree(pl->dev_items[P]);
+        if (pl->dev_stages[P]) cudaFree(pl->dev_stages[P]);
         if (pl->dev_coef[P]) cudaFree(pl->dev_coef[P]);
         if (pl->dev_fin[P]) cudaFree(pl->dev_fin[P]);
         if (pl->dev_src[P]) cudaFree(pl->dev_src[P]);
-        pl->dev_items[P] = pl->dev_coef[P] = pl->dev_fin[P] = pl->dev_src[P] = nullptr;
+        pl->dev_stages[P] = pl->dev_coef[P] = pl->dev_fin[P] = pl->dev_src[P] = nullptr;
     }
 }
 
@@ -133,32 +133,38 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
         if (v != 0.0) ++covered;
         return (float)(-v / h);
     };
+    int4 cur = make_int4(-1, -1, -1, -1);
     auto emit_input = [&](int lp, int q, int imag) -> bool {
         int local;
         if (!local_of(lp, q, imag, gin[imag], local)) return false;
-        t.items.push_back(((uint32_t)imag << ITEM_MAP_SHIFT) | (uint32_t)local);
+        if (imag) cur.y = local; else cur.x = local;
         const int k = comp_index(lp, lp - 2 * q, imag);
         // targets Pm (lp-1, q-1), P0 (lp-1, q), N0 (lp+1, q), Np (lp+1, q+1)
         const int TL[4] = {lp - 1, lp - 1, lp + 1, lp + 1};
         const int TQ[4] = {q - 1, q, q, q + 1};
-        float row[8];
+        float row[16];
         for (int s = 0; s < 4; ++s) {
-            row[s] = coef_of(sys.Mx, TL[s], TQ[s], imag, k, dx);          // same kind through Mx
-            row[4 + s] = coef_of(sys.My, TL[s], TQ[s], 1 - imag, k, dy);  // other kind through My
+            row[2 * s] = row[2 * s + 1] = coef_of(sys.Mx, TL[s], TQ[s], imag, k, dx);          // same kind, Mx
+            row[8 + 2 * s] = row[8 + 2 * s + 1] = coef_of(sys.My, TL[s], TQ[s], 1 - imag, k, dy);  // other kind, My
         }
-        t.coef.insert(t.coef.end(), row, row + 8);
+        t.coef.insert(t.coef.end(), row, row + 16);
         ++t.nin;
         return true;
     };
     auto emit_fin = [&](int L, int q, int imag) -> bool {
         int local;
         if (!local_of(L, q, imag, gout[imag], local)) return false;
-        t.items.push_back(((uint32_t)(2 + imag) << ITEM_MAP_SHIFT) | (uint32_t)local);
+        if (imag) cur.w = local; else cur.z = local;
         const int j = comp_index(L, L - 2 * q, imag);
         t.fin.push_back(make_int2(local, comp_class[j]));
         t.fin_comp.push_back(j);
         return true;
     };
+    auto close_stage = [&]() {
+        t.stages.push_back(cur);
+        cur = make_int4(-1, -1, -1, -1);
+    };
+    // the stages of the consumer loop (see k_tiled_pass)
     const int first = 1 - P;
     int last_in = first;
     bool ok = true;
@@ -172,10 +178,12 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
                 ok = ok && emit_fin(lp - 1, q - 1, 0);
                 if (has_imag(lp - 1, q - 1)) ok = ok && emit_fin(lp - 1, q - 1, 1);
             }
+            close_stage();
         }
         if (ok && nq - 1 < nqp) {
             ok = ok && emit_fin(lp - 1, nq - 1, 0);
             if (has_imag(lp - 1, nq - 1)) ok = ok && emit_fin(lp - 1, nq - 1, 1);
+            close_stage();
         }
     }
     const int L = last_in + 1;
@@ -183,6 +191,7 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
         for (int q = 0; q < nq_of(L) && ok; ++q) {
             ok = ok && emit_fin(L, q, 0);
             if (has_imag(L, q)) ok = ok && emit_fin(L, q, 1);
+            close_stage();
         }
     if (!ok) { err = "moment placement differs from the tiled kernel's"; return false; }
     // every component of the output parity is finalised exactly once
@@ -241,26 +250,29 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
     for (int P = 0; P < 2; ++P) {
         PassTables& t = pl->tab[P];
         if (!build_pass(pl, sys, comp_class, P, dx, dy, t, pl->err)) return -8;
-        std::vector<const float*> src(t.fin.size(), nullptr);
+        // finalise events: element offset of the component (| class << 48), source array
+        std::vector<longlong2> fin(t.fin.size());
         for (size_t e = 0; e < t.fin.size(); ++e) {
-            int s = src_slot[t.fin_comp[e]];
-            if (s >= 0) src[e] = (const float*)src_dev[s];
+            const int g = gout[P][sys.moms[t.fin_comp[e]].imag ? 1 : 0];
+            const long long off = (long long)t.fin[e].x * pl->geo.cstride[g];
+            fin[e].x = off | ((long long)t.fin[e].y << 48);
+            int sl = src_slot[t.fin_comp[e]];
+            fin[e].y = sl >= 0 ? (long long)(uintptr_t)src_dev[sl] : 0;
         }
-        if (!upload(&pl->dev_items[P], t.items) || !upload(&pl->dev_coef[P], t.coef) || !upload(&pl->dev_fin[P], t.fin) ||
-            !upload(&pl->dev_src[P], src)) {
+        if (!upload(&pl->dev_stages[P], t.stages) || !upload(&pl->dev_coef[P], t.coef) || !upload(&pl->dev_fin[P], fin)) {
             pl->err = "uploading the tiled tables failed";
             return -4;
         }
         // shared memory: barriers, ring, coefficient rows, finalise events, partial sums
-        int off = 256 + NSLOTS * SLOT;
+        int off = RING_OFF + NSTAGES * STAGE_BYTES;
         const int coef_off = off;
-        off += (int)(t.nin * 2 * sizeof(float4));
+        off += (int)(t.nin * 4 * sizeof(float4));
         off = (off + 15) & ~15;
         const int fin_off = off;
-        off += (int)(t.fin.size() * sizeof(int2));
+        off += (int)(t.fin.size() * sizeof(longlong2));
         off = (off + 15) & ~15;
         const int part_off = off;
-        off += (nq_of(pl->N) + 1) * 2 * CONSUMERS * (int)sizeof(float);
+        off += (nq_of(pl->N) + 1) * 2 * CONSUMERS * 8;
         pl->smem_bytes[P] = off;
         int dev = 0, maxsm = 0;
         cudaGetDevice(&dev);
@@ -292,13 +304,12 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             prm.P = P;
             prm.which = w;
             prm.nclasses = pl->nclasses;
-            prm.nitems = (int)t.items.size();
+            prm.nstages = (int)t.stages.size();
             prm.nin = t.nin;
             prm.nfin = (int)t.fin.size();
-            prm.items = (const uint32_t*)pl->dev_items[P];
+            prm.stages = (const int4*)pl->dev_stages[P];
             prm.coef = (const float4*)pl->dev_coef[P];
-            prm.fin = (const int2*)pl->dev_fin[P];
-            prm.src = (const float* const*)pl->dev_src[P];
+            prm.fin = (const longlong2*)pl->dev_fin[P];
             prm.err = pl->err_dev;
             prm.smem_coef_off = coef_off;
             prm.smem_fin_off = fin_off;

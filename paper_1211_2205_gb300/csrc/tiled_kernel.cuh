@@ -1,10 +1,11 @@
 // Tiled half-step pass for the 2D real P_N system in FP32 (sm_103a).
 //
 // One CTA owns a TX x TY tile of point indices, shared by the four staggered
-// grids (section 4.1).  A pass updates the components of one parity (odd l:
-// grids G21 (R) and G12 (I); even l: G11 (R) and G22 (I)) from the half-grid
-// differences (eq. central_differences) of the other parity, weighted by
-// -Mx/dx and -My/dy, followed by the exact sub-step u <- a u + b (W + q)
+// grids (section 4.1); each consumer thread owns PX points of one row.  A
+// pass updates the components of one parity (odd l: grids G21 (R) and G12
+// (I); even l: G11 (R) and G22 (I)) from the half-grid differences
+// (eq. central_differences) of the other parity, weighted by -Mx/dx and
+// -My/dy, followed by the exact sub-step u <- a u + b (W + q)
 // (eq. sub_step_solution).
 //
 // Streaming by moment order.  Input components of order l' are visited in
@@ -23,14 +24,16 @@
 // Every input value is read from HBM once, every output read and written
 // once; the differences of an input are formed once per point.
 //
-// Data movement: one producer warp walks a host-built item list and issues
-// one TMA box (cp.async.bulk.tensor.3d) per item into a ring of shared-memory
-// slots guarded by mbarriers (full: transaction bytes, empty: one arrival per
-// consumer warp).  Input boxes are BX x (TY+1) (one-point halo, x start
-// aligned to 16 bytes); output boxes TX x TY.  Boundary conditions live in
-// ghost cells, which the finalising thread writes with each boundary value.
-// Every wait is bounded: on expiry the kernel raises an error flag, waits
-// (bounded) for its copies in flight, and returns.
+// Data movement: one producer warp walks a host-built stage list and issues
+// the TMA boxes (cp.async.bulk.tensor.3d) of each stage into a ring of
+// shared-memory stages guarded by mbarriers (full: transaction bytes, empty:
+// one arrival per consumer warp).  A stage is one step of the consumer loop:
+// slots for the R and I input of (l', q') and the R and I output finalised
+// there.  Input boxes are BX x (TY+1) (one-point halo, x start aligned to 16
+// bytes); output boxes TX x TY.  Boundary conditions live in ghost cells,
+// which the finalising thread writes with each boundary value.  Every wait
+// is bounded: on expiry the kernel raises an error flag, waits (bounded) for
+// its copies in flight, and returns.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -40,26 +43,24 @@
 namespace starmap {
 namespace tiled {
 
-constexpr int TX = 32;                  // tile width (one warp per row)
+constexpr int PX = 2;                   // points per consumer thread (along x)
+constexpr int TX = 32 * PX;             // tile width
 constexpr int TY = 8;                   // tile height (one consumer warp per row)
 constexpr int VEC = 4;                  // 16 bytes of FP32: TMA x alignment
 constexpr int BX = TX + VEC;            // input box width (halo + alignment)
 constexpr int BYI = TY + 1;             // input box height (halo)
-constexpr int IN_BYTES = BX * BYI * 4;  // 1296
-constexpr int OUT_BYTES = TX * TY * 4;  // 1024
-constexpr int SLOT = 1408;              // slot stride in bytes, multiple of 128
-constexpr int GROUP = 4;                // items per mbarrier stage
-constexpr int NSTAGES = 8;              // stages in the ring
-constexpr int NSLOTS = GROUP * NSTAGES;
+constexpr int IN_BYTES = BX * BYI * 4;
+constexpr int OUT_BYTES = TX * TY * 4;
+constexpr int SLOT = ((IN_BYTES + 127) / 128) * 128;   // slot stride in bytes
+constexpr int SLOTS_PER_STAGE = 4;      // input R, input I, output R, output I
+constexpr int STAGE_BYTES = SLOT * SLOTS_PER_STAGE;
+constexpr int NSTAGES = 6;              // stages in the ring
 constexpr int CONSUMER_WARPS = TY;
 constexpr int CONSUMERS = CONSUMER_WARPS * 32;
 constexpr int THREADS = CONSUMERS + 32;
 constexpr int MAXN = 63;
+constexpr int RING_OFF = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded waits: 2 s
-
-// item codes: bits 30..31 = map (0 input R, 1 input I, 2 output R, 3 output I),
-// bits 0..29 = component index inside its grid
-constexpr uint32_t ITEM_MAP_SHIFT = 30;
 
 struct OutGrid {
     float* base;        // point (0,0) of component 0
@@ -77,11 +78,10 @@ struct Params {
     int N, P;                   // moment order, pass parity (1 odd, 0 even)
     int which;                  // 0 half-step coefficients, 1 full-step
     int nclasses;               // 2 = isotropic (class 0: l = 0, 1: l >= 1), else class = l
-    int nitems, nin, nfin;
-    const uint32_t* items;      // TMA item stream
-    const float4* coef;         // per input: (cx Pm, P0, N0, Np), (cy Pm, P0, N0, Np)
-    const int2* fin;            // per finalise event: (component index in grid, class)
-    const float* const* src;    // per finalise event: source array or null
+    int nstages, nin, nfin;
+    const int4* stages;         // per stage: component (in its grid) of slot 0..3, -1 if absent
+    const float4* coef;         // per input: cx Pm, P0, N0, Np, cy Pm, P0, N0, Np, each twice
+    const longlong2* fin;       // per finalise event: (element offset | class << 48, source array or 0)
     int* err;                   // bounded-wait failure flag
     int smem_coef_off, smem_fin_off, smem_part_off;   // byte offsets in dynamic smem
 };
@@ -151,23 +151,74 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, vol
 
 // Offsets of the right / upper neighbour of the staggered outputs read from
 // the input grid of kind k (0 = R, 1 = I) in pass P.
-__device__ __forceinline__ void input_shift(int P, int k, const int p[2], int& sx, int& sy) {
+__device__ __forceinline__ void input_shift(int P, int k, int px, int py, int& sx, int& sy) {
     // input grids: odd pass (P=1) R -> G11, I -> G22; even pass R -> G21, I -> G12
     const int g = P == 1 ? (k == 0 ? 0 : 3) : (k == 0 ? 1 : 2);
     const bool xnode = g & 1, ynode = g & 2;
-    sx = xnode ? 1 - p[0] : p[0];
-    sy = ynode ? 1 - p[1] : p[1];
+    sx = xnode ? 1 - px : px;
+    sy = ynode ? 1 - py : py;
 }
 
-__global__ void __launch_bounds__(THREADS, 2) k_tiled_pass(const __grid_constant__ Params prm) {
+// Packed pair of FP32 values (point A in the low half, point B in the high
+// half) and the f32x2 arithmetic of sm_100-family parts.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_make(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_split(f2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 lds2(const float* p) { return *reinterpret_cast<const f2*>(p); }
+
+// x-differences of points A (column c) and B (column c + 1) of one box row:
+// right operands at columns c, c + 1, left operands at c - 1, c.  The pair
+// load starts at the even column of the two.
+__device__ __forceinline__ f2 diff_x(const float* row, int c, bool c_even) {
+    if (c_even) {
+        const f2 P = lds2(row + c);                 // v[c], v[c+1]
+        const float Q = row[c - 1];
+        float lo, hi;
+        f2_split(P, lo, hi);
+        return f2_sub(P, f2_make(Q, lo));
+    }
+    const f2 P = lds2(row + c - 1);                 // v[c-1], v[c]
+    const float Q = row[c + 1];
+    float lo, hi;
+    f2_split(P, lo, hi);
+    return f2_sub(f2_make(hi, Q), P);
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant__ Params prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + NSTAGES;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NSTAGES);
-    float* ring = reinterpret_cast<float*>(smem + 256);
-    float4* s_coef = reinterpret_cast<float4*>(smem + prm.smem_coef_off);
-    int2* s_fin = reinterpret_cast<int2*>(smem + prm.smem_fin_off);
-    float* s_part = reinterpret_cast<float*>(smem + prm.smem_part_off);
+    unsigned char* ring = smem + RING_OFF;
+    const float4* s_coef = reinterpret_cast<const float4*>(smem + prm.smem_coef_off);
+    const longlong2* s_fin = reinterpret_cast<const longlong2*>(smem + prm.smem_fin_off);
+    f2* s_part = reinterpret_cast<f2*>(smem + prm.smem_part_off);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -184,49 +235,47 @@ __global__ void __launch_bounds__(THREADS, 2) k_tiled_pass(const __grid_constant
         fence_mbar_init();
     }
     // stage the coefficient and finalise tables in shared memory
-    for (int i = tid; i < 2 * prm.nin; i += THREADS) s_coef[i] = __ldg(prm.coef + i);
-    for (int i = tid; i < prm.nfin; i += THREADS) s_fin[i] = __ldg(prm.fin + i);
+    {
+        float4* c = reinterpret_cast<float4*>(smem + prm.smem_coef_off);
+        for (int i = tid; i < 4 * prm.nin; i += THREADS) c[i] = __ldg(prm.coef + i);
+        longlong2* f = reinterpret_cast<longlong2*>(smem + prm.smem_fin_off);
+        for (int i = tid; i < prm.nfin; i += THREADS) f[i] = __ldg(prm.fin + i);
+    }
     __syncthreads();
 
-    int sx[2], sy[2];
-    input_shift(prm.P, 0, prm.p, sx[0], sy[0]);
-    input_shift(prm.P, 1, prm.p, sx[1], sy[1]);
+    int sxR, syR, sxI, syI;
+    input_shift(prm.P, 0, prm.p[0], prm.p[1], sxR, syR);
+    input_shift(prm.P, 1, prm.p[0], prm.p[1], sxI, syI);
 
     // --------------------------------------------------------- producer
     if (warp == CONSUMER_WARPS) {
         if (lane == 0) {
-            int issued_stages = 0;
+            // box origins in tensor coordinates (x' = x + VEC, row = y + 1)
+            const int bxR = x0 + (sxR == 0 ? 0 : VEC), byR = y0 + (syR == 0 ? -1 : 0) + 1;
+            const int bxI = x0 + (sxI == 0 ? 0 : VEC), byI = y0 + (syI == 0 ? -1 : 0) + 1;
+            int issued = 0;
             bool ok = true;
-            for (int s = 0; s * GROUP < prm.nitems; ++s) {
+            for (int s = 0; s < prm.nstages; ++s) {
                 const int r = s % NSTAGES;
                 if (s >= NSTAGES && !wait_bounded(&empty[r], ((s / NSTAGES) - 1) & 1, abort_flag, prm.err)) {
                     ok = false;
                     break;
                 }
-                const int i0 = s * GROUP, i1 = min(prm.nitems, i0 + GROUP);
-                uint32_t bytes = 0;
-                for (int i = i0; i < i1; ++i) bytes += (__ldg(prm.items + i) >> ITEM_MAP_SHIFT) < 2 ? IN_BYTES : OUT_BYTES;
+                const int4 st = __ldg(prm.stages + s);
+                const uint32_t bytes = (st.x >= 0 ? IN_BYTES : 0) + (st.y >= 0 ? IN_BYTES : 0) +
+                                       (st.z >= 0 ? OUT_BYTES : 0) + (st.w >= 0 ? OUT_BYTES : 0);
+                unsigned char* base = ring + r * STAGE_BYTES;
                 fence_proxy_async();
                 mbar_expect_tx(&full[r], bytes);
-                for (int i = i0; i < i1; ++i) {
-                    const uint32_t code = __ldg(prm.items + i);
-                    const int map = code >> ITEM_MAP_SHIFT;
-                    const int comp = code & ((1u << ITEM_MAP_SHIFT) - 1);
-                    float* dst = ring + (size_t)(i % NSLOTS) * (SLOT / 4);
-                    if (map < 2) {
-                        // x' = x + VEC; start VEC early when the left neighbour is needed
-                        const int bx = x0 + (sx[map] == 0 ? 0 : VEC);
-                        const int by = y0 + (sy[map] == 0 ? -1 : 0) + 1;
-                        tma_load_3d(dst, &prm.maps[map], bx, by, comp, &full[r]);
-                    } else {
-                        tma_load_3d(dst, &prm.maps[map], x0 + VEC, y0 + 1, comp, &full[r]);
-                    }
-                }
-                ++issued_stages;
+                if (st.x >= 0) tma_load_3d(base, &prm.maps[0], bxR, byR, st.x, &full[r]);
+                if (st.y >= 0) tma_load_3d(base + SLOT, &prm.maps[1], bxI, byI, st.y, &full[r]);
+                if (st.z >= 0) tma_load_3d(base + 2 * SLOT, &prm.maps[2], x0 + VEC, y0 + 1, st.z, &full[r]);
+                if (st.w >= 0) tma_load_3d(base + 3 * SLOT, &prm.maps[3], x0 + VEC, y0 + 1, st.w, &full[r]);
+                ++issued;
             }
             if (!ok) {
                 // aborted: wait (bounded) for the copies still in flight
-                for (int s = issued_stages - 1; s >= 0 && s >= issued_stages - NSTAGES; --s) {
+                for (int s = issued - 1; s >= 0 && s >= issued - NSTAGES; --s) {
                     const unsigned long long t0 = global_ns();
                     while (!mbar_try_wait(&full[s % NSTAGES], (s / NSTAGES) & 1))
                         if (global_ns() - t0 > WAIT_NS) break;
@@ -237,139 +286,188 @@ __global__ void __launch_bounds__(THREADS, 2) k_tiled_pass(const __grid_constant
     }
 
     // --------------------------------------------------------- consumers
-    const int gx = x0 + lane, gy = y0 + warp;
-    // smem offsets of the difference operands inside an input box of kind k
-    int dxr[2], dyu[2];
-    for (int k = 0; k < 2; ++k) {
-        const int bxs = sx[k] == 0 ? -VEC : 0;       // box x start relative to x0
-        const int oy = sy[k] == 0 ? -1 : 0;          // box y start relative to y0
-        dxr[k] = (warp - oy) * BX + (lane + sx[k] - bxs);
-        dyu[k] = (warp + sy[k] - oy) * BX + (lane - bxs);
+    // this thread owns points A = (x0 + 2 lane, y) and B = A + (1, 0)
+    const int gy = y0 + warp;
+    const int gxA = x0 + 2 * lane;
+    // float offsets, inside a stage, of the difference operands
+    int rxR, cxR, uR, rxI, cxI, uI;          // x: row start, column of A's right operand; y: up pair
+    bool evR, evI;
+    {
+        const int bxsR = sxR == 0 ? -VEC : 0, oyR = syR == 0 ? -1 : 0;
+        const int bxsI = sxI == 0 ? -VEC : 0, oyI = syI == 0 ? -1 : 0;
+        rxR = (warp - oyR) * BX;
+        cxR = 2 * lane + sxR - bxsR;
+        evR = (cxR & 1) == 0;
+        uR = (warp + syR - oyR) * BX + (2 * lane - bxsR);
+        rxI = SLOT / 4 + (warp - oyI) * BX;
+        cxI = 2 * lane + sxI - bxsI;
+        evI = (cxI & 1) == 0;
+        uI = SLOT / 4 + (warp + syI - oyI) * BX + (2 * lane - bxsI);
     }
-    // output grids (kind 0 = R, 1 = I)
-    bool inr[2];
-    long row_off[2], cidx[2], plane[2];
-    int gxa[2], gxb[2], gya[2], gyb[2];
-    float ca[2][2], cb[2][2];
+    // output kinds k = 0 (R), 1 (I)
+    float* pptr[2];                           // point A in component 0 of the output grid
+    bool inA[2], inB[2], both[2], bndAny[2];
+    long cidxA[2];
+    f2 ca2[2][2], cb2[2][2];                  // decay pairs by class (isotropic)
+#pragma unroll
     for (int k = 0; k < 2; ++k) {
         const OutGrid& G = prm.out[k];
         const int g = prm.P == 1 ? (k == 0 ? 1 : 2) : (k == 0 ? 0 : 3);
         const bool xnode = g & 1, ynode = g & 2;
-        inr[k] = gx < G.nx && gy < G.ny;
-        row_off[k] = (long)(gy + 1) * prm.pitch + gx;
-        plane[k] = (long)G.nx * G.ny;
-        cidx[k] = (long)gy * G.nx + gx;
+        const long plane = (long)G.nx * G.ny;
+        inA[k] = gxA < G.nx && gy < G.ny;
+        inB[k] = gxA + 1 < G.nx && gy < G.ny;
+        both[k] = inA[k] && inB[k];
+        pptr[k] = G.base + (long)(gy + 1) * prm.pitch + gxA;
+        cidxA[k] = (long)gy * G.nx + gxA;
+        bool bnd = false;
+        for (int pt = 0; pt < 2; ++pt) {
+            const int gx = gxA + pt;
+            if (prm.p[0]) bnd |= (gx == G.nx - 1) || (gx == 0);
+            else if (!xnode) bnd |= (gx == 0) || (gx == G.nx - 1);
+            if (prm.p[1]) bnd |= (gy == G.ny - 1) || (gy == 0);
+            else if (!ynode) bnd |= (gy == 0) || (gy == G.ny - 1);
+        }
+        bndAny[k] = bnd && (inA[k] || inB[k]);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
+            if (prm.nclasses == 2 && G.coef != nullptr) {
+                const float* cf = G.coef + (long)c * 4 * plane + cidxA[k];
+                if (inA[k]) { a[0] = __ldg(cf + 2 * prm.which * plane); b[0] = __ldg(cf + (2 * prm.which + 1) * plane); }
+                if (inB[k]) { a[1] = __ldg(cf + 2 * prm.which * plane + 1); b[1] = __ldg(cf + (2 * prm.which + 1) * plane + 1); }
+            }
+            ca2[k][c] = f2_make(a[0], a[1]);
+            cb2[k][c] = f2_make(b[0], b[1]);
+        }
+    }
+
+    int s = 0, ii = 0, e = 0;
+    bool alive = true;
+    auto stage_ptr = [&]() -> const float* {
+        const int r = s % NSTAGES;
+        if (alive) alive = wait_bounded(&full[r], (s / NSTAGES) & 1, abort_flag, prm.err);
+        return reinterpret_cast<const float*>(ring + r * STAGE_BYTES);
+    };
+    auto stage_done = [&]() {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s % NSTAGES]);
+        ++s;
+    };
+    auto part = [&](int q, int k) -> f2& { return s_part[(q * 2 + k) * CONSUMERS + tid]; };
+    // write one point (and its boundary copies) of output kind k
+    auto store_point = [&](int k, float* dst, int gx, float v) {
+        const OutGrid& G = prm.out[k];
+        const int g = prm.P == 1 ? (k == 0 ? 1 : 2) : (k == 0 ? 0 : 3);
+        const bool xnode = g & 1, ynode = g & 2;
+        *dst = v;
         int xa = -2, xb = -2, ya = -2, yb = -2;
         if (prm.p[0]) { if (gx == G.nx - 1) xa = -1; if (gx == 0) xb = G.nx; }
         else if (!xnode) { if (gx == 0) xa = -1; if (gx == G.nx - 1) xb = G.nx; }
         if (prm.p[1]) { if (gy == G.ny - 1) ya = -1; if (gy == 0) yb = G.ny; }
         else if (!ynode) { if (gy == 0) ya = -1; if (gy == G.ny - 1) yb = G.ny; }
-        gxa[k] = xa; gxb[k] = xb; gya[k] = ya; gyb[k] = yb;
-        for (int c = 0; c < 2; ++c) {
-            ca[k][c] = 0.f;
-            cb[k][c] = 0.f;
-            if (inr[k] && prm.nclasses == 2 && G.coef != nullptr) {
-                const float* cf = G.coef + (long)c * 4 * plane[k] + cidx[k];
-                ca[k][c] = __ldg(cf + 2 * prm.which * plane[k]);
-                cb[k][c] = __ldg(cf + (2 * prm.which + 1) * plane[k]);
-            }
-        }
-    }
-
-    int it = 0, ii = 0, e = 0;
-    bool alive = true;
-    auto acquire = [&](int i) -> const float* {
-        if (i % GROUP == 0 && alive)
-            alive = wait_bounded(&full[(i / GROUP) % NSTAGES], ((i / GROUP) / NSTAGES) & 1, abort_flag, prm.err);
-        return ring + (size_t)(i % NSLOTS) * (SLOT / 4);
+        float* row = dst - gx;
+        if (xa != -2) row[xa] = v;
+        if (xb != -2) row[xb] = v;
+        float* col = dst - (long)(gy + 1) * prm.pitch;
+        if (ya != -2) col[(long)(ya + 1) * prm.pitch] = v;
+        if (yb != -2) col[(long)(yb + 1) * prm.pitch] = v;
     };
-    auto release = [&](int i) {
-        if (i % GROUP == GROUP - 1 || i == prm.nitems - 1) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[(i / GROUP) % NSTAGES]);
-        }
-    };
-    auto part = [&](int q, int k) -> float& { return s_part[(q * 2 + k) * CONSUMERS + tid]; };
-    auto finalize = [&](int k, int L, float W) {
-        const float* t = acquire(it);
-        const int2 f = s_fin[e];
-        float aa, bb;
-        if (prm.nclasses == 2) {
-            aa = ca[k][L == 0 ? 0 : 1];
-            bb = cb[k][L == 0 ? 0 : 1];
-        } else {
-            const float* cf = prm.out[k].coef + (long)f.y * 4 * plane[k] + cidx[k];
-            aa = inr[k] ? __ldg(cf + 2 * prm.which * plane[k]) : 0.f;
-            bb = inr[k] ? __ldg(cf + (2 * prm.which + 1) * plane[k]) : 0.f;
-        }
-        const float u = t[warp * TX + lane];
-        const float* qs = prm.src[e];
-        if (qs != nullptr && inr[k]) W += __ldg(qs + cidx[k]);
-        const float v = fmaf(aa, u, bb * W);
-        if (inr[k] && alive) {
-            float* comp = prm.out[k].base + (long)f.x * prm.out[k].cstride;
-            comp[row_off[k]] = v;
-            const long rowb = row_off[k] - gx;
-            if (gxa[k] != -2) comp[rowb + gxa[k]] = v;
-            if (gxb[k] != -2) comp[rowb + gxb[k]] = v;
-            const long colb = row_off[k] - (long)(gy + 1) * prm.pitch;
-            if (gya[k] != -2) comp[colb + (long)(gya[k] + 1) * prm.pitch] = v;
-            if (gyb[k] != -2) comp[colb + (long)(gyb[k] + 1) * prm.pitch] = v;
-        }
-        release(it);
-        ++it;
+    // finalise output kind k (slot 2 + k of stage t) of order L with sums W
+    auto finalize = [&](const float* t, int k, int L, f2 W) {
+        const longlong2 f = s_fin[e];                 // (element offset of the component, source pointer)
         ++e;
+        const f2 u = lds2(t + (2 + k) * (SLOT / 4) + warp * TX + 2 * lane);
+        f2 aa, bb;
+        if (prm.nclasses == 2) {
+            aa = L == 0 ? ca2[k][0] : ca2[k][1];
+            bb = L == 0 ? cb2[k][0] : cb2[k][1];
+        } else {
+            const long plane = (long)prm.out[k].nx * prm.out[k].ny;
+            const long cls = (long)(f.x >> 48);
+            const float* cf = prm.out[k].coef + cls * 4 * plane + cidxA[k];
+            float a0 = inA[k] ? __ldg(cf + 2 * prm.which * plane) : 0.f;
+            float b0 = inA[k] ? __ldg(cf + (2 * prm.which + 1) * plane) : 0.f;
+            float a1 = inB[k] ? __ldg(cf + 2 * prm.which * plane + 1) : 0.f;
+            float b1 = inB[k] ? __ldg(cf + (2 * prm.which + 1) * plane + 1) : 0.f;
+            aa = f2_make(a0, a1);
+            bb = f2_make(b0, b1);
+        }
+        const float* qs = reinterpret_cast<const float*>(f.y);
+        if (qs != nullptr) {
+            const float q0 = inA[k] ? __ldg(qs + cidxA[k]) : 0.f;
+            const float q1 = inB[k] ? __ldg(qs + cidxA[k] + 1) : 0.f;
+            W = f2_add(W, f2_make(q0, q1));
+        }
+        const f2 v = f2_fma(aa, u, f2_mul(bb, W));
+        if (!alive) return;
+        float* dst = pptr[k] + (f.x & 0xFFFFFFFFFFFFll);
+        if (both[k] && !bndAny[k]) {
+            *reinterpret_cast<f2*>(dst) = v;
+        } else {
+            float v0, v1;
+            f2_split(v, v0, v1);
+            if (inA[k]) store_point(k, dst, gxA, v0);
+            if (inB[k]) store_point(k, dst + 1, gxA + 1, v1);
+        }
     };
 
     const int N = prm.N;
     const int first = 1 - prm.P;              // first input order: even l' for the odd pass
     int last_in = first;
+    const f2 zero = 0ull;
     for (int lp = first; lp <= N && alive; lp += 2) {
         last_in = lp;
         const int nq = nq_of(lp);
         const int nqp = nq_of(lp - 1);                    // previous-order targets
         const int nqn = lp + 1 <= N ? nq_of(lp + 1) : 0;  // next-order targets
-        float PcR = 0.f, PcI = 0.f, NcR = 0.f, NcI = 0.f;
+        f2 PcR = zero, PcI = zero, NcR = zero, NcI = zero;
         for (int q = 0; q < nq && alive; ++q) {
-            float PnR = 0.f, PnI = 0.f, NnR = 0.f, NnI = 0.f;
+            const bool inI = has_imag(lp, q);
             // partial sums of a previous-order target exist once order
             // lp - 2 has streamed by (not for the first input order)
-            if (q < nqp && lp > first) {
-                PnR = part(q, 0);
-                if (has_imag(lp - 1, q)) PnI = part(q, 1);
-            }
-            // input R (k = 0) then I (k = 1, only for m' >= 1):
-            // d_x feeds targets of the same kind, d_y those of the other kind
+            const bool ldP = q < nqp && lp > first;
+            f2 PnR = ldP ? part(q, 0) : zero;
+            f2 PnI = (ldP && has_imag(lp - 1, q)) ? part(q, 1) : zero;
+            f2 NnR = zero, NnI = zero;
+            const float* t = stage_ptr();
             {
-                const float* t = acquire(it);
-                const float dx = t[dxr[0]] - t[dxr[0] - 1];
-                const float dy = t[dyu[0]] - t[dyu[0] - BX];
-                const float4 c0 = s_coef[2 * ii], c1 = s_coef[2 * ii + 1];
-                release(it);
-                ++it;
+                // input R: d_x feeds R targets, d_y feeds I targets
+                const float4* c = s_coef + 4 * ii;
                 ++ii;
-                PcR = fmaf(c0.x, dx, PcR); PnR = fmaf(c0.y, dx, PnR);
-                NcR = fmaf(c0.z, dx, NcR); NnR = fmaf(c0.w, dx, NnR);
-                PcI = fmaf(c1.x, dy, PcI); PnI = fmaf(c1.y, dy, PnI);
-                NcI = fmaf(c1.z, dy, NcI); NnI = fmaf(c1.w, dy, NnI);
+                const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
+                const f2 dx = diff_x(t + rxR, cxR, evR);
+                const f2 dy = f2_sub(lds2(t + uR), lds2(t + uR - BX));
+                PcR = f2_fma(f2_make(c0.x, c0.y), dx, PcR);
+                PnR = f2_fma(f2_make(c0.z, c0.w), dx, PnR);
+                NcR = f2_fma(f2_make(c1.x, c1.y), dx, NcR);
+                NnR = f2_fma(f2_make(c1.z, c1.w), dx, NnR);
+                PcI = f2_fma(f2_make(c2.x, c2.y), dy, PcI);
+                PnI = f2_fma(f2_make(c2.z, c2.w), dy, PnI);
+                NcI = f2_fma(f2_make(c3.x, c3.y), dy, NcI);
+                NnI = f2_fma(f2_make(c3.z, c3.w), dy, NnI);
             }
-            if (has_imag(lp, q)) {
-                const float* t = acquire(it);
-                const float dx = t[dxr[1]] - t[dxr[1] - 1];
-                const float dy = t[dyu[1]] - t[dyu[1] - BX];
-                const float4 c0 = s_coef[2 * ii], c1 = s_coef[2 * ii + 1];
-                release(it);
-                ++it;
+            if (inI) {
+                // input I: d_x feeds I targets, d_y feeds R targets
+                const float4* c = s_coef + 4 * ii;
                 ++ii;
-                PcI = fmaf(c0.x, dx, PcI); PnI = fmaf(c0.y, dx, PnI);
-                NcI = fmaf(c0.z, dx, NcI); NnI = fmaf(c0.w, dx, NnI);
-                PcR = fmaf(c1.x, dy, PcR); PnR = fmaf(c1.y, dy, PnR);
-                NcR = fmaf(c1.z, dy, NcR); NnR = fmaf(c1.w, dy, NnR);
+                const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
+                const f2 dx = diff_x(t + rxI, cxI, evI);
+                const f2 dy = f2_sub(lds2(t + uI), lds2(t + uI - BX));
+                PcI = f2_fma(f2_make(c0.x, c0.y), dx, PcI);
+                PnI = f2_fma(f2_make(c0.z, c0.w), dx, PnI);
+                NcI = f2_fma(f2_make(c1.x, c1.y), dx, NcI);
+                NnI = f2_fma(f2_make(c1.z, c1.w), dx, NnI);
+                PcR = f2_fma(f2_make(c2.x, c2.y), dy, PcR);
+                PnR = f2_fma(f2_make(c2.z, c2.w), dy, PnR);
+                NcR = f2_fma(f2_make(c3.x, c3.y), dy, NcR);
+                NnR = f2_fma(f2_make(c3.z, c3.w), dy, NnR);
             }
             if (q >= 1 && q - 1 < nqp) {
-                finalize(0, lp - 1, PcR);
-                if (has_imag(lp - 1, q - 1)) finalize(1, lp - 1, PcI);
+                finalize(t, 0, lp - 1, PcR);
+                if (has_imag(lp - 1, q - 1)) finalize(t, 1, lp - 1, PcI);
             }
+            stage_done();
             if (q < nqn) {
                 part(q, 0) = NcR;
                 if (has_imag(lp + 1, q)) part(q, 1) = NcI;
@@ -377,8 +475,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_tiled_pass(const __grid_constant
             PcR = PnR; PcI = PnI; NcR = NnR; NcI = NnI;
         }
         if (alive && nq - 1 < nqp) {
-            finalize(0, lp - 1, PcR);
-            if (has_imag(lp - 1, nq - 1)) finalize(1, lp - 1, PcI);
+            // tail stage: the last previous-order target
+            const float* t = stage_ptr();
+            finalize(t, 0, lp - 1, PcR);
+            if (has_imag(lp - 1, nq - 1)) finalize(t, 1, lp - 1, PcI);
+            stage_done();
         }
         if (nq < nqn) {
             part(nq, 0) = NcR;
@@ -387,10 +488,15 @@ __global__ void __launch_bounds__(THREADS, 2) k_tiled_pass(const __grid_constant
     }
     // outputs of the order above the last input order have no further inputs
     const int L = last_in + 1;
-    if (L <= N && alive) {
+    if (L <= N) {
         for (int q = 0; q < nq_of(L) && alive; ++q) {
-            finalize(0, L, part(q, 0));
-            if (has_imag(L, q)) finalize(1, L, part(q, 1));
+            const bool hi = has_imag(L, q);
+            const f2 WR = part(q, 0);
+            const f2 WI = hi ? part(q, 1) : zero;
+            const float* t = stage_ptr();
+            finalize(t, 0, L, WR);
+            if (hi) finalize(t, 1, L, WI);
+            stage_done();
         }
     }
 }
