@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "tiled.h"
@@ -160,6 +161,21 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
         t.fin_comp.push_back(j);
         return true;
     };
+    // a finalising stage carries entries for both kinds; absent I gets a placeholder
+    auto emit_fin_pair = [&](int L, int q) -> bool {
+        if (!emit_fin(L, q, 0)) return false;
+        if (has_imag(L, q)) return emit_fin(L, q, 1);
+        t.fin.push_back(make_int2(-1, 0));
+        t.fin_comp.push_back(-1);
+        return true;
+    };
+    // a q step carries coefficient rows for both kinds; absent I gets zeros
+    auto emit_input_pair = [&](int lp, int q) -> bool {
+        if (!emit_input(lp, q, 0)) return false;
+        if (has_imag(lp, q)) return emit_input(lp, q, 1);
+        t.coef.insert(t.coef.end(), 16, 0.f);
+        return true;
+    };
     auto close_stage = [&]() {
         t.stages.push_back(cur);
         cur = make_int4(-1, -1, -1, -1);
@@ -172,32 +188,28 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
         last_in = lp;
         const int nq = nq_of(lp), nqp = nq_of(lp - 1);
         for (int q = 0; q < nq && ok; ++q) {
-            ok = ok && emit_input(lp, q, 0);
-            if (has_imag(lp, q)) ok = ok && emit_input(lp, q, 1);
-            if (q >= 1 && q - 1 < nqp) {
-                ok = ok && emit_fin(lp - 1, q - 1, 0);
-                if (has_imag(lp - 1, q - 1)) ok = ok && emit_fin(lp - 1, q - 1, 1);
-            }
+            ok = ok && emit_input_pair(lp, q);
+            if (q >= 1 && q - 1 < nqp) ok = ok && emit_fin_pair(lp - 1, q - 1);
             close_stage();
         }
         if (ok && nq - 1 < nqp) {
-            ok = ok && emit_fin(lp - 1, nq - 1, 0);
-            if (has_imag(lp - 1, nq - 1)) ok = ok && emit_fin(lp - 1, nq - 1, 1);
+            ok = ok && emit_fin_pair(lp - 1, nq - 1);
             close_stage();
         }
     }
     const int L = last_in + 1;
     if (ok && L <= N)
         for (int q = 0; q < nq_of(L) && ok; ++q) {
-            ok = ok && emit_fin(L, q, 0);
-            if (has_imag(L, q)) ok = ok && emit_fin(L, q, 1);
+            ok = ok && emit_fin_pair(L, q);
             close_stage();
         }
     if (!ok) { err = "moment placement differs from the tiled kernel's"; return false; }
     // every component of the output parity is finalised exactly once
     long nout = 0;
     for (int j = 0; j < n; ++j) nout += (sys.moms[j].l % 2 == P);
-    if ((long)t.fin.size() != nout) { err = "tiled schedule does not cover every output"; return false; }
+    long nreal = 0;
+    for (int c : t.fin_comp) nreal += c >= 0;
+    if (nreal != nout) { err = "tiled schedule does not cover every output"; return false; }
     // every nonzero coupling between the two parities is covered
     long total = 0;
     for (int j = 0; j < n; ++j) {
@@ -253,6 +265,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
         // finalise events: element offset of the component (| class << 48), source array
         std::vector<longlong2> fin(t.fin.size());
         for (size_t e = 0; e < t.fin.size(); ++e) {
+            if (t.fin_comp[e] < 0) { fin[e].x = -1; fin[e].y = 0; continue; }
             const int g = gout[P][sys.moms[t.fin_comp[e]].imag ? 1 : 0];
             const long long off = (long long)t.fin[e].x * pl->geo.cstride[g];
             fin[e].x = off | ((long long)t.fin[e].y << 48);
@@ -266,13 +279,16 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
         // shared memory: barriers, ring, coefficient rows, finalise events, partial sums
         int off = RING_OFF + NSTAGES * STAGE_BYTES;
         const int coef_off = off;
-        off += (int)(t.nin * 4 * sizeof(float4));
+        off += (int)(t.coef.size() * sizeof(float));
         off = (off + 15) & ~15;
         const int fin_off = off;
         off += (int)(t.fin.size() * sizeof(longlong2));
         off = (off + 15) & ~15;
+        const int stage_off = off;
+        off += (int)(t.stages.size() * sizeof(int4));
+        off = (off + 15) & ~15;
         const int part_off = off;
-        off += (nq_of(pl->N) + 1) * 2 * CONSUMERS * 8;
+        off += (nq_of(pl->N) + 1) * CONSUMERS * 8;   // one pair of partial sums per consumer thread and q
         pl->smem_bytes[P] = off;
         int dev = 0, maxsm = 0;
         cudaGetDevice(&dev);
@@ -305,7 +321,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             prm.which = w;
             prm.nclasses = pl->nclasses;
             prm.nstages = (int)t.stages.size();
-            prm.nin = t.nin;
+            prm.nin = (int)(t.coef.size() / 16);
             prm.nfin = (int)t.fin.size();
             prm.stages = (const int4*)pl->dev_stages[P];
             prm.coef = (const float4*)pl->dev_coef[P];
@@ -314,6 +330,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             prm.smem_coef_off = coef_off;
             prm.smem_fin_off = fin_off;
             prm.smem_part_off = part_off;
+            prm.smem_stage_off = stage_off;
         }
     }
     pl->ready = true;

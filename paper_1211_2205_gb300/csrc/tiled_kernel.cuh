@@ -54,10 +54,11 @@ constexpr int OUT_BYTES = TX * TY * 4;
 constexpr int SLOT = ((IN_BYTES + 127) / 128) * 128;   // slot stride in bytes
 constexpr int SLOTS_PER_STAGE = 4;      // input R, input I, output R, output I
 constexpr int STAGE_BYTES = SLOT * SLOTS_PER_STAGE;
-constexpr int NSTAGES = 6;              // stages in the ring
-constexpr int CONSUMER_WARPS = TY;
+constexpr int NSTAGES = 8;              // stages in the ring (power of two)
+constexpr int CONSUMER_WARPS = 2 * TY;  // one warp per tile row and output kind (R, I)
 constexpr int CONSUMERS = CONSUMER_WARPS * 32;
-constexpr int THREADS = CONSUMERS + 32;
+constexpr int PRODUCER_WARPS = 2;       // independent TMA issue streams (even / odd stages)
+constexpr int THREADS = CONSUMERS + 32 * PRODUCER_WARPS;
 constexpr int MAXN = 63;
 constexpr int RING_OFF = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded waits: 2 s
@@ -80,10 +81,12 @@ struct Params {
     int nclasses;               // 2 = isotropic (class 0: l = 0, 1: l >= 1), else class = l
     int nstages, nin, nfin;
     const int4* stages;         // per stage: component (in its grid) of slot 0..3, -1 if absent
-    const float4* coef;         // per input: cx Pm, P0, N0, Np, cy Pm, P0, N0, Np, each twice
-    const longlong2* fin;       // per finalise event: (element offset | class << 48, source array or 0)
+    const float4* coef;         // per q step: rows of input R and input I (zero row if absent);
+                                // a row is cx Pm, P0, N0, Np, cy Pm, P0, N0, Np, each twice
+    const longlong2* fin;       // per finalising stage: entries for output R and output I:
+                                // (element offset | class << 48, or -1 if absent; source array or 0)
     int* err;                   // bounded-wait failure flag
-    int smem_coef_off, smem_fin_off, smem_part_off;   // byte offsets in dynamic smem
+    int smem_coef_off, smem_fin_off, smem_part_off, smem_stage_off;   // byte offsets in dynamic smem
 };
 
 __host__ __device__ constexpr int nq_of(int l) { return l < 0 ? 0 : l / 2 + 1; }
@@ -128,9 +131,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Wait for a barrier phase with a time limit; on expiry raise the CTA's
@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
     const float4* s_coef = reinterpret_cast<const float4*>(smem + prm.smem_coef_off);
     const longlong2* s_fin = reinterpret_cast<const longlong2*>(smem + prm.smem_fin_off);
     f2* s_part = reinterpret_cast<f2*>(smem + prm.smem_part_off);
+    const int4* s_stages = reinterpret_cast<const int4*>(smem + prm.smem_stage_off);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -240,6 +241,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
         for (int i = tid; i < 4 * prm.nin; i += THREADS) c[i] = __ldg(prm.coef + i);
         longlong2* f = reinterpret_cast<longlong2*>(smem + prm.smem_fin_off);
         for (int i = tid; i < prm.nfin; i += THREADS) f[i] = __ldg(prm.fin + i);
+        int4* st = reinterpret_cast<int4*>(smem + prm.smem_stage_off);
+        for (int i = tid; i < prm.nstages; i += THREADS) st[i] = __ldg(prm.stages + i);
     }
     __syncthreads();
 
@@ -248,168 +251,192 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
     input_shift(prm.P, 1, prm.p[0], prm.p[1], sxI, syI);
 
     // --------------------------------------------------------- producer
-    if (warp == CONSUMER_WARPS) {
-        if (lane == 0) {
-            // box origins in tensor coordinates (x' = x + VEC, row = y + 1)
-            const int bxR = x0 + (sxR == 0 ? 0 : VEC), byR = y0 + (syR == 0 ? -1 : 0) + 1;
-            const int bxI = x0 + (sxI == 0 ? 0 : VEC), byI = y0 + (syI == 0 ? -1 : 0) + 1;
-            int issued = 0;
-            bool ok = true;
-            for (int s = 0; s < prm.nstages; ++s) {
-                const int r = s % NSTAGES;
-                if (s >= NSTAGES && !wait_bounded(&empty[r], ((s / NSTAGES) - 1) & 1, abort_flag, prm.err)) {
-                    ok = false;
-                    break;
+    // Producer warp pw owns the stages s = pw (mod PRODUCER_WARPS).  Its
+    // lane 0 waits for the slot to drain and arms the barrier with the
+    // stage's byte count; lanes 0..3 then issue the (up to) four boxes.
+    if (warp >= CONSUMER_WARPS) {
+        const int pw = warp - CONSUMER_WARPS;
+        const int bxR = x0 + (sxR == 0 ? 0 : VEC), byR = y0 + (syR == 0 ? -1 : 0) + 1;
+        const int bxI = x0 + (sxI == 0 ? 0 : VEC), byI = y0 + (syI == 0 ? -1 : 0) + 1;
+        // box origin of this lane's slot (tensor coordinates x' = x + VEC, row = y + 1)
+        const int bx = lane == 0 ? bxR : lane == 1 ? bxI : x0 + VEC;
+        const int by = lane == 0 ? byR : lane == 1 ? byI : y0 + 1;
+        const CUtensorMap* map = &prm.maps[lane & 3];
+        int last = -1;
+        bool ok = true;
+        for (int s = pw; s < prm.nstages; s += PRODUCER_WARPS) {
+            const int r = s & (NSTAGES - 1);
+            const int4 st = s_stages[s];
+            if (lane == 0) {
+                if (s >= NSTAGES && !wait_bounded(&empty[r], ((s / NSTAGES) - 1) & 1, abort_flag, prm.err)) ok = false;
+                if (ok) {
+                    const uint32_t bytes = (st.x >= 0 ? IN_BYTES : 0) + (st.y >= 0 ? IN_BYTES : 0) +
+                                           (st.z >= 0 ? OUT_BYTES : 0) + (st.w >= 0 ? OUT_BYTES : 0);
+                    mbar_expect_tx(&full[r], bytes);
                 }
-                const int4 st = __ldg(prm.stages + s);
-                const uint32_t bytes = (st.x >= 0 ? IN_BYTES : 0) + (st.y >= 0 ? IN_BYTES : 0) +
-                                       (st.z >= 0 ? OUT_BYTES : 0) + (st.w >= 0 ? OUT_BYTES : 0);
-                unsigned char* base = ring + r * STAGE_BYTES;
-                fence_proxy_async();
-                mbar_expect_tx(&full[r], bytes);
-                if (st.x >= 0) tma_load_3d(base, &prm.maps[0], bxR, byR, st.x, &full[r]);
-                if (st.y >= 0) tma_load_3d(base + SLOT, &prm.maps[1], bxI, byI, st.y, &full[r]);
-                if (st.z >= 0) tma_load_3d(base + 2 * SLOT, &prm.maps[2], x0 + VEC, y0 + 1, st.z, &full[r]);
-                if (st.w >= 0) tma_load_3d(base + 3 * SLOT, &prm.maps[3], x0 + VEC, y0 + 1, st.w, &full[r]);
-                ++issued;
             }
-            if (!ok) {
-                // aborted: wait (bounded) for the copies still in flight
-                for (int s = issued - 1; s >= 0 && s >= issued - NSTAGES; --s) {
-                    const unsigned long long t0 = global_ns();
-                    while (!mbar_try_wait(&full[s % NSTAGES], (s / NSTAGES) & 1))
-                        if (global_ns() - t0 > WAIT_NS) break;
-                }
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            const int comp = lane == 0 ? st.x : lane == 1 ? st.y : lane == 2 ? st.z : st.w;
+            if (lane < 4 && comp >= 0)
+                tma_load_3d(ring + r * STAGE_BYTES + lane * SLOT, map, bx, by, comp, &full[r]);
+            last = s;
+        }
+        if (!ok && lane == 0) {
+            // aborted: wait (bounded) for this warp's copies still in flight
+            for (int s = last; s >= 0 && s > last - NSTAGES; s -= PRODUCER_WARPS) {
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try_wait(&full[s & (NSTAGES - 1)], (s / NSTAGES) & 1))
+                    if (global_ns() - t0 > WAIT_NS) break;
             }
         }
         return;
     }
 
     // --------------------------------------------------------- consumers
-    // this thread owns points A = (x0 + 2 lane, y) and B = A + (1, 0)
-    const int gy = y0 + warp;
+    // Warp w handles tile row w % TY for the targets of kind K = w / TY
+    // (0: R outputs, 1: I outputs), at points A = (x0 + 2 lane, y) and
+    // B = A + (1, 0).  Targets of kind K take d_x of the inputs of kind K
+    // (through Mx) and d_y of the inputs of the other kind (through My).
+    const int K = warp / TY;
+    const int row = warp % TY;
+    const int gy = y0 + row;
     const int gxA = x0 + 2 * lane;
-    // float offsets, inside a stage, of the difference operands
-    int rxR, cxR, uR, rxI, cxI, uI;          // x: row start, column of A's right operand; y: up pair
-    bool evR, evI;
+    // float offsets, inside a stage, of the difference operands: d_x from the
+    // input of kind K (slot K), d_y from the input of kind 1 - K (slot 1 - K)
+    int rx, cx, uy;
+    bool ev;
     {
-        const int bxsR = sxR == 0 ? -VEC : 0, oyR = syR == 0 ? -1 : 0;
-        const int bxsI = sxI == 0 ? -VEC : 0, oyI = syI == 0 ? -1 : 0;
-        rxR = (warp - oyR) * BX;
-        cxR = 2 * lane + sxR - bxsR;
-        evR = (cxR & 1) == 0;
-        uR = (warp + syR - oyR) * BX + (2 * lane - bxsR);
-        rxI = SLOT / 4 + (warp - oyI) * BX;
-        cxI = 2 * lane + sxI - bxsI;
-        evI = (cxI & 1) == 0;
-        uI = SLOT / 4 + (warp + syI - oyI) * BX + (2 * lane - bxsI);
+        const int sxK = K == 0 ? sxR : sxI;
+        const int syO = K == 0 ? syI : syR;
+        const int syK = K == 0 ? syR : syI;
+        const int sxO = K == 0 ? sxI : sxR;
+        const int bxsK = sxK == 0 ? -VEC : 0, oyK = syK == 0 ? -1 : 0;
+        const int bxsO = sxO == 0 ? -VEC : 0, oyO = syO == 0 ? -1 : 0;
+        rx = K * (SLOT / 4) + (row - oyK) * BX;
+        cx = 2 * lane + sxK - bxsK;
+        ev = (cx & 1) == 0;
+        uy = (1 - K) * (SLOT / 4) + (row + syO - oyO) * BX + (2 * lane - bxsO);
     }
-    // output kinds k = 0 (R), 1 (I)
-    float* pptr[2];                           // point A in component 0 of the output grid
-    bool inA[2], inB[2], both[2], bndAny[2];
-    long cidxA[2];
-    f2 ca2[2][2], cb2[2][2];                  // decay pairs by class (isotropic)
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const OutGrid& G = prm.out[k];
-        const int g = prm.P == 1 ? (k == 0 ? 1 : 2) : (k == 0 ? 0 : 3);
-        const bool xnode = g & 1, ynode = g & 2;
-        const long plane = (long)G.nx * G.ny;
-        inA[k] = gxA < G.nx && gy < G.ny;
-        inB[k] = gxA + 1 < G.nx && gy < G.ny;
-        both[k] = inA[k] && inB[k];
-        pptr[k] = G.base + (long)(gy + 1) * prm.pitch + gxA;
-        cidxA[k] = (long)gy * G.nx + gxA;
-        bool bnd = false;
-        for (int pt = 0; pt < 2; ++pt) {
-            const int gx = gxA + pt;
-            if (prm.p[0]) bnd |= (gx == G.nx - 1) || (gx == 0);
-            else if (!xnode) bnd |= (gx == 0) || (gx == G.nx - 1);
-            if (prm.p[1]) bnd |= (gy == G.ny - 1) || (gy == 0);
-            else if (!ynode) bnd |= (gy == 0) || (gy == G.ny - 1);
+    // the output grid of kind K
+    const OutGrid& G = prm.out[K];
+    const int gK = prm.P == 1 ? (K == 0 ? 1 : 2) : (K == 0 ? 0 : 3);
+    const bool xnode = gK & 1, ynode = gK & 2;
+    const long plane = (long)G.nx * G.ny;
+    const bool inA = gxA < G.nx && gy < G.ny;
+    const bool inB = gxA + 1 < G.nx && gy < G.ny;
+    float* const pptr = G.base + (long)(gy + 1) * prm.pitch + gxA;   // point A in component 0
+    const long cidxA = (long)gy * G.nx + gxA;
+    bool bnd = false;
+    for (int pt = 0; pt < 2; ++pt) {
+        const int gx = gxA + pt;
+        if (prm.p[0]) bnd |= (gx == G.nx - 1) || (gx == 0);
+        else if (!xnode) bnd |= (gx == 0) || (gx == G.nx - 1);
+        if (prm.p[1]) bnd |= (gy == G.ny - 1) || (gy == 0);
+        else if (!ynode) bnd |= (gy == 0) || (gy == G.ny - 1);
+    }
+    const bool fast = inA && inB && !bnd;     // plain paired store
+    f2 ca2[2], cb2[2];                         // decay pairs by class (isotropic)
+    for (int c = 0; c < 2; ++c) {
+        float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
+        if (prm.nclasses == 2 && G.coef != nullptr) {
+            const float* cf = G.coef + (long)c * 4 * plane + cidxA;
+            if (inA) { a[0] = __ldg(cf + 2 * prm.which * plane); b[0] = __ldg(cf + (2 * prm.which + 1) * plane); }
+            if (inB) { a[1] = __ldg(cf + 2 * prm.which * plane + 1); b[1] = __ldg(cf + (2 * prm.which + 1) * plane + 1); }
         }
-        bndAny[k] = bnd && (inA[k] || inB[k]);
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
-            if (prm.nclasses == 2 && G.coef != nullptr) {
-                const float* cf = G.coef + (long)c * 4 * plane + cidxA[k];
-                if (inA[k]) { a[0] = __ldg(cf + 2 * prm.which * plane); b[0] = __ldg(cf + (2 * prm.which + 1) * plane); }
-                if (inB[k]) { a[1] = __ldg(cf + 2 * prm.which * plane + 1); b[1] = __ldg(cf + (2 * prm.which + 1) * plane + 1); }
-            }
-            ca2[k][c] = f2_make(a[0], a[1]);
-            cb2[k][c] = f2_make(b[0], b[1]);
-        }
+        ca2[c] = f2_make(a[0], a[1]);
+        cb2[c] = f2_make(b[0], b[1]);
     }
 
+    static_assert((NSTAGES & (NSTAGES - 1)) == 0, "ring depth must be a power of two");
     int s = 0, ii = 0, e = 0;
     bool alive = true;
     auto stage_ptr = [&]() -> const float* {
-        const int r = s % NSTAGES;
+        const int r = s & (NSTAGES - 1);
         if (alive) alive = wait_bounded(&full[r], (s / NSTAGES) & 1, abort_flag, prm.err);
         return reinterpret_cast<const float*>(ring + r * STAGE_BYTES);
     };
     auto stage_done = [&]() {
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s % NSTAGES]);
+        if (lane == 0) mbar_arrive(&empty[s & (NSTAGES - 1)]);
         ++s;
     };
-    auto part = [&](int q, int k) -> f2& { return s_part[(q * 2 + k) * CONSUMERS + tid]; };
-    // write one point (and its boundary copies) of output kind k
-    auto store_point = [&](int k, float* dst, int gx, float v) {
-        const OutGrid& G = prm.out[k];
-        const int g = prm.P == 1 ? (k == 0 ? 1 : 2) : (k == 0 ? 0 : 3);
-        const bool xnode = g & 1, ynode = g & 2;
+    auto part = [&](int q) -> f2& { return s_part[q * CONSUMERS + tid]; };
+    // write one point (and its boundary copies)
+    auto store_point = [&](float* dst, int gx, float v) {
         *dst = v;
         int xa = -2, xb = -2, ya = -2, yb = -2;
         if (prm.p[0]) { if (gx == G.nx - 1) xa = -1; if (gx == 0) xb = G.nx; }
         else if (!xnode) { if (gx == 0) xa = -1; if (gx == G.nx - 1) xb = G.nx; }
         if (prm.p[1]) { if (gy == G.ny - 1) ya = -1; if (gy == 0) yb = G.ny; }
         else if (!ynode) { if (gy == 0) ya = -1; if (gy == G.ny - 1) yb = G.ny; }
-        float* row = dst - gx;
-        if (xa != -2) row[xa] = v;
-        if (xb != -2) row[xb] = v;
+        float* rw = dst - gx;
+        if (xa != -2) rw[xa] = v;
+        if (xb != -2) rw[xb] = v;
         float* col = dst - (long)(gy + 1) * prm.pitch;
         if (ya != -2) col[(long)(ya + 1) * prm.pitch] = v;
         if (yb != -2) col[(long)(yb + 1) * prm.pitch] = v;
     };
-    // finalise output kind k (slot 2 + k of stage t) of order L with sums W
-    auto finalize = [&](const float* t, int k, int L, f2 W) {
-        const longlong2 f = s_fin[e];                 // (element offset of the component, source pointer)
-        ++e;
-        const f2 u = lds2(t + (2 + k) * (SLOT / 4) + warp * TX + 2 * lane);
+    // finalise this warp's output (slot 2 + K of stage t) of order L with sums W;
+    // the finalise entries come in (R, I) pairs; f.x < 0 marks an absent output
+    auto finalize = [&](const float* t, int L, f2 W) {
+        const longlong2 f = s_fin[e + K];
+        e += 2;
+        const f2 u = lds2(t + (2 + K) * (SLOT / 4) + row * TX + 2 * lane);
         f2 aa, bb;
         if (prm.nclasses == 2) {
-            aa = L == 0 ? ca2[k][0] : ca2[k][1];
-            bb = L == 0 ? cb2[k][0] : cb2[k][1];
+            aa = L == 0 ? ca2[0] : ca2[1];
+            bb = L == 0 ? cb2[0] : cb2[1];
         } else {
-            const long plane = (long)prm.out[k].nx * prm.out[k].ny;
-            const long cls = (long)(f.x >> 48);
-            const float* cf = prm.out[k].coef + cls * 4 * plane + cidxA[k];
-            float a0 = inA[k] ? __ldg(cf + 2 * prm.which * plane) : 0.f;
-            float b0 = inA[k] ? __ldg(cf + (2 * prm.which + 1) * plane) : 0.f;
-            float a1 = inB[k] ? __ldg(cf + 2 * prm.which * plane + 1) : 0.f;
-            float b1 = inB[k] ? __ldg(cf + (2 * prm.which + 1) * plane + 1) : 0.f;
+            const long cls = f.x < 0 ? 0 : (long)(f.x >> 48);
+            const float* cf = G.coef + cls * 4 * plane + cidxA;
+            float a0 = inA ? __ldg(cf + 2 * prm.which * plane) : 0.f;
+            float b0 = inA ? __ldg(cf + (2 * prm.which + 1) * plane) : 0.f;
+            float a1 = inB ? __ldg(cf + 2 * prm.which * plane + 1) : 0.f;
+            float b1 = inB ? __ldg(cf + (2 * prm.which + 1) * plane + 1) : 0.f;
             aa = f2_make(a0, a1);
             bb = f2_make(b0, b1);
         }
         const float* qs = reinterpret_cast<const float*>(f.y);
         if (qs != nullptr) {
-            const float q0 = inA[k] ? __ldg(qs + cidxA[k]) : 0.f;
-            const float q1 = inB[k] ? __ldg(qs + cidxA[k] + 1) : 0.f;
+            const float q0 = inA ? __ldg(qs + cidxA) : 0.f;
+            const float q1 = inB ? __ldg(qs + cidxA + 1) : 0.f;
             W = f2_add(W, f2_make(q0, q1));
         }
         const f2 v = f2_fma(aa, u, f2_mul(bb, W));
-        if (!alive) return;
-        float* dst = pptr[k] + (f.x & 0xFFFFFFFFFFFFll);
-        if (both[k] && !bndAny[k]) {
+        if (!alive || f.x < 0) return;
+        float* dst = pptr + (f.x & 0xFFFFFFFFFFFFll);
+        if (fast) {
             *reinterpret_cast<f2*>(dst) = v;
         } else {
             float v0, v1;
             f2_split(v, v0, v1);
-            if (inA[k]) store_point(k, dst, gxA, v0);
-            if (inB[k]) store_point(k, dst + 1, gxA + 1, v1);
+            if (inA) store_point(dst, gxA, v0);
+            if (inB) store_point(dst + 1, gxA + 1, v1);
         }
+    };
+    // accumulate a q step into the four targets of kind K in reach; the
+    // coefficient rows of the step are (input R, input I), each (cx, cy);
+    // the I input's differences are masked when I_l'^m' does not exist
+    auto accumulate = [&](const float* t, bool inI, f2& Pc, f2& Pn, f2& Nc, f2& Nn) {
+        const ulonglong2* c = reinterpret_cast<const ulonglong2*>(s_coef) + 4 * ii;   // rows ii (R), ii + 1 (I)
+        ii += 2;
+        // d_x of the input of kind K with its cx; d_y of the other input with its cy
+        const ulonglong2 xa = c[4 * K], xb = c[4 * K + 1];
+        const ulonglong2 ya = c[4 * (1 - K) + 2], yb = c[4 * (1 - K) + 3];
+        const bool inX = K == 0 || inI, inY = K == 1 || inI;
+        f2 dx = diff_x(t + rx, cx, ev);
+        f2 dy = f2_sub(lds2(t + uy), lds2(t + uy - BX));
+        dx = inX ? dx : 0ull;
+        dy = inY ? dy : 0ull;
+        Pc = f2_fma(xa.x, dx, Pc);
+        Pn = f2_fma(xa.y, dx, Pn);
+        Nc = f2_fma(xb.x, dx, Nc);
+        Nn = f2_fma(xb.y, dx, Nn);
+        Pc = f2_fma(ya.x, dy, Pc);
+        Pn = f2_fma(ya.y, dy, Pn);
+        Nc = f2_fma(yb.x, dy, Nc);
+        Nn = f2_fma(yb.y, dy, Nn);
     };
 
     const int N = prm.N;
@@ -421,81 +448,43 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
         const int nq = nq_of(lp);
         const int nqp = nq_of(lp - 1);                    // previous-order targets
         const int nqn = lp + 1 <= N ? nq_of(lp + 1) : 0;  // next-order targets
-        f2 PcR = zero, PcI = zero, NcR = zero, NcI = zero;
-        for (int q = 0; q < nq && alive; ++q) {
-            const bool inI = has_imag(lp, q);
-            // partial sums of a previous-order target exist once order
-            // lp - 2 has streamed by (not for the first input order)
-            const bool ldP = q < nqp && lp > first;
-            f2 PnR = ldP ? part(q, 0) : zero;
-            f2 PnI = (ldP && has_imag(lp - 1, q)) ? part(q, 1) : zero;
-            f2 NnR = zero, NnI = zero;
+        const bool ld = lp > first;   // previous-order partial sums exist once order lp - 2 has passed
+        f2 Pc = zero, Nc = zero;
+        // one q step: (Pc, Nc) carried in, (Pn, Nn) started here
+        auto qstep = [&](int q, f2& Pc_, f2& Nc_, f2& Pn_, f2& Nn_) {
+            Pn_ = (ld && q < nqp) ? part(q) : zero;
+            Nn_ = zero;
             const float* t = stage_ptr();
-            {
-                // input R: d_x feeds R targets, d_y feeds I targets
-                const float4* c = s_coef + 4 * ii;
-                ++ii;
-                const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
-                const f2 dx = diff_x(t + rxR, cxR, evR);
-                const f2 dy = f2_sub(lds2(t + uR), lds2(t + uR - BX));
-                PcR = f2_fma(f2_make(c0.x, c0.y), dx, PcR);
-                PnR = f2_fma(f2_make(c0.z, c0.w), dx, PnR);
-                NcR = f2_fma(f2_make(c1.x, c1.y), dx, NcR);
-                NnR = f2_fma(f2_make(c1.z, c1.w), dx, NnR);
-                PcI = f2_fma(f2_make(c2.x, c2.y), dy, PcI);
-                PnI = f2_fma(f2_make(c2.z, c2.w), dy, PnI);
-                NcI = f2_fma(f2_make(c3.x, c3.y), dy, NcI);
-                NnI = f2_fma(f2_make(c3.z, c3.w), dy, NnI);
-            }
-            if (inI) {
-                // input I: d_x feeds I targets, d_y feeds R targets
-                const float4* c = s_coef + 4 * ii;
-                ++ii;
-                const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
-                const f2 dx = diff_x(t + rxI, cxI, evI);
-                const f2 dy = f2_sub(lds2(t + uI), lds2(t + uI - BX));
-                PcI = f2_fma(f2_make(c0.x, c0.y), dx, PcI);
-                PnI = f2_fma(f2_make(c0.z, c0.w), dx, PnI);
-                NcI = f2_fma(f2_make(c1.x, c1.y), dx, NcI);
-                NnI = f2_fma(f2_make(c1.z, c1.w), dx, NnI);
-                PcR = f2_fma(f2_make(c2.x, c2.y), dy, PcR);
-                PnR = f2_fma(f2_make(c2.z, c2.w), dy, PnR);
-                NcR = f2_fma(f2_make(c3.x, c3.y), dy, NcR);
-                NnR = f2_fma(f2_make(c3.z, c3.w), dy, NnR);
-            }
-            if (q >= 1 && q - 1 < nqp) {
-                finalize(t, 0, lp - 1, PcR);
-                if (has_imag(lp - 1, q - 1)) finalize(t, 1, lp - 1, PcI);
-            }
+            accumulate(t, has_imag(lp, q), Pc_, Pn_, Nc_, Nn_);
+            if (q >= 1 && q - 1 < nqp) finalize(t, lp - 1, Pc_);
             stage_done();
-            if (q < nqn) {
-                part(q, 0) = NcR;
-                if (has_imag(lp + 1, q)) part(q, 1) = NcI;
-            }
-            PcR = PnR; PcI = PnI; NcR = NnR; NcI = NnI;
+            if (q < nqn) part(q) = Nc_;
+        };
+        int q = 0;
+        f2 Pn, Nn;
+        for (; q + 1 < nq && alive; q += 2) {
+            qstep(q, Pc, Nc, Pn, Nn);
+            qstep(q + 1, Pn, Nn, Pc, Nc);
+        }
+        if (q < nq && alive) {
+            qstep(q, Pc, Nc, Pn, Nn);
+            Pc = Pn; Nc = Nn;
         }
         if (alive && nq - 1 < nqp) {
             // tail stage: the last previous-order target
             const float* t = stage_ptr();
-            finalize(t, 0, lp - 1, PcR);
-            if (has_imag(lp - 1, nq - 1)) finalize(t, 1, lp - 1, PcI);
+            finalize(t, lp - 1, Pc);
             stage_done();
         }
-        if (nq < nqn) {
-            part(nq, 0) = NcR;
-            if (has_imag(lp + 1, nq)) part(nq, 1) = NcI;
-        }
+        if (nq < nqn) part(nq) = Nc;
     }
     // outputs of the order above the last input order have no further inputs
     const int L = last_in + 1;
     if (L <= N) {
         for (int q = 0; q < nq_of(L) && alive; ++q) {
-            const bool hi = has_imag(L, q);
-            const f2 WR = part(q, 0);
-            const f2 WI = hi ? part(q, 1) : zero;
+            const f2 W = part(q);
             const float* t = stage_ptr();
-            finalize(t, 0, L, WR);
-            if (hi) finalize(t, 1, L, WI);
+            finalize(t, L, W);
             stage_done();
         }
     }
