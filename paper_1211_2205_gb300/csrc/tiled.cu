@@ -83,9 +83,9 @@ struct TiledPlan {
     CUtensorMap maps_in[4], maps_out[4];
     PassTables tab[2];
     void* dev_stages[2] = {nullptr, nullptr};
-    void* dev_coef[2] = {nullptr, nullptr};
-    void* dev_fin[2] = {nullptr, nullptr};
-    void* dev_src[2] = {nullptr, nullptr};
+    void* dev_coef[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [P][K]
+    void* dev_fin[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    void* dev_src = nullptr;
     int tiles_x = 0, tiles_y = 0;
     int smem_bytes[2] = {0, 0};
     Params prm[2][2];                     // [P][which]
@@ -97,11 +97,15 @@ namespace {
 void free_tables(TiledPlan* pl) {
     for (int P = 0; P < 2; ++P) {
         if (pl->dev_stages[P]) cudaFree(pl->dev_stages[P]);
-        if (pl->dev_coef[P]) cudaFree(pl->dev_coef[P]);
-        if (pl->dev_fin[P]) cudaFree(pl->dev_fin[P]);
-        if (pl->dev_src[P]) cudaFree(pl->dev_src[P]);
-        pl->dev_stages[P] = pl->dev_coef[P] = pl->dev_fin[P] = pl->dev_src[P] = nullptr;
+        pl->dev_stages[P] = nullptr;
+        for (int K = 0; K < 2; ++K) {
+            if (pl->dev_coef[P][K]) cudaFree(pl->dev_coef[P][K]);
+            if (pl->dev_fin[P][K]) cudaFree(pl->dev_fin[P][K]);
+            pl->dev_coef[P][K] = pl->dev_fin[P][K] = nullptr;
+        }
     }
+    if (pl->dev_src) cudaFree(pl->dev_src);
+    pl->dev_src = nullptr;
 }
 
 template <class V>
@@ -257,33 +261,60 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
                  const std::vector<int>& src_slot, const std::vector<void*>& src_dev, double dx, double dy) {
     free_tables(pl);
     pl->ready = false;
+    {
+        std::vector<const float*> sp(src_dev.size());
+        for (size_t i = 0; i < src_dev.size(); ++i) sp[i] = (const float*)src_dev[i];
+        if (!upload(&pl->dev_src, sp)) { pl->err = "uploading the source table failed"; return -4; }
+    }
     const int gin[2][2] = {{1, 2}, {0, 3}};
     const int gout[2][2] = {{0, 3}, {1, 2}};
     for (int P = 0; P < 2; ++P) {
         PassTables& t = pl->tab[P];
         if (!build_pass(pl, sys, comp_class, P, dx, dy, t, pl->err)) return -8;
-        // finalise events: element offset of the component (| class << 48), source array
-        std::vector<longlong2> fin(t.fin.size());
-        for (size_t e = 0; e < t.fin.size(); ++e) {
-            if (t.fin_comp[e] < 0) { fin[e].x = -1; fin[e].y = 0; continue; }
-            const int g = gout[P][sys.moms[t.fin_comp[e]].imag ? 1 : 0];
-            const long long off = (long long)t.fin[e].x * pl->geo.cstride[g];
-            fin[e].x = off | ((long long)t.fin[e].y << 48);
-            int sl = src_slot[t.fin_comp[e]];
-            fin[e].y = sl >= 0 ? (long long)(uintptr_t)src_dev[sl] : 0;
+        // per output kind K: coefficient rows (x part of the kind-K input,
+        // y part of the other input) and finalise entries (offset, source slot)
+        const size_t nsteps = t.coef.size() / 32;
+        std::vector<float> ck[2];
+        for (int K = 0; K < 2; ++K) {
+            ck[K].resize(nsteps * 16);
+            for (size_t k = 0; k < nsteps; ++k) {
+                const float* rowK = t.coef.data() + 32 * k + 16 * K;
+                const float* rowO = t.coef.data() + 32 * k + 16 * (1 - K);
+                std::copy(rowK, rowK + 8, ck[K].begin() + 16 * k);
+                std::copy(rowO + 8, rowO + 16, ck[K].begin() + 16 * k + 8);
+            }
         }
-        if (!upload(&pl->dev_stages[P], t.stages) || !upload(&pl->dev_coef[P], t.coef) || !upload(&pl->dev_fin[P], fin)) {
+        std::vector<int2> fk[2];
+        for (size_t e = 0; e + 1 < t.fin.size() + 1; e += 2) {
+            for (int K = 0; K < 2; ++K) {
+                const int comp = t.fin_comp[e + K];
+                if (comp < 0) { fk[K].push_back(make_int2(-1, -1)); continue; }
+                const int g = gout[P][K];
+                const long long off = (long long)t.fin[e + K].x * pl->geo.cstride[g];
+                if (off > 0x7fffffffll) { pl->err = "state too large for the tiled kernel's 32-bit offsets"; return -8; }
+                fk[K].push_back(make_int2((int)off, src_slot[comp]));
+            }
+        }
+        for (int K = 0; K < 2; ++K)
+            if (!upload(&pl->dev_coef[P][K], ck[K]) || !upload(&pl->dev_fin[P][K], fk[K])) {
+                pl->err = "uploading the tiled tables failed";
+                return -4;
+            }
+        if (!upload(&pl->dev_stages[P], t.stages)) {
             pl->err = "uploading the tiled tables failed";
             return -4;
         }
         // shared memory: barriers, ring, coefficient rows, finalise events, partial sums
         int off = RING_OFF + NSTAGES * STAGE_BYTES;
-        const int coef_off = off;
-        off += (int)(t.coef.size() * sizeof(float));
-        off = (off + 15) & ~15;
-        const int fin_off = off;
-        off += (int)(t.fin.size() * sizeof(longlong2));
-        off = (off + 15) & ~15;
+        int coef_off[2], fin_off[2];
+        for (int K = 0; K < 2; ++K) {
+            coef_off[K] = off;
+            off += (int)(ck[K].size() * sizeof(float));
+            off = (off + 15) & ~15;
+            fin_off[K] = off;
+            off += (int)(fk[K].size() * sizeof(int2));
+            off = (off + 15) & ~15;
+        }
         const int stage_off = off;
         off += (int)(t.stages.size() * sizeof(int4));
         off = (off + 15) & ~15;
@@ -321,14 +352,17 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             prm.which = w;
             prm.nclasses = pl->nclasses;
             prm.nstages = (int)t.stages.size();
-            prm.nin = (int)(t.coef.size() / 16);
-            prm.nfin = (int)t.fin.size();
+            prm.nin = (int)nsteps;
+            prm.nfin = (int)fk[0].size();
             prm.stages = (const int4*)pl->dev_stages[P];
-            prm.coef = (const float4*)pl->dev_coef[P];
-            prm.fin = (const longlong2*)pl->dev_fin[P];
+            for (int K = 0; K < 2; ++K) {
+                prm.coef[K] = (const float4*)pl->dev_coef[P][K];
+                prm.fin[K] = (const int2*)pl->dev_fin[P][K];
+                prm.smem_coef_off[K] = coef_off[K];
+                prm.smem_fin_off[K] = fin_off[K];
+            }
+            prm.srcs = (const float* const*)pl->dev_src;
             prm.err = pl->err_dev;
-            prm.smem_coef_off = coef_off;
-            prm.smem_fin_off = fin_off;
             prm.smem_part_off = part_off;
             prm.smem_stage_off = stage_off;
         }

@@ -81,12 +81,14 @@ struct Params {
     int nclasses;               // 2 = isotropic (class 0: l = 0, 1: l >= 1), else class = l
     int nstages, nin, nfin;
     const int4* stages;         // per stage: component (in its grid) of slot 0..3, -1 if absent
-    const float4* coef;         // per q step: rows of input R and input I (zero row if absent);
-                                // a row is cx Pm, P0, N0, Np, cy Pm, P0, N0, Np, each twice
-    const longlong2* fin;       // per finalising stage: entries for output R and output I:
-                                // (element offset | class << 48, or -1 if absent; source array or 0)
+    const float4* coef[2];      // per output kind K, per q step: (cx Pm, cx P0, cx N0, cx Np) of the
+                                // input of kind K and (cy Pm, cy P0, cy N0, cy Np) of the other
+                                // input, each value twice (f32x2 operands); zero if absent
+    const int2* fin[2];         // per output kind K, per finalising stage: (element offset of the
+                                // component, or -1 if absent; source slot or -1)
+    const float* const* srcs;   // source arrays by slot
     int* err;                   // bounded-wait failure flag
-    int smem_coef_off, smem_fin_off, smem_part_off, smem_stage_off;   // byte offsets in dynamic smem
+    int smem_coef_off[2], smem_fin_off[2], smem_part_off, smem_stage_off;   // byte offsets in dynamic smem
 };
 
 __host__ __device__ constexpr int nq_of(int l) { return l < 0 ? 0 : l / 2 + 1; }
@@ -191,6 +193,7 @@ __device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
     return d;
 }
 __device__ __forceinline__ f2 lds2(const float* p) { return *reinterpret_cast<const f2*>(p); }
+__device__ __forceinline__ f2 zero2() { return 0ull; }
 
 // x-differences of points A (column c) and B (column c + 1) of one box row:
 // right operands at columns c, c + 1, left operands at c - 1, c.  The pair
@@ -216,8 +219,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
     uint64_t* empty = full + NSTAGES;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NSTAGES);
     unsigned char* ring = smem + RING_OFF;
-    const float4* s_coef = reinterpret_cast<const float4*>(smem + prm.smem_coef_off);
-    const longlong2* s_fin = reinterpret_cast<const longlong2*>(smem + prm.smem_fin_off);
     f2* s_part = reinterpret_cast<f2*>(smem + prm.smem_part_off);
     const int4* s_stages = reinterpret_cast<const int4*>(smem + prm.smem_stage_off);
 
@@ -235,12 +236,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
         *abort_flag = 0;
         fence_mbar_init();
     }
-    // stage the coefficient and finalise tables in shared memory
+    // stage the coefficient, finalise and stage tables in shared memory
+    for (int k = 0; k < 2; ++k) {
+        float4* c = reinterpret_cast<float4*>(smem + prm.smem_coef_off[k]);
+        for (int i = tid; i < 4 * prm.nin; i += THREADS) c[i] = __ldg(prm.coef[k] + i);
+        int2* f = reinterpret_cast<int2*>(smem + prm.smem_fin_off[k]);
+        for (int i = tid; i < prm.nfin; i += THREADS) f[i] = __ldg(prm.fin[k] + i);
+    }
     {
-        float4* c = reinterpret_cast<float4*>(smem + prm.smem_coef_off);
-        for (int i = tid; i < 4 * prm.nin; i += THREADS) c[i] = __ldg(prm.coef + i);
-        longlong2* f = reinterpret_cast<longlong2*>(smem + prm.smem_fin_off);
-        for (int i = tid; i < prm.nfin; i += THREADS) f[i] = __ldg(prm.fin + i);
         int4* st = reinterpret_cast<int4*>(smem + prm.smem_stage_off);
         for (int i = tid; i < prm.nstages; i += THREADS) st[i] = __ldg(prm.stages + i);
     }
@@ -349,19 +352,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
     }
 
     static_assert((NSTAGES & (NSTAGES - 1)) == 0, "ring depth must be a power of two");
-    int s = 0, ii = 0, e = 0;
+    // walking pointers into this kind's tables and this thread's partial sums
+    const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(smem + prm.smem_coef_off[K]);
+    const int2* fp = reinterpret_cast<const int2*>(smem + prm.smem_fin_off[K]);
+    f2* const pp = s_part + tid;
+    const unsigned char* const ring_c = ring;
+    const int uoff = (2 + K) * (SLOT / 4) + row * TX + 2 * lane;    // old value inside a stage
+    int s = 0;
     bool alive = true;
     auto stage_ptr = [&]() -> const float* {
         const int r = s & (NSTAGES - 1);
         if (alive) alive = wait_bounded(&full[r], (s / NSTAGES) & 1, abort_flag, prm.err);
-        return reinterpret_cast<const float*>(ring + r * STAGE_BYTES);
+        return reinterpret_cast<const float*>(ring_c + r * STAGE_BYTES);
     };
     auto stage_done = [&]() {
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s & (NSTAGES - 1)]);
         ++s;
     };
-    auto part = [&](int q) -> f2& { return s_part[q * CONSUMERS + tid]; };
     // write one point (and its boundary copies)
     auto store_point = [&](float* dst, int gx, float v) {
         *dst = v;
@@ -377,35 +385,36 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
         if (ya != -2) col[(long)(ya + 1) * prm.pitch] = v;
         if (yb != -2) col[(long)(yb + 1) * prm.pitch] = v;
     };
-    // finalise this warp's output (slot 2 + K of stage t) of order L with sums W;
-    // the finalise entries come in (R, I) pairs; f.x < 0 marks an absent output
-    auto finalize = [&](const float* t, int L, f2 W) {
-        const longlong2 f = s_fin[e + K];
-        e += 2;
-        const f2 u = lds2(t + (2 + K) * (SLOT / 4) + row * TX + 2 * lane);
-        f2 aa, bb;
+    // decay pair (a, b) of the outputs of order L
+    f2 aL = zero2(), bL = zero2();
+    auto set_order = [&](int L) {
         if (prm.nclasses == 2) {
-            aa = L == 0 ? ca2[0] : ca2[1];
-            bb = L == 0 ? cb2[0] : cb2[1];
+            aL = L == 0 ? ca2[0] : ca2[1];
+            bL = L == 0 ? cb2[0] : cb2[1];
         } else {
-            const long cls = f.x < 0 ? 0 : (long)(f.x >> 48);
-            const float* cf = G.coef + cls * 4 * plane + cidxA;
+            const float* cf = G.coef + (long)L * 4 * plane + cidxA;
             float a0 = inA ? __ldg(cf + 2 * prm.which * plane) : 0.f;
             float b0 = inA ? __ldg(cf + (2 * prm.which + 1) * plane) : 0.f;
             float a1 = inB ? __ldg(cf + 2 * prm.which * plane + 1) : 0.f;
             float b1 = inB ? __ldg(cf + (2 * prm.which + 1) * plane + 1) : 0.f;
-            aa = f2_make(a0, a1);
-            bb = f2_make(b0, b1);
+            aL = f2_make(a0, a1);
+            bL = f2_make(b0, b1);
         }
-        const float* qs = reinterpret_cast<const float*>(f.y);
-        if (qs != nullptr) {
+    };
+    // finalise this warp's output of the current finalising stage (slot 2 + K)
+    auto finalize = [&](const float* t, f2 W) {
+        const int2 f = *fp;
+        fp += 1;
+        const f2 u = lds2(t + uoff);
+        if (f.y >= 0) {
+            const float* qs = prm.srcs[f.y];
             const float q0 = inA ? __ldg(qs + cidxA) : 0.f;
             const float q1 = inB ? __ldg(qs + cidxA + 1) : 0.f;
             W = f2_add(W, f2_make(q0, q1));
         }
-        const f2 v = f2_fma(aa, u, f2_mul(bb, W));
-        if (!alive || f.x < 0) return;
-        float* dst = pptr + (f.x & 0xFFFFFFFFFFFFll);
+        const f2 v = f2_fma(aL, u, f2_mul(bL, W));
+        if (f.x < 0 || !alive) return;
+        float* dst = pptr + f.x;
         if (fast) {
             *reinterpret_cast<f2*>(dst) = v;
         } else {
@@ -415,20 +424,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
             if (inB) store_point(dst + 1, gxA + 1, v1);
         }
     };
-    // accumulate a q step into the four targets of kind K in reach; the
-    // coefficient rows of the step are (input R, input I), each (cx, cy);
-    // the I input's differences are masked when I_l'^m' does not exist
+    // accumulate a q step into the four targets of kind K in reach: d_x of
+    // the input of kind K (slot K), d_y of the other input (slot 1 - K);
+    // a missing I input has zero coefficients and its differences masked
     auto accumulate = [&](const float* t, bool inI, f2& Pc, f2& Pn, f2& Nc, f2& Nn) {
-        const ulonglong2* c = reinterpret_cast<const ulonglong2*>(s_coef) + 4 * ii;   // rows ii (R), ii + 1 (I)
-        ii += 2;
-        // d_x of the input of kind K with its cx; d_y of the other input with its cy
-        const ulonglong2 xa = c[4 * K], xb = c[4 * K + 1];
-        const ulonglong2 ya = c[4 * (1 - K) + 2], yb = c[4 * (1 - K) + 3];
-        const bool inX = K == 0 || inI, inY = K == 1 || inI;
+        const ulonglong2 xa = cp[0], xb = cp[1], ya = cp[2], yb = cp[3];
+        cp += 4;
         f2 dx = diff_x(t + rx, cx, ev);
         f2 dy = f2_sub(lds2(t + uy), lds2(t + uy - BX));
-        dx = inX ? dx : 0ull;
-        dy = inY ? dy : 0ull;
+        if (!inI) {
+            if (K == 1) dx = zero2(); else dy = zero2();
+        }
         Pc = f2_fma(xa.x, dx, Pc);
         Pn = f2_fma(xa.y, dx, Pn);
         Nc = f2_fma(xb.x, dx, Nc);
@@ -442,23 +448,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
     const int N = prm.N;
     const int first = 1 - prm.P;              // first input order: even l' for the odd pass
     int last_in = first;
-    const f2 zero = 0ull;
     for (int lp = first; lp <= N && alive; lp += 2) {
         last_in = lp;
         const int nq = nq_of(lp);
         const int nqp = nq_of(lp - 1);                    // previous-order targets
         const int nqn = lp + 1 <= N ? nq_of(lp + 1) : 0;  // next-order targets
-        const bool ld = lp > first;   // previous-order partial sums exist once order lp - 2 has passed
-        f2 Pc = zero, Nc = zero;
+        const int nqload = lp > first ? nqp : 0;          // previous-order partial sums exist once order lp - 2 passed
+        set_order(lp - 1);
+        f2 Pc = zero2(), Nc = zero2();
         // one q step: (Pc, Nc) carried in, (Pn, Nn) started here
         auto qstep = [&](int q, f2& Pc_, f2& Nc_, f2& Pn_, f2& Nn_) {
-            Pn_ = (ld && q < nqp) ? part(q) : zero;
-            Nn_ = zero;
+            Pn_ = q < nqload ? pp[q * CONSUMERS] : zero2();
+            Nn_ = zero2();
             const float* t = stage_ptr();
             accumulate(t, has_imag(lp, q), Pc_, Pn_, Nc_, Nn_);
-            if (q >= 1 && q - 1 < nqp) finalize(t, lp - 1, Pc_);
+            if (q >= 1 && q - 1 < nqp) finalize(t, Pc_);
             stage_done();
-            if (q < nqn) part(q) = Nc_;
+            if (q < nqn) pp[q * CONSUMERS] = Nc_;
         };
         int q = 0;
         f2 Pn, Nn;
@@ -473,18 +479,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
         if (alive && nq - 1 < nqp) {
             // tail stage: the last previous-order target
             const float* t = stage_ptr();
-            finalize(t, lp - 1, Pc);
+            finalize(t, Pc);
             stage_done();
         }
-        if (nq < nqn) part(nq) = Nc;
+        if (nq < nqn) pp[nq * CONSUMERS] = Nc;
     }
     // outputs of the order above the last input order have no further inputs
     const int L = last_in + 1;
     if (L <= N) {
+        set_order(L);
         for (int q = 0; q < nq_of(L) && alive; ++q) {
-            const f2 W = part(q);
+            const f2 W = pp[q * CONSUMERS];
             const float* t = stage_ptr();
-            finalize(t, L, W);
+            finalize(t, W);
             stage_done();
         }
     }
