@@ -171,6 +171,10 @@ int starmap_set_scattering_factors(starmap_t* h, const double* factor, int count
 int starmap_set_source(starmap_t* h, int j, const double* q, size_t count);
 /* Set component j (initial condition, par.ic); count = nx*ny of its grid. */
 int starmap_set_moment(starmap_t* h, int j, const double* u, size_t count);
+/* Zero every component (and its boundary copies) on the device and reset
+ * time and step count to 0; material and sources are kept.  Use before
+ * setting a new initial condition with starmap_set_moment. */
+int starmap_clear(starmap_t* h);
 /* Set the time t (for starmap_time / advance_to bookkeeping). */
 int starmap_set_time(starmap_t* h, double t);
 

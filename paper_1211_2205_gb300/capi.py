@@ -91,6 +91,7 @@ def lib():
         "starmap_set_source": (ctypes.c_int, [H, ctypes.c_int, _dp, ctypes.c_size_t]),
         "starmap_set_moment": (ctypes.c_int, [H, ctypes.c_int, _dp, ctypes.c_size_t]),
         "starmap_set_time": (ctypes.c_int, [H, ctypes.c_double]),
+        "starmap_clear": (ctypes.c_int, [H]),
         "starmap_step": (ctypes.c_int, [H, ctypes.c_long]),
         "starmap_advance_to": (ctypes.c_int, [H, ctypes.c_double]),
         "starmap_pass": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int]),
@@ -253,6 +254,9 @@ class Stepper:
     def set_moment(self, j: int, u: np.ndarray):
         a = np.ascontiguousarray(u, dtype=np.float64).ravel()
         self._check(self._L.starmap_set_moment(self._h, j, _dptr(a), a.size))
+
+    def clear(self):
+        self._check(self._L.starmap_clear(self._h))
 
     def set_time(self, t: float):
         self._check(self._L.starmap_set_time(self._h, float(t)))

@@ -652,6 +652,17 @@ int starmap_set_moment(starmap_t* h, int j, const double* u, size_t count) {
     return STARMAP_OK;
 }
 
+int starmap_clear(starmap_t* h) {
+    if (!h) return STARMAP_E_ARG;
+    for (int g = 0; g < 4; ++g)
+        CK(cudaMemsetAsync(h->alloc[g], 0, h->grid_bytes[g], h->stream), "clear");
+    h->t = 0.0;
+    h->steps = 0;
+    h->have_output = false;
+    h->ghosts_dirty = false;      // all ghosts are zero, consistent with the zero state
+    return STARMAP_OK;
+}
+
 int starmap_set_time(starmap_t* h, double t) {
     if (!h) return STARMAP_E_ARG;
     h->t = t;

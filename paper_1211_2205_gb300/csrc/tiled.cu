@@ -319,7 +319,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
         off += (int)(t.stages.size() * sizeof(int4));
         off = (off + 15) & ~15;
         const int part_off = off;
-        off += (nq_of(pl->N) + 1) * CONSUMERS * 8;   // one pair of partial sums per consumer thread and q
+        off += (nq_of(pl->N) + 1) * PP * CONSUMERS * 8;   // PP pairs of partial sums per consumer thread and q
         pl->smem_bytes[P] = off;
         int dev = 0, maxsm = 0;
         cudaGetDevice(&dev);

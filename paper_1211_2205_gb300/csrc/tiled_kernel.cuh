@@ -1,7 +1,7 @@
 // Tiled half-step pass for the 2D real P_N system in FP32 (sm_103a).
 //
 // One CTA owns a TX x TY tile of point indices, shared by the four staggered
-// grids (section 4.1); each consumer thread owns PX points of one row.  A
+// grids (section 4.1); each consumer thread owns PP pairs of points of one row.  A
 // pass updates the components of one parity (odd l: grids G21 (R) and G12
 // (I); even l: G11 (R) and G22 (I)) from the half-grid differences
 // (eq. central_differences) of the other parity, weighted by -Mx/dx and
@@ -43,21 +43,23 @@
 namespace starmap {
 namespace tiled {
 
-constexpr int PX = 2;                   // points per consumer thread (along x)
-constexpr int TX = 32 * PX;             // tile width
-constexpr int TY = 8;                   // tile height (one consumer warp per row)
+constexpr int PP = 1;                   // point pairs per consumer thread (along x)
+constexpr int TX = 64 * PP;             // tile width: pair j of lane l covers x0 + 64 j + 2 l, +1
+constexpr int TY = 10;                  // tile height
 constexpr int VEC = 4;                  // 16 bytes of FP32: TMA x alignment
 constexpr int BX = TX + VEC;            // input box width (halo + alignment)
 constexpr int BYI = TY + 1;             // input box height (halo)
 constexpr int IN_BYTES = BX * BYI * 4;
 constexpr int OUT_BYTES = TX * TY * 4;
 constexpr int SLOT = ((IN_BYTES + 127) / 128) * 128;   // slot stride in bytes
-constexpr int SLOTS_PER_STAGE = 4;      // input R, input I, output R, output I
-constexpr int STAGE_BYTES = SLOT * SLOTS_PER_STAGE;
-constexpr int NSTAGES = 8;              // stages in the ring (power of two)
+constexpr int SLOTS_PER_STEP = 4;       // input R, input I, output R, output I of one consumer step
+constexpr int STEPS_PER_STAGE = 1;      // consumer steps sharing one mbarrier stage
+constexpr int STEP_BYTES = SLOT * SLOTS_PER_STEP;
+constexpr int STAGE_BYTES = STEP_BYTES * STEPS_PER_STAGE;
+constexpr int NSTAGES = 6;              // stages in the ring
 constexpr int CONSUMER_WARPS = 2 * TY;  // one warp per tile row and output kind (R, I)
 constexpr int CONSUMERS = CONSUMER_WARPS * 32;
-constexpr int PRODUCER_WARPS = 2;       // independent TMA issue streams (even / odd stages)
+constexpr int PRODUCER_WARPS = 2;       // independent TMA issue streams (stage s mod 2)
 constexpr int THREADS = CONSUMERS + 32 * PRODUCER_WARPS;
 constexpr int MAXN = 63;
 constexpr int RING_OFF = 256;
@@ -254,42 +256,47 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
     input_shift(prm.P, 1, prm.p[0], prm.p[1], sxI, syI);
 
     // --------------------------------------------------------- producer
-    // Producer warp pw owns the stages s = pw (mod PRODUCER_WARPS).  Its
-    // lane 0 waits for the slot to drain and arms the barrier with the
-    // stage's byte count; lanes 0..3 then issue the (up to) four boxes.
+    // Producer warp pw owns the stages k = pw (mod PRODUCER_WARPS); stage k
+    // holds the consumer steps 2k and 2k + 1.  Lane 0 waits for the stage to
+    // drain and arms its barrier with the byte count; lanes 0..7 then issue
+    // the (up to) eight boxes, lane = 4 * (step in stage) + slot.
     if (warp >= CONSUMER_WARPS) {
         const int pw = warp - CONSUMER_WARPS;
+        const int slot = lane & 3;
         const int bxR = x0 + (sxR == 0 ? 0 : VEC), byR = y0 + (syR == 0 ? -1 : 0) + 1;
         const int bxI = x0 + (sxI == 0 ? 0 : VEC), byI = y0 + (syI == 0 ? -1 : 0) + 1;
         // box origin of this lane's slot (tensor coordinates x' = x + VEC, row = y + 1)
-        const int bx = lane == 0 ? bxR : lane == 1 ? bxI : x0 + VEC;
-        const int by = lane == 0 ? byR : lane == 1 ? byI : y0 + 1;
-        const CUtensorMap* map = &prm.maps[lane & 3];
+        const int bx = slot == 0 ? bxR : slot == 1 ? bxI : x0 + VEC;
+        const int by = slot == 0 ? byR : slot == 1 ? byI : y0 + 1;
+        const CUtensorMap* map = &prm.maps[slot];
+        const int nst = (prm.nstages + STEPS_PER_STAGE - 1) / STEPS_PER_STAGE;
         int last = -1;
         bool ok = true;
-        for (int s = pw; s < prm.nstages; s += PRODUCER_WARPS) {
-            const int r = s & (NSTAGES - 1);
-            const int4 st = s_stages[s];
+        for (int k = pw; k < nst; k += PRODUCER_WARPS) {
+            const int r = k % NSTAGES;
+            const int step = STEPS_PER_STAGE * k + (lane >> 2);
+            int4 st = make_int4(-1, -1, -1, -1);
+            if (lane < 4 * STEPS_PER_STAGE && step < prm.nstages) st = s_stages[step];
+            const int comp = slot == 0 ? st.x : slot == 1 ? st.y : slot == 2 ? st.z : st.w;
+            const uint32_t mine = lane < 4 * STEPS_PER_STAGE && comp >= 0 ? (slot < 2 ? IN_BYTES : OUT_BYTES) : 0u;
+            uint32_t bytes = mine;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
             if (lane == 0) {
-                if (s >= NSTAGES && !wait_bounded(&empty[r], ((s / NSTAGES) - 1) & 1, abort_flag, prm.err)) ok = false;
-                if (ok) {
-                    const uint32_t bytes = (st.x >= 0 ? IN_BYTES : 0) + (st.y >= 0 ? IN_BYTES : 0) +
-                                           (st.z >= 0 ? OUT_BYTES : 0) + (st.w >= 0 ? OUT_BYTES : 0);
-                    mbar_expect_tx(&full[r], bytes);
-                }
+                if (k >= NSTAGES && !wait_bounded(&empty[r], ((k / NSTAGES) - 1) & 1, abort_flag, prm.err)) ok = false;
+                if (ok) mbar_expect_tx(&full[r], bytes);
             }
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
-            const int comp = lane == 0 ? st.x : lane == 1 ? st.y : lane == 2 ? st.z : st.w;
-            if (lane < 4 && comp >= 0)
-                tma_load_3d(ring + r * STAGE_BYTES + lane * SLOT, map, bx, by, comp, &full[r]);
-            last = s;
+            if (mine != 0u)
+                tma_load_3d(ring + r * STAGE_BYTES + (lane >> 2) * STEP_BYTES + slot * SLOT, map, bx, by, comp, &full[r]);
+            last = k;
         }
         if (!ok && lane == 0) {
             // aborted: wait (bounded) for this warp's copies still in flight
-            for (int s = last; s >= 0 && s > last - NSTAGES; s -= PRODUCER_WARPS) {
+            for (int k = last; k >= 0 && k > last - NSTAGES; k -= PRODUCER_WARPS) {
                 const unsigned long long t0 = global_ns();
-                while (!mbar_try_wait(&full[s & (NSTAGES - 1)], (s / NSTAGES) & 1))
+                while (!mbar_try_wait(&full[k % NSTAGES], (k / NSTAGES) & 1))
                     if (global_ns() - t0 > WAIT_NS) break;
             }
         }
@@ -298,15 +305,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
 
     // --------------------------------------------------------- consumers
     // Warp w handles tile row w % TY for the targets of kind K = w / TY
-    // (0: R outputs, 1: I outputs), at points A = (x0 + 2 lane, y) and
-    // B = A + (1, 0).  Targets of kind K take d_x of the inputs of kind K
-    // (through Mx) and d_y of the inputs of the other kind (through My).
+    // (0: R outputs, 1: I outputs), at the point pairs j = 0..PP-1:
+    // A_j = (x0 + 64 j + 2 lane, y), B_j = A_j + (1, 0).  Targets of kind K
+    // take d_x of the inputs of kind K (through Mx) and d_y of the inputs of
+    // the other kind (through My).
     const int K = warp / TY;
     const int row = warp % TY;
     const int gy = y0 + row;
-    const int gxA = x0 + 2 * lane;
-    // float offsets, inside a stage, of the difference operands: d_x from the
-    // input of kind K (slot K), d_y from the input of kind 1 - K (slot 1 - K)
+    // float offsets, inside a step, of the difference operands of pair 0
+    // (pair j sits 64 j floats further): d_x from the input of kind K (slot
+    // K), d_y from the input of kind 1 - K (slot 1 - K)
     int rx, cx, uy;
     bool ev;
     {
@@ -326,48 +334,60 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
     const int gK = prm.P == 1 ? (K == 0 ? 1 : 2) : (K == 0 ? 0 : 3);
     const bool xnode = gK & 1, ynode = gK & 2;
     const long plane = (long)G.nx * G.ny;
-    const bool inA = gxA < G.nx && gy < G.ny;
-    const bool inB = gxA + 1 < G.nx && gy < G.ny;
-    float* const pptr = G.base + (long)(gy + 1) * prm.pitch + gxA;   // point A in component 0
-    const long cidxA = (long)gy * G.nx + gxA;
-    bool bnd = false;
-    for (int pt = 0; pt < 2; ++pt) {
-        const int gx = gxA + pt;
-        if (prm.p[0]) bnd |= (gx == G.nx - 1) || (gx == 0);
-        else if (!xnode) bnd |= (gx == 0) || (gx == G.nx - 1);
-        if (prm.p[1]) bnd |= (gy == G.ny - 1) || (gy == 0);
-        else if (!ynode) bnd |= (gy == 0) || (gy == G.ny - 1);
-    }
-    const bool fast = inA && inB && !bnd;     // plain paired store
-    f2 ca2[2], cb2[2];                         // decay pairs by class (isotropic)
-    for (int c = 0; c < 2; ++c) {
-        float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
-        if (prm.nclasses == 2 && G.coef != nullptr) {
-            const float* cf = G.coef + (long)c * 4 * plane + cidxA;
-            if (inA) { a[0] = __ldg(cf + 2 * prm.which * plane); b[0] = __ldg(cf + (2 * prm.which + 1) * plane); }
-            if (inB) { a[1] = __ldg(cf + 2 * prm.which * plane + 1); b[1] = __ldg(cf + (2 * prm.which + 1) * plane + 1); }
+    int gxA[PP];
+    bool inA[PP], inB[PP], fast[PP];
+    float* pptr[PP];          // point A_j in component 0
+    long cidxA[PP];
+    f2 ca2[PP][2], cb2[PP][2];  // decay pairs by class (isotropic)
+#pragma unroll
+    for (int j = 0; j < PP; ++j) {
+        gxA[j] = x0 + 64 * j + 2 * lane;
+        inA[j] = gxA[j] < G.nx && gy < G.ny;
+        inB[j] = gxA[j] + 1 < G.nx && gy < G.ny;
+        pptr[j] = G.base + (long)(gy + 1) * prm.pitch + gxA[j];
+        cidxA[j] = (long)gy * G.nx + gxA[j];
+        bool bnd = false;
+        for (int pt = 0; pt < 2; ++pt) {
+            const int gx = gxA[j] + pt;
+            if (prm.p[0]) bnd |= (gx == G.nx - 1) || (gx == 0);
+            else if (!xnode) bnd |= (gx == 0) || (gx == G.nx - 1);
+            if (prm.p[1]) bnd |= (gy == G.ny - 1) || (gy == 0);
+            else if (!ynode) bnd |= (gy == 0) || (gy == G.ny - 1);
         }
-        ca2[c] = f2_make(a[0], a[1]);
-        cb2[c] = f2_make(b[0], b[1]);
+        fast[j] = inA[j] && inB[j] && !bnd;
+        for (int c = 0; c < 2; ++c) {
+            float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
+            if (prm.nclasses == 2 && G.coef != nullptr) {
+                const float* cf = G.coef + (long)c * 4 * plane + cidxA[j];
+                if (inA[j]) { a[0] = __ldg(cf + 2 * prm.which * plane); b[0] = __ldg(cf + (2 * prm.which + 1) * plane); }
+                if (inB[j]) { a[1] = __ldg(cf + 2 * prm.which * plane + 1); b[1] = __ldg(cf + (2 * prm.which + 1) * plane + 1); }
+            }
+            ca2[j][c] = f2_make(a[0], a[1]);
+            cb2[j][c] = f2_make(b[0], b[1]);
+        }
     }
 
-    static_assert((NSTAGES & (NSTAGES - 1)) == 0, "ring depth must be a power of two");
     // walking pointers into this kind's tables and this thread's partial sums
     const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(smem + prm.smem_coef_off[K]);
     const int2* fp = reinterpret_cast<const int2*>(smem + prm.smem_fin_off[K]);
-    f2* const pp = s_part + tid;
-    const unsigned char* const ring_c = ring;
-    const int uoff = (2 + K) * (SLOT / 4) + row * TX + 2 * lane;    // old value inside a stage
+    f2* const pp = s_part + tid;            // entry (q, j) at pp[(q * PP + j) * CONSUMERS]
+    const int uoff = (2 + K) * (SLOT / 4) + row * TX + 2 * lane;    // old value of pair 0 inside a step
     int s = 0;
     bool alive = true;
+    // consumer step s lives in stage s / STEPS_PER_STAGE; the stage's barrier
+    // is awaited at its first step and released after its last step
+    const int last_step = prm.nstages - 1;
     auto stage_ptr = [&]() -> const float* {
-        const int r = s & (NSTAGES - 1);
-        if (alive) alive = wait_bounded(&full[r], (s / NSTAGES) & 1, abort_flag, prm.err);
-        return reinterpret_cast<const float*>(ring_c + r * STAGE_BYTES);
+        const int k = s / STEPS_PER_STAGE;
+        const int r = k % NSTAGES;
+        if (s % STEPS_PER_STAGE == 0 && alive) alive = wait_bounded(&full[r], (k / NSTAGES) & 1, abort_flag, prm.err);
+        return reinterpret_cast<const float*>(ring + r * STAGE_BYTES + (s % STEPS_PER_STAGE) * STEP_BYTES);
     };
     auto stage_done = [&]() {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s & (NSTAGES - 1)]);
+        if (s % STEPS_PER_STAGE == STEPS_PER_STAGE - 1 || s == last_step) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[(s / STEPS_PER_STAGE) % NSTAGES]);
+        }
         ++s;
     };
     // write one point (and its boundary copies)
@@ -385,64 +405,74 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
         if (ya != -2) col[(long)(ya + 1) * prm.pitch] = v;
         if (yb != -2) col[(long)(yb + 1) * prm.pitch] = v;
     };
-    // decay pair (a, b) of the outputs of order L
-    f2 aL = zero2(), bL = zero2();
+    // decay pairs (a, b) of the outputs of order L
+    f2 aL[PP], bL[PP];
     auto set_order = [&](int L) {
-        if (prm.nclasses == 2) {
-            aL = L == 0 ? ca2[0] : ca2[1];
-            bL = L == 0 ? cb2[0] : cb2[1];
-        } else {
-            const float* cf = G.coef + (long)L * 4 * plane + cidxA;
-            float a0 = inA ? __ldg(cf + 2 * prm.which * plane) : 0.f;
-            float b0 = inA ? __ldg(cf + (2 * prm.which + 1) * plane) : 0.f;
-            float a1 = inB ? __ldg(cf + 2 * prm.which * plane + 1) : 0.f;
-            float b1 = inB ? __ldg(cf + (2 * prm.which + 1) * plane + 1) : 0.f;
-            aL = f2_make(a0, a1);
-            bL = f2_make(b0, b1);
+#pragma unroll
+        for (int j = 0; j < PP; ++j) {
+            if (prm.nclasses == 2) {
+                aL[j] = L == 0 ? ca2[j][0] : ca2[j][1];
+                bL[j] = L == 0 ? cb2[j][0] : cb2[j][1];
+            } else {
+                const float* cf = G.coef + (long)L * 4 * plane + cidxA[j];
+                const float a0 = inA[j] ? __ldg(cf + 2 * prm.which * plane) : 0.f;
+                const float b0 = inA[j] ? __ldg(cf + (2 * prm.which + 1) * plane) : 0.f;
+                const float a1 = inB[j] ? __ldg(cf + 2 * prm.which * plane + 1) : 0.f;
+                const float b1 = inB[j] ? __ldg(cf + (2 * prm.which + 1) * plane + 1) : 0.f;
+                aL[j] = f2_make(a0, a1);
+                bL[j] = f2_make(b0, b1);
+            }
         }
     };
-    // finalise this warp's output of the current finalising stage (slot 2 + K)
-    auto finalize = [&](const float* t, f2 W) {
+    // finalise this warp's output of the current finalising step (slot 2 + K)
+    auto finalize = [&](const float* t, const f2 (&W)[PP]) {
         const int2 f = *fp;
         fp += 1;
-        const f2 u = lds2(t + uoff);
-        if (f.y >= 0) {
-            const float* qs = prm.srcs[f.y];
-            const float q0 = inA ? __ldg(qs + cidxA) : 0.f;
-            const float q1 = inB ? __ldg(qs + cidxA + 1) : 0.f;
-            W = f2_add(W, f2_make(q0, q1));
-        }
-        const f2 v = f2_fma(aL, u, f2_mul(bL, W));
-        if (f.x < 0 || !alive) return;
-        float* dst = pptr + f.x;
-        if (fast) {
-            *reinterpret_cast<f2*>(dst) = v;
-        } else {
-            float v0, v1;
-            f2_split(v, v0, v1);
-            if (inA) store_point(dst, gxA, v0);
-            if (inB) store_point(dst + 1, gxA + 1, v1);
+#pragma unroll
+        for (int j = 0; j < PP; ++j) {
+            const f2 u = lds2(t + uoff + 64 * j);
+            f2 w = W[j];
+            if (f.y >= 0) {
+                const float* qs = prm.srcs[f.y];
+                const float q0 = inA[j] ? __ldg(qs + cidxA[j]) : 0.f;
+                const float q1 = inB[j] ? __ldg(qs + cidxA[j] + 1) : 0.f;
+                w = f2_add(w, f2_make(q0, q1));
+            }
+            const f2 v = f2_fma(aL[j], u, f2_mul(bL[j], w));
+            if (f.x < 0 || !alive) continue;
+            float* dst = pptr[j] + f.x;
+            if (fast[j]) {
+                *reinterpret_cast<f2*>(dst) = v;
+            } else {
+                float v0, v1;
+                f2_split(v, v0, v1);
+                if (inA[j]) store_point(dst, gxA[j], v0);
+                if (inB[j]) store_point(dst + 1, gxA[j] + 1, v1);
+            }
         }
     };
     // accumulate a q step into the four targets of kind K in reach: d_x of
     // the input of kind K (slot K), d_y of the other input (slot 1 - K);
     // a missing I input has zero coefficients and its differences masked
-    auto accumulate = [&](const float* t, bool inI, f2& Pc, f2& Pn, f2& Nc, f2& Nn) {
+    auto accumulate = [&](const float* t, bool inI, f2 (&Pc)[PP], f2 (&Pn)[PP], f2 (&Nc)[PP], f2 (&Nn)[PP]) {
         const ulonglong2 xa = cp[0], xb = cp[1], ya = cp[2], yb = cp[3];
         cp += 4;
-        f2 dx = diff_x(t + rx, cx, ev);
-        f2 dy = f2_sub(lds2(t + uy), lds2(t + uy - BX));
-        if (!inI) {
-            if (K == 1) dx = zero2(); else dy = zero2();
+#pragma unroll
+        for (int j = 0; j < PP; ++j) {
+            f2 dx = diff_x(t + rx + 64 * j, cx, ev);
+            f2 dy = f2_sub(lds2(t + uy + 64 * j), lds2(t + uy + 64 * j - BX));
+            if (!inI) {
+                if (K == 1) dx = zero2(); else dy = zero2();
+            }
+            Pc[j] = f2_fma(xa.x, dx, Pc[j]);
+            Pn[j] = f2_fma(xa.y, dx, Pn[j]);
+            Nc[j] = f2_fma(xb.x, dx, Nc[j]);
+            Nn[j] = f2_fma(xb.y, dx, Nn[j]);
+            Pc[j] = f2_fma(ya.x, dy, Pc[j]);
+            Pn[j] = f2_fma(ya.y, dy, Pn[j]);
+            Nc[j] = f2_fma(yb.x, dy, Nc[j]);
+            Nn[j] = f2_fma(yb.y, dy, Nn[j]);
         }
-        Pc = f2_fma(xa.x, dx, Pc);
-        Pn = f2_fma(xa.y, dx, Pn);
-        Nc = f2_fma(xb.x, dx, Nc);
-        Nn = f2_fma(xb.y, dx, Nn);
-        Pc = f2_fma(ya.x, dy, Pc);
-        Pn = f2_fma(ya.y, dy, Pn);
-        Nc = f2_fma(yb.x, dy, Nc);
-        Nn = f2_fma(yb.y, dy, Nn);
     };
 
     const int N = prm.N;
@@ -455,41 +485,54 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
         const int nqn = lp + 1 <= N ? nq_of(lp + 1) : 0;  // next-order targets
         const int nqload = lp > first ? nqp : 0;          // previous-order partial sums exist once order lp - 2 passed
         set_order(lp - 1);
-        f2 Pc = zero2(), Nc = zero2();
+        f2 Pc[PP], Nc[PP], Pn[PP], Nn[PP];
+#pragma unroll
+        for (int j = 0; j < PP; ++j) { Pc[j] = zero2(); Nc[j] = zero2(); }
         // one q step: (Pc, Nc) carried in, (Pn, Nn) started here
-        auto qstep = [&](int q, f2& Pc_, f2& Nc_, f2& Pn_, f2& Nn_) {
-            Pn_ = q < nqload ? pp[q * CONSUMERS] : zero2();
-            Nn_ = zero2();
+        auto qstep = [&](int q, f2 (&Pc_)[PP], f2 (&Nc_)[PP], f2 (&Pn_)[PP], f2 (&Nn_)[PP]) {
+#pragma unroll
+            for (int j = 0; j < PP; ++j) {
+                Pn_[j] = q < nqload ? pp[(q * PP + j) * CONSUMERS] : zero2();
+                Nn_[j] = zero2();
+            }
             const float* t = stage_ptr();
             accumulate(t, has_imag(lp, q), Pc_, Pn_, Nc_, Nn_);
             if (q >= 1 && q - 1 < nqp) finalize(t, Pc_);
             stage_done();
-            if (q < nqn) pp[q * CONSUMERS] = Nc_;
+            if (q < nqn) {
+#pragma unroll
+                for (int j = 0; j < PP; ++j) pp[(q * PP + j) * CONSUMERS] = Nc_[j];
+            }
         };
         int q = 0;
-        f2 Pn, Nn;
         for (; q + 1 < nq && alive; q += 2) {
             qstep(q, Pc, Nc, Pn, Nn);
             qstep(q + 1, Pn, Nn, Pc, Nc);
         }
         if (q < nq && alive) {
             qstep(q, Pc, Nc, Pn, Nn);
-            Pc = Pn; Nc = Nn;
+#pragma unroll
+            for (int j = 0; j < PP; ++j) { Pc[j] = Pn[j]; Nc[j] = Nn[j]; }
         }
         if (alive && nq - 1 < nqp) {
-            // tail stage: the last previous-order target
+            // tail step: the last previous-order target
             const float* t = stage_ptr();
             finalize(t, Pc);
             stage_done();
         }
-        if (nq < nqn) pp[nq * CONSUMERS] = Nc;
+        if (nq < nqn) {
+#pragma unroll
+            for (int j = 0; j < PP; ++j) pp[(nq * PP + j) * CONSUMERS] = Nc[j];
+        }
     }
     // outputs of the order above the last input order have no further inputs
     const int L = last_in + 1;
     if (L <= N) {
         set_order(L);
         for (int q = 0; q < nq_of(L) && alive; ++q) {
-            const f2 W = pp[q * CONSUMERS];
+            f2 W[PP];
+#pragma unroll
+            for (int j = 0; j < PP; ++j) W[j] = pp[(q * PP + j) * CONSUMERS];
             const float* t = stage_ptr();
             finalize(t, W);
             stage_done();
