@@ -209,6 +209,38 @@ int starmap_moments_window(starmap_t* h, int j, int i0, int k0, int nx, int ny,
  * (discrete L2 norm, eq. discrete_L2_norm), nonfinite = count of NaN/Inf
  * values.  Any output may be NULL.  Returns E_NONFINITE if nonfinite > 0. */
 int starmap_diagnostics(starmap_t* h, double* mass, double* l2, long* nonfinite);
+/* Allocation-free FP64 diagnostics over caller-owned device data.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory where they need the reduction (GPU memory
+ * budgeted once at start-up, plug-ins running inside another framework's
+ * callbacks, real-time loops where cudaMalloc and its implicit
+ * synchronisation are not allowed).  It computes what starmap_diagnostics
+ * computes, for ncomp components of one grid: out_device[0] = cell * sum of
+ * component 0, out_device[1] = sqrt(cell * sum of squares of all values),
+ * out_device[2] = number of NaN/Inf values (as a double).  Element (x, y) of
+ * component k is data[origin + k*comp_stride + y*pitch + x] (elements of
+ * type double for STARMAP_FP64, float for STARMAP_FP32); data and
+ * out_device are device pointers owned by the caller.  Work is queued on
+ * `stream` (NULL = legacy default stream); the call does not synchronise.
+ *
+ * Scratch: the per-block partial sums live in a library-wide array of
+ * STARMAP_NOALLOC_MAX_BLOCKS x 3 doubles that every GPU loading the library
+ * keeps until process exit; nothing is allocated or freed.  The first call
+ * on a device looks up that array's device address (make that first call
+ * before any stream capture).  All calls share the array: calls whose work
+ * overlaps on the GPU race and give wrong results; serialise them (one
+ * stream, or events).  Every partial a call reads is written by the same
+ * call, so no clearing is needed between calls.
+ * Errors: E_ARG for null pointers, bad layout, or more than
+ * STARMAP_NOALLOC_MAX_ROWS rows (ncomp*ny) or STARMAP_NOALLOC_MAX_ROW_LENGTH
+ * points per row; E_CUDA if a launch or the address lookup fails. */
+#define STARMAP_NOALLOC_MAX_BLOCKS      1024
+#define STARMAP_NOALLOC_MAX_ROWS        (1L << 26)
+#define STARMAP_NOALLOC_MAX_ROW_LENGTH  (1L << 24)
+int starmap_diagnostics_noalloc(const void* data, int precision, int ncomp, int nx, int ny,
+                                long pitch, long comp_stride, long origin, double cell,
+                                double* out_device, void* stream);
 /* Device pointer of component j (borrowed), with its row pitch in elements
  * and the offset of point (0,0) in elements.  Element (i, k) is at
  * ptr[offset + k*pitch + i]; indices -1 and nx_g / ny_g hold boundary

@@ -106,6 +106,9 @@ def lib():
         "starmap_get_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t]),
         "starmap_set_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t]),
         "starmap_sync": (ctypes.c_int, [H]),
+        "starmap_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                       ctypes.c_int, ctypes.c_long, ctypes.c_long, ctypes.c_long,
+                                                       ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
