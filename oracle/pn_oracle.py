@@ -257,7 +257,8 @@ class StaggeredSolver:
                  sl_factor: Optional[Sequence[float]] = None,
                  sources: Sequence[Tuple[int, Field]] = (),
                  ic: Sequence[Tuple[int, Field]] = (),
-                 time_dependent: bool = False, dt: Optional[float] = None):
+                 time_dependent: bool = False, dt: Optional[float] = None,
+                 frozen: Sequence[int] = (), pre_odd: Optional[Callable] = None):
         self.Mx = np.asarray(Mx, dtype=np.float64)
         self.My = np.asarray(My, dtype=np.float64)
         self.order = np.asarray(mom_order)
@@ -275,9 +276,14 @@ class StaggeredSolver:
         self.time_dependent = time_dependent
         self.t = 0.0
         self.nsteps_done = 0
+        # Closure extension (not in the paper): components that the even
+        # half-steps leave alone, and a hook that sets them from the state
+        # right before every odd half-step.
+        self.frozen = set(int(j) for j in frozen)
+        self.pre_odd = pre_odd
 
         # Section 4.1: even components live on G11 u G22, odd on G21 u G12.
-        self.even = [j for j in range(self.ncomp) if self.grid[j] in ((1, 1), (2, 2))]
+        self.even = [j for j in range(self.ncomp) if self.grid[j] in ((1, 1), (2, 2)) and j not in self.frozen]
         self.odd = [j for j in range(self.ncomp) if self.grid[j] in ((2, 1), (1, 2))]
 
         # eq. grid11 / staggered_grids: coordinates of the four grids
@@ -367,12 +373,17 @@ class StaggeredSolver:
         tm = self.t + self.dt / 2.0
         if self._materials_at is None or self.time_dependent:
             self._evaluate(tm)
-        dxU, dyU = self._differences(self.even)
+        inputs_even = self.even + sorted(self.frozen)
+        if self.pre_odd is not None:
+            self.pre_odd(self)
+        dxU, dyU = self._differences(inputs_even)
         self._half_step(self.odd, dxU, dyU)
         dxU, dyU = self._differences(self.odd)     # computed once for both even halves
         self._half_step(self.even, dxU, dyU)
         self._half_step(self.even, dxU, dyU)
-        dxU, dyU = self._differences(self.even)
+        if self.pre_odd is not None:
+            self.pre_odd(self)
+        dxU, dyU = self._differences(inputs_even)
         self._half_step(self.odd, dxU, dyU)
         self.t += self.dt
         self.nsteps_done += 1
