@@ -82,6 +82,21 @@ extern "C" {
 #define STARMAP_KERNEL_GATHER  1  /* one thread per point, CSR loop over moments */
 #define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N, N <= 63) */
 
+/* Closure of the moment hierarchy.  NONE: the P_N truncation of section 3
+ * (moments of order N+1 are zero).  MLP8: not in the paper (its outlook,
+ * section 7, names closures that add information at the highest order):
+ * only with the 2D system and N = 7.  The handle then holds the P_8 system
+ * (45 components; 36..44 are the order-8 moments R_8^8, I_8^8, R_8^6, I_8^6,
+ * R_8^4, I_8^4, R_8^2, I_8^2, R_8^0).  The even passes leave the order-8
+ * components alone; before every odd half-step a per-cell network (set by
+ * starmap_set_closure) predicts them from the local moments of order <= 7,
+ * so the order-7 rows see the P_8 couplings times the prediction instead of
+ * zero.  Only the literal schedule is allowed (the prediction depends on
+ * the odd moments, so two odd halves do not merge); dt defaults to the
+ * P_8 bound cn * min(dx, dy) / lambda_max(Mx of P_8). */
+#define STARMAP_CLOSURE_NONE 0
+#define STARMAP_CLOSURE_MLP8 1
+
 typedef struct starmap_s starmap_t;
 
 typedef struct {
@@ -97,10 +112,11 @@ typedef struct {
     int    kernel;      /* STARMAP_KERNEL_*                                     */
     void*  cuda_stream; /* cudaStream_t to queue work on, or NULL for the
                            library's own stream                               */
+    int    closure;     /* STARMAP_CLOSURE_*                                    */
 } starmap_config;
 
 /* Fill *cfg with defaults: 2D P_N, N = 1, [0,1]^2, 16x16 periodic, cn = 0.5,
- * FP64, literal schedule, auto kernel, library stream. */
+ * FP64, literal schedule, auto kernel, library stream, no closure. */
 void starmap_config_default(starmap_config* cfg);
 
 /* ----------------------------------------------------------- host math
@@ -257,6 +273,74 @@ int starmap_set_state(starmap_t* h, const void* buf, size_t bytes);
 
 /* Wait for all queued work of the handle. */
 int starmap_sync(starmap_t* h);
+
+/* ------------------------------------------------------ learned closure
+ * Not in the paper.  The network maps 38 inputs to the 9 order-8 moments:
+ *   inputs  x = (u_0 .. u_35) / s, log(1 + sigma_a), log(1 + sigma_s0), the
+ *           36 moments of order <= 7 averaged to a cell centre from their
+ *           own grid (two neighbours on G21 / G12, four on G22) and divided
+ *           by their RMS s over the 36 values; sigma from grid G11's
+ *           material (starmap_set_material(h, 0, ...));
+ *   network h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = W3 h2 + b3
+ *           (128 hidden units per layer; BF16 operands, FP32 accumulation);
+ *   output  s * y = (R_8^8, I_8^8, R_8^6, I_8^6, R_8^4, I_8^4, R_8^2,
+ *           I_8^2, R_8^0) at the cell centre.  R_8^m are stored at the cell
+ *           centres (G11), I_8^m at each G22 point as the mean of its four
+ *           surrounding cells (boundary cells wrapped when periodic, the
+ *           nearest boundary cell for extrapolation).
+ * Parameters are one FP32 vector of STARMAP_MLP_PARAMS values: W1[128][38],
+ * b1[128], W2[128][128], b2[128], W3[9][128], b3[9] (row-major [out][in]). */
+#define STARMAP_MLP_INPUTS   38
+#define STARMAP_MLP_HIDDEN   128
+#define STARMAP_MLP_OUTPUTS  9
+#define STARMAP_MLP_PARAMS   22665
+
+/* Set the closure network of a STARMAP_CLOSURE_MLP8 handle from host FP32
+ * parameters (count = STARMAP_MLP_PARAMS; copied, rounded to BF16 on the
+ * device).  Stepping such a handle before this call returns E_STATE.
+ * E_STATE also for a handle without closure. */
+int starmap_set_closure(starmap_t* h, const float* params, size_t count);
+
+/* Training samples of the current state, on the device: for each cell
+ * m = iy*n_x + ix (M = n_x*n_y cells) the 38 network inputs X[m][38], the
+ * scale s[m], and, if targets is not NULL, the 9 order-8 moments averaged
+ * to the cell centre targets[m][9] (unscaled; the network's target is
+ * targets / s).  X, scale, targets are caller-owned device pointers of M*38,
+ * M and M*9 floats; count must equal M.  Needs the 2D system with N >= 7
+ * (N >= 8 or the closure for targets).  Asynchronous on the handle's
+ * stream. */
+int starmap_closure_samples(starmap_t* h, float* X, float* scale, float* targets, size_t count);
+
+/* Network object for inference and training on the device.  All X, Y, T,
+ * grad, loss and idx pointers are caller-owned device pointers; work is
+ * queued on the object's stream (cuda_stream, or a library stream if NULL)
+ * and does not synchronise unless stated. */
+typedef struct starmap_mlp_s starmap_mlp_t;
+/* Create from host FP32 parameters (count = STARMAP_MLP_PARAMS). */
+int  starmap_mlp_create(const float* params, size_t count, void* cuda_stream, starmap_mlp_t** out);
+void starmap_mlp_destroy(starmap_mlp_t* net);
+const char* starmap_mlp_last_error(const starmap_mlp_t* net);
+/* Copy the FP32 master parameters to / from the host (synchronises).
+ * set_params also resets the optimiser state. */
+int starmap_mlp_get_params(starmap_mlp_t* net, float* params, size_t count);
+int starmap_mlp_set_params(starmap_mlp_t* net, const float* params, size_t count);
+/* Y[m][9] = network(X[m][38]) for m < M. */
+int starmap_mlp_forward(starmap_mlp_t* net, const float* X, size_t M, float* Y);
+/* Mean squared error L = sum_{b,o} (y_bo - T_bo)^2 / (9 B) over the B
+ * samples idx[0..B) (idx NULL: samples 0..B-1) and its gradient: grad gets
+ * STARMAP_MLP_PARAMS floats in the parameter layout, loss one float (may be
+ * NULL).  Deterministic: per-tile partial sums reduced in a fixed order. */
+int starmap_mlp_loss_grad(starmap_mlp_t* net, const float* X, const float* T, const int32_t* idx,
+                          size_t B, float* grad, float* loss);
+/* One Adam step (Kingma & Ba 2015; beta1 = 0.9, beta2 = 0.999, eps = 1e-8,
+ * bias-corrected) on the gradient of the minibatch idx[0..B) with learning
+ * rate lr; loss (device, may be NULL) gets the minibatch loss before the
+ * step. */
+int starmap_mlp_train_step(starmap_mlp_t* net, const float* X, const float* T, const int32_t* idx,
+                           size_t B, float lr, float* loss);
+/* Number of Adam steps taken since creation or the last set_params. */
+long starmap_mlp_steps(const starmap_mlp_t* net);
+int  starmap_mlp_sync(starmap_mlp_t* net);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,8 @@ PN2D, SLAB = 0, 1
 FP64, FP32 = 0, 1
 SCHEDULE_LITERAL, SCHEDULE_MERGED = 0, 1
 KERNEL_AUTO, KERNEL_GATHER, KERNEL_TILED = 0, 1, 2
+CLOSURE_NONE, CLOSURE_MLP8 = 0, 1
+MLP_INPUTS, MLP_HIDDEN, MLP_OUTPUTS, MLP_PARAMS = 38, 128, 9, 22665
 
 
 class StarmapError(RuntimeError):
@@ -45,12 +47,14 @@ class Config(ctypes.Structure):
         ("schedule", ctypes.c_int),
         ("kernel", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
+        ("closure", ctypes.c_int),
     ]
 
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
+_fp = ctypes.POINTER(ctypes.c_float)
 
 
 def exported_functions() -> list:
@@ -109,6 +113,21 @@ def lib():
         "starmap_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                        ctypes.c_int, ctypes.c_long, ctypes.c_long, ctypes.c_long,
                                                        ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
+        "starmap_set_closure": (ctypes.c_int, [H, _fp, ctypes.c_size_t]),
+        "starmap_closure_samples": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_size_t]),
+        "starmap_mlp_create": (ctypes.c_int, [_fp, ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(H)]),
+        "starmap_mlp_destroy": (None, [H]),
+        "starmap_mlp_last_error": (ctypes.c_char_p, [H]),
+        "starmap_mlp_get_params": (ctypes.c_int, [H, _fp, ctypes.c_size_t]),
+        "starmap_mlp_set_params": (ctypes.c_int, [H, _fp, ctypes.c_size_t]),
+        "starmap_mlp_forward": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+        "starmap_mlp_loss_grad": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+        "starmap_mlp_train_step": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_size_t, ctypes.c_float, ctypes.c_void_p]),
+        "starmap_mlp_steps": (ctypes.c_long, [H]),
+        "starmap_mlp_sync": (ctypes.c_int, [H]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -120,6 +139,20 @@ def lib():
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(_dp)
+
+
+def _addr(x) -> Optional[int]:
+    """Device address of a tensor-like (``data_ptr()``) or an int; None stays NULL."""
+    if x is None:
+        return None
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+
+def _params32(params) -> np.ndarray:
+    a = np.ascontiguousarray(params, dtype=np.float32).ravel()
+    if a.size != MLP_PARAMS:
+        raise ValueError(f"closure network needs {MLP_PARAMS} parameters, got {a.size}")
+    return a
 
 
 def host_matrices(system: int, N: int):
@@ -152,7 +185,7 @@ class Stepper:
 
     def __init__(self, N: int, ax, n, bc=("periodic", "periodic"), cn: float = 0.5,
                  precision: str = "fp64", system: str = "pn2d", schedule: str = "literal",
-                 kernel: str = "auto", dt: float = 0.0, stream: Optional[int] = None):
+                 kernel: str = "auto", dt: float = 0.0, stream: Optional[int] = None, closure: str = "none"):
         self._L = lib()
         c = Config()
         self._L.starmap_config_default(ctypes.byref(c))
@@ -169,6 +202,7 @@ class Stepper:
         c.schedule = {"literal": SCHEDULE_LITERAL, "merged": SCHEDULE_MERGED}[schedule]
         c.kernel = {"auto": KERNEL_AUTO, "gather": KERNEL_GATHER, "tiled": KERNEL_TILED}[kernel]
         c.cuda_stream = stream
+        c.closure = {"none": CLOSURE_NONE, "mlp8": CLOSURE_MLP8}[closure]
         h = ctypes.c_void_p()
         rc = self._L.starmap_create(ctypes.byref(c), ctypes.byref(h))
         if rc != OK:
@@ -321,6 +355,19 @@ class Stepper:
         buf = ctypes.create_string_buffer(data, len(data))
         self._check(self._L.starmap_set_state(self._h, buf, len(data)))
 
+    # -- learned closure -------------------------------------------------
+    def set_closure(self, params):
+        """Network of a closure handle from FP32 parameters (MLP_PARAMS values)."""
+        a = _params32(params)
+        self._check(self._L.starmap_set_closure(self._h, a.ctypes.data_as(_fp), a.size))
+
+    def closure_samples(self, X, scale, targets=None):
+        """Network inputs X [M, 38], scales [M] and (optionally) order-8
+        targets [M, 9] of the current state, written into caller-owned
+        device buffers (torch tensors or addresses), M = n_x * n_y."""
+        nx, ny, *_ = self.grid_info(0)
+        self._check(self._L.starmap_closure_samples(self._h, _addr(X), _addr(scale), _addr(targets), nx * ny))
+
     # -- convenience: load an input-module Problem ---------------------------
     @classmethod
     def from_problem(cls, problem, t_eval: float = 0.0, **over) -> "Stepper":
@@ -354,3 +401,80 @@ class Stepper:
             for j, f in problem.ic:
                 X, Y = self.grid_coords(self.moment_info(j)["grid"])
                 self.set_moment(j, np.broadcast_to(f(0.0, X, Y), X.shape))
+
+
+class Network:
+    """The closure network on the device (starmap_mlp_t): inference, loss
+    gradient and Adam training steps over caller-owned device buffers."""
+
+    def __init__(self, params, stream: Optional[int] = None):
+        self._L = lib()
+        a = _params32(params)
+        h = ctypes.c_void_p()
+        rc = self._L.starmap_mlp_create(a.ctypes.data_as(_fp), a.size, stream, ctypes.byref(h))
+        if rc != OK:
+            raise StarmapError(rc, self._L.starmap_mlp_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.starmap_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != OK:
+            raise StarmapError(rc, self._L.starmap_mlp_last_error(self._h).decode())
+
+    @property
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        self._check(self._L.starmap_mlp_get_params(self._h, out.ctypes.data_as(_fp), out.size))
+        return out
+
+    @params.setter
+    def params(self, p):
+        a = _params32(p)
+        self._check(self._L.starmap_mlp_set_params(self._h, a.ctypes.data_as(_fp), a.size))
+
+    @property
+    def steps(self) -> int:
+        return self._L.starmap_mlp_steps(self._h)
+
+    def forward(self, X, M: int, Y):
+        self._check(self._L.starmap_mlp_forward(self._h, _addr(X), int(M), _addr(Y)))
+
+    def loss_grad(self, X, T, B: int, grad, loss=None, idx=None):
+        self._check(self._L.starmap_mlp_loss_grad(self._h, _addr(X), _addr(T), _addr(idx), int(B), _addr(grad),
+                                                  _addr(loss)))
+
+    def train_step(self, X, T, B: int, lr: float, loss=None, idx=None):
+        self._check(self._L.starmap_mlp_train_step(self._h, _addr(X), _addr(T), _addr(idx), int(B), float(lr),
+                                                   _addr(loss)))
+
+    def sync(self):
+        self._check(self._L.starmap_mlp_sync(self._h))
+
+
+def params_from_dict(p) -> np.ndarray:
+    """Flatten {W1, b1, W2, b2, W3, b3} into the C ABI's parameter vector."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float32).ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+
+def params_to_dict(v) -> dict:
+    """Inverse of params_from_dict (float64 arrays)."""
+    v = np.asarray(v, dtype=np.float64)
+    shapes = [("W1", (MLP_HIDDEN, MLP_INPUTS)), ("b1", (MLP_HIDDEN,)), ("W2", (MLP_HIDDEN, MLP_HIDDEN)),
+              ("b2", (MLP_HIDDEN,)), ("W3", (MLP_OUTPUTS, MLP_HIDDEN)), ("b3", (MLP_OUTPUTS,))]
+    out, o = {}, 0
+    for k, shp in shapes:
+        n = int(np.prod(shp))
+        out[k] = v[o:o + n].reshape(shp).copy()
+        o += n
+    assert o == MLP_PARAMS
+    return out

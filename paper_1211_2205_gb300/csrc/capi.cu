@@ -10,6 +10,7 @@
 
 #include "host_math.h"
 #include "internal.h"
+#include "mlp.h"
 #include "tiled.h"
 #include "../../include/starmap.h"
 
@@ -58,6 +59,16 @@ struct starmap_s {
     bool ghosts_dirty = true;
     int kernel_used = STARMAP_KERNEL_GATHER;
     TiledPlan* tiled = nullptr;
+    // learned closure (STARMAP_CLOSURE_MLP8)
+    int closure = STARMAP_CLOSURE_NONE;
+    int nsys = 0;                          // order of the assembled system
+    std::vector<char> frozen;              // per component: left alone by the even passes
+    float* net_params = nullptr;           // FP32 parameters (device)
+    mlp::Packed* net = nullptr;            // BF16 packed network (device)
+    bool net_ready = false;
+    float* ctr = nullptr;                  // centre values of I_8 [9][n_x n_y]
+    float* lsig = nullptr;                 // log(1 + sigma_a), log(1 + sigma_s0) at the cell centres
+    bool lsig_dirty = true;
     std::string err;
 };
 
@@ -109,6 +120,7 @@ int build_tables(starmap_t* h) {
     for (int g = 0; g < 4; ++g) {
         h->tbeg[g] = (int)outs.size();
         for (int j : h->members[g]) {
+            if (h->frozen[j]) continue;
             GatherOut o{};
             GatherCoef<T> c{};
             o.grid = g;
@@ -153,7 +165,7 @@ int build_tables(starmap_t* h) {
     if (!ptrs.empty())
         CK(cudaMemcpy(h->src_ptrs_dev, ptrs.data(), ptrs.size() * sizeof(void*), cudaMemcpyHostToDevice), "upload sources");
     if (h->tiled) {
-        int rc = tiled_update(h->tiled, h->sys, h->comp_class, h->src_slot, h->src_dev, h->dx, h->dy);
+        int rc = tiled_update(h->tiled, h->sys, h->comp_class, h->src_slot, h->src_dev, h->frozen, h->dx, h->dy);
         if (rc) return fail(h, rc, tiled_error(h->tiled));
     }
     return STARMAP_OK;
@@ -258,9 +270,63 @@ int run_pass(starmap_t* h, bool odd, int which) {
     return STARMAP_OK;
 }
 
+// log(1 + sigma) of grid G11's material, FP32 on the device (network inputs).
+int ensure_lsig(starmap_t* h) {
+    const size_t M = (size_t)h->nxg[0] * h->nyg[0];
+    if (!h->lsig) CK(cudaMalloc(&h->lsig, std::max<size_t>(1, 2 * M) * sizeof(float)), "cudaMalloc closure inputs");
+    if (!h->lsig_dirty) return STARMAP_OK;
+    std::vector<float> buf(2 * M);
+    for (size_t i = 0; i < M; ++i) {
+        buf[i] = (float)std::log1p(h->sig_a[0][i]);
+        buf[M + i] = (float)std::log1p(h->sig_s[0][i]);
+    }
+    CK(cudaMemcpyAsync(h->lsig, buf.data(), buf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream),
+       "upload closure inputs");
+    CK(cudaStreamSynchronize(h->stream), "upload closure inputs");
+    h->lsig_dirty = false;
+    return STARMAP_OK;
+}
+
+template <class T>
+mlp::ClosureArgs<T> closure_args(const starmap_t* h) {
+    mlp::ClosureArgs<T> a;
+    for (int g = 0; g < 4; ++g) a.g[g] = grid_dev<T>(h, g);
+    a.pitch = h->pitch;
+    a.p[0] = h->p[0];
+    a.p[1] = h->p[1];
+    a.nx = h->nxg[0];
+    a.ny = h->nyg[0];
+    for (int j = 0; j < mlp::NMOM + mlp::NOUT; ++j)
+        a.slot[j] = j < h->ncomp ? make_int2(h->sys.moms[j].grid, h->sys.moms[j].local) : make_int2(0, 0);
+    const size_t M = (size_t)a.nx * a.ny;
+    a.lsa = h->lsig;
+    a.lss = h->lsig + M;
+    return a;
+}
+
+// Network prediction of the order-8 moments from the current state.
+template <class T>
+int run_closure(starmap_t* h) {
+    if (!h->net_ready) return fail(h, STARMAP_E_STATE, "closure handle stepped before starmap_set_closure");
+    int rc = ensure_lsig(h);
+    if (rc) return rc;
+    const size_t M = (size_t)h->nxg[0] * h->nyg[0];
+    if (!h->ctr) CK(cudaMalloc(&h->ctr, std::max<size_t>(1, (size_t)mlp::NOUT * M) * sizeof(float)), "cudaMalloc closure scratch");
+    if (mlp::closure<T>(closure_args<T>(h), h->net, h->ctr, h->stream)) return cuda_fail(h, cudaGetLastError(), "closure");
+    return STARMAP_OK;
+}
+
+// Odd pass, preceded by the closure where there is one.
+template <class T>
+int odd_pass(starmap_t* h, int which) {
+    if (h->closure) { int rc = run_closure<T>(h); if (rc) return rc; }
+    return run_pass<T>(h, true, which);
+}
+
 template <class T>
 int do_steps(starmap_t* h, long n) {
     if (n <= 0) return STARMAP_OK;
+    if (h->closure && !h->net_ready) return fail(h, STARMAP_E_STATE, "closure handle stepped before starmap_set_closure");
     if (h->ghosts_dirty) { int rc = fill_ghosts_all<T>(h); if (rc) return rc; }
     int rc;
     if (h->cfg.schedule == STARMAP_SCHEDULE_MERGED) {
@@ -271,9 +337,9 @@ int do_steps(starmap_t* h, long n) {
         }
     } else {
         for (long i = 0; i < n; ++i) {
-            if ((rc = run_pass<T>(h, true, 0))) return rc;
+            if ((rc = odd_pass<T>(h, 0))) return rc;
             if ((rc = run_pass<T>(h, false, 1))) return rc;
-            if ((rc = run_pass<T>(h, true, 0))) return rc;
+            if ((rc = odd_pass<T>(h, 0))) return rc;
         }
     }
     h->t += n * h->dt;
@@ -342,6 +408,10 @@ void release(starmap_t* h) {
     if (h->coefs_dev) cudaFree(h->coefs_dev);
     if (h->partials) cudaFree(h->partials);
     if (h->result) cudaFree(h->result);
+    if (h->net_params) cudaFree(h->net_params);
+    if (h->net) cudaFree(h->net);
+    if (h->ctr) cudaFree(h->ctr);
+    if (h->lsig) cudaFree(h->lsig);
     if (h->tiled) tiled_destroy(h->tiled);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -364,6 +434,7 @@ void starmap_config_default(starmap_config* c) {
     c->schedule = STARMAP_SCHEDULE_LITERAL;
     c->kernel = STARMAP_KERNEL_AUTO;
     c->cuda_stream = nullptr;
+    c->closure = STARMAP_CLOSURE_NONE;
 }
 
 int starmap_host_matrices(int system, int N, int cap, double* Mx, double* My, int* grid, int* order,
@@ -408,13 +479,26 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
     if (c.schedule != STARMAP_SCHEDULE_LITERAL && c.schedule != STARMAP_SCHEDULE_MERGED)
         return fail(nullptr, STARMAP_E_ARG, "unknown schedule");
     if (c.kernel < STARMAP_KERNEL_AUTO || c.kernel > STARMAP_KERNEL_TILED) return fail(nullptr, STARMAP_E_ARG, "unknown kernel");
+    if (c.closure != STARMAP_CLOSURE_NONE && c.closure != STARMAP_CLOSURE_MLP8)
+        return fail(nullptr, STARMAP_E_ARG, "unknown closure");
+    if (c.closure == STARMAP_CLOSURE_MLP8) {
+        if (c.system != STARMAP_PN2D || c.N != 7)
+            return fail(nullptr, STARMAP_E_UNSUPPORTED, "the learned closure is defined for the 2D system with N = 7");
+        if (c.schedule != STARMAP_SCHEDULE_LITERAL)
+            return fail(nullptr, STARMAP_E_ARG, "the learned closure needs the literal schedule");
+    }
 
     starmap_t* h = new (std::nothrow) starmap_t();
     if (!h) return fail(nullptr, STARMAP_E_NOMEM, "host allocation failed");
     h->cfg = c;
+    h->closure = c.closure;
+    h->nsys = c.closure == STARMAP_CLOSURE_MLP8 ? 8 : c.N;
     std::string err;
-    if (!build_system(c.system, c.N, h->sys, err)) { delete h; return fail(nullptr, STARMAP_E_ARG, err); }
+    if (!build_system(c.system, h->nsys, h->sys, err)) { delete h; return fail(nullptr, STARMAP_E_ARG, err); }
     h->ncomp = h->sys.ncomp;
+    h->frozen.assign(h->ncomp, 0);
+    if (h->closure)
+        for (int j = 0; j < h->ncomp; ++j) h->frozen[j] = h->sys.moms[j].l == h->nsys;
     h->dx = (c.ax[1] - c.ax[0]) / c.n[0];
     h->dy = (c.ax[3] - c.ax[2]) / c.n[1];
     for (int d = 0; d < 2; ++d) h->p[d] = c.bc[d] == STARMAP_PERIODIC ? 1 : 0;
@@ -457,7 +541,7 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
         h->sig_s[g].assign(plane, 0.0);
     }
     // kernel choice
-    bool tiled_ok = tiled_supported(c.system, c.N, c.precision);
+    bool tiled_ok = tiled_supported(c.system, h->nsys, c.precision);
     if (c.kernel == STARMAP_KERNEL_TILED && !tiled_ok) {
         delete h;
         return fail(nullptr, STARMAP_E_UNSUPPORTED, "tiled kernel needs FP32, the 2D P_N system, N <= 63 and TMA support");
@@ -495,7 +579,7 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
             geo.base[g] = h->base[g]; geo.cstride[g] = h->cstride[g];
             geo.nx[g] = h->nxg[g]; geo.ny[g] = h->nyg[g]; geo.K[g] = h->Kg[g];
         }
-        geo.pitch = h->pitch; geo.rows = h->rows; geo.p[0] = h->p[0]; geo.p[1] = h->p[1]; geo.N = c.N;
+        geo.pitch = h->pitch; geo.rows = h->rows; geo.p[0] = h->p[0]; geo.p[1] = h->p[1]; geo.N = h->nsys;
         int rc = tiled_create(geo, &h->tiled);
         if (rc) { std::string m = h->tiled ? tiled_error(h->tiled) : "tiled kernel setup failed"; return bail(fail(h, rc, m)); }
     }
@@ -569,6 +653,7 @@ int starmap_set_material(starmap_t* h, int g, const double* sigma_a, const doubl
     CK(cudaStreamSynchronize(h->stream), "set_material");
     h->sig_a[g].assign(sigma_a, sigma_a + plane);
     h->sig_s[g].assign(sigma_s0, sigma_s0 + plane);
+    if (g == 0) h->lsig_dirty = true;
     int rc = ensure_coef_alloc(h);
     if (rc) return rc;
     rc = h->fp32 ? upload_coefficients<float>(h, g) : upload_coefficients<double>(h, g);
@@ -584,9 +669,10 @@ int starmap_set_scattering_factors(starmap_t* h, const double* factor, int count
         h->sl_factor.clear();
         h->nclasses = 2;
     } else {
-        if (count != h->cfg.N + 1) return fail(h, STARMAP_E_ARG, "factor must have N+1 entries");
+        if (count != h->nsys + 1)
+            return fail(h, STARMAP_E_ARG, "factor must have one entry per order of the system (N+1; 9 with the closure)");
         h->sl_factor.assign(factor, factor + count);
-        h->nclasses = h->cfg.N + 1;
+        h->nclasses = h->nsys + 1;
     }
     for (int j = 0; j < h->ncomp; ++j) h->comp_class[j] = class_of(h, h->sys.moms[j].l);
     int rc = upload_all_coefficients(h);
@@ -598,6 +684,7 @@ int starmap_set_scattering_factors(starmap_t* h, const double* factor, int count
 int starmap_set_source(starmap_t* h, int j, const double* q, size_t count) {
     int rc = check_j(h, j);
     if (rc) return rc;
+    if (h->frozen[j] && q) return fail(h, STARMAP_E_ARG, "the order-8 components of the closure take no source");
     CK(cudaStreamSynchronize(h->stream), "set_source");
     size_t np = comp_points(h, j);
     if (!q) {
@@ -680,12 +767,14 @@ int starmap_pass(starmap_t* h, int parity, int which) {
     if (!h) return STARMAP_E_ARG;
     if ((parity != 0 && parity != 1) || (which != 0 && which != 1)) return fail(h, STARMAP_E_ARG, "parity and which must be 0 or 1");
     h->have_output = false;
+    if (h->closure && parity == 1 && !h->net_ready)
+        return fail(h, STARMAP_E_STATE, "closure handle stepped before starmap_set_closure");
     if (h->fp32) {
         if (h->ghosts_dirty) { int rc = fill_ghosts_all<float>(h); if (rc) return rc; }
-        return run_pass<float>(h, parity == 1, which);
+        return parity == 1 ? odd_pass<float>(h, which) : run_pass<float>(h, false, which);
     }
     if (h->ghosts_dirty) { int rc = fill_ghosts_all<double>(h); if (rc) return rc; }
-    return run_pass<double>(h, parity == 1, which);
+    return parity == 1 ? odd_pass<double>(h, which) : run_pass<double>(h, false, which);
 }
 
 int starmap_advance_to(starmap_t* h, double t_out) {
@@ -844,6 +933,40 @@ int starmap_sync(starmap_t* h) {
     if (!h) return STARMAP_E_ARG;
     CK(cudaStreamSynchronize(h->stream), "sync");
     return poll_kernel(h);
+}
+
+int starmap_set_closure(starmap_t* h, const float* params, size_t count) {
+    if (!h) return STARMAP_E_ARG;
+    if (!h->closure) return fail(h, STARMAP_E_STATE, "handle was created without a closure");
+    if (!params || count != (size_t)mlp::NPARAM) return fail(h, STARMAP_E_ARG, "closure needs STARMAP_MLP_PARAMS floats");
+    for (size_t i = 0; i < count; ++i)
+        if (!std::isfinite(params[i])) return fail(h, STARMAP_E_NONFINITE, "closure parameters contain NaN or Inf");
+    if (!h->net_params) CK(cudaMalloc(&h->net_params, (size_t)mlp::NPARAM * sizeof(float)), "cudaMalloc closure");
+    if (!h->net) CK(cudaMalloc(&h->net, sizeof(mlp::Packed)), "cudaMalloc closure");
+    CK(cudaMemcpyAsync(h->net_params, params, count * sizeof(float), cudaMemcpyHostToDevice, h->stream), "upload closure");
+    if (mlp::pack(h->net_params, h->net, h->stream)) return cuda_fail(h, cudaGetLastError(), "pack closure");
+    CK(cudaStreamSynchronize(h->stream), "set_closure");
+    h->net_ready = true;
+    return STARMAP_OK;
+}
+
+int starmap_closure_samples(starmap_t* h, float* X, float* scale, float* targets, size_t count) {
+    if (!h) return STARMAP_E_ARG;
+    if (h->cfg.system != STARMAP_PN2D || h->nsys < 7)
+        return fail(h, STARMAP_E_UNSUPPORTED, "closure samples need the 2D system with N >= 7");
+    if (targets && h->nsys < 8) return fail(h, STARMAP_E_UNSUPPORTED, "order-8 targets need N >= 8");
+    const size_t M = (size_t)h->nxg[0] * h->nyg[0];
+    if (!X || !scale || count != M) return fail(h, STARMAP_E_ARG, "samples need X, scale and count = n_x * n_y");
+    if (h->ghosts_dirty) {
+        int rc = h->fp32 ? fill_ghosts_all<float>(h) : fill_ghosts_all<double>(h);
+        if (rc) return rc;
+    }
+    int rc = ensure_lsig(h);
+    if (rc) return rc;
+    rc = h->fp32 ? mlp::samples<float>(closure_args<float>(h), X, scale, targets, h->stream)
+                 : mlp::samples<double>(closure_args<double>(h), X, scale, targets, h->stream);
+    if (rc) return cuda_fail(h, cudaGetLastError(), "closure samples");
+    return STARMAP_OK;
 }
 
 }  // extern "C"

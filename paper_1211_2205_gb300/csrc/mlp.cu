@@ -1,0 +1,683 @@
+// Learned order-8 closure: the per-cell perceptron 38 -> 128 -> 128 -> 9
+// (tanh hidden layers) on the tensor cores (BF16 operands, FP32
+// accumulation), its training kernels, and its use inside the step.
+//
+// Network input at a cell centre: the 36 moments of order <= 7 averaged to
+// the centre from their own staggered grid, divided by their RMS s, then
+// log(1 + sigma_a), log(1 + sigma_s0).  Output y (9 values) times s gives the
+// order-8 moments R_8^{8,6,4,2,0}, I_8^{8,6,4,2} at the centre; R_8^m are
+// written at the cell centres (grid G11), I_8^m at the points of G22 as the
+// mean of the four surrounding centres.  The closed system is the P_8 system
+// of section 3 with the order-8 components frozen in the even passes and set
+// by the network before every odd half-step, so the order-7 rows see
+// predicted order-8 moments instead of the zero of the P_7 truncation.
+//
+// Tiles: one CTA of 8 warps handles 128 samples at a time; warp w owns rows
+// 16w..16w+15 through all three layers (mma.sync m16n8k16, fragments by
+// ldmatrix from padded shared-memory rows, so no bank conflicts).  Hidden
+// activations are kept in BF16 in shared memory; the weights stay resident
+// in shared memory for the CTA's whole (persistent) loop.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+#include "mlp.h"
+
+namespace starmap {
+namespace mlp {
+
+namespace {
+
+constexpr int ROWS = 128;          // samples per tile
+constexpr int WARPS = 8;           // 16 samples per warp
+constexpr int THREADS = WARPS * 32;
+constexpr int KX = 48;             // input width rounded up to the mma k (16)
+constexpr int LDO = 24;            // padded row of dY (16 used)
+
+struct Smem {
+    Packed w;
+    __nv_bfloat16 X[ROWS * LDX];
+    __nv_bfloat16 H1[ROWS * LDH];
+    __nv_bfloat16 H2[ROWS * LDH];
+};
+// backward buffers behind Smem (training kernel only)
+struct SmemBack {
+    __nv_bfloat16 dY[ROWS * LDO];
+    __nv_bfloat16 dZ2[ROWS * LDH];
+    __nv_bfloat16 dZ1[ROWS * LDH];
+    float wloss[WARPS];
+};
+static_assert(sizeof(Packed) % 16 == 0, "packed weights must keep 16-byte rows");
+static_assert(sizeof(Smem) % 16 == 0, "shared layout must keep 16-byte rows");
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(su32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(su32(p)));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t (&r)[2], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(su32(p)));
+}
+// D += A (16x16 bf16, row-major) * B (16x8 bf16, column-major), FP32 accumulate
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// A fragment: 16x16 tile at (r0, c0) of a row-major matrix
+__device__ __forceinline__ void frag_a(uint32_t (&a)[4], const __nv_bfloat16* M, int ld, int r0, int c0, int lane) {
+    ldsm_x4(a, M + (r0 + (lane & 15)) * ld + c0 + (lane >> 4) * 8);
+}
+// B fragments of the two 8-column tiles n0, n0 + 8 at k0, from a matrix
+// stored [n][k] (a weight matrix [out][in]): b[0..1] tile n0, b[2..3] tile n0 + 8
+__device__ __forceinline__ void frag_b_nk(uint32_t (&b)[4], const __nv_bfloat16* W, int ld, int n0, int k0, int lane) {
+    const int n = n0 + (lane & 7) + ((lane >> 4) << 3);
+    const int k = k0 + ((lane >> 3) & 1) * 8;
+    ldsm_x4(b, W + n * ld + k);
+}
+// B fragment of one 8-column tile from a matrix stored [k][n]
+__device__ __forceinline__ void frag_b_kn(uint32_t (&b)[2], const __nv_bfloat16* M, int ld, int k0, int n0, int lane) {
+    const int k = k0 + (lane & 7) + ((lane >> 3) & 1) * 8;
+    ldsm_x2_t(b, M + k * ld + n0);
+}
+// A fragment of the tile (m0, k0) of A = S^T, S stored [k][m]
+__device__ __forceinline__ void frag_a_t(uint32_t (&a)[4], const __nv_bfloat16* S, int ld, int m0, int k0, int lane) {
+    const int k = k0 + (lane & 7) + ((lane >> 4) << 3);
+    const int m = m0 + ((lane >> 3) & 1) * 8;
+    ldsm_x4_t(a, S + k * ld + m);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ void load_weights(Packed& dst, const Packed* src) {
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(Packed) / 16); i += blockDim.x) d[i] = s[i];
+}
+
+// Hidden layer of this warp's 16 rows: Hout = tanh(A W^T + b), 128 outputs.
+__device__ void dense_tanh(const __nv_bfloat16* A, int lda, int kdim, const __nv_bfloat16* W, int ldw,
+                           const float* bias, __nv_bfloat16* Hout, int warp, int lane) {
+    const int r0 = warp * 16;
+    const int g = lane >> 2, tg = lane & 3;
+#pragma unroll 1
+    for (int nb = 0; nb < HID; nb += 32) {
+        float acc[4][4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+#pragma unroll 2
+        for (int k0 = 0; k0 < kdim; k0 += 16) {
+            uint32_t a[4], b01[4], b23[4];
+            frag_a(a, A, lda, r0, k0, lane);
+            frag_b_nk(b01, W, ldw, nb, k0, lane);
+            frag_b_nk(b23, W, ldw, nb + 16, k0, lane);
+            mma16816(acc[0], a, b01[0], b01[1]);
+            mma16816(acc[1], a, b01[2], b01[3]);
+            mma16816(acc[2], a, b23[0], b23[1]);
+            mma16816(acc[3], a, b23[2], b23[3]);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int c = nb + t * 8 + 2 * tg;
+            const float bl = bias[c], bh = bias[c + 1];
+            *reinterpret_cast<uint32_t*>(Hout + (r0 + g) * LDH + c) =
+                pack_bf16(tanhf(acc[t][0] + bl), tanhf(acc[t][1] + bh));
+            *reinterpret_cast<uint32_t*>(Hout + (r0 + g + 8) * LDH + c) =
+                pack_bf16(tanhf(acc[t][2] + bl), tanhf(acc[t][3] + bh));
+        }
+    }
+}
+
+// Output layer of this warp's rows: y = H2 W3^T + b3 in registers.  y[t][e]:
+// tile t (columns 8t..8t+7), e = 0,1 row g columns 2tg, 2tg+1; e = 2,3 row g+8.
+__device__ void dense_out(const Smem& S, int warp, int lane, float (&y)[2][4]) {
+    const int r0 = warp * 16;
+    const int tg = lane & 3;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) y[t][0] = y[t][1] = y[t][2] = y[t][3] = 0.f;
+#pragma unroll 2
+    for (int k0 = 0; k0 < HID; k0 += 16) {
+        uint32_t a[4], b[4];
+        frag_a(a, S.H2, LDH, r0, k0, lane);
+        frag_b_nk(b, S.w.W3, LDH, 0, k0, lane);
+        mma16816(y[0], a, b[0], b[1]);
+        mma16816(y[1], a, b[2], b[3]);
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int c = t * 8 + 2 * tg;
+        y[t][0] += S.w.b3[c]; y[t][1] += S.w.b3[c + 1];
+        y[t][2] += S.w.b3[c]; y[t][3] += S.w.b3[c + 1];
+    }
+}
+
+// The three layers of one tile whose inputs sit in S.X.
+__device__ __forceinline__ void network(Smem& S, int warp, int lane, float (&y)[2][4]) {
+    dense_tanh(S.X, LDX, KX, S.w.W1, LDX, S.w.b1, S.H1, warp, lane);
+    __syncwarp();
+    dense_tanh(S.H1, LDH, HID, S.w.W2, LDH, S.w.b2, S.H2, warp, lane);
+    __syncwarp();
+    dense_out(S, warp, lane, y);
+}
+
+// Stage rows row0.. of X (FP32 [M][38]) into S.X as BF16, zero-padded.
+__device__ void stage_inputs(Smem& S, const float* __restrict__ X, const int* __restrict__ idx, long row0, long M) {
+    for (int i = threadIdx.x; i < ROWS * LDX; i += THREADS) {
+        const int r = i / LDX, c = i % LDX;
+        const long m = row0 + r;
+        float v = 0.f;
+        if (m < M && c < NIN) {
+            const long src = idx ? (long)idx[m] : m;
+            v = X[src * NIN + c];
+        }
+        S.X[i] = __float2bfloat16_rn(v);
+    }
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
+__global__ void __launch_bounds__(THREADS) k_forward(const float* __restrict__ X, long M, const Packed* __restrict__ P,
+                                                     float* __restrict__ Y) {
+    extern __shared__ __align__(128) unsigned char raw[];
+    Smem& S = *reinterpret_cast<Smem*>(raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tg = lane & 3;
+    load_weights(S.w, P);
+    const long tiles = (M + ROWS - 1) / ROWS;
+    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long row0 = tile * ROWS;
+        stage_inputs(S, X, nullptr, row0, M);
+        __syncthreads();
+        float y[2][4];
+        network(S, warp, lane, y);
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const long m = row0 + warp * 16 + g + 8 * (e >> 1);
+                const int c = t * 8 + 2 * tg + (e & 1);
+                if (m < M && c < NOUT) Y[m * NOUT + c] = y[t][e];
+            }
+        __syncthreads();
+    }
+}
+
+// Loss sum_{s,o} (y - t)^2 / (B 9) and its gradient over one tile of 128
+// samples; the CTA writes its partial sums to part[blockIdx.x][NPARAM + 1].
+__global__ void __launch_bounds__(THREADS) k_loss_grad(const float* __restrict__ X, const float* __restrict__ T,
+                                                       const int* __restrict__ idx, long B,
+                                                       const Packed* __restrict__ P, float* __restrict__ part) {
+    extern __shared__ __align__(128) unsigned char raw[];
+    Smem& S = *reinterpret_cast<Smem*>(raw);
+    SmemBack& D = *reinterpret_cast<SmemBack*>(raw + sizeof(Smem));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tg = lane & 3;
+    const int r0 = warp * 16;
+    float* out = part + (long)blockIdx.x * (NPARAM + 1);
+    load_weights(S.w, P);
+    const long row0 = (long)blockIdx.x * ROWS;
+    stage_inputs(S, X, idx, row0, B);
+    __syncthreads();
+    float y[2][4];
+    network(S, warp, lane, y);
+    // dY = 2 (y - t) / (B 9) on valid samples and outputs, else 0
+    const float inv = 2.f / (float)(B * NOUT);
+    float lsum = 0.f;
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = r0 + g + 8 * h;
+            const long m = row0 + r;
+            float d[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int c = t * 8 + 2 * tg + e;
+                float v = 0.f;
+                if (m < B && c < NOUT) {
+                    const long src = idx ? (long)idx[m] : m;
+                    const float rr = y[t][2 * h + e] - T[src * NOUT + c];
+                    lsum += rr * rr;
+                    v = inv * rr;
+                }
+                d[e] = v;
+            }
+            *reinterpret_cast<uint32_t*>(D.dY + r * LDO + t * 8 + 2 * tg) = pack_bf16(d[0], d[1]);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) D.wloss[warp] = lsum / (float)(B * NOUT);
+    __syncwarp();
+    // dZ2 = (dY W3) * (1 - H2^2), K = 16 outputs (9 used)
+    {
+        uint32_t a[4];
+        frag_a(a, D.dY, LDO, r0, 0, lane);
+#pragma unroll 4
+        for (int nb = 0; nb < HID; nb += 8) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            uint32_t b[2];
+            frag_b_kn(b, S.w.W3, LDH, 0, nb, lane);
+            mma16816(acc, a, b[0], b[1]);
+            const int c = nb + 2 * tg;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + g + 8 * h;
+                const float h0 = __bfloat162float(S.H2[r * LDH + c]), h1 = __bfloat162float(S.H2[r * LDH + c + 1]);
+                *reinterpret_cast<uint32_t*>(D.dZ2 + r * LDH + c) =
+                    pack_bf16(acc[2 * h] * (1.f - h0 * h0), acc[2 * h + 1] * (1.f - h1 * h1));
+            }
+        }
+    }
+    __syncwarp();
+    // dZ1 = (dZ2 W2) * (1 - H1^2), K = 128
+    {
+#pragma unroll 1
+        for (int nb = 0; nb < HID; nb += 8) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+            for (int k0 = 0; k0 < HID; k0 += 16) {
+                uint32_t a[4], b[2];
+                frag_a(a, D.dZ2, LDH, r0, k0, lane);
+                frag_b_kn(b, S.w.W2, LDH, k0, nb, lane);
+                mma16816(acc, a, b[0], b[1]);
+            }
+            const int c = nb + 2 * tg;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + g + 8 * h;
+                const float h0 = __bfloat162float(S.H1[r * LDH + c]), h1 = __bfloat162float(S.H1[r * LDH + c + 1]);
+                *reinterpret_cast<uint32_t*>(D.dZ1 + r * LDH + c) =
+                    pack_bf16(acc[2 * h] * (1.f - h0 * h0), acc[2 * h + 1] * (1.f - h1 * h1));
+            }
+        }
+    }
+    __syncthreads();
+    // weight gradients over the tile's samples (K = 128): warp w owns rows
+    // 16w..16w+15 of dW2 and dW1; warp 0 also the rows of dW3.
+    {
+        const int m0 = r0;
+#pragma unroll 1
+        for (int nb = 0; nb < HID; nb += 8) {               // dW2[o][i] = sum_s dZ2[s][o] H1[s][i]
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+            for (int k0 = 0; k0 < ROWS; k0 += 16) {
+                uint32_t a[4], b[2];
+                frag_a_t(a, D.dZ2, LDH, m0, k0, lane);
+                frag_b_kn(b, S.H1, LDH, k0, nb, lane);
+                mma16816(acc, a, b[0], b[1]);
+            }
+            float* o = out + OFF_W2;
+            const int c = nb + 2 * tg;
+            o[(m0 + g) * HID + c] = acc[0];
+            o[(m0 + g) * HID + c + 1] = acc[1];
+            o[(m0 + g + 8) * HID + c] = acc[2];
+            o[(m0 + g + 8) * HID + c + 1] = acc[3];
+        }
+#pragma unroll 1
+        for (int nb = 0; nb < KX; nb += 8) {                // dW1[o][i] = sum_s dZ1[s][o] X[s][i]
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+            for (int k0 = 0; k0 < ROWS; k0 += 16) {
+                uint32_t a[4], b[2];
+                frag_a_t(a, D.dZ1, LDH, m0, k0, lane);
+                frag_b_kn(b, S.X, LDX, k0, nb, lane);
+                mma16816(acc, a, b[0], b[1]);
+            }
+            float* o = out + OFF_W1;
+            const int c = nb + 2 * tg;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (c + (e & 1) < NIN) o[(m0 + g + 8 * (e >> 1)) * NIN + c + (e & 1)] = acc[e];
+        }
+        if (warp == 0) {
+#pragma unroll 1
+            for (int nb = 0; nb < HID; nb += 8) {           // dW3[o][i] = sum_s dY[s][o] H2[s][i]
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+                for (int k0 = 0; k0 < ROWS; k0 += 16) {
+                    uint32_t a[4], b[2];
+                    frag_a_t(a, D.dY, LDO, 0, k0, lane);
+                    frag_b_kn(b, S.H2, LDH, k0, nb, lane);
+                    mma16816(acc, a, b[0], b[1]);
+                }
+                float* o = out + OFF_W3;
+                const int c = nb + 2 * tg;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int row = g + 8 * (e >> 1);
+                    if (row < NOUT) o[row * HID + c + (e & 1)] = acc[e];
+                }
+            }
+        }
+    }
+    // bias gradients: column sums of dZ1, dZ2, dY over the tile
+    for (int c = threadIdx.x; c < HID; c += THREADS) {
+        float s1 = 0.f, s2 = 0.f;
+        for (int r = 0; r < ROWS; ++r) {
+            s1 += __bfloat162float(D.dZ1[r * LDH + c]);
+            s2 += __bfloat162float(D.dZ2[r * LDH + c]);
+        }
+        out[OFF_B1 + c] = s1;
+        out[OFF_B2 + c] = s2;
+    }
+    if (threadIdx.x < NOUT) {
+        float s3 = 0.f;
+        for (int r = 0; r < ROWS; ++r) s3 += __bfloat162float(D.dY[r * LDO + threadIdx.x]);
+        out[OFF_B3 + threadIdx.x] = s3;
+    }
+    if (threadIdx.x == 0) {
+        float l = 0.f;
+        for (int w = 0; w < WARPS; ++w) l += D.wloss[w];
+        out[NPARAM] = l;
+    }
+}
+
+// grad[i] = sum over CTAs of part[cta][i], i <= NPARAM (the last entry is the loss)
+__global__ void k_reduce_grad(const float* __restrict__ part, long nblk, float* __restrict__ grad,
+                              float* __restrict__ loss) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= NPARAM; i += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (long b = 0; b < nblk; ++b) s += part[b * (NPARAM + 1) + i];
+        if (i < NPARAM) grad[i] = s;
+        else if (loss) *loss = s;
+    }
+}
+
+// Adam (Kingma & Ba, 2015) on the FP32 master parameters; c1, c2 are the
+// bias corrections 1 - beta^t.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// FP32 parameters -> BF16 weights in the padded layout, FP32 biases.
+__global__ void k_pack(const float* __restrict__ params, Packed* __restrict__ P) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = tid; i < HID * LDX; i += stride) {
+        const int o = i / LDX, c = i % LDX;
+        P->W1[i] = __float2bfloat16_rn(c < NIN ? params[OFF_W1 + o * NIN + c] : 0.f);
+    }
+    for (int i = tid; i < HID * LDH; i += stride) {
+        const int o = i / LDH, c = i % LDH;
+        P->W2[i] = __float2bfloat16_rn(c < HID ? params[OFF_W2 + o * HID + c] : 0.f);
+    }
+    for (int i = tid; i < OUTP * LDH; i += stride) {
+        const int o = i / LDH, c = i % LDH;
+        P->W3[i] = __float2bfloat16_rn(o < NOUT && c < HID ? params[OFF_W3 + o * HID + c] : 0.f);
+    }
+    for (int i = tid; i < HID; i += stride) { P->b1[i] = params[OFF_B1 + i]; P->b2[i] = params[OFF_B2 + i]; }
+    for (int i = tid; i < OUTP; i += stride) P->b3[i] = i < NOUT ? params[OFF_B3 + i] : 0.f;
+}
+
+// ------------------------------------------------------------ closure glue
+// Component (grid g, local k) averaged to cell centre (ix, iy): a node axis
+// takes the mean of the nodes k - p and k - p + 1 around cell k (node -1 is
+// the periodic ghost), a cell axis the value itself.
+template <class T>
+__device__ __forceinline__ float centre_value(const ClosureArgs<T>& A, int g, int k, int ix, int iy) {
+    const T* c = A.g[g].base + (long)k * A.g[g].cstride;
+    const long P = A.pitch;
+    const bool xn = g & 1, yn = g & 2;
+    const int xl = xn ? ix - A.p[0] : ix, yl = yn ? iy - A.p[1] : iy;
+    float v = (float)c[(long)(yl + 1) * P + xl];
+    if (xn) v += (float)c[(long)(yl + 1) * P + xl + 1];
+    if (yn) v += (float)c[(long)(yl + 2) * P + xl];
+    if (xn && yn) v += (float)c[(long)(yl + 2) * P + xl + 1];
+    return v * ((xn ? 0.5f : 1.f) * (yn ? 0.5f : 1.f));
+}
+
+// Features of cell m = iy * nx + ix and the RMS scale of its moments.
+template <class T>
+__device__ __forceinline__ void cell_features(const ClosureArgs<T>& A, long m, float (&f)[NIN], float& scale) {
+    const int ix = (int)(m % A.nx), iy = (int)(m / A.nx);
+    float ss = 0.f;
+#pragma unroll
+    for (int j = 0; j < NMOM; ++j) {
+        const float v = centre_value(A, A.slot[j].x, A.slot[j].y, ix, iy);
+        f[j] = v;
+        ss += v * v;
+    }
+    scale = sqrtf(ss / (float)NMOM) + 1e-30f;
+    const float inv = 1.f / scale;
+#pragma unroll
+    for (int j = 0; j < NMOM; ++j) f[j] *= inv;
+    f[NMOM] = A.lsa[m];
+    f[NMOM + 1] = A.lss[m];
+}
+
+template <class T>
+__global__ void __launch_bounds__(THREADS) k_samples(const ClosureArgs<T> A, float* __restrict__ X,
+                                                     float* __restrict__ scale, float* __restrict__ tgt) {
+    const long M = (long)A.nx * A.ny;
+    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+        float f[NIN], s;
+        cell_features(A, m, f, s);
+#pragma unroll
+        for (int c = 0; c < NIN; ++c) X[m * NIN + c] = f[c];
+        scale[m] = s;
+        if (tgt) {
+            const int ix = (int)(m % A.nx), iy = (int)(m / A.nx);
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o)
+                tgt[m * NOUT + o] = centre_value(A, A.slot[NMOM + o].x, A.slot[NMOM + o].y, ix, iy);
+        }
+    }
+}
+
+// Fused closure evaluation over all cells: features -> network -> s * y.
+// R_8^m go straight to G11 (with their ghost copies); the centre values of
+// I_8^m go to ctr[o][M] for the node averaging of k_closure_nodes.
+template <class T>
+__global__ void __launch_bounds__(THREADS) k_closure(const ClosureArgs<T> A, const Packed* __restrict__ P,
+                                                     float* __restrict__ ctr) {
+    extern __shared__ __align__(128) unsigned char raw[];
+    Smem& S = *reinterpret_cast<Smem*>(raw);
+    float* s_scale = reinterpret_cast<float*>(raw + sizeof(Smem));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tg = lane & 3;
+    load_weights(S.w, P);
+    const long M = (long)A.nx * A.ny;
+    const long tiles = (M + ROWS - 1) / ROWS;
+    const long Pp = A.pitch;
+    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long row0 = tile * ROWS;
+        if (threadIdx.x < ROWS) {
+            const int r = threadIdx.x;
+            const long m = row0 + r;
+            float f[NIN], s = 1.f;
+            if (m < M) {
+                cell_features(A, m, f, s);
+            } else {
+#pragma unroll
+                for (int c = 0; c < NIN; ++c) f[c] = 0.f;
+            }
+            uint32_t* row = reinterpret_cast<uint32_t*>(S.X + r * LDX);
+#pragma unroll
+            for (int c = 0; c < LDX / 2; ++c)
+                row[c] = pack_bf16(2 * c < NIN ? f[2 * c] : 0.f, 2 * c + 1 < NIN ? f[2 * c + 1] : 0.f);
+            s_scale[r] = s;
+        }
+        __syncthreads();
+        float y[2][4];
+        network(S, warp, lane, y);
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = warp * 16 + g + 8 * (e >> 1);
+                const long m = row0 + r;
+                const int o = t * 8 + 2 * tg + (e & 1);
+                if (m >= M || o >= NOUT) continue;
+                const float v = s_scale[r] * y[t][e];
+                if (A.slot[NMOM + o].x != 0) { ctr[(long)o * M + m] = v; continue; }
+                const int ix = (int)(m % A.nx), iy = (int)(m / A.nx);
+                const int n = A.nx, ny = A.ny;
+                T* c = A.g[0].base + (long)A.slot[NMOM + o].y * A.g[0].cstride;
+                const T tv = (T)v;
+                c[(long)(iy + 1) * Pp + ix] = tv;
+                // ghost copies: periodic -1 <- n-1, n <- 0; extrapolation -1 <- 0, n <- n-1
+                if (ix == (A.p[0] ? n - 1 : 0)) c[(long)(iy + 1) * Pp - 1] = tv;
+                if (ix == (A.p[0] ? 0 : n - 1)) c[(long)(iy + 1) * Pp + n] = tv;
+                if (iy == (A.p[1] ? ny - 1 : 0)) c[ix] = tv;
+                if (iy == (A.p[1] ? 0 : ny - 1)) c[(long)(ny + 1) * Pp + ix] = tv;
+            }
+        __syncthreads();
+    }
+}
+
+// I_8^m at the points of G22: mean of the four surrounding cell centres.
+// Node k of an axis lies between cells k + p - 1 and k + p (wrapped when
+// periodic, clamped to the boundary cell for extrapolation); ghost copies
+// only on periodic axes (extrapolation node axes are never read outside).
+template <class T>
+__global__ void k_closure_nodes(const ClosureArgs<T> A, const float* __restrict__ ctr) {
+    const GridDev<T>& G = A.g[3];
+    const long M = (long)A.nx * A.ny;
+    const long total = (long)G.nx * G.ny;
+    const long Pp = A.pitch;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int kx = (int)(t % G.nx), ky = (int)(t / G.nx);
+        int cx0 = kx + A.p[0] - 1, cx1 = kx + A.p[0];
+        int cy0 = ky + A.p[1] - 1, cy1 = ky + A.p[1];
+        if (A.p[0]) { cx0 = (cx0 + A.nx) % A.nx; cx1 = cx1 % A.nx; }
+        else { cx0 = max(cx0, 0); cx1 = min(cx1, A.nx - 1); }
+        if (A.p[1]) { cy0 = (cy0 + A.ny) % A.ny; cy1 = cy1 % A.ny; }
+        else { cy0 = max(cy0, 0); cy1 = min(cy1, A.ny - 1); }
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            if (A.slot[NMOM + o].x != 3) continue;
+            const float* c = ctr + (long)o * M;
+            const float v = 0.25f * (c[(long)cy0 * A.nx + cx0] + c[(long)cy0 * A.nx + cx1] +
+                                     c[(long)cy1 * A.nx + cx0] + c[(long)cy1 * A.nx + cx1]);
+            T* d = G.base + (long)A.slot[NMOM + o].y * G.cstride;
+            const T tv = (T)v;
+            d[(long)(ky + 1) * Pp + kx] = tv;
+            if (A.p[0]) {
+                if (kx == G.nx - 1) d[(long)(ky + 1) * Pp - 1] = tv;
+                if (kx == 0) d[(long)(ky + 1) * Pp + G.nx] = tv;
+            }
+            if (A.p[1]) {
+                if (ky == G.ny - 1) d[kx] = tv;
+                if (ky == 0) d[(long)(G.ny + 1) * Pp + kx] = tv;
+            }
+        }
+    }
+}
+
+int status(cudaError_t e) { return e == cudaSuccess ? 0 : -4; }
+
+template <class K>
+int set_smem(K kernel, size_t bytes, bool& done) {
+    if (done) return 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return -4;
+    done = true;
+    return 0;
+}
+
+constexpr size_t SMEM_FWD = sizeof(Smem);
+constexpr size_t SMEM_TRAIN = sizeof(Smem) + sizeof(SmemBack);
+constexpr size_t SMEM_CLOSURE = sizeof(Smem) + ROWS * sizeof(float);
+static_assert(SMEM_TRAIN <= 227 * 1024, "training tile exceeds shared memory");
+
+}  // namespace
+
+long grad_blocks(long B) { return (B + ROWS - 1) / ROWS; }
+
+int pack(const float* params, Packed* P, void* stream) {
+    k_pack<<<64, 256, 0, (cudaStream_t)stream>>>(params, P);
+    return status(cudaGetLastError());
+}
+
+int forward(const float* X, long M, const Packed* P, float* Y, void* stream) {
+    if (M <= 0) return 0;
+    static bool attr = false;
+    if (set_smem(k_forward, SMEM_FWD, attr)) return -4;
+    long blocks = (M + ROWS - 1) / ROWS;
+    if (blocks > sm_count()) blocks = sm_count();
+    k_forward<<<(unsigned)blocks, THREADS, SMEM_FWD, (cudaStream_t)stream>>>(X, M, P, Y);
+    return status(cudaGetLastError());
+}
+
+int loss_grad(const float* X, const float* T, const int* idx, long B, const Packed* P, float* part, float* grad,
+              float* loss, void* stream) {
+    if (B <= 0) return 0;
+    static bool attr = false;
+    if (set_smem(k_loss_grad, SMEM_TRAIN, attr)) return -4;
+    const long blocks = grad_blocks(B);
+    k_loss_grad<<<(unsigned)blocks, THREADS, SMEM_TRAIN, (cudaStream_t)stream>>>(X, T, idx, B, P, part);
+    if (cudaGetLastError() != cudaSuccess) return -4;
+    k_reduce_grad<<<(NPARAM + 1 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(part, blocks, grad, loss);
+    return status(cudaGetLastError());
+}
+
+int adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps, long step,
+         void* stream) {
+    const float c1 = (float)(1.0 - std::pow((double)b1, (double)step));
+    const float c2 = (float)(1.0 - std::pow((double)b2, (double)step));
+    k_adam<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return status(cudaGetLastError());
+}
+
+template <class T>
+int samples(const ClosureArgs<T>& A, float* X, float* scale, float* tgt, void* stream) {
+    const long M = (long)A.nx * A.ny;
+    if (M <= 0) return 0;
+    long blocks = (M + THREADS - 1) / THREADS;
+    if (blocks > 8L * sm_count()) blocks = 8L * sm_count();
+    k_samples<T><<<(unsigned)blocks, THREADS, 0, (cudaStream_t)stream>>>(A, X, scale, tgt);
+    return status(cudaGetLastError());
+}
+
+template <class T>
+int closure(const ClosureArgs<T>& A, const Packed* P, float* ctr, void* stream) {
+    static bool attr = false;
+    if (set_smem(k_closure<T>, SMEM_CLOSURE, attr)) return -4;
+    const long M = (long)A.nx * A.ny;
+    if (M <= 0) return 0;
+    long blocks = (M + ROWS - 1) / ROWS;
+    if (blocks > sm_count()) blocks = sm_count();
+    k_closure<T><<<(unsigned)blocks, THREADS, SMEM_CLOSURE, (cudaStream_t)stream>>>(A, P, ctr);
+    if (cudaGetLastError() != cudaSuccess) return -4;
+    const long total = (long)A.g[3].nx * A.g[3].ny;
+    long nb = (total + 255) / 256;
+    if (nb > 8L * sm_count()) nb = 8L * sm_count();
+    if (nb > 0) k_closure_nodes<T><<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(A, ctr);
+    return status(cudaGetLastError());
+}
+
+template int samples<float>(const ClosureArgs<float>&, float*, float*, float*, void*);
+template int samples<double>(const ClosureArgs<double>&, float*, float*, float*, void*);
+template int closure<float>(const ClosureArgs<float>&, const Packed*, float*, void*);
+template int closure<double>(const ClosureArgs<double>&, const Packed*, float*, void*);
+
+}  // namespace mlp
+}  // namespace starmap

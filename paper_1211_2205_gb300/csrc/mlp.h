@@ -1,0 +1,63 @@
+// Internal interface of the learned order-8 closure (network kernels and the
+// closure evaluation inside the step).
+#pragma once
+#include <cuda_bf16.h>
+
+#include <cstddef>
+
+#include "internal.h"
+
+namespace starmap {
+namespace mlp {
+
+constexpr int NMOM = 36;          // moments of order <= 7
+constexpr int NIN = NMOM + 2;     // + log(1 + sigma_a), log(1 + sigma_s0)
+constexpr int HID = 128;
+constexpr int NOUT = 9;           // moments of order 8
+constexpr int OUTP = 16;          // output rows padded to two 8-wide tiles
+constexpr int LDX = 56;           // padded row of X and W1 (bf16 elements)
+constexpr int LDH = 136;          // padded row of H1, H2, W2, W3
+
+// FP32 parameter vector: W1[128][38], b1[128], W2[128][128], b2[128], W3[9][128], b3[9]
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + HID * NIN;
+constexpr int OFF_W2 = OFF_B1 + HID;
+constexpr int OFF_B2 = OFF_W2 + HID * HID;
+constexpr int OFF_W3 = OFF_B2 + HID;
+constexpr int OFF_B3 = OFF_W3 + NOUT * HID;
+constexpr int NPARAM = OFF_B3 + NOUT;        // 22665
+
+// BF16 weights in the padded layout the kernels stage into shared memory.
+struct alignas(16) Packed {
+    __nv_bfloat16 W1[HID * LDX];
+    __nv_bfloat16 W2[HID * LDH];
+    __nv_bfloat16 W3[OUTP * LDH];
+    float b1[HID], b2[HID], b3[OUTP];
+};
+
+template <class T>
+struct ClosureArgs {
+    GridDev<T> g[4];
+    long pitch;
+    int p[2];
+    int nx, ny;                   // cells (points of G11)
+    int2 slot[NMOM + NOUT];       // (grid, local) of components 0..44 of P_8
+    const float* lsa;             // log(1 + sigma_a) at the cell centres [ny][nx]
+    const float* lss;             // log(1 + sigma_s0)
+};
+
+int pack(const float* params, Packed* P, void* stream);
+int forward(const float* X, long M, const Packed* P, float* Y, void* stream);
+// Per-CTA partial gradients (and losses) of the mean squared error over the
+// B samples idx[0..B) (idx NULL: samples 0..B); part holds
+// blocks(B) x (NPARAM + 1) floats, reduced into grad[NPARAM], loss[1].
+int loss_grad(const float* X, const float* T, const int* idx, long B, const Packed* P, float* part, float* grad,
+              float* loss, void* stream);
+long grad_blocks(long B);
+int adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps, long step,
+         void* stream);
+template <class T> int samples(const ClosureArgs<T>& A, float* X, float* scale, float* tgt, void* stream);
+template <class T> int closure(const ClosureArgs<T>& A, const Packed* P, float* ctr, void* stream);
+
+}  // namespace mlp
+}  // namespace starmap

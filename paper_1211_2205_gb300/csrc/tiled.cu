@@ -258,7 +258,8 @@ int tiled_create(const TiledGeometry& geo, TiledPlan** out) {
 }
 
 int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>& comp_class,
-                 const std::vector<int>& src_slot, const std::vector<void*>& src_dev, double dx, double dy) {
+                 const std::vector<int>& src_slot, const std::vector<void*>& src_dev,
+                 const std::vector<char>& frozen, double dx, double dy) {
     free_tables(pl);
     pl->ready = false;
     {
@@ -288,7 +289,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
         for (size_t e = 0; e + 1 < t.fin.size() + 1; e += 2) {
             for (int K = 0; K < 2; ++K) {
                 const int comp = t.fin_comp[e + K];
-                if (comp < 0) { fk[K].push_back(make_int2(-1, -1)); continue; }
+                if (comp < 0 || frozen[comp]) { fk[K].push_back(make_int2(-1, -1)); continue; }
                 const int g = gout[P][K];
                 const long long off = (long long)t.fin[e + K].x * pl->geo.cstride[g];
                 if (off > 0x7fffffffll) { pl->err = "state too large for the tiled kernel's 32-bit offsets"; return -8; }

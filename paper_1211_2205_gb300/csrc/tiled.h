@@ -20,8 +20,10 @@ struct TiledGeometry {
 
 bool tiled_supported(int system, int N, int precision);
 int tiled_create(const TiledGeometry& geo, TiledPlan** out);
+// frozen[j] != 0: component j is read but never written (closure moments)
 int tiled_update(TiledPlan* plan, const SystemMatrices& sys, const std::vector<int>& comp_class,
-                 const std::vector<int>& src_slot, const std::vector<void*>& src_dev, double dx, double dy);
+                 const std::vector<int>& src_slot, const std::vector<void*>& src_dev,
+                 const std::vector<char>& frozen, double dx, double dy);
 void tiled_set_coef(TiledPlan* plan, int g, void* coef, int nclasses);
 int tiled_pass(TiledPlan* plan, bool odd, int which, void* stream);
 // Read and clear the bounded-wait failure flag (synchronises the stream).

@@ -1,0 +1,293 @@
+"""GPU parity of the learned order-8 closure and of its network kernels
+against the FP64 closure oracle.
+
+The network runs with BF16 operands and FP32 accumulation; the oracle gets
+the same BF16-rounded weights (and, for the plain network tests, the same
+BF16-rounded inputs), so what remains is the rounding of the hidden
+activations and of the backward intermediates to BF16: bar 1e-2 relative
+per tensor.  The features, the node averaging and the coupling into the
+P_8 step are plain FP32/FP64 arithmetic and are held to those precisions."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import rel_l2
+from oracle import closure_oracle as C
+from oracle import pn_oracle as O
+from paper_1211_2205_gb300 import capi, inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+BF16_TOL = 1e-2
+
+
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float32."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = a.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _params(seed, scale_out=1.0, bias=0.1):
+    mlp = C.MLP.init(seed, scale_out=scale_out)
+    rng = np.random.default_rng(seed + 1000)
+    for k in ("b1", "b2", "b3"):
+        mlp.p[k] = rng.normal(0, bias, mlp.p[k].shape)
+    return capi.params_from_dict(mlp.p)
+
+
+def _oracle_mlp(params32):
+    """The oracle network with the GPU's BF16 weights (biases stay FP32)."""
+    d = capi.params_to_dict(params32)
+    for k in ("W1", "W2", "W3"):
+        d[k] = bf16(d[k]).astype(np.float64)
+    return C.MLP(d)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(got, ref):
+    return float(np.linalg.norm(np.asarray(got, np.float64) - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+@pytest.mark.parametrize("M", [1, 127, 1000])
+def test_forward_matches_oracle(M):
+    rng = np.random.default_rng(M)
+    X = rng.normal(size=(M, C.N_IN)).astype(np.float32)
+    params = _params(3)
+    net = capi.Network(params)
+    Xd, Yd = _dev(X), torch.full((M * C.N_OUT,), float("nan"), device="cuda")
+    torch.cuda.synchronize()
+    net.forward(Xd, M, Yd)
+    net.sync()
+    Y = Yd.cpu().numpy().reshape(M, C.N_OUT)
+    ref, _ = _oracle_mlp(params).forward(bf16(X).astype(np.float64))
+    assert np.isfinite(Y).all()
+    assert _rel(Y, ref) <= BF16_TOL
+    assert np.max(np.abs(Y - ref)) <= 3 * BF16_TOL * np.max(np.abs(ref))
+
+
+def test_gradients_match_oracle():
+    """Loss and gradient of a minibatch given by an index list (700 of 1000
+    samples: five full tiles and a ragged one) against the oracle's
+    backward with the same BF16 weights and inputs."""
+    rng = np.random.default_rng(11)
+    Mall, B = 1000, 700
+    X = rng.normal(size=(Mall, C.N_IN)).astype(np.float32)
+    T = rng.normal(size=(Mall, C.N_OUT)).astype(np.float32)
+    idx = rng.permutation(Mall)[:B].astype(np.int32)
+    params = _params(5, scale_out=0.7)
+    net = capi.Network(params)
+    g = torch.zeros(capi.MLP_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    Xd, Td, Id = _dev(X), _dev(T), _dev(idx)
+    torch.cuda.synchronize()
+    net.loss_grad(Xd, Td, B, g, loss, idx=Id)
+    net.sync()
+    got = capi.params_to_dict(g.cpu().numpy())
+    ref_loss, ref = C.loss_and_grad(_oracle_mlp(params), bf16(X[idx]).astype(np.float64), T[idx].astype(np.float64))
+    assert abs(float(loss.item()) - ref_loss) <= BF16_TOL * ref_loss
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert _rel(got[k], ref[k]) <= BF16_TOL, k
+
+
+def test_gradient_is_deterministic():
+    rng = np.random.default_rng(12)
+    X = rng.normal(size=(900, C.N_IN)).astype(np.float32)
+    T = rng.normal(size=(900, C.N_OUT)).astype(np.float32)
+    net = capi.Network(_params(6))
+    Xd, Td = _dev(X), _dev(T)
+    g1 = torch.zeros(capi.MLP_PARAMS, device="cuda")
+    g2 = torch.zeros(capi.MLP_PARAMS, device="cuda")
+    torch.cuda.synchronize()
+    net.loss_grad(Xd, Td, 900, g1)
+    net.loss_grad(Xd, Td, 900, g2)
+    net.sync()
+    assert torch.equal(g1, g2)
+
+
+def test_adam_steps_match_oracle_optimizer():
+    """Three Adam steps on the GPU against the oracle's Adam fed with the
+    GPU's own gradients (the optimiser arithmetic in isolation)."""
+    rng = np.random.default_rng(13)
+    X = rng.normal(size=(512, C.N_IN)).astype(np.float32)
+    T = rng.normal(size=(512, C.N_OUT)).astype(np.float32)
+    params = _params(7)
+    net = capi.Network(params)
+    ref = capi.params_to_dict(params)
+    opt = C.Adam(ref, lr=2e-3)
+    Xd, Td = _dev(X), _dev(T)
+    g = torch.zeros(capi.MLP_PARAMS, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(3):
+        net.loss_grad(Xd, Td, 512, g)
+        net.sync()
+        gd = capi.params_to_dict(g.cpu().numpy())
+        net.train_step(Xd, Td, 512, 2e-3)
+        net.sync()
+        opt.step(ref, gd)
+    assert net.steps == 3
+    np.testing.assert_allclose(net.params, capi.params_from_dict(ref), rtol=0, atol=2e-6)
+
+
+def test_training_fits_a_teacher_network():
+    """Minibatch Adam on the GPU learns the map of another network."""
+    rng = np.random.default_rng(14)
+    M = 8192
+    X = rng.normal(size=(M, C.N_IN)).astype(np.float32)
+    teacher = C.MLP(capi.params_to_dict(_params(21, scale_out=1.0)))
+    T = teacher.forward(X.astype(np.float64))[0].astype(np.float32)
+    net = capi.Network(_params(22, scale_out=0.1))
+    Xd, Td = _dev(X), _dev(T)
+    loss = torch.zeros(1, device="cuda")
+    torch.cuda.synchronize()
+    net.loss_grad(Xd, Td, M, torch.zeros(capi.MLP_PARAMS, device="cuda"), loss)
+    net.sync()
+    first = float(loss.item())
+    perm = _dev(np.concatenate([rng.permutation(M) for _ in range(40)]).astype(np.int32))
+    B = 1024
+    for it in range(320):
+        net.train_step(Xd, Td, B, 3e-3, idx=perm[it * B:(it + 1) * B])
+    net.loss_grad(Xd, Td, M, torch.zeros(capi.MLP_PARAMS, device="cuda"), loss)
+    net.sync()
+    assert float(loss.item()) < 0.2 * first
+
+
+# ----------------------------------------------------------- closure in the step
+def _closure_problem(n=(37, 29), bc=("periodic", "extrapolation"), precision="fp64", N=7, seed=31, nsteps=4):
+    ax = (0.0, 1.1, 0.0, 0.9)
+    rng = inputs.SplitMix64(seed)
+    ncomp = (N + 1) * (N + 2) // 2
+    ic = []
+    for j in range(min(ncomp, 36)):
+        c = rng.uniforms(3)
+        ic.append((j, inputs.gaussian_std(0.2 + 0.7 * c[0], 0.2 + 0.5 * c[1], 0.12 + 0.1 * c[2],
+                                          mass=(-1) ** j / (1 + j // 6))))
+    return inputs.Problem(name="closure", N=N, ax=ax, n=n, bc=bc, precision=precision,
+                          sigma_a=inputs.piecewise_blocks(rng, 4, 0.0, 2.0, ax),
+                          sigma_s0=inputs.piecewise_blocks(rng, 4, 0.2, 4.0, ax),
+                          sources=[(0, inputs.gaussian_std(0.5, 0.45, 0.1))], ic=ic, nsteps=nsteps)
+
+
+def _state(s):
+    return [s.moments(j) for j in range(s.ncomp)]
+
+
+@pytest.mark.parametrize("bc", [("periodic", "periodic"), ("extrapolation", "extrapolation"),
+                                ("periodic", "extrapolation")])
+@pytest.mark.parametrize("precision,kernel", [("fp64", "gather"), ("fp32", "tiled")])
+def test_samples_match_oracle_features_and_targets(bc, precision, kernel):
+    """Features, scales and order-8 targets of a plain P_8 run (two steps)
+    against the oracle's definitions on the oracle's own run."""
+    p = _closure_problem(bc=bc, precision=precision, N=8, nsteps=2)
+    s = capi.Stepper.from_problem(p, kernel=kernel)
+    s.step(2)
+    o = O.solver_from_problem(p, dt=s.dt)
+    o.run(2)
+    X0, Y0 = o.coords[(1, 1)]
+    Xr, scale_r = C.features(o, p.sigma_a(0, X0, Y0), p.sigma_s0(0, X0, Y0))
+    Tr = C.targets(o)
+    M = p.n[0] * p.n[1]
+    Xd = torch.empty(M * C.N_IN, device="cuda")
+    Sd = torch.empty(M, device="cuda")
+    Td = torch.empty(M * C.N_OUT, device="cuda")
+    torch.cuda.synchronize()
+    s.closure_samples(Xd, Sd, Td)
+    s.sync()
+    tol = 2e-6 if precision == "fp64" else 2e-5
+    assert _rel(Sd.cpu().numpy(), scale_r) <= tol
+    assert _rel(Xd.cpu().numpy().reshape(M, C.N_IN), Xr) <= tol
+    assert _rel(Td.cpu().numpy().reshape(M, C.N_OUT), Tr) <= tol
+
+
+@pytest.mark.parametrize("precision,kernel,tol", [("fp64", "gather", 1e-12), ("fp32", "tiled", 1e-5)])
+def test_zero_network_is_plain_p7(precision, kernel, tol):
+    """A network with zero output layer predicts zero order-8 moments: the
+    closed run equals plain P_7 (oracle) with the same dt."""
+    p = _closure_problem(precision=precision)
+    s = capi.Stepper.from_problem(p, kernel=kernel, closure="mlp8")
+    assert s.ncomp == 45
+    params = _params(40)
+    params[-(C.N_OUT * C.HIDDEN + C.N_OUT):] = 0.0          # W3 and b3
+    s.set_closure(params)
+    s.step(p.nsteps)
+    got = _state(s)
+    o = O.solver_from_problem(p, dt=s.dt)
+    o.run(p.nsteps)
+    assert rel_l2(got[:36], [u.T for u in o.U]) <= tol
+    for j in range(36, 45):
+        assert not got[j].any()
+
+
+@pytest.mark.parametrize("bc", [("periodic", "periodic"), ("extrapolation", "extrapolation")])
+def test_closure_prediction_matches_oracle_hook(bc):
+    """One odd pass of a closure handle sets the order-8 moments from the
+    state before it; they match the oracle's closure on that same state."""
+    p = _closure_problem(bc=bc, nsteps=3)
+    params = _params(41, scale_out=0.6)
+    s = capi.Stepper.from_problem(p, kernel="gather", closure="mlp8")
+    s.set_closure(params)
+    s.step(3)
+    before = _state(s)
+    s.run_pass(1, 0)
+    after = _state(s)
+    o = C.closed_solver(p, _oracle_mlp(params), dt=s.dt)
+    for j in range(45):
+        o.U[j] = before[j].T.copy()
+    o.pre_odd(o)
+    ref = [o.U[j].T for j in range(36, 45)]
+    assert rel_l2(after[36:], ref) <= 2 * BF16_TOL
+    assert max(float(np.max(np.abs(r))) for r in ref) > 0
+
+
+@pytest.mark.parametrize("precision,kernel", [("fp64", "gather"), ("fp32", "tiled")])
+def test_closed_run_matches_oracle(precision, kernel):
+    """A closed run against the oracle's closed run: the difference stays a
+    small fraction of what the closure changes relative to plain P_7."""
+    p = _closure_problem(precision=precision, nsteps=5)
+    params = _params(42, scale_out=0.6)
+    s = capi.Stepper.from_problem(p, kernel=kernel, closure="mlp8")
+    s.set_closure(params)
+    s.step(p.nsteps)
+    got = _state(s)
+    o = C.closed_solver(p, _oracle_mlp(params), dt=s.dt)
+    o.run(p.nsteps)
+    plain = O.solver_from_problem(p, dt=s.dt)
+    plain.run(p.nsteps)
+    ref = [u.T for u in o.U[:36]]
+    effect = rel_l2([u.T for u in plain.U], ref)
+    assert effect > 1e-6
+    assert rel_l2(got[:36], ref) <= 0.05 * effect
+
+
+def test_closure_errors():
+    p = _closure_problem()
+    with pytest.raises(capi.StarmapError) as e:
+        capi.Stepper(N=5, ax=p.ax, n=p.n, closure="mlp8")
+    assert e.value.code == capi.E_UNSUPPORTED
+    with pytest.raises(capi.StarmapError) as e:
+        capi.Stepper(N=7, ax=p.ax, n=p.n, closure="mlp8", schedule="merged")
+    assert e.value.code == capi.E_ARG
+    s = capi.Stepper(N=7, ax=p.ax, n=p.n, closure="mlp8")
+    with pytest.raises(capi.StarmapError) as e:
+        s.step(1)
+    assert e.value.code == capi.E_STATE
+    with pytest.raises(ValueError):
+        s.set_closure(np.zeros(10))
+    bad = _params(1)
+    bad[5] = np.nan
+    with pytest.raises(capi.StarmapError) as e:
+        s.set_closure(bad)
+    assert e.value.code == capi.E_NONFINITE
+    with pytest.raises(capi.StarmapError) as e:
+        s.set_source(40, np.ones(p.n[0] * p.n[1]))
+    assert e.value.code == capi.E_ARG
+    plain = capi.Stepper(N=7, ax=p.ax, n=p.n)
+    with pytest.raises(capi.StarmapError) as e:
+        plain.set_closure(_params(1))
+    assert e.value.code == capi.E_STATE
