@@ -440,19 +440,25 @@ __global__ void k_pack(const float* __restrict__ params, Packed* __restrict__ P)
 
 // ------------------------------------------------------------ closure glue
 // Component (grid g, local k) averaged to cell centre (ix, iy): a node axis
-// takes the mean of the nodes k - p and k - p + 1 around cell k (node -1 is
-// the periodic ghost), a cell axis the value itself.
+// takes the mean of the nodes i - p and i - p + 1 around cell i (node -1 of
+// a periodic axis is node n - 1, indexed directly: the corner boundary
+// copies of a grid are not maintained), a cell axis the value itself.
 template <class T>
 __device__ __forceinline__ float centre_value(const ClosureArgs<T>& A, int g, int k, int ix, int iy) {
     const T* c = A.g[g].base + (long)k * A.g[g].cstride;
     const long P = A.pitch;
     const bool xn = g & 1, yn = g & 2;
-    const int xl = xn ? ix - A.p[0] : ix, yl = yn ? iy - A.p[1] : iy;
-    float v = (float)c[(long)(yl + 1) * P + xl];
-    if (xn) v += (float)c[(long)(yl + 1) * P + xl + 1];
-    if (yn) v += (float)c[(long)(yl + 2) * P + xl];
-    if (xn && yn) v += (float)c[(long)(yl + 2) * P + xl + 1];
-    return v * ((xn ? 0.5f : 1.f) * (yn ? 0.5f : 1.f));
+    int xa = ix, xb = ix, ya = iy, yb = iy;
+    if (xn) { xa = ix - A.p[0]; xb = xa + 1; if (xa < 0) xa = A.g[g].nx - 1; }
+    if (yn) { ya = iy - A.p[1]; yb = ya + 1; if (ya < 0) ya = A.g[g].ny - 1; }
+    const T* ra = c + (long)(ya + 1) * P;
+    const T* rb = c + (long)(yb + 1) * P;
+    float v;
+    if (xn && yn) v = 0.25f * (((float)ra[xa] + (float)ra[xb]) + ((float)rb[xa] + (float)rb[xb]));
+    else if (xn) v = 0.5f * ((float)ra[xa] + (float)ra[xb]);
+    else if (yn) v = 0.5f * ((float)ra[xa] + (float)rb[xa]);
+    else v = (float)ra[xa];
+    return v;
 }
 
 // Features of cell m = iy * nx + ix and the RMS scale of its moments.
