@@ -279,8 +279,9 @@ int starmap_sync(starmap_t* h);
  *   inputs  x = (u_0 .. u_35) / s, log(1 + sigma_a), log(1 + sigma_s0), the
  *           36 moments of order <= 7 averaged to a cell centre from their
  *           own grid (two neighbours on G21 / G12, four on G22) and divided
- *           by their RMS s over the 36 values; sigma from grid G11's
- *           material (starmap_set_material(h, 0, ...));
+ *           by their RMS s over the 36 values (x = 0 and s = 0 where all
+ *           36 vanish); sigma from grid G11's material
+ *           (starmap_set_material(h, 0, ...));
  *   network h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = W3 h2 + b3
  *           (128 hidden units per layer; BF16 operands, FP32 accumulation);
  *   output  s * y = (R_8^8, I_8^8, R_8^6, I_8^6, R_8^4, I_8^4, R_8^2,
@@ -304,8 +305,8 @@ int starmap_set_closure(starmap_t* h, const float* params, size_t count);
 /* Training samples of the current state, on the device: for each cell
  * m = iy*n_x + ix (M = n_x*n_y cells) the 38 network inputs X[m][38], the
  * scale s[m], and, if targets is not NULL, the 9 order-8 moments averaged
- * to the cell centre targets[m][9] (unscaled; the network's target is
- * targets / s).  X, scale, targets are caller-owned device pointers of M*38,
+ * to the cell centre and divided by s[m] (0 where s[m] = 0), targets[m][9]
+ * (the network's regression target).  X, scale, targets are caller-owned device pointers of M*38,
  * M and M*9 floats; count must equal M.  Needs the 2D system with N >= 7
  * (N >= 8 or the closure for targets).  Asynchronous on the handle's
  * stream. */

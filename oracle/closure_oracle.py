@@ -16,7 +16,8 @@ that predicts the order-8 moments from the local state:
 * features at each cell centre (the points of G11): the 36 moments of order
   <= 7 averaged to the cell centre from their own staggered grid (two
   neighbours on G21 / G12, four on G22), divided by their RMS s, plus
-  log(1 + sigma_a) and log(1 + sigma_s0);
+  log(1 + sigma_a) and log(1 + sigma_s0); a cell whose largest moment
+  magnitude is at most 1e-30 is empty: its moment features and s are 0;
 * network: 38 -> 128 -> 128 -> 9, tanh hidden layers, linear output; the
   prediction is s * y (positively homogeneous in the moments, as the linear
   transport equation is);
@@ -44,7 +45,7 @@ N_FEAT_MOM = (N_BASE + 1) * (N_BASE + 2) // 2      # 36
 N_OUT = N_CLOSED + 1                                 # 9 moments of order 8
 N_IN = N_FEAT_MOM + 2                                # 38
 HIDDEN = 128
-EPS = 1e-30
+EMPTY = 1e-30          # largest moment magnitude of an empty cell
 
 
 def order8_components() -> List[int]:
@@ -78,8 +79,10 @@ def features(s: O.StaggeredSolver, sigma_a_cc: np.ndarray, sigma_s0_cc: np.ndarr
     """Network inputs X [M, 38] and scales [M] at the M = nx*ny cell centres,
     cell index = iy * nx + ix."""
     u = np.stack([to_cell_centres(s, j).T.ravel() for j in range(N_FEAT_MOM)], axis=1)
-    scale = np.sqrt(np.mean(u * u, axis=1)) + EPS
-    X = np.concatenate([u / scale[:, None],
+    empty = np.max(np.abs(u), axis=1) <= EMPTY
+    scale = np.where(empty, 0.0, np.sqrt(np.mean(u * u, axis=1)))
+    inv = np.where(empty, 0.0, 1.0 / np.where(empty, 1.0, scale))
+    X = np.concatenate([u * inv[:, None],
                         np.log1p(sigma_a_cc.T.ravel())[:, None],
                         np.log1p(sigma_s0_cc.T.ravel())[:, None]], axis=1)
     return X, scale

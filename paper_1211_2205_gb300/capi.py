@@ -362,9 +362,10 @@ class Stepper:
         self._check(self._L.starmap_set_closure(self._h, a.ctypes.data_as(_fp), a.size))
 
     def closure_samples(self, X, scale, targets=None):
-        """Network inputs X [M, 38], scales [M] and (optionally) order-8
-        targets [M, 9] of the current state, written into caller-owned
-        device buffers (torch tensors or addresses), M = n_x * n_y."""
+        """Network inputs X [M, 38], scales s [M] and (optionally) the
+        order-8 moments divided by s, targets [M, 9], of the current state,
+        written into caller-owned device buffers (torch tensors or
+        addresses), M = n_x * n_y."""
         nx, ny, *_ = self.grid_info(0)
         self._check(self._L.starmap_closure_samples(self._h, _addr(X), _addr(scale), _addr(targets), nx * ny))
 

@@ -1,0 +1,256 @@
+"""Learned order-8 closure of P_7: training data from high-order runs of the
+method, training on the GPU with the library's own network kernels, and
+the error-matched comparison with plain P_N.
+
+Every numerical step runs in libstarmap.so (the P_N passes, the closure
+kernel, feature extraction, forward/backward/Adam); this module only
+orchestrates: it allocates device buffers with torch, draws seeded
+minibatch orders with numpy and times runs with CUDA events.
+
+Workflow
+--------
+1. ``generate``: for each training medium (``inputs.closure_medium``) run
+   plain P_{N_ref} (default P_39) from the initial pulses and, at evenly
+   spaced time levels, extract per cell the 38 network inputs and the
+   order-8 moments divided by the local RMS scale (the regression target).
+2. ``train``: minibatch Adam on the mean squared error of the scaled
+   targets (cosine learning-rate decay).
+3. ``evaluate``: on held-out media, run P_{N_ref} as the reference, plain
+   P_N for N in ``orders`` and P_7 with the trained closure, all with the
+   same dt (the P_{N_ref} bound) and step count; report the relative L2
+   error of R_0^0 against the reference and the device time of each run.
+   The error-matched speedup is time(P_N*) / time(closure) for the lowest
+   N* whose error is at most the closure's.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import capi, inputs
+
+N_BASE = 7
+
+
+def lambda_max(N: int) -> float:
+    return capi.host_matrices(capi.PN2D, N)[4]
+
+
+def common_dt(problem: inputs.Problem, N_ref: int) -> float:
+    """cn * min(dx, dy) / lambda_max of P_{N_ref}: stable for every N <= N_ref."""
+    h = min((problem.ax[1] - problem.ax[0]) / problem.n[0], (problem.ax[3] - problem.ax[2]) / problem.n[1])
+    return problem.cn * h / lambda_max(N_ref)
+
+
+def init_params(seed: int, scale_out: float = 0.1) -> np.ndarray:
+    """Parameters with N(0, 1/fan_in) weights and zero biases; the output
+    layer scaled by scale_out (a small initial closure)."""
+    rng = np.random.default_rng(seed)
+    H, I, O = capi.MLP_HIDDEN, capi.MLP_INPUTS, capi.MLP_OUTPUTS
+    p = {
+        "W1": rng.normal(0, 1 / math.sqrt(I), (H, I)),
+        "b1": np.zeros(H),
+        "W2": rng.normal(0, 1 / math.sqrt(H), (H, H)),
+        "b2": np.zeros(H),
+        "W3": scale_out * rng.normal(0, 1 / math.sqrt(H), (O, H)),
+        "b3": np.zeros(O),
+    }
+    return capi.params_from_dict(p)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the closure workflow runs on the GPU (CUDA device required)")
+    return torch
+
+
+@dataclass
+class SampleSet:
+    X: object            # torch [S, 38] float32 (device)
+    T: object            # torch [S, 9] float32 (device): order-8 moments / scale
+    index: np.ndarray    # int32 indices of the samples used for training
+    count: int           # len(index)
+    seeds: List[int]
+    snapshots: int
+    n: int
+    N_ref: int
+
+
+def _set_ic(s: capi.Stepper, problem: inputs.Problem):
+    for j, f in problem.ic:
+        X, Y = s.grid_coords(s.moment_info(j)["grid"])
+        s.set_moment(j, np.broadcast_to(f(0.0, X, Y), X.shape))
+
+
+def generate(seeds: Sequence[int], n: int = 512, N_ref: int = 39, snapshots: int = 8,
+             t_final: float = 0.5, rel_floor: float = 1e-4) -> SampleSet:
+    """Training samples from plain P_{N_ref} runs on the media of `seeds`.
+    Cells whose moment scale s lies below rel_floor times the largest s of
+    their snapshot are left out: there the moments are round-off far from
+    the pulses, and the network's prediction s * y is negligible anyway."""
+    torch = _torch()
+    M = n * n
+    total = len(seeds) * snapshots * M
+    X = torch.empty((total, capi.MLP_INPUTS), device="cuda", dtype=torch.float32)
+    T = torch.empty((total, capi.MLP_OUTPUTS), device="cuda", dtype=torch.float32)
+    scale = torch.empty(M, device="cuda", dtype=torch.float32)
+    off = 0
+    keep = []
+    for seed in seeds:
+        p = inputs.closure_medium(seed, n=n, N=N_ref, t_final=t_final)
+        dt = common_dt(p, N_ref)
+        nsteps = int(round(t_final / dt))
+        marks = [int(round((k + 1) * nsteps / snapshots)) for k in range(snapshots)]
+        s = capi.Stepper.from_problem(p, dt=dt, schedule="merged")
+        done = 0
+        torch.cuda.synchronize()
+        for mk in marks:
+            s.step(mk - done)
+            done = mk
+            s.closure_samples(X[off:off + M], scale, T[off:off + M])
+            sc = scale.cpu().numpy()
+            keep.append(off + np.nonzero(sc >= rel_floor * sc.max())[0].astype(np.int64))
+            off += M
+        s.sync()
+        s.close()
+    torch.cuda.synchronize()
+    index = np.concatenate(keep).astype(np.int32)
+    return SampleSet(X=X, T=T, index=index, count=int(index.size), seeds=list(seeds), snapshots=snapshots, n=n,
+                     N_ref=N_ref)
+
+
+@dataclass
+class TrainResult:
+    params: np.ndarray
+    losses: List[float] = field(default_factory=list)    # full-batch-free running minibatch losses
+    steps: int = 0
+
+
+def train(data: SampleSet, steps: int = 6000, batch: int = 8192, lr0: float = 2e-3, lr1: float = 2e-5,
+          seed: int = 0, log_every: int = 200) -> TrainResult:
+    """Minibatch Adam with cosine decay from lr0 to lr1."""
+    torch = _torch()
+    net = capi.Network(init_params(seed))
+    rng = np.random.default_rng(seed)
+    loss = torch.zeros(1, device="cuda")
+    res = TrainResult(params=np.empty(0))
+    idx = None
+    pos = data.count
+    torch.cuda.synchronize()
+    for it in range(steps):
+        if pos + batch > data.count:
+            idx = torch.from_numpy(data.index[rng.permutation(data.count)]).cuda()
+            torch.cuda.synchronize()
+            pos = 0
+        lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * it / max(1, steps - 1)))
+        net.train_step(data.X, data.T, batch, lr, loss=loss if (it % log_every == 0) else None,
+                       idx=idx[pos:pos + batch])
+        pos += batch
+        if it % log_every == 0:
+            net.sync()
+            res.losses.append(float(loss.item()))
+    net.sync()
+    res.params = net.params
+    res.steps = steps
+    net.close()
+    return res
+
+
+def mean_loss(params: np.ndarray, data: SampleSet, limit: Optional[int] = None) -> float:
+    """Mean squared error of the network on (a prefix of) a sample set."""
+    torch = _torch()
+    net = capi.Network(params)
+    B = data.count if limit is None else min(limit, data.count)
+    idx = torch.from_numpy(data.index[:B].copy()).cuda()
+    g = torch.empty(capi.MLP_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    torch.cuda.synchronize()
+    net.loss_grad(data.X, data.T, B, g, loss, idx=idx)
+    net.sync()
+    v = float(loss.item())
+    net.close()
+    return v
+
+
+@dataclass
+class RunResult:
+    N: int
+    closure: bool
+    R00: np.ndarray
+    ms: float
+    steps: int
+
+
+def run_case(problem: inputs.Problem, N: int, dt: float, nsteps: int, params: Optional[np.ndarray] = None,
+             repeats: int = 1) -> RunResult:
+    """Run P_N (params None) or P_7 with the closure network from the
+    problem's initial condition for nsteps steps of size dt; device time of
+    the stepping (after one untimed warm-up run) on a dedicated stream."""
+    torch = _torch()
+    stream = torch.cuda.Stream()
+    closure = params is not None
+    q = inputs.Problem(**{**problem.__dict__, "N": N})
+    s = capi.Stepper.from_problem(q, dt=dt, stream=stream.cuda_stream,
+                                  schedule="literal" if closure else "merged",
+                                  closure="mlp8" if closure else "none")
+    if closure:
+        s.set_closure(params)
+    times = []
+    for r in range(repeats + 1):
+        s.clear()
+        _set_ic(s, q)
+        s.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            s.step(nsteps)
+            b.record(stream)
+        s.sync()
+        b.synchronize()
+        if r > 0:
+            times.append(a.elapsed_time(b))
+    R00 = s.moments(0)
+    s.close()
+    return RunResult(N=N, closure=closure, R00=R00, ms=float(np.median(times)), steps=nsteps)
+
+
+def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
+    return float(np.linalg.norm(a - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def evaluate(params: np.ndarray, seeds: Sequence[int], n: int = 512, orders: Sequence[int] = (7, 9, 11, 13, 15),
+             N_ref: int = 39, t_final: float = 0.5, repeats: int = 1) -> Dict:
+    """Errors of R_0^0 against P_{N_ref} and device times, per held-out medium."""
+    cases = []
+    for seed in seeds:
+        p = inputs.closure_medium(seed, n=n, N=N_ref, t_final=t_final)
+        dt = common_dt(p, N_ref)
+        nsteps = int(round(t_final / dt))
+        ref = run_case(p, N_ref, dt, nsteps)
+        row = {"seed": seed, "dt": dt, "steps": nsteps, "ref_ms": ref.ms, "plain": {}}
+        for N in orders:
+            r = run_case(p, N, dt, nsteps, repeats=repeats)
+            row["plain"][N] = {"err": rel_l2(r.R00, ref.R00), "ms": r.ms}
+        r = run_case(p, N_BASE, dt, nsteps, params=params, repeats=repeats)
+        row["closure"] = {"err": rel_l2(r.R00, ref.R00), "ms": r.ms}
+        cases.append(row)
+    return summarize(cases, orders)
+
+
+def summarize(cases: List[Dict], orders: Sequence[int]) -> Dict:
+    """Mean error and time per method over the cases, and the error-matched
+    speedup of the closure against the lowest plain order at least as
+    accurate on average."""
+    plain = {N: {"err": float(np.mean([c["plain"][N]["err"] for c in cases])),
+                 "ms": float(np.mean([c["plain"][N]["ms"] for c in cases]))} for N in orders}
+    cl = {"err": float(np.mean([c["closure"]["err"] for c in cases])),
+          "ms": float(np.mean([c["closure"]["ms"] for c in cases]))}
+    match = next((N for N in sorted(orders) if plain[N]["err"] <= cl["err"]), None)
+    out = {"cases": cases, "plain": plain, "closure": cl, "matched_N": match,
+           "error_matched_speedup": (plain[match]["ms"] / cl["ms"]) if match is not None else None,
+           "gain_vs_p7": plain[N_BASE]["err"] / cl["err"] if N_BASE in plain and cl["err"] > 0 else None}
+    return out

@@ -36,6 +36,7 @@ constexpr int WARPS = 8;           // 16 samples per warp
 constexpr int THREADS = WARPS * 32;
 constexpr int KX = 48;             // input width rounded up to the mma k (16)
 constexpr int LDO = 24;            // padded row of dY (16 used)
+constexpr float EMPTY = 1e-30f;    // largest moment magnitude of an empty cell
 
 struct Smem {
     Packed w;
@@ -461,19 +462,32 @@ __device__ __forceinline__ float centre_value(const ClosureArgs<T>& A, int g, in
     return v;
 }
 
-// Features of cell m = iy * nx + ix and the RMS scale of its moments.
+// Features of cell m = iy * nx + ix, the RMS scale s of its moments and
+// 1/s.  A cell whose largest moment magnitude is at most EMPTY counts as
+// empty: features 0, s = 0, 1/s = 0.  Otherwise the RMS is formed relative
+// to the largest magnitude, so that squares of tiny far-field values do not
+// underflow in FP32.
 template <class T>
-__device__ __forceinline__ void cell_features(const ClosureArgs<T>& A, long m, float (&f)[NIN], float& scale) {
+__device__ __forceinline__ void cell_features(const ClosureArgs<T>& A, long m, float (&f)[NIN], float& scale,
+                                              float& inv) {
     const int ix = (int)(m % A.nx), iy = (int)(m / A.nx);
-    float ss = 0.f;
+    float mx = 0.f;
 #pragma unroll
     for (int j = 0; j < NMOM; ++j) {
         const float v = centre_value(A, A.slot[j].x, A.slot[j].y, ix, iy);
         f[j] = v;
-        ss += v * v;
+        mx = fmaxf(mx, fabsf(v));
     }
-    scale = sqrtf(ss / (float)NMOM) + 1e-30f;
-    const float inv = 1.f / scale;
+    scale = 0.f;
+    inv = 0.f;
+    if (mx > EMPTY) {
+        const float im = 1.f / mx;
+        float ss = 0.f;
+#pragma unroll
+        for (int j = 0; j < NMOM; ++j) ss += (f[j] * im) * (f[j] * im);
+        scale = mx * sqrtf(ss / (float)NMOM);
+        inv = 1.f / scale;
+    }
 #pragma unroll
     for (int j = 0; j < NMOM; ++j) f[j] *= inv;
     f[NMOM] = A.lsa[m];
@@ -485,8 +499,8 @@ __global__ void __launch_bounds__(THREADS) k_samples(const ClosureArgs<T> A, flo
                                                      float* __restrict__ scale, float* __restrict__ tgt) {
     const long M = (long)A.nx * A.ny;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        float f[NIN], s;
-        cell_features(A, m, f, s);
+        float f[NIN], s, inv;
+        cell_features(A, m, f, s, inv);
 #pragma unroll
         for (int c = 0; c < NIN; ++c) X[m * NIN + c] = f[c];
         scale[m] = s;
@@ -494,7 +508,7 @@ __global__ void __launch_bounds__(THREADS) k_samples(const ClosureArgs<T> A, flo
             const int ix = (int)(m % A.nx), iy = (int)(m / A.nx);
 #pragma unroll
             for (int o = 0; o < NOUT; ++o)
-                tgt[m * NOUT + o] = centre_value(A, A.slot[NMOM + o].x, A.slot[NMOM + o].y, ix, iy);
+                tgt[m * NOUT + o] = centre_value(A, A.slot[NMOM + o].x, A.slot[NMOM + o].y, ix, iy) * inv;
         }
     }
 }
@@ -519,9 +533,9 @@ __global__ void __launch_bounds__(THREADS) k_closure(const ClosureArgs<T> A, con
         if (threadIdx.x < ROWS) {
             const int r = threadIdx.x;
             const long m = row0 + r;
-            float f[NIN], s = 1.f;
+            float f[NIN], s = 0.f, inv;
             if (m < M) {
-                cell_features(A, m, f, s);
+                cell_features(A, m, f, s, inv);
             } else {
 #pragma unroll
                 for (int c = 0; c < NIN; ++c) f[c] = 0.f;

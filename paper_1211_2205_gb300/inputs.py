@@ -229,6 +229,33 @@ def piecewise_blocks(rng: SplitMix64, blocks: int, lo: float, hi: float,
     return f
 
 
+def closure_medium(seed: int, n: int = 512, N: int = 39, t_final: float = 0.5,
+                   precision: str = "fp32") -> Problem:
+    """Instance of the learned-closure workload (seed 2205000 + seed):
+    periodic [-1, 1]^2 with n x n cells; sigma_a constant on 8 x 8 blocks,
+    iid U[0, 0.5]; sigma_s0 = 10**v on another 8 x 8 block lattice, v iid
+    U[-1, 1] (log-uniform in [0.1, 10]); initial R_0^0 the sum of three
+    Gaussian pulses (centres U[-0.7, 0.7]^2, std U[0.04, 0.1], mass
+    U[0.5, 1.5]); all other moments zero, no source."""
+    rng = SplitMix64(2205000 + seed)
+    ax = (-1.0, 1.0, -1.0, 1.0)
+    sigma_a = piecewise_blocks(rng, 8, 0.0, 0.5, ax)
+    log_s = piecewise_blocks(rng, 8, -1.0, 1.0, ax, shift=0.61)
+    pulses = []
+    for _ in range(3):
+        u = rng.uniforms(4)
+        pulses.append(gaussian_std(-0.7 + 1.4 * u[0], -0.7 + 1.4 * u[1], 0.04 + 0.06 * u[2], mass=0.5 + u[3]))
+
+    def sigma_s0(t, x, y):
+        return 10.0 ** log_s(t, x, y)
+
+    def ic0(t, x, y):
+        return sum(f(t, x, y) for f in pulses)
+    return Problem(
+        name=f"closure_medium_{seed}_p{N}_{n}", N=N, ax=ax, n=(n, n), bc=("periodic", "periodic"), cn=0.5,
+        precision=precision, sigma_a=sigma_a, sigma_s0=sigma_s0, ic=[(0, ic0)], t_final=t_final)
+
+
 def batched_instance(k: int, nsteps: int = 100) -> Problem:
     """Instance k of the batched workload (seed 12112205 + k)."""
     rng = SplitMix64(12112205 + k)

@@ -202,7 +202,7 @@ def test_samples_match_oracle_features_and_targets(bc, precision, kernel):
     tol = 2e-6 if precision == "fp64" else 2e-5
     assert _rel(Sd.cpu().numpy(), scale_r) <= tol
     assert _rel(Xd.cpu().numpy().reshape(M, C.N_IN), Xr) <= tol
-    assert _rel(Td.cpu().numpy().reshape(M, C.N_OUT), Tr) <= tol
+    assert _rel(Td.cpu().numpy().reshape(M, C.N_OUT), Tr / scale_r[:, None]) <= tol
 
 
 @pytest.mark.parametrize("precision,kernel,tol", [("fp64", "gather", 1e-12), ("fp32", "tiled", 1e-5)])
