@@ -91,9 +91,12 @@ extern "C" {
  * components alone; before every odd half-step a per-cell network (set by
  * starmap_set_closure) predicts them from the local moments of order <= 7,
  * so the order-7 rows see the P_8 couplings times the prediction instead of
- * zero.  Only the literal schedule is allowed (the prediction depends on
- * the odd moments, so two odd halves do not merge); dt defaults to the
- * P_8 bound cn * min(dx, dy) / lambda_max(Mx of P_8). */
+ * zero.  The network runs before every odd pass: with the literal schedule
+ * before each odd half-step (two evaluations per step), with the merged
+ * schedule once per merged odd pass (the second odd half of a step and the
+ * first of the next share one prediction; n + 1 evaluations per
+ * starmap_step(h, n)).  dt defaults to the P_8 bound
+ * cn * min(dx, dy) / lambda_max(Mx of P_8). */
 #define STARMAP_CLOSURE_NONE 0
 #define STARMAP_CLOSURE_MLP8 1
 

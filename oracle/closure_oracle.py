@@ -23,7 +23,10 @@ that predicts the order-8 moments from the local state:
   transport equation is);
 * R_8^m are written at the cell centres, I_8^m at the G22 points as the mean
   of the four surrounding cell-centre predictions (boundary cells copied for
-  extrapolation boundaries, wrapped for periodic ones).
+  extrapolation boundaries, wrapped for periodic ones);
+* schedules: literal -- the network runs before every odd half-step;
+  merged -- consecutive odd halves form one odd pass with one evaluation
+  (StaggeredSolver.run(n, merged_closure=True)).
 
 Functions here follow that definition step by step in FP64.  The learned
 mapping itself has no counterpart in the paper: its parity is unpinned

@@ -369,12 +369,16 @@ class StaggeredSolver:
             self.U[j] = self.U[j] + self.dt / 2.0 * (W + Q - self.decay[j] * self.U[j]) * self.ET[j]
 
     # -- eq. solution_operator_full_step ---------------------------------
-    def step(self):
+    def step(self, reuse_closure: bool = False):
+        """One full step O_1/2 E E O_1/2 (eq. solution_operator_full_step).
+        reuse_closure: skip the pre_odd hook before the first odd half (its
+        values from the previous step's second half are kept: the two odd
+        halves then form one merged odd pass with one closure evaluation)."""
         tm = self.t + self.dt / 2.0
         if self._materials_at is None or self.time_dependent:
             self._evaluate(tm)
         inputs_even = self.even + sorted(self.frozen)
-        if self.pre_odd is not None:
+        if self.pre_odd is not None and not reuse_closure:
             self.pre_odd(self)
         dxU, dyU = self._differences(inputs_even)
         self._half_step(self.odd, dxU, dyU)
@@ -388,9 +392,14 @@ class StaggeredSolver:
         self.t += self.dt
         self.nsteps_done += 1
 
-    def run(self, nsteps: int):
-        for _ in range(int(nsteps)):
-            self.step()
+    def run(self, nsteps: int, merged_closure: bool = False):
+        """nsteps full steps.  merged_closure: the closure hook is evaluated
+        once per merged odd pass -- before the first odd half of the run and
+        before every second odd half, whose values the next step's first
+        odd half reuses (the schedule O_1/2 (E O)^(n-1) E O_1/2 with one
+        evaluation before each odd pass)."""
+        for k in range(int(nsteps)):
+            self.step(reuse_closure=merged_closure and k > 0)
 
     def run_to(self, t_final: float) -> List[np.ndarray]:
         """Step until t_final lies in (t, t + dt]; return the solution at

@@ -186,7 +186,7 @@ class RunResult:
 
 
 def run_case(problem: inputs.Problem, N: int, dt: float, nsteps: int, params: Optional[np.ndarray] = None,
-             repeats: int = 1) -> RunResult:
+             repeats: int = 1, closure_schedule: str = "merged") -> RunResult:
     """Run P_N (params None) or P_7 with the closure network from the
     problem's initial condition for nsteps steps of size dt; device time of
     the stepping (after one untimed warm-up run) on a dedicated stream."""
@@ -195,7 +195,7 @@ def run_case(problem: inputs.Problem, N: int, dt: float, nsteps: int, params: Op
     closure = params is not None
     q = inputs.Problem(**{**problem.__dict__, "N": N})
     s = capi.Stepper.from_problem(q, dt=dt, stream=stream.cuda_stream,
-                                  schedule="literal" if closure else "merged",
+                                  schedule=closure_schedule if closure else "merged",
                                   closure="mlp8" if closure else "none")
     if closure:
         s.set_closure(params)
@@ -223,7 +223,8 @@ def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
 
 
 def evaluate(params: np.ndarray, seeds: Sequence[int], n: int = 512, orders: Sequence[int] = (7, 9, 11, 13, 15),
-             N_ref: int = 39, t_final: float = 0.5, repeats: int = 1) -> Dict:
+             N_ref: int = 39, t_final: float = 0.5, repeats: int = 1,
+             closure_schedules: Sequence[str] = ("merged",)) -> Dict:
     """Errors of R_0^0 against P_{N_ref} and device times, per held-out medium."""
     cases = []
     for seed in seeds:
@@ -235,8 +236,9 @@ def evaluate(params: np.ndarray, seeds: Sequence[int], n: int = 512, orders: Seq
         for N in orders:
             r = run_case(p, N, dt, nsteps, repeats=repeats)
             row["plain"][N] = {"err": rel_l2(r.R00, ref.R00), "ms": r.ms}
-        r = run_case(p, N_BASE, dt, nsteps, params=params, repeats=repeats)
-        row["closure"] = {"err": rel_l2(r.R00, ref.R00), "ms": r.ms}
+        for k, sched in enumerate(closure_schedules):
+            r = run_case(p, N_BASE, dt, nsteps, params=params, repeats=repeats, closure_schedule=sched)
+            row["closure" if k == 0 else "closure_" + sched] = {"err": rel_l2(r.R00, ref.R00), "ms": r.ms}
         cases.append(row)
     return summarize(cases, orders)
 

@@ -66,7 +66,7 @@ struct starmap_s {
     float* net_params = nullptr;           // FP32 parameters (device)
     mlp::Packed* net = nullptr;            // BF16 packed network (device)
     bool net_ready = false;
-    float* ctr = nullptr;                  // centre values of I_8 [9][n_x n_y]
+    float* ctr = nullptr;                  // closure scratch (input fragments, scales, I_8 centre values)
     float* lsig = nullptr;                 // log(1 + sigma_a), log(1 + sigma_s0) at the cell centres
     bool lsig_dirty = true;
     std::string err;
@@ -270,6 +270,15 @@ int run_pass(starmap_t* h, bool odd, int which) {
     return STARMAP_OK;
 }
 
+// The closure kernels are unrolled over the grid placement of components
+// 0..44 (mlp::GRID45); check it against the handle's own placement.
+bool closure_layout_ok(const starmap_t* h) {
+    const int n = std::min(h->ncomp, mlp::NMOM + mlp::NOUT);
+    for (int j = 0; j < n; ++j)
+        if (h->sys.moms[j].grid != mlp::GRID45[j]) return false;
+    return true;
+}
+
 // log(1 + sigma) of grid G11's material, FP32 on the device (network inputs).
 int ensure_lsig(starmap_t* h) {
     const size_t M = (size_t)h->nxg[0] * h->nyg[0];
@@ -311,7 +320,8 @@ int run_closure(starmap_t* h) {
     int rc = ensure_lsig(h);
     if (rc) return rc;
     const size_t M = (size_t)h->nxg[0] * h->nyg[0];
-    if (!h->ctr) CK(cudaMalloc(&h->ctr, std::max<size_t>(1, (size_t)mlp::NOUT * M) * sizeof(float)), "cudaMalloc closure scratch");
+    if (!h->ctr) CK(cudaMalloc(&h->ctr, std::max<size_t>(1, (size_t)mlp::closure_scratch_floats((long)M)) * sizeof(float)),
+                    "cudaMalloc closure scratch");
     if (mlp::closure<T>(closure_args<T>(h), h->net, h->ctr, h->stream)) return cuda_fail(h, cudaGetLastError(), "closure");
     return STARMAP_OK;
 }
@@ -330,10 +340,10 @@ int do_steps(starmap_t* h, long n) {
     if (h->ghosts_dirty) { int rc = fill_ghosts_all<T>(h); if (rc) return rc; }
     int rc;
     if (h->cfg.schedule == STARMAP_SCHEDULE_MERGED) {
-        if ((rc = run_pass<T>(h, true, 0))) return rc;
+        if ((rc = odd_pass<T>(h, 0))) return rc;
         for (long i = 0; i < n; ++i) {
             if ((rc = run_pass<T>(h, false, 1))) return rc;
-            if ((rc = run_pass<T>(h, true, i == n - 1 ? 0 : 1))) return rc;
+            if ((rc = odd_pass<T>(h, i == n - 1 ? 0 : 1))) return rc;
         }
     } else {
         for (long i = 0; i < n; ++i) {
@@ -484,8 +494,6 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
     if (c.closure == STARMAP_CLOSURE_MLP8) {
         if (c.system != STARMAP_PN2D || c.N != 7)
             return fail(nullptr, STARMAP_E_UNSUPPORTED, "the learned closure is defined for the 2D system with N = 7");
-        if (c.schedule != STARMAP_SCHEDULE_LITERAL)
-            return fail(nullptr, STARMAP_E_ARG, "the learned closure needs the literal schedule");
     }
 
     starmap_t* h = new (std::nothrow) starmap_t();
@@ -497,8 +505,10 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
     if (!build_system(c.system, h->nsys, h->sys, err)) { delete h; return fail(nullptr, STARMAP_E_ARG, err); }
     h->ncomp = h->sys.ncomp;
     h->frozen.assign(h->ncomp, 0);
-    if (h->closure)
+    if (h->closure) {
         for (int j = 0; j < h->ncomp; ++j) h->frozen[j] = h->sys.moms[j].l == h->nsys;
+        if (!closure_layout_ok(h)) { delete h; return fail(nullptr, STARMAP_E_UNSUPPORTED, "moment placement differs from the closure kernels'"); }
+    }
     h->dx = (c.ax[1] - c.ax[0]) / c.n[0];
     h->dy = (c.ax[3] - c.ax[2]) / c.n[1];
     for (int d = 0; d < 2; ++d) h->p[d] = c.bc[d] == STARMAP_PERIODIC ? 1 : 0;
@@ -955,6 +965,7 @@ int starmap_closure_samples(starmap_t* h, float* X, float* scale, float* targets
     if (h->cfg.system != STARMAP_PN2D || h->nsys < 7)
         return fail(h, STARMAP_E_UNSUPPORTED, "closure samples need the 2D system with N >= 7");
     if (targets && h->nsys < 8) return fail(h, STARMAP_E_UNSUPPORTED, "order-8 targets need N >= 8");
+    if (!closure_layout_ok(h)) return fail(h, STARMAP_E_UNSUPPORTED, "moment placement differs from the closure kernels'");
     const size_t M = (size_t)h->nxg[0] * h->nyg[0];
     if (!X || !scale || count != M) return fail(h, STARMAP_E_ARG, "samples need X, scale and count = n_x * n_y");
     if (h->ghosts_dirty) {

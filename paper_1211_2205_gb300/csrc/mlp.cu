@@ -12,16 +12,18 @@
 // by the network before every odd half-step, so the order-7 rows see
 // predicted order-8 moments instead of the zero of the P_7 truncation.
 //
-// Tiles: one CTA of 8 warps handles 128 samples at a time; warp w owns rows
-// 16w..16w+15 through all three layers (mma.sync m16n8k16, fragments by
-// ldmatrix from padded shared-memory rows, so no bank conflicts).  Hidden
-// activations are kept in BF16 in shared memory; the weights stay resident
-// in shared memory for the CTA's whole (persistent) loop.
+// Inference (k_forward, k_closure): one warp per 16 samples with the
+// activations in registers (see warp_mlp).  Training (k_loss_grad): one CTA
+// of 8 warps per tile of 128 samples, activations and their gradients in
+// shared memory (the weight gradients contract over the samples).  Both
+// use mma.sync m16n8k16 with fragments loaded by ldmatrix from padded
+// shared-memory rows (no bank conflicts).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
+#include <utility>
 
 #include "internal.h"
 #include "mlp.h"
@@ -103,6 +105,17 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// Hidden-layer activation of two pre-activations: rounded to BF16, then
+// the hardware tanh on the BF16 pair (the result is the packed BF16 pair
+// the next layer consumes).  Training and inference share it, so a trained
+// network is evaluated with the function it was trained on.
+__device__ __forceinline__ uint32_t act2(float lo, float hi) {
+    const uint32_t x = pack_bf16(lo, hi);
+    uint32_t y;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
+    return y;
+}
+
 __device__ void load_weights(Packed& dst, const Packed* src) {
     const uint4* s = reinterpret_cast<const uint4*>(src);
     uint4* d = reinterpret_cast<uint4*>(&dst);
@@ -134,10 +147,8 @@ __device__ void dense_tanh(const __nv_bfloat16* A, int lda, int kdim, const __nv
         for (int t = 0; t < 4; ++t) {
             const int c = nb + t * 8 + 2 * tg;
             const float bl = bias[c], bh = bias[c + 1];
-            *reinterpret_cast<uint32_t*>(Hout + (r0 + g) * LDH + c) =
-                pack_bf16(tanhf(acc[t][0] + bl), tanhf(acc[t][1] + bh));
-            *reinterpret_cast<uint32_t*>(Hout + (r0 + g + 8) * LDH + c) =
-                pack_bf16(tanhf(acc[t][2] + bl), tanhf(acc[t][3] + bh));
+            *reinterpret_cast<uint32_t*>(Hout + (r0 + g) * LDH + c) = act2(acc[t][0] + bl, acc[t][1] + bh);
+            *reinterpret_cast<uint32_t*>(Hout + (r0 + g + 8) * LDH + c) = act2(acc[t][2] + bl, acc[t][3] + bh);
         }
     }
 }
@@ -198,29 +209,142 @@ int sm_count() {
     return n;
 }
 
-__global__ void __launch_bounds__(THREADS) k_forward(const float* __restrict__ X, long M, const Packed* __restrict__ P,
-                                                     float* __restrict__ Y) {
-    extern __shared__ __align__(128) unsigned char raw[];
-    Smem& S = *reinterpret_cast<Smem*>(raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, tg = lane & 3;
-    load_weights(S.w, P);
-    const long tiles = (M + ROWS - 1) / ROWS;
-    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const long row0 = tile * ROWS;
-        stage_inputs(S, X, nullptr, row0, M);
-        __syncthreads();
-        float y[2][4];
-        network(S, warp, lane, y);
+// ------------------------------------------------ register-resident inference
+// One warp evaluates the network for 32 samples (two 16-row blocks) with
+// the activations in registers: each layer's accumulator fragments become,
+// after bias and activation, the A fragments of the next layer (the m16n8
+// accumulator layout of two adjacent 8-column tiles is the m16k16 A
+// layout).  Layers are computed 16 output columns at a time, so every
+// weight fragment read from shared memory serves both row blocks.  The
+// inputs come from a per-warp shared tile of 32 rows (ldmatrix).  Warps run
+// independent persistent loops, so the input gathers of some warps overlap
+// the tensor work of others.
+constexpr int IW = 8;                   // warps per inference CTA
+constexpr int ITHREADS = IW * 32;
+constexpr int IROWS = 32;               // samples per warp and tile
+
+struct InferSmem {
+    Packed w;
+    __nv_bfloat16 X[IW][IROWS * LDX];  // per-warp input tile
+    float scale[IW][IROWS];
+};
+
+// Bias + activation of accumulator pair (tile 2np, 2np + 1) into A fragments
+__device__ __forceinline__ void act_frag(uint32_t (&h)[4], const float (&a0)[4], const float (&a1)[4], const float* bias,
+                                         int np, int tg) {
+    const float2 bA = *reinterpret_cast<const float2*>(bias + np * 16 + 2 * tg);
+    const float2 bB = *reinterpret_cast<const float2*>(bias + np * 16 + 8 + 2 * tg);
+    h[0] = act2(a0[0] + bA.x, a0[1] + bA.y);
+    h[1] = act2(a0[2] + bA.x, a0[3] + bA.y);
+    h[2] = act2(a1[0] + bB.x, a1[1] + bB.y);
+    h[3] = act2(a1[2] + bB.x, a1[3] + bB.y);
+}
+
+// y[mb][t][e]: row block mb, output tile t (columns 8t..8t+7); e = 0, 1:
+// row g, columns 2tg, 2tg+1; e = 2, 3: row g + 8.
+__device__ __forceinline__ void warp_mlp32(const Packed& W, const __nv_bfloat16* Xs, float (&y)[2][2][4], int lane) {
+    const int tg = lane & 3;
+    uint32_t h1[2][8][4];
+    {
+        uint32_t xa[2][3][4];
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+        for (int mb = 0; mb < 2; ++mb)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const long m = row0 + warp * 16 + g + 8 * (e >> 1);
-                const int c = t * 8 + 2 * tg + (e & 1);
-                if (m < M && c < NOUT) Y[m * NOUT + c] = y[t][e];
+            for (int kb = 0; kb < 3; ++kb) frag_a(xa[mb][kb], Xs, LDX, 16 * mb, 16 * kb, lane);
+#pragma unroll
+        for (int np = 0; np < 8; ++np) {
+            float acc[2][2][4] = {};
+#pragma unroll
+            for (int kb = 0; kb < 3; ++kb) {
+                uint32_t b[4];
+                frag_b_nk(b, W.W1, LDX, np * 16, kb * 16, lane);
+#pragma unroll
+                for (int mb = 0; mb < 2; ++mb) {
+                    mma16816(acc[mb][0], xa[mb][kb], b[0], b[1]);
+                    mma16816(acc[mb][1], xa[mb][kb], b[2], b[3]);
+                }
             }
-        __syncthreads();
+#pragma unroll
+            for (int mb = 0; mb < 2; ++mb) act_frag(h1[mb][np], acc[mb][0], acc[mb][1], W.b1, np, tg);
+        }
+    }
+    uint32_t h2[2][8][4];
+#pragma unroll
+    for (int np = 0; np < 8; ++np) {
+        float acc[2][2][4] = {};
+#pragma unroll
+        for (int kb = 0; kb < 8; ++kb) {
+            uint32_t b[4];
+            frag_b_nk(b, W.W2, LDH, np * 16, kb * 16, lane);
+#pragma unroll
+            for (int mb = 0; mb < 2; ++mb) {
+                mma16816(acc[mb][0], h1[mb][kb], b[0], b[1]);
+                mma16816(acc[mb][1], h1[mb][kb], b[2], b[3]);
+            }
+        }
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) act_frag(h2[mb][np], acc[mb][0], acc[mb][1], W.b2, np, tg);
+    }
+#pragma unroll
+    for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+        for (int t = 0; t < 2; ++t) y[mb][t][0] = y[mb][t][1] = y[mb][t][2] = y[mb][t][3] = 0.f;
+#pragma unroll
+    for (int kb = 0; kb < 8; ++kb) {
+        uint32_t b[4];
+        frag_b_nk(b, W.W3, LDH, 0, kb * 16, lane);
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+            mma16816(y[mb][0], h2[mb][kb], b[0], b[1]);
+            mma16816(y[mb][1], h2[mb][kb], b[2], b[3]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const float2 bo = *reinterpret_cast<const float2*>(W.b3 + t * 8 + 2 * tg);
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+            y[mb][t][0] += bo.x; y[mb][t][1] += bo.y;
+            y[mb][t][2] += bo.x; y[mb][t][3] += bo.y;
+        }
+    }
+}
+
+// Row of output element (mb, e) within a warp tile, and its output column (t, e).
+__device__ __forceinline__ int out_row(int mb, int e, int lane) { return 16 * mb + (lane >> 2) + 8 * (e >> 1); }
+__device__ __forceinline__ int out_col(int t, int e, int lane) { return 8 * t + 2 * (lane & 3) + (e & 1); }
+
+__global__ void __launch_bounds__(ITHREADS, 1) k_forward(const float* __restrict__ X, long M,
+                                                         const Packed* __restrict__ P, float* __restrict__ Y) {
+    extern __shared__ __align__(128) unsigned char raw[];
+    InferSmem& S = *reinterpret_cast<InferSmem*>(raw);
+    load_weights(S.w, P);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __nv_bfloat16* Xs = S.X[warp];
+    const long tiles = (M + IROWS - 1) / IROWS;
+    for (long tile = (long)blockIdx.x * IW + warp; tile < tiles; tile += (long)gridDim.x * IW) {
+        const long m0 = tile * IROWS;
+        // the tile's rows are contiguous in X: coalesced copy into the tile
+        for (int i = lane; i < IROWS * LDX; i += 32) {
+            const int r = i / LDX, c = i % LDX;
+            const long m = m0 + r;
+            Xs[i] = __float2bfloat16_rn(m < M && c < NIN ? X[m * NIN + c] : 0.f);
+        }
+        __syncwarp();
+        float y[2][2][4];
+        warp_mlp32(S.w, Xs, y, lane);
+        __syncwarp();
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const long m = m0 + out_row(mb, e, lane);
+                    const int o = out_col(t, e, lane);
+                    if (m < M && o < NOUT) Y[m * NOUT + o] = y[mb][t][e];
+                }
     }
 }
 
@@ -440,43 +564,65 @@ __global__ void k_pack(const float* __restrict__ params, Packed* __restrict__ P)
 }
 
 // ------------------------------------------------------------ closure glue
-// Component (grid g, local k) averaged to cell centre (ix, iy): a node axis
-// takes the mean of the nodes i - p and i - p + 1 around cell i (node -1 of
-// a periodic axis is node n - 1, indexed directly: the corner boundary
-// copies of a grid are not maintained), a cell axis the value itself.
-template <class T>
-__device__ __forceinline__ float centre_value(const ClosureArgs<T>& A, int g, int k, int ix, int iy) {
-    const T* c = A.g[g].base + (long)k * A.g[g].cstride;
-    const long P = A.pitch;
-    const bool xn = g & 1, yn = g & 2;
-    int xa = ix, xb = ix, ya = iy, yb = iy;
-    if (xn) { xa = ix - A.p[0]; xb = xa + 1; if (xa < 0) xa = A.g[g].nx - 1; }
-    if (yn) { ya = iy - A.p[1]; yb = ya + 1; if (ya < 0) ya = A.g[g].ny - 1; }
-    const T* ra = c + (long)(ya + 1) * P;
-    const T* rb = c + (long)(yb + 1) * P;
-    float v;
-    if (xn && yn) v = 0.25f * (((float)ra[xa] + (float)ra[xb]) + ((float)rb[xa] + (float)rb[xb]));
-    else if (xn) v = 0.5f * ((float)ra[xa] + (float)ra[xb]);
-    else if (yn) v = 0.5f * ((float)ra[xa] + (float)rb[xa]);
-    else v = (float)ra[xa];
-    return v;
+// Offsets (elements from point (0, 0) of a component) of the stencil of
+// cell (ix, iy) on each grid type: the cell itself (G11), the nodes west /
+// east of it (G21), south / north (G12) and the four corners (G22).  Node i
+// of an axis lies between cells i + p - 1 and i + p; node -1 of a periodic
+// axis is node n - 1, indexed directly (the corner boundary copies of a
+// grid are not maintained).
+struct Stencil {
+    long c, w, e, s, n, sw, se, nw, ne;
+};
+
+__device__ __forceinline__ Stencil stencil(int ix, int iy, int nx, int ny, int px, int py, long P) {
+    const int xw = ix - px < 0 ? nx - 1 : ix - px, xe = ix - px + 1;
+    const int ys = iy - py < 0 ? ny - 1 : iy - py, yn = iy - py + 1;
+    const long rc = (long)(iy + 1) * P, rs = (long)(ys + 1) * P, rn = (long)(yn + 1) * P;
+    return Stencil{rc + ix, rc + xw, rc + xe, rs + ix, rn + ix, rs + xw, rs + xe, rn + xw, rn + xe};
 }
 
-// Features of cell m = iy * nx + ix, the RMS scale s of its moments and
-// 1/s.  A cell whose largest moment magnitude is at most EMPTY counts as
-// empty: features 0, s = 0, 1/s = 0.  Otherwise the RMS is formed relative
-// to the largest magnitude, so that squares of tiny far-field values do not
-// underflow in FP32.
+// Value of a component on grid G averaged to the cell centre: the point
+// itself, the mean of two nodes, or of four.
+template <class T, int G>
+__device__ __forceinline__ float centre(const T* c, const Stencil& o) {
+    if constexpr (G == 0) return (float)c[o.c];
+    else if constexpr (G == 1) return 0.5f * ((float)c[o.w] + (float)c[o.e]);
+    else if constexpr (G == 2) return 0.5f * ((float)c[o.s] + (float)c[o.n]);
+    else return 0.25f * (((float)c[o.sw] + (float)c[o.se]) + ((float)c[o.nw] + (float)c[o.ne]));
+}
+
+template <class T, int... J>
+__device__ __forceinline__ void gather(const T* const* colp, const Stencil& o, float* f, std::integer_sequence<int, J...>) {
+    ((f[J] = centre<T, grid_of(J)>(colp[J], o)), ...);
+}
+template <class T, int... J>
+__device__ __forceinline__ void gather8(const T* const* colp, const Stencil& o, float* f, std::integer_sequence<int, J...>) {
+    ((f[J] = centre<T, grid_of(NMOM + J)>(colp[NMOM + J], o)), ...);
+}
+
+// Base pointers of components 0..count-1 (grid, local from the slot table).
 template <class T>
-__device__ __forceinline__ void cell_features(const ClosureArgs<T>& A, long m, float (&f)[NIN], float& scale,
-                                              float& inv) {
-    const int ix = (int)(m % A.nx), iy = (int)(m / A.nx);
+__device__ __forceinline__ void column_table(const ClosureArgs<T>& A, const T** colp, int count) {
+    if (threadIdx.x < count) {
+        const int gg = A.slot[threadIdx.x].x;
+        colp[threadIdx.x] = A.g[gg].base + (long)A.slot[threadIdx.x].y * A.g[gg].cstride;
+    }
+}
+
+// The 36 moment features of a cell (order <= 7 averaged to the centre and
+// divided by their RMS s), s and 1/s.  A cell whose largest moment
+// magnitude is at most EMPTY counts as empty: features 0, s = 0, 1/s = 0.
+// Otherwise the RMS is formed relative to the largest magnitude, so that
+// squares of tiny far-field values do not underflow in FP32.
+template <class T>
+__device__ __forceinline__ void features36(const T* const* colp, const Stencil& o, bool ok, float (&f)[NMOM],
+                                           float& scale, float& inv) {
+    gather<T>(colp, o, f, std::make_integer_sequence<int, NMOM>{});
     float mx = 0.f;
 #pragma unroll
     for (int j = 0; j < NMOM; ++j) {
-        const float v = centre_value(A, A.slot[j].x, A.slot[j].y, ix, iy);
-        f[j] = v;
-        mx = fmaxf(mx, fabsf(v));
+        f[j] = ok ? f[j] : 0.f;
+        mx = fmaxf(mx, fabsf(f[j]));
     }
     scale = 0.f;
     inv = 0.f;
@@ -490,87 +636,142 @@ __device__ __forceinline__ void cell_features(const ClosureArgs<T>& A, long m, f
     }
 #pragma unroll
     for (int j = 0; j < NMOM; ++j) f[j] *= inv;
-    f[NMOM] = A.lsa[m];
-    f[NMOM + 1] = A.lss[m];
 }
 
+// Training samples: X[m][38] (FP32), scale[m], and (tgt not NULL) the
+// order-8 moments at the centre divided by the scale.
 template <class T>
-__global__ void __launch_bounds__(THREADS) k_samples(const ClosureArgs<T> A, float* __restrict__ X,
-                                                     float* __restrict__ scale, float* __restrict__ tgt) {
-    const long M = (long)A.nx * A.ny;
+__global__ void __launch_bounds__(256) k_samples(const ClosureArgs<T> A, float* __restrict__ X,
+                                                 float* __restrict__ scale, float* __restrict__ tgt) {
+    __shared__ const T* colp[NMOM + NOUT];
+    column_table(A, colp, tgt ? NMOM + NOUT : NMOM);
+    __syncthreads();
+    const int nx = A.nx, ny = A.ny;
+    const long M = (long)nx * ny;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        float f[NIN], s, inv;
-        cell_features(A, m, f, s, inv);
+        const int ix = (int)(m % nx), iy = (int)(m / nx);
+        const Stencil o = stencil(ix, iy, nx, ny, A.p[0], A.p[1], A.pitch);
+        float f[NMOM], s, inv;
+        features36<T>(colp, o, true, f, s, inv);
 #pragma unroll
-        for (int c = 0; c < NIN; ++c) X[m * NIN + c] = f[c];
+        for (int c = 0; c < NMOM; ++c) X[m * NIN + c] = f[c];
+        X[m * NIN + NMOM] = A.lsa[m];
+        X[m * NIN + NMOM + 1] = A.lss[m];
         scale[m] = s;
         if (tgt) {
-            const int ix = (int)(m % A.nx), iy = (int)(m / A.nx);
+            float t[NOUT];
+            gather8<T>(colp, o, t, std::make_integer_sequence<int, NOUT>{});
 #pragma unroll
-            for (int o = 0; o < NOUT; ++o)
-                tgt[m * NOUT + o] = centre_value(A, A.slot[NMOM + o].x, A.slot[NMOM + o].y, ix, iy) * inv;
+            for (int k = 0; k < NOUT; ++k) tgt[m * NOUT + k] = t[k] * inv;
         }
     }
 }
 
-// Fused closure evaluation over all cells: features -> network -> s * y.
-// R_8^m go straight to G11 (with their ghost copies); the centre values of
-// I_8^m go to ctr[o][M] for the node averaging of k_closure_nodes.
+// Closure inputs of every cell as padded BF16 rows xg[m][LDX] (columns 38..
+// LDX-1 zero; rows up to a whole number of 32-row tiles) and the scale
+// sc[m]: one thread per cell, exactly the features of k_samples (the
+// training samples), rounded to BF16.
 template <class T>
-__global__ void __launch_bounds__(THREADS) k_closure(const ClosureArgs<T> A, const Packed* __restrict__ P,
-                                                     float* __restrict__ ctr) {
+__global__ void __launch_bounds__(256) k_closure_features(const ClosureArgs<T> A, __nv_bfloat16* __restrict__ xg,
+                                                          float* __restrict__ sc) {
+    __shared__ const T* colp[NMOM];
+    column_table(A, colp, NMOM);
+    __syncthreads();
+    const int nx = A.nx, ny = A.ny;
+    const int M = nx * ny;
+    const int Mpad = (M + IROWS - 1) / IROWS * IROWS;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < Mpad; m += gridDim.x * blockDim.x) {
+        const bool ok = m < M;
+        const int ix = ok ? m % nx : 0, iy = ok ? m / nx : 0;
+        const Stencil o = stencil(ix, iy, nx, ny, A.p[0], A.p[1], A.pitch);
+        float f[NMOM], scale, inv;
+        features36<T>(colp, o, ok, f, scale, inv);
+        uint32_t w[LDX / 2];
+#pragma unroll
+        for (int c = 0; c < NMOM / 2; ++c) w[c] = pack_bf16(f[2 * c], f[2 * c + 1]);
+        w[NMOM / 2] = pack_bf16(ok ? A.lsa[m] : 0.f, ok ? A.lss[m] : 0.f);
+#pragma unroll
+        for (int c = NIN / 2; c < LDX / 2; ++c) w[c] = 0u;
+        uint4* row = reinterpret_cast<uint4*>(xg + (long)m * LDX);
+#pragma unroll
+        for (int q = 0; q < LDX / 8; ++q) row[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        sc[m] = scale;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(su32(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Closure prediction from the input rows: persistent warps, each
+// double-buffering its 32-row tiles with cp.async, network in registers,
+// s * y written out: R_8^m straight to G11 (with their ghost copies), the
+// centre values of I_8^m to ctr[o][M] for the node averaging of
+// k_closure_nodes.
+struct ClosureSmem {
+    Packed w;
+    __nv_bfloat16 X[IW][2][IROWS * LDX];
+};
+
+template <class T>
+__global__ void __launch_bounds__(ITHREADS, 1) k_closure_mlp(const ClosureArgs<T> A, const Packed* __restrict__ P,
+                                                             const __nv_bfloat16* __restrict__ xg,
+                                                             const float* __restrict__ sc, float* __restrict__ ctr) {
     extern __shared__ __align__(128) unsigned char raw[];
-    Smem& S = *reinterpret_cast<Smem*>(raw);
-    float* s_scale = reinterpret_cast<float*>(raw + sizeof(Smem));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, tg = lane & 3;
+    ClosureSmem& S = *reinterpret_cast<ClosureSmem*>(raw);
     load_weights(S.w, P);
-    const long M = (long)A.nx * A.ny;
-    const long tiles = (M + ROWS - 1) / ROWS;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nx = A.nx, ny = A.ny;
+    const int M = nx * ny;
+    const int tiles = (M + IROWS - 1) / IROWS;
     const long Pp = A.pitch;
-    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const long row0 = tile * ROWS;
-        if (threadIdx.x < ROWS) {
-            const int r = threadIdx.x;
-            const long m = row0 + r;
-            float f[NIN], s = 0.f, inv;
-            if (m < M) {
-                cell_features(A, m, f, s, inv);
-            } else {
+    constexpr int CHUNKS = IROWS * LDX * 2 / 16;      // 16-byte pieces of a tile
+    auto issue = [&](int tile, int buf) {
+        const char* src = reinterpret_cast<const char*>(xg + (long)tile * IROWS * LDX);
+        char* dst = reinterpret_cast<char*>(S.X[warp][buf]);
+        for (int i = lane; i < CHUNKS; i += 32) cp_async16(dst + 16 * i, src + 16 * i);
+        cp_async_commit();
+    };
+    const int stride = gridDim.x * IW;
+    int tile = blockIdx.x * IW + warp;
+    if (tile < tiles) issue(tile, 0);
+    for (int k = 0; tile < tiles; tile += stride, k ^= 1) {
+        if (tile + stride < tiles) issue(tile + stride, k ^ 1);
+        else cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        float scl[2][2];
 #pragma unroll
-                for (int c = 0; c < NIN; ++c) f[c] = 0.f;
-            }
-            uint32_t* row = reinterpret_cast<uint32_t*>(S.X + r * LDX);
+        for (int mb = 0; mb < 2; ++mb)
 #pragma unroll
-            for (int c = 0; c < LDX / 2; ++c)
-                row[c] = pack_bf16(2 * c < NIN ? f[2 * c] : 0.f, 2 * c + 1 < NIN ? f[2 * c + 1] : 0.f);
-            s_scale[r] = s;
-        }
-        __syncthreads();
-        float y[2][4];
-        network(S, warp, lane, y);
+            for (int h = 0; h < 2; ++h) scl[mb][h] = __ldg(sc + tile * IROWS + out_row(mb, 2 * h, lane));
+        float y[2][2][4];
+        warp_mlp32(S.w, S.X[warp][k], y, lane);
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+        for (int mb = 0; mb < 2; ++mb)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int r = warp * 16 + g + 8 * (e >> 1);
-                const long m = row0 + r;
-                const int o = t * 8 + 2 * tg + (e & 1);
-                if (m >= M || o >= NOUT) continue;
-                const float v = s_scale[r] * y[t][e];
-                if (A.slot[NMOM + o].x != 0) { ctr[(long)o * M + m] = v; continue; }
-                const int ix = (int)(m % A.nx), iy = (int)(m / A.nx);
-                const int n = A.nx, ny = A.ny;
-                T* c = A.g[0].base + (long)A.slot[NMOM + o].y * A.g[0].cstride;
-                const T tv = (T)v;
-                c[(long)(iy + 1) * Pp + ix] = tv;
-                // ghost copies: periodic -1 <- n-1, n <- 0; extrapolation -1 <- 0, n <- n-1
-                if (ix == (A.p[0] ? n - 1 : 0)) c[(long)(iy + 1) * Pp - 1] = tv;
-                if (ix == (A.p[0] ? 0 : n - 1)) c[(long)(iy + 1) * Pp + n] = tv;
-                if (iy == (A.p[1] ? ny - 1 : 0)) c[ix] = tv;
-                if (iy == (A.p[1] ? 0 : ny - 1)) c[(long)(ny + 1) * Pp + ix] = tv;
-            }
-        __syncthreads();
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int m = tile * IROWS + out_row(mb, e, lane);
+                    const int o = out_col(t, e, lane);
+                    if (m >= M || o >= NOUT) continue;
+                    const float val = scl[mb][e >> 1] * y[mb][t][e];
+                    if (A.slot[NMOM + o].x != 0) { ctr[(long)o * M + m] = val; continue; }
+                    const int ix = m % nx, iy = m / nx;
+                    T* c = A.g[0].base + (long)A.slot[NMOM + o].y * A.g[0].cstride;
+                    const T tv = (T)val;
+                    c[(long)(iy + 1) * Pp + ix] = tv;
+                    // ghost copies: periodic -1 <- n-1, n <- 0; extrapolation -1 <- 0, n <- n-1
+                    if (ix == (A.p[0] ? nx - 1 : 0)) c[(long)(iy + 1) * Pp - 1] = tv;
+                    if (ix == (A.p[0] ? 0 : nx - 1)) c[(long)(iy + 1) * Pp + nx] = tv;
+                    if (iy == (A.p[1] ? ny - 1 : 0)) c[ix] = tv;
+                    if (iy == (A.p[1] ? 0 : ny - 1)) c[(long)(ny + 1) * Pp + ix] = tv;
+                }
+        __syncwarp();
     }
 }
 
@@ -578,36 +779,38 @@ __global__ void __launch_bounds__(THREADS) k_closure(const ClosureArgs<T> A, con
 // Node k of an axis lies between cells k + p - 1 and k + p (wrapped when
 // periodic, clamped to the boundary cell for extrapolation); ghost copies
 // only on periodic axes (extrapolation node axes are never read outside).
+// Rows of G22 by blockIdx.y, points along x by threads.
 template <class T>
 __global__ void k_closure_nodes(const ClosureArgs<T> A, const float* __restrict__ ctr) {
     const GridDev<T>& G = A.g[3];
-    const long M = (long)A.nx * A.ny;
-    const long total = (long)G.nx * G.ny;
+    const int nx = A.nx, ny = A.ny;
+    const long M = (long)nx * ny;
     const long Pp = A.pitch;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int kx = (int)(t % G.nx), ky = (int)(t / G.nx);
-        int cx0 = kx + A.p[0] - 1, cx1 = kx + A.p[0];
+    for (int ky = blockIdx.y; ky < G.ny; ky += gridDim.y) {
         int cy0 = ky + A.p[1] - 1, cy1 = ky + A.p[1];
-        if (A.p[0]) { cx0 = (cx0 + A.nx) % A.nx; cx1 = cx1 % A.nx; }
-        else { cx0 = max(cx0, 0); cx1 = min(cx1, A.nx - 1); }
-        if (A.p[1]) { cy0 = (cy0 + A.ny) % A.ny; cy1 = cy1 % A.ny; }
-        else { cy0 = max(cy0, 0); cy1 = min(cy1, A.ny - 1); }
+        if (A.p[1]) { cy0 = cy0 < 0 ? ny - 1 : cy0; cy1 = cy1 == ny ? 0 : cy1; }
+        else { cy0 = max(cy0, 0); cy1 = min(cy1, ny - 1); }
+        for (int kx = blockIdx.x * blockDim.x + threadIdx.x; kx < G.nx; kx += gridDim.x * blockDim.x) {
+            int cx0 = kx + A.p[0] - 1, cx1 = kx + A.p[0];
+            if (A.p[0]) { cx0 = cx0 < 0 ? nx - 1 : cx0; cx1 = cx1 == nx ? 0 : cx1; }
+            else { cx0 = max(cx0, 0); cx1 = min(cx1, nx - 1); }
 #pragma unroll
-        for (int o = 0; o < NOUT; ++o) {
-            if (A.slot[NMOM + o].x != 3) continue;
-            const float* c = ctr + (long)o * M;
-            const float v = 0.25f * (c[(long)cy0 * A.nx + cx0] + c[(long)cy0 * A.nx + cx1] +
-                                     c[(long)cy1 * A.nx + cx0] + c[(long)cy1 * A.nx + cx1]);
-            T* d = G.base + (long)A.slot[NMOM + o].y * G.cstride;
-            const T tv = (T)v;
-            d[(long)(ky + 1) * Pp + kx] = tv;
-            if (A.p[0]) {
-                if (kx == G.nx - 1) d[(long)(ky + 1) * Pp - 1] = tv;
-                if (kx == 0) d[(long)(ky + 1) * Pp + G.nx] = tv;
-            }
-            if (A.p[1]) {
-                if (ky == G.ny - 1) d[kx] = tv;
-                if (ky == 0) d[(long)(G.ny + 1) * Pp + kx] = tv;
+            for (int o = 0; o < NOUT; ++o) {
+                if (A.slot[NMOM + o].x != 3) continue;
+                const float* c = ctr + (long)o * M;
+                const float v = 0.25f * ((c[(long)cy0 * nx + cx0] + c[(long)cy0 * nx + cx1]) +
+                                         (c[(long)cy1 * nx + cx0] + c[(long)cy1 * nx + cx1]));
+                T* d = G.base + (long)A.slot[NMOM + o].y * G.cstride;
+                const T tv = (T)v;
+                d[(long)(ky + 1) * Pp + kx] = tv;
+                if (A.p[0]) {
+                    if (kx == G.nx - 1) d[(long)(ky + 1) * Pp - 1] = tv;
+                    if (kx == 0) d[(long)(ky + 1) * Pp + G.nx] = tv;
+                }
+                if (A.p[1]) {
+                    if (ky == G.ny - 1) d[kx] = tv;
+                    if (ky == 0) d[(long)(G.ny + 1) * Pp + kx] = tv;
+                }
             }
         }
     }
@@ -623,9 +826,8 @@ int set_smem(K kernel, size_t bytes, bool& done) {
     return 0;
 }
 
-constexpr size_t SMEM_FWD = sizeof(Smem);
+constexpr size_t SMEM_FWD = sizeof(InferSmem);
 constexpr size_t SMEM_TRAIN = sizeof(Smem) + sizeof(SmemBack);
-constexpr size_t SMEM_CLOSURE = sizeof(Smem) + ROWS * sizeof(float);
 static_assert(SMEM_TRAIN <= 227 * 1024, "training tile exceeds shared memory");
 
 }  // namespace
@@ -641,9 +843,9 @@ int forward(const float* X, long M, const Packed* P, float* Y, void* stream) {
     if (M <= 0) return 0;
     static bool attr = false;
     if (set_smem(k_forward, SMEM_FWD, attr)) return -4;
-    long blocks = (M + ROWS - 1) / ROWS;
+    long blocks = (M + IROWS * IW - 1) / (IROWS * IW);
     if (blocks > sm_count()) blocks = sm_count();
-    k_forward<<<(unsigned)blocks, THREADS, SMEM_FWD, (cudaStream_t)stream>>>(X, M, P, Y);
+    k_forward<<<(unsigned)blocks, ITHREADS, SMEM_FWD, (cudaStream_t)stream>>>(X, M, P, Y);
     return status(cudaGetLastError());
 }
 
@@ -671,26 +873,41 @@ template <class T>
 int samples(const ClosureArgs<T>& A, float* X, float* scale, float* tgt, void* stream) {
     const long M = (long)A.nx * A.ny;
     if (M <= 0) return 0;
-    long blocks = (M + THREADS - 1) / THREADS;
-    if (blocks > 8L * sm_count()) blocks = 8L * sm_count();
-    k_samples<T><<<(unsigned)blocks, THREADS, 0, (cudaStream_t)stream>>>(A, X, scale, tgt);
+    long blocks = (M + 255) / 256;
+    if (blocks > 16L * sm_count()) blocks = 16L * sm_count();
+    k_samples<T><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(A, X, scale, tgt);
     return status(cudaGetLastError());
 }
 
+long closure_scratch_floats(long M) {
+    const long Mpad = (M + IROWS - 1) / IROWS * IROWS;
+    return Mpad * LDX / 2 + Mpad + (long)NOUT * M;      // BF16 input rows, scales, I_8 centre values
+}
+
 template <class T>
-int closure(const ClosureArgs<T>& A, const Packed* P, float* ctr, void* stream) {
+int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, void* stream) {
     static bool attr = false;
-    if (set_smem(k_closure<T>, SMEM_CLOSURE, attr)) return -4;
+    if (set_smem(k_closure_mlp<T>, sizeof(ClosureSmem), attr)) return -4;
     const long M = (long)A.nx * A.ny;
     if (M <= 0) return 0;
-    long blocks = (M + ROWS - 1) / ROWS;
-    if (blocks > sm_count()) blocks = sm_count();
-    k_closure<T><<<(unsigned)blocks, THREADS, SMEM_CLOSURE, (cudaStream_t)stream>>>(A, P, ctr);
+    if (M > 0x7fff0000L) return -8;
+    const long tiles = (M + IROWS - 1) / IROWS;
+    const long Mpad = tiles * IROWS;
+    __nv_bfloat16* xg = reinterpret_cast<__nv_bfloat16*>(scratch);
+    float* sc = scratch + Mpad * LDX / 2;
+    float* ctr = sc + Mpad;
+    long fb = (Mpad + 255) / 256;
+    if (fb > 32L * sm_count()) fb = 32L * sm_count();
+    k_closure_features<T><<<(unsigned)fb, 256, 0, (cudaStream_t)stream>>>(A, xg, sc);
     if (cudaGetLastError() != cudaSuccess) return -4;
-    const long total = (long)A.g[3].nx * A.g[3].ny;
-    long nb = (total + 255) / 256;
-    if (nb > 8L * sm_count()) nb = 8L * sm_count();
-    if (nb > 0) k_closure_nodes<T><<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(A, ctr);
+    long blocks = (tiles + IW - 1) / IW;
+    if (blocks > sm_count()) blocks = sm_count();
+    k_closure_mlp<T><<<(unsigned)blocks, ITHREADS, sizeof(ClosureSmem), (cudaStream_t)stream>>>(A, P, xg, sc, ctr);
+    if (cudaGetLastError() != cudaSuccess) return -4;
+    if (A.g[3].nx > 0 && A.g[3].ny > 0) {
+        const dim3 grid((A.g[3].nx + 255) / 256, A.g[3].ny < 65535 ? A.g[3].ny : 65535);
+        k_closure_nodes<T><<<grid, 256, 0, (cudaStream_t)stream>>>(A, ctr);
+    }
     return status(cudaGetLastError());
 }
 

@@ -18,6 +18,15 @@ constexpr int OUTP = 16;          // output rows padded to two 8-wide tiles
 constexpr int LDX = 56;           // padded row of X and W1 (bf16 elements)
 constexpr int LDH = 136;          // padded row of H1, H2, W2, W3
 
+// Grid of components 0..44 of P_8 in the real ordering of section 3 (per
+// order l: R_l^l, I_l^l, R_l^(l-2), ..., R_l^0): R with even l on G11 (0),
+// R with odd l on G21 (1), I with odd l on G12 (2), I with even l on G22
+// (3), as the placement of section 4.1 puts them.  The closure kernels are
+// unrolled over this table; the host checks it against its own placement.
+constexpr int GRID45[45] = {0, 1, 2, 0, 3, 0, 1, 2, 1, 2, 0, 3, 0, 3, 0, 1, 2, 1, 2, 1, 2, 0, 3,
+                            0, 3, 0, 3, 0, 1, 2, 1, 2, 1, 2, 1, 2, 0, 3, 0, 3, 0, 3, 0, 3, 0};
+constexpr int grid_of(int j) { return GRID45[j]; }
+
 // FP32 parameter vector: W1[128][38], b1[128], W2[128][128], b2[128], W3[9][128], b3[9]
 constexpr int OFF_W1 = 0;
 constexpr int OFF_B1 = OFF_W1 + HID * NIN;
@@ -57,7 +66,11 @@ long grad_blocks(long B);
 int adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps, long step,
          void* stream);
 template <class T> int samples(const ClosureArgs<T>& A, float* X, float* scale, float* tgt, void* stream);
-template <class T> int closure(const ClosureArgs<T>& A, const Packed* P, float* ctr, void* stream);
+// Closure evaluation (features, network, order-8 moments written to G11 and
+// G22); scratch holds closure_scratch_floats(n_x n_y) floats; n_x n_y must
+// stay below 2^31 (else -8).
+long closure_scratch_floats(long M);
+template <class T> int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, void* stream);
 
 }  // namespace mlp
 }  // namespace starmap

@@ -65,3 +65,16 @@ def test_create_without_gpu_fails_cleanly(capi):
     with pytest.raises(capi.StarmapError) as ei:
         capi.Stepper(N=3, ax=(0, 1, 0, 1), n=(8, 8))
     assert ei.value.code == capi.E_CUDA
+
+
+@pytest.mark.parametrize("N", [8, 39])
+def test_grid_placement_follows_kind_and_parity(capi, N):
+    """Section 4.1: R_l^m with even l on G11, odd l on G21; I_l^m with odd l
+    on G12, even l on G22 -- the placement the closure kernels are unrolled
+    over (the first 45 components of any P_N with N >= 8)."""
+    _, _, grid, order, _ = capi.host_matrices(capi.PN2D, N)
+    kinds = [k for (k, _, _) in O.real_moments(N)]
+    for j in range(len(kinds)):
+        l = order[j]
+        want = (0 if l % 2 == 0 else 1) if kinds[j] == "R" else (2 if l % 2 == 1 else 3)
+        assert grid[j] == want, j

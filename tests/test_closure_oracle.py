@@ -125,3 +125,23 @@ def test_adam_first_step_is_signed_learning_rate():
     opt.step(params, {"w": np.array([3.0, -0.2, 0.0])})
     # bias-corrected first step: -lr * g / (|g| + eps)
     np.testing.assert_allclose(params["w"], [1.0 - 0.01, -2.0 + 0.01, 0.5], atol=1e-9)
+
+
+def test_merged_closure_schedule_reuses_one_evaluation_per_odd_pass():
+    """With the merged closure schedule the hook runs n + 1 times in n steps
+    (literal: 2n); with a zero network both equal plain P_7."""
+    p = _problem()
+    calls = []
+    mlp = C.MLP.init(3, scale_out=0.0)
+    s = C.closed_solver(p, mlp)
+    hook = s.pre_odd
+    s.pre_odd = lambda st: (calls.append(st.t), hook(st))
+    s.run(4, merged_closure=True)
+    assert len(calls) == 5
+    base = O.solver_from_problem(p, dt=s.dt)
+    base.run(4)
+    for j in range(36):
+        np.testing.assert_allclose(s.U[j], base.U[j], rtol=0, atol=1e-14 * np.max(np.abs(base.U[0])))
+    calls.clear()
+    s.run(3)
+    assert len(calls) == 6

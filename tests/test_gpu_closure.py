@@ -205,12 +205,13 @@ def test_samples_match_oracle_features_and_targets(bc, precision, kernel):
     assert _rel(Td.cpu().numpy().reshape(M, C.N_OUT), Tr / scale_r[:, None]) <= tol
 
 
+@pytest.mark.parametrize("schedule", ["literal", "merged"])
 @pytest.mark.parametrize("precision,kernel,tol", [("fp64", "gather", 1e-12), ("fp32", "tiled", 1e-5)])
-def test_zero_network_is_plain_p7(precision, kernel, tol):
+def test_zero_network_is_plain_p7(precision, kernel, tol, schedule):
     """A network with zero output layer predicts zero order-8 moments: the
     closed run equals plain P_7 (oracle) with the same dt."""
     p = _closure_problem(precision=precision)
-    s = capi.Stepper.from_problem(p, kernel=kernel, closure="mlp8")
+    s = capi.Stepper.from_problem(p, kernel=kernel, closure="mlp8", schedule=schedule)
     assert s.ncomp == 45
     params = _params(40)
     params[-(C.N_OUT * C.HIDDEN + C.N_OUT):] = 0.0          # W3 and b3
@@ -245,18 +246,20 @@ def test_closure_prediction_matches_oracle_hook(bc):
     assert max(float(np.max(np.abs(r))) for r in ref) > 0
 
 
+@pytest.mark.parametrize("schedule", ["literal", "merged"])
 @pytest.mark.parametrize("precision,kernel", [("fp64", "gather"), ("fp32", "tiled")])
-def test_closed_run_matches_oracle(precision, kernel):
-    """A closed run against the oracle's closed run: the difference stays a
-    small fraction of what the closure changes relative to plain P_7."""
+def test_closed_run_matches_oracle(precision, kernel, schedule):
+    """A closed run against the oracle's closed run (same closure schedule):
+    the difference stays a small fraction of what the closure changes
+    relative to plain P_7."""
     p = _closure_problem(precision=precision, nsteps=5)
     params = _params(42, scale_out=0.6)
-    s = capi.Stepper.from_problem(p, kernel=kernel, closure="mlp8")
+    s = capi.Stepper.from_problem(p, kernel=kernel, closure="mlp8", schedule=schedule)
     s.set_closure(params)
     s.step(p.nsteps)
     got = _state(s)
     o = C.closed_solver(p, _oracle_mlp(params), dt=s.dt)
-    o.run(p.nsteps)
+    o.run(p.nsteps, merged_closure=schedule == "merged")
     plain = O.solver_from_problem(p, dt=s.dt)
     plain.run(p.nsteps)
     ref = [u.T for u in o.U[:36]]
@@ -270,9 +273,6 @@ def test_closure_errors():
     with pytest.raises(capi.StarmapError) as e:
         capi.Stepper(N=5, ax=p.ax, n=p.n, closure="mlp8")
     assert e.value.code == capi.E_UNSUPPORTED
-    with pytest.raises(capi.StarmapError) as e:
-        capi.Stepper(N=7, ax=p.ax, n=p.n, closure="mlp8", schedule="merged")
-    assert e.value.code == capi.E_ARG
     s = capi.Stepper(N=7, ax=p.ax, n=p.n, closure="mlp8")
     with pytest.raises(capi.StarmapError) as e:
         s.step(1)
