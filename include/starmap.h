@@ -342,6 +342,34 @@ int starmap_mlp_loss_grad(starmap_mlp_t* net, const float* X, const float* T, co
  * step. */
 int starmap_mlp_train_step(starmap_mlp_t* net, const float* X, const float* T, const int32_t* idx,
                            size_t B, float lr, float* loss);
+/* ------------------------------------------------------------- batches
+ * Not in the paper: many independent problems advanced together.  A batch
+ * holds `count` FP32 2D P_N instances (any N <= 63, any grid size, without
+ * closure), each a full handle with its own state, material and sources.
+ * starmap_batch_step advances every instance by nsteps of its own dt with
+ * one CUDA graph launch: per pass, one persistent kernel walks the tiles of
+ * all instances (heaviest first) with each instance's own tables; the
+ * pass sequence of a step count is captured once and replayed.  The
+ * schedule is cfgs[0].schedule for all; cfgs[0].cuda_stream (if not NULL)
+ * must be a non-default stream (graphs are captured on it).  Errors:
+ * E_UNSUPPORTED for an FP64, slab or closure instance, else as
+ * starmap_create (the message names the instance). */
+typedef struct starmap_batch_s starmap_batch_t;
+int  starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t** out);
+void starmap_batch_destroy(starmap_batch_t* b);
+const char* starmap_batch_last_error(const starmap_batch_t* b);
+int  starmap_batch_count(const starmap_batch_t* b);
+/* Handle of instance i (borrowed; valid until starmap_batch_destroy) for
+ * the problem-data, read-out and diagnostics entry points.  Stepping an
+ * instance alone with starmap_step is allowed.  NULL if i is out of range. */
+starmap_t* starmap_batch_instance(starmap_batch_t* b, int i);
+/* Kernel launches of one starmap_batch_step(b, nsteps) (inside its graph). */
+long starmap_batch_launches(const starmap_batch_t* b, long nsteps);
+int  starmap_batch_step(starmap_batch_t* b, long nsteps);
+/* Wait for the batch's stream; reports a bounded-wait failure of any
+ * instance (E_TIMEOUT). */
+int  starmap_batch_sync(starmap_batch_t* b);
+
 /* Number of Adam steps taken since creation or the last set_params. */
 long starmap_mlp_steps(const starmap_mlp_t* net);
 int  starmap_mlp_sync(starmap_mlp_t* net);

@@ -127,6 +127,14 @@ def lib():
         "starmap_mlp_train_step": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.c_size_t, ctypes.c_float, ctypes.c_void_p]),
         "starmap_mlp_steps": (ctypes.c_long, [H]),
+        "starmap_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(H)]),
+        "starmap_batch_destroy": (None, [H]),
+        "starmap_batch_last_error": (ctypes.c_char_p, [H]),
+        "starmap_batch_count": (ctypes.c_int, [H]),
+        "starmap_batch_instance": (H, [H, ctypes.c_int]),
+        "starmap_batch_launches": (ctypes.c_long, [H, ctypes.c_long]),
+        "starmap_batch_step": (ctypes.c_int, [H, ctypes.c_long]),
+        "starmap_batch_sync": (ctypes.c_int, [H]),
         "starmap_mlp_sync": (ctypes.c_int, [H]),
     }
     for name, (res, args) in sig.items():
@@ -180,6 +188,29 @@ def host_expm1div(c) -> np.ndarray:
     return a
 
 
+def make_config(N: int, ax, n, bc=("periodic", "periodic"), cn: float = 0.5, precision: str = "fp64",
+                system: str = "pn2d", schedule: str = "literal", kernel: str = "auto", dt: float = 0.0,
+                stream: Optional[int] = None, closure: str = "none") -> Config:
+    """A starmap_config from keyword values (library defaults elsewhere)."""
+    c = Config()
+    lib().starmap_config_default(ctypes.byref(c))
+    c.system = {"pn2d": PN2D, "slab": SLAB}[system]
+    c.N = int(N)
+    for i in range(4):
+        c.ax[i] = float(ax[i])
+    c.n[0], c.n[1] = int(n[0]), int(n[1])
+    bmap = {"periodic": PERIODIC, "extrapolation": EXTRAPOLATION}
+    c.bc[0], c.bc[1] = bmap[bc[0]], bmap[bc[1]]
+    c.cn = float(cn)
+    c.dt = float(dt)
+    c.precision = {"fp64": FP64, "fp32": FP32}[precision]
+    c.schedule = {"literal": SCHEDULE_LITERAL, "merged": SCHEDULE_MERGED}[schedule]
+    c.kernel = {"auto": KERNEL_AUTO, "gather": KERNEL_GATHER, "tiled": KERNEL_TILED}[kernel]
+    c.cuda_stream = stream
+    c.closure = {"none": CLOSURE_NONE, "mlp8": CLOSURE_MLP8}[closure]
+    return c
+
+
 class Stepper:
     """One StaRMAP stepper (a handle of the C ABI)."""
 
@@ -187,34 +218,32 @@ class Stepper:
                  precision: str = "fp64", system: str = "pn2d", schedule: str = "literal",
                  kernel: str = "auto", dt: float = 0.0, stream: Optional[int] = None, closure: str = "none"):
         self._L = lib()
-        c = Config()
-        self._L.starmap_config_default(ctypes.byref(c))
-        c.system = {"pn2d": PN2D, "slab": SLAB}[system]
-        c.N = int(N)
-        for i in range(4):
-            c.ax[i] = float(ax[i])
-        c.n[0], c.n[1] = int(n[0]), int(n[1])
-        bmap = {"periodic": PERIODIC, "extrapolation": EXTRAPOLATION}
-        c.bc[0], c.bc[1] = bmap[bc[0]], bmap[bc[1]]
-        c.cn = float(cn)
-        c.dt = float(dt)
-        c.precision = {"fp64": FP64, "fp32": FP32}[precision]
-        c.schedule = {"literal": SCHEDULE_LITERAL, "merged": SCHEDULE_MERGED}[schedule]
-        c.kernel = {"auto": KERNEL_AUTO, "gather": KERNEL_GATHER, "tiled": KERNEL_TILED}[kernel]
-        c.cuda_stream = stream
-        c.closure = {"none": CLOSURE_NONE, "mlp8": CLOSURE_MLP8}[closure]
+        c = make_config(N, ax, n, bc, cn, precision, system, schedule, kernel, dt, stream, closure)
         h = ctypes.c_void_p()
         rc = self._L.starmap_create(ctypes.byref(c), ctypes.byref(h))
         if rc != OK:
             raise StarmapError(rc, self._L.starmap_last_error(None).decode())
         self._h = h
+        self._owned = True
         self.precision = precision
         self.config = c
+
+    @classmethod
+    def _borrow(cls, handle, precision: str) -> "Stepper":
+        """View of a handle owned elsewhere (a batch instance)."""
+        s = cls.__new__(cls)
+        s._L = lib()
+        s._h = ctypes.c_void_p(handle)
+        s._owned = False
+        s.precision = precision
+        s.config = None
+        return s
 
     # -- lifetime -------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None):
-            self._L.starmap_destroy(self._h)
+            if getattr(self, "_owned", True):
+                self._L.starmap_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -479,3 +508,66 @@ def params_to_dict(v) -> dict:
         o += n
     assert o == MLP_PARAMS
     return out
+
+
+class Batch:
+    """Independent FP32 2D P_N instances stepped together (starmap_batch_t):
+    one graph launch per step call, a persistent kernel per pass."""
+
+    def __init__(self, configs, stream: Optional[int] = None):
+        """configs: list of dicts of make_config keywords (precision fp32)."""
+        self._L = lib()
+        arr = (Config * len(configs))()
+        for i, kw in enumerate(configs):
+            kw = dict(kw)
+            kw.setdefault("precision", "fp32")
+            arr[i] = make_config(**kw)
+        if stream is not None:
+            arr[0].cuda_stream = stream
+        h = ctypes.c_void_p()
+        rc = self._L.starmap_batch_create(arr, len(configs), ctypes.byref(h))
+        if rc != OK:
+            raise StarmapError(rc, self._L.starmap_batch_last_error(None).decode())
+        self._h = h
+        self._inst = [Stepper._borrow(self._L.starmap_batch_instance(h, i), "fp32") for i in range(len(configs))]
+
+    @classmethod
+    def from_problems(cls, problems, schedule: str = "merged", stream: Optional[int] = None) -> "Batch":
+        cfgs = [dict(N=p.N, ax=p.ax, n=p.n, bc=p.bc, cn=p.cn, precision="fp32", schedule=schedule) for p in problems]
+        b = cls(cfgs, stream=stream)
+        for inst, p in zip(b.instances, problems):
+            inst.load_problem(p)
+        return b
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for s in self._inst:
+                s._h = None
+            self._L.starmap_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != OK:
+            raise StarmapError(rc, self._L.starmap_batch_last_error(self._h).decode())
+
+    @property
+    def instances(self):
+        return self._inst
+
+    def __len__(self):
+        return len(self._inst)
+
+    def launches(self, nsteps: int) -> int:
+        return self._L.starmap_batch_launches(self._h, int(nsteps))
+
+    def step(self, n: int = 1):
+        self._check(self._L.starmap_batch_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._L.starmap_batch_sync(self._h))

@@ -69,6 +69,23 @@ struct starmap_s {
     float* ctr = nullptr;                  // closure scratch (input fragments, scales, I_8 centre values)
     float* lsig = nullptr;                 // log(1 + sigma_a), log(1 + sigma_s0) at the cell centres
     bool lsig_dirty = true;
+    unsigned long version = 0;             // bumped whenever the tiled pass parameters change
+    std::string err;
+};
+
+struct starmap_batch_s {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int schedule = STARMAP_SCHEDULE_MERGED;
+    std::vector<starmap_t*> inst;
+    std::vector<unsigned long> uploaded;   // parameter version of each instance on the device
+    std::vector<char> staging;             // host copy of the parameter blocks
+    void* dev_params = nullptr;
+    void* dev_items = nullptr;
+    int nitems = 0;
+    int smem = 0;
+    int grid = 0;
+    std::vector<std::pair<long, cudaGraphExec_t>> graphs;   // captured step sequences by step count
     std::string err;
 };
 
@@ -168,6 +185,7 @@ int build_tables(starmap_t* h) {
         int rc = tiled_update(h->tiled, h->sys, h->comp_class, h->src_slot, h->src_dev, h->frozen, h->dx, h->dy);
         if (rc) return fail(h, rc, tiled_error(h->tiled));
     }
+    ++h->version;
     return STARMAP_OK;
 }
 
@@ -669,6 +687,7 @@ int starmap_set_material(starmap_t* h, int g, const double* sigma_a, const doubl
     rc = h->fp32 ? upload_coefficients<float>(h, g) : upload_coefficients<double>(h, g);
     if (rc) return rc;
     if (h->tiled) tiled_set_coef(h->tiled, g, h->coef[g], h->nclasses);
+    ++h->version;
     return STARMAP_OK;
 }
 
@@ -977,6 +996,209 @@ int starmap_closure_samples(starmap_t* h, float* X, float* scale, float* targets
     rc = h->fp32 ? mlp::samples<float>(closure_args<float>(h), X, scale, targets, h->stream)
                  : mlp::samples<double>(closure_args<double>(h), X, scale, targets, h->stream);
     if (rc) return cuda_fail(h, cudaGetLastError(), "closure samples");
+    return STARMAP_OK;
+}
+
+
+// ---------------------------------------------------------------- batches
+namespace {
+thread_local std::string g_batch_create_error;
+
+int bfail(starmap_batch_t* b, int code, const std::string& msg) {
+    if (b) b->err = msg; else g_batch_create_error = msg;
+    return code;
+}
+
+void batch_release(starmap_batch_t* b) {
+    for (auto& gx : b->graphs) cudaGraphExecDestroy(gx.second);
+    b->graphs.clear();
+    for (starmap_t* h : b->inst) starmap_destroy(h);
+    b->inst.clear();
+    if (b->dev_params) cudaFree(b->dev_params);
+    if (b->dev_items) cudaFree(b->dev_items);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+// Upload the pass parameters of instances whose tables changed.
+int batch_sync_params(starmap_batch_t* b) {
+    const size_t pb = 4 * tiled_params_bytes();
+    bool any = false;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        starmap_t* h = b->inst[i];
+        if (b->uploaded[i] == h->version) continue;
+        if (tiled_export_params(h->tiled, b->staging.data() + i * pb)) return bfail(b, STARMAP_E_STATE, "instance tables not built");
+        b->uploaded[i] = h->version;
+        any = true;
+    }
+    if (!any) return STARMAP_OK;
+    cudaError_t e = cudaMemcpyAsync(b->dev_params, b->staging.data(), b->staging.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, STARMAP_E_CUDA, std::string("upload batch parameters: ") + cudaGetErrorString(e));
+    return STARMAP_OK;
+}
+
+// The pass launches of one starmap_batch_step(b, n) (same schedules as do_steps).
+int batch_issue(starmap_batch_t* b, long n) {
+    auto pass = [&](int P, int w) {
+        return tiled_batch_pass(b->dev_params, b->dev_items, b->nitems, P, w, b->grid, b->smem, b->stream);
+    };
+    if (b->schedule == STARMAP_SCHEDULE_MERGED) {
+        if (pass(1, 0)) return STARMAP_E_CUDA;
+        for (long i = 0; i < n; ++i) {
+            if (pass(0, 1)) return STARMAP_E_CUDA;
+            if (pass(1, i == n - 1 ? 0 : 1)) return STARMAP_E_CUDA;
+        }
+    } else {
+        for (long i = 0; i < n; ++i)
+            if (pass(1, 0) || pass(0, 1) || pass(1, 0)) return STARMAP_E_CUDA;
+    }
+    return STARMAP_OK;
+}
+}  // namespace
+
+int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t** out) {
+    if (!out) return bfail(nullptr, STARMAP_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfgs || count < 1) return bfail(nullptr, STARMAP_E_ARG, "a batch needs at least one configuration");
+    starmap_batch_t* b = new (std::nothrow) starmap_batch_t();
+    if (!b) return bfail(nullptr, STARMAP_E_NOMEM, "host allocation failed");
+    auto bail = [&](int rc) {
+        std::string m = b->err;
+        batch_release(b);
+        delete b;
+        g_batch_create_error = m;
+        return rc;
+    };
+    b->schedule = cfgs[0].schedule;
+    if (b->schedule != STARMAP_SCHEDULE_LITERAL && b->schedule != STARMAP_SCHEDULE_MERGED)
+        return bail(bfail(b, STARMAP_E_ARG, "unknown schedule"));
+    cudaError_t e;
+    if (cfgs[0].cuda_stream) {
+        b->stream = (cudaStream_t)cfgs[0].cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(bfail(b, STARMAP_E_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
+        b->own_stream = true;
+    }
+    struct Item { int inst, tile, cost; };
+    std::vector<Item> items;
+    for (int i = 0; i < count; ++i) {
+        starmap_config c = cfgs[i];
+        if (c.system != STARMAP_PN2D || c.precision != STARMAP_FP32 || c.closure != STARMAP_CLOSURE_NONE)
+            return bail(bfail(b, STARMAP_E_UNSUPPORTED, "batch instance " + std::to_string(i) +
+                                                            ": batches hold FP32 2D P_N instances without closure"));
+        c.kernel = STARMAP_KERNEL_TILED;
+        c.schedule = b->schedule;
+        c.cuda_stream = b->stream;
+        starmap_t* h = nullptr;
+        int rc = starmap_create(&c, &h);
+        if (rc) return bail(bfail(b, rc, "batch instance " + std::to_string(i) + ": " + g_create_error));
+        b->inst.push_back(h);
+        int tx = 0, ty = 0;
+        tiled_tile_grid(h->tiled, &tx, &ty);
+        const int cost = tiled_stage_count(h->tiled, 0) + tiled_stage_count(h->tiled, 1);
+        for (int t = 0; t < tx * ty; ++t) items.push_back({i, t, cost});
+        b->smem = std::max(b->smem, std::max(tiled_smem_bytes(h->tiled, 0), tiled_smem_bytes(h->tiled, 1)));
+    }
+    // heaviest tiles first: CTA k takes items k, k + grid, ... of this order
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& c) { return a.cost > c.cost; });
+    if (items.size() > 0x7fffffffu) return bail(bfail(b, STARMAP_E_ARG, "too many tiles in one batch"));
+    b->nitems = (int)items.size();
+    std::vector<int2> it(items.size());
+    for (size_t k = 0; k < items.size(); ++k) it[k] = make_int2(items[k].inst, items[k].tile);
+    int rc = tiled_batch_prepare(b->smem);
+    if (rc) return bail(bfail(b, rc, "batch kernel needs more shared memory than the device offers"));
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = std::max(1, std::min(b->nitems, sms));
+    b->staging.assign((size_t)count * 4 * tiled_params_bytes(), 0);
+    b->uploaded.assign(count, ~0ul);
+    e = cudaMalloc(&b->dev_params, b->staging.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int2));
+    if (e == cudaSuccess && !it.empty())
+        e = cudaMemcpyAsync(b->dev_items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bail(bfail(b, e == cudaErrorMemoryAllocation ? STARMAP_E_NOMEM : STARMAP_E_CUDA,
+                                            std::string("batch setup: ") + cudaGetErrorString(e)));
+    rc = batch_sync_params(b);
+    if (rc) return bail(rc);
+    *out = b;
+    return STARMAP_OK;
+}
+
+void starmap_batch_destroy(starmap_batch_t* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    delete b;
+}
+
+const char* starmap_batch_last_error(const starmap_batch_t* b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
+
+int starmap_batch_count(const starmap_batch_t* b) { return b ? (int)b->inst.size() : 0; }
+
+starmap_t* starmap_batch_instance(starmap_batch_t* b, int i) {
+    if (!b || i < 0 || i >= (int)b->inst.size()) return nullptr;
+    return b->inst[i];
+}
+
+long starmap_batch_launches(const starmap_batch_t* b, long nsteps) {
+    if (!b || nsteps <= 0) return 0;
+    return b->schedule == STARMAP_SCHEDULE_MERGED ? 2 * nsteps + 1 : 3 * nsteps;
+}
+
+int starmap_batch_step(starmap_batch_t* b, long nsteps) {
+    if (!b) return STARMAP_E_ARG;
+    if (nsteps < 0) return bfail(b, STARMAP_E_ARG, "negative step count");
+    if (nsteps == 0) return STARMAP_OK;
+    for (starmap_t* h : b->inst)
+        if (h->ghosts_dirty) {
+            int rc = fill_ghosts_all<float>(h);
+            if (rc) return bfail(b, rc, h->err);
+        }
+    int rc = batch_sync_params(b);
+    if (rc) return rc;
+    cudaGraphExec_t exec = nullptr;
+    for (auto& gx : b->graphs)
+        if (gx.first == nsteps) exec = gx.second;
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bfail(b, STARMAP_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+        rc = batch_issue(b, nsteps);
+        e = cudaStreamEndCapture(b->stream, &graph);
+        if (rc || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return bfail(b, STARMAP_E_CUDA, std::string("capture of the batch step: ") + cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return bfail(b, STARMAP_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        if (b->graphs.size() >= 8) {
+            cudaGraphExecDestroy(b->graphs.front().second);
+            b->graphs.erase(b->graphs.begin());
+        }
+        b->graphs.push_back({nsteps, exec});
+    }
+    cudaError_t e = cudaGraphLaunch(exec, b->stream);
+    if (e != cudaSuccess) return bfail(b, STARMAP_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    for (starmap_t* h : b->inst) {
+        h->t += nsteps * h->dt;
+        h->steps += nsteps;
+        h->have_output = false;
+    }
+    return STARMAP_OK;
+}
+
+int starmap_batch_sync(starmap_batch_t* b) {
+    if (!b) return STARMAP_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, STARMAP_E_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        int rc = poll_kernel(b->inst[i]);
+        if (rc) return bfail(b, rc, "instance " + std::to_string(i) + ": " + b->inst[i]->err);
+    }
     return STARMAP_OK;
 }
 

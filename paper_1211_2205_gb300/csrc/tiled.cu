@@ -416,6 +416,42 @@ int tiled_poll(TiledPlan* pl, void* stream) {
 
 const char* tiled_error(TiledPlan* p) { return p ? p->err.c_str() : "tiled kernel unavailable"; }
 
+size_t tiled_params_bytes() { return sizeof(Params); }
+
+int tiled_export_params(TiledPlan* pl, void* host4) {
+    if (!pl || !pl->ready) return -7;
+    Params* d = static_cast<Params*>(host4);
+    for (int P = 0; P < 2; ++P)
+        for (int w = 0; w < 2; ++w) d[2 * P + w] = pl->prm[P][w];
+    return 0;
+}
+
+int tiled_smem_bytes(TiledPlan* pl, int P) { return pl ? pl->smem_bytes[P] : 0; }
+
+void tiled_tile_grid(TiledPlan* pl, int* tx, int* ty) {
+    *tx = pl ? pl->tiles_x : 0;
+    *ty = pl ? pl->tiles_y : 0;
+}
+
+int tiled_stage_count(TiledPlan* pl, int P) { return pl ? (int)pl->tab[P].stages.size() : 0; }
+
+int tiled_batch_prepare(int smem_bytes) {
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem_bytes + (int)sizeof(Params) > maxsm) return -8;
+    return cudaFuncSetAttribute(k_tiled_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) == cudaSuccess
+               ? 0 : -4;
+}
+
+int tiled_batch_pass(const void* params, const void* items, int nitems, int P, int which, int grid, int smem_bytes,
+                     void* stream) {
+    if (nitems <= 0) return 0;
+    k_tiled_batch<<<grid, THREADS, smem_bytes, (cudaStream_t)stream>>>(
+        static_cast<const Params*>(params), static_cast<const int2*>(items), nitems, P, which);
+    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
 void tiled_destroy(TiledPlan* p) {
     if (!p) return;
     free_tables(p);

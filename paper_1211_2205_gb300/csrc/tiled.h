@@ -31,4 +31,18 @@ int tiled_poll(TiledPlan* plan, void* stream);
 const char* tiled_error(TiledPlan* plan);
 void tiled_destroy(TiledPlan* plan);
 
+// Batched passes over several plans (one persistent launch per pass).
+size_t tiled_params_bytes();
+// Copy the plan's four pass parameter blocks (index 2 P + which) to host4.
+int tiled_export_params(TiledPlan* plan, void* host4);
+int tiled_smem_bytes(TiledPlan* plan, int P);
+void tiled_tile_grid(TiledPlan* plan, int* tiles_x, int* tiles_y);
+int tiled_stage_count(TiledPlan* plan, int P);
+// Allow the batch kernel smem_bytes of dynamic shared memory.
+int tiled_batch_prepare(int smem_bytes);
+// items: device array of (instance, tile); params: device array of
+// 4 * instances parameter blocks (instance i, parity P, which at 4 i + 2 P + which).
+int tiled_batch_pass(const void* params, const void* items, int nitems, int P, int which, int grid, int smem_bytes,
+                     void* stream);
+
 }  // namespace starmap

@@ -105,6 +105,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -215,7 +218,11 @@ __device__ __forceinline__ f2 diff_x(const float* row, int c, bool c_even) {
     return f2_sub(f2_make(hi, Q), P);
 }
 
-__global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant__ Params prm) {
+// One tile of one pass.  maps: the pass's four tensor maps (in parameter or
+// global memory: TMA reads them from there); prm: everything else.
+// first_tile: the CTA's first tile (later tiles of a persistent CTA invalidate and
+// re-initialise the barriers; the caller synchronises the CTA in between).
+__device__ __forceinline__ void tiled_tile(const Params& prm, const CUtensorMap* maps, int tile, bool first_tile) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + NSTAGES;
@@ -226,12 +233,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x;
     const int x0 = (tile % prm.tiles_x) * TX;
     const int y0 = (tile / prm.tiles_x) * TY;
 
     if (tid == 0) {
         for (int r = 0; r < NSTAGES; ++r) {
+            if (!first_tile) {
+                mbar_inval(&full[r]);
+                mbar_inval(&empty[r]);
+            }
             mbar_init(&full[r], 1);
             mbar_init(&empty[r], CONSUMER_WARPS);
         }
@@ -268,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
         // box origin of this lane's slot (tensor coordinates x' = x + VEC, row = y + 1)
         const int bx = slot == 0 ? bxR : slot == 1 ? bxI : x0 + VEC;
         const int by = slot == 0 ? byR : slot == 1 ? byI : y0 + 1;
-        const CUtensorMap* map = &prm.maps[slot];
+        const CUtensorMap* map = maps + slot;
         const int nst = (prm.nstages + STEPS_PER_STAGE - 1) / STEPS_PER_STAGE;
         int last = -1;
         bool ok = true;
@@ -537,6 +547,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant
             finalize(t, W);
             stage_done();
         }
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant__ Params prm) {
+    tiled_tile(prm, prm.maps, blockIdx.x, true);
+}
+
+// Batched pass: a persistent grid walks the (instance, tile) items of all
+// instances (items sorted by decreasing cost, CTA b takes items b, b + grid,
+// ...).  Instance i's parameters for parity P and coefficient set `which`
+// are prms[(2 i + P) * 2 + which] in global memory; the CTA copies them to
+// shared memory and hands TMA the tensor maps of the global copy.
+__global__ void __launch_bounds__(THREADS, 1) k_tiled_batch(const Params* __restrict__ prms,
+                                                            const int2* __restrict__ items, int nitems, int P,
+                                                            int which) {
+    __shared__ Params s_prm;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = items[it];
+        const Params* g = prms + (2 * item.x + P) * 2 + which;
+        if (it != (int)blockIdx.x) __syncthreads();          // previous tile done with s_prm and the barriers
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(g);
+            uint4* dst = reinterpret_cast<uint4*>(&s_prm);
+            for (int i = threadIdx.x; i < (int)(sizeof(Params) / 16); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        tiled_tile(s_prm, g->maps, item.y, it == (int)blockIdx.x);
     }
 }
 
