@@ -9,7 +9,16 @@ steps.  A bench step is one full time step dt of every moment at every grid
 point; the metric is moment-cell updates per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                  [--workload random_p39|checkerboard_p13|gaussian_p5] [--kernel auto|gather|tiled]
+                  [--workload random_p39|checkerboard_p13|gaussian_p5|batched_256|closure_p7]
+                  [--kernel auto|gather|tiled]
+
+batched_256: 256 independent FP32 instances (grids 64^2..512^2, N in
+{3,..,15}, random piecewise-constant media, Gaussian sources) advanced by
+one graph launch per step call; same metric over all instances.
+closure_p7: the learned order-8 closure of P_7, trained on the GPU from
+P_39 runs on 512x512 random media; the line reports the error-matched
+speedup against plain P_N on held-out media (a bench step is one held-out
+medium).
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (weak scaling; the method has no cross-replica exchange), timing is bracketed
@@ -54,6 +63,10 @@ def workload(name: str):
         return inputs.checkerboard_p13(), "2D P_13 FP32 512x512 checkerboard, extrapolation, source"
     if name == "gaussian_p5":
         return inputs.gaussian_p5(), "2D P_5 FP64 64x64 periodic Gaussian"
+    if name == "batched_256":
+        return ([inputs.batched_instance(k) for k in range(256)],
+                "256 independent 2D P_N FP32 instances, grids 64^2-512^2, N in {3..15}, piecewise-constant media, "
+                "Gaussian sources, one graph launch per step call")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -195,8 +208,15 @@ def run_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
         return 0
+    if args.workload == "closure_p7":
+        print(json.dumps({"impl": "reference", "unavailable": "the error-matched speedup compares GPU runs of "
+                          "the closed and plain systems; the oracle's closed P_7 is exercised by the tests"}))
+        return 0
     problem, desc = workload(args.workload)
-    cells = {"random_p39": 48, "checkerboard_p13": 96, "gaussian_p5": 64}[args.workload]
+    if args.workload == "batched_256":
+        problem = min(problem, key=lambda p: p.n[0] * (p.N + 1) ** 2)
+        desc += f"; oracle sample from the smallest instance ({problem.name})"
+    cells = {"random_p39": 48, "checkerboard_p13": 96, "gaussian_p5": 64, "batched_256": 64}[args.workload]
     vals = []
     for _ in range(args.warmup):
         oracle_sample(problem, cells, 1)
@@ -348,6 +368,170 @@ def run_native(args):
     return 0
 
 
+def run_batch(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1211_2205_gb300 import capi
+
+    problems, desc = workload("batched_256")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    b = capi.Batch.from_problems(problems, schedule="merged", stream=stream.cuda_stream)
+    inst = b.instances
+    pts = [[inst[i].moment_info(j)["nx"] * inst[i].moment_info(j)["ny"] for j in range(inst[i].ncomp)]
+           for i in range(len(inst))]
+    updates_per_step = sum(sum(p) for p in pts)
+    state_bytes = sum(s.state_bytes() for s in inst)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    b.step(args.warmup)
+    b.sync()
+    barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        b.step(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    b.sync()
+    ms = start.elapsed_time(stop)
+    units, ms_max = aggregate(updates_per_step * args.steps, ms, world)
+    value = units / (ms_max / 1e3)
+    # roofline of the batch kernel: every launch in the timed region is one
+    # batched pass; algorithmic bytes of all of them over the region's time
+    even = sum(algorithmic_pass_bytes(s, 0, 4) for s in inst)
+    odd = sum(algorithmic_pass_bytes(s, 1, 4) for s in inst)
+    launches = b.launches(args.steps)
+    alg_total = args.steps * even + (args.steps + 1) * odd
+    achieved = alg_total / (ms / 1e3) / 1e9
+    pk, pk_kind = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+
+    # end to end from host buffers: re-upload every instance's source from
+    # the host, K steps, read back every R_0^0
+    srcs = []
+    for s, p in zip(inst, problems):
+        X, Y = s.grid_coords(0)
+        srcs.append(np.ascontiguousarray(np.broadcast_to(p.sources[0][1](0.0, X, Y), X.shape), dtype=np.float64))
+    h2d = sum(a.nbytes for a in srcs)
+    d2h = sum(s.moment_info(0)["nx"] * s.moment_info(0)["ny"] * 8 for s in inst)
+    barrier()
+    t0 = time.perf_counter()
+    for s, a in zip(inst, srcs):
+        s.clear()
+        s.set_source(0, a)
+    b.step(args.steps)
+    finite = all(np.isfinite(s.moments(0)).all() for s in inst)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_units, e2e_ms = aggregate(updates_per_step * args.steps, e2e_s * 1e3, world)
+    assert finite
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched_256", "description": desc, "instances": len(inst),
+                   "updates_per_step": updates_per_step, "state_bytes": state_bytes, "schedule": "merged",
+                   "kernel": "tiled_batch (persistent, CUDA graph)",
+                   "l2_flush": "none: state larger than L2", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "tiled_batch", "algorithmic_bytes_per_launch": alg_total / launches,
+                     "launch_ms": ms / launches, "peak_kind": f"{pk_kind} hbm_gbs"},
+        "e2e": {"value": e2e_units / (e2e_ms / 1e3), "unit": "updates/s",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        small = min(problems, key=lambda p: p.n[0] * (p.N + 1) ** 2)
+        v, sample, el = oracle_sample(small, 64, 6)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                                "sample": sample + f" (instance {small.name})"}
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_closure(args):
+    """Train the closure on P_39 runs, then evaluate K held-out media."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1211_2205_gb300 import capi, closure
+
+    t0 = time.perf_counter()
+    data = closure.generate(list(range(8)), n=512, N_ref=39, snapshots=8, t_final=0.5)
+    t1 = time.perf_counter()
+    tr = closure.train(data, steps=6000, batch=8192)
+    t2 = time.perf_counter()
+    media = max(1, min(args.steps, 4))
+    ev = closure.evaluate(tr.params, [100 + k for k in range(media)], n=512, repeats=2)
+    # cost of one closure evaluation: closure + odd pass minus the same odd pass without closure
+    p = inputs.closure_medium(100, n=512, N=7)
+    dt = closure.common_dt(p, 39)
+    stream = torch.cuda.Stream()
+    cl = capi.Stepper.from_problem(p, dt=dt, closure="mlp8", schedule="merged", stream=stream.cuda_stream)
+    cl.set_closure(tr.params)
+    pl = capi.Stepper.from_problem(inputs.Problem(**{**p.__dict__, "N": 8}), dt=dt, schedule="merged",
+                                   stream=stream.cuda_stream)
+    times = {}
+    for name, st in (("closed", cl), ("plain", pl)):
+        st.step(2)
+        st.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            for _ in range(20):
+                st.run_pass(1, 1)
+            b.record(stream)
+        st.sync()
+        b.synchronize()
+        times[name] = a.elapsed_time(b) / 20
+    eval_ms = times["closed"] - times["plain"]
+    cells = p.n[0] * p.n[1]
+    flops = 2.0 * cells * (capi.MLP_INPUTS * capi.MLP_HIDDEN + capi.MLP_HIDDEN ** 2 + capi.MLP_HIDDEN * capi.MLP_OUTPUTS)
+    pk, pk_kind = peaks()
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    achieved = flops / (eval_ms / 1e3) / 1e12
+    cl.close()
+    pl.close()
+    value = ev["error_matched_speedup"]
+    line = {
+        "metric": "error-matched speedup vs plain P_N", "value": value, "unit": "x", "n_gpus": world,
+        "steps": media, "warmup": 0, "ms_per_step": ev["closure"]["ms"] / ev["cases"][0]["steps"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+        "data": "synthetic",
+        "config": {"workload": "closure_p7", "description": "P_7 FP32 + per-cell MLP 38-128-128-9 (BF16, FP32 "
+                   "accumulation) predicting the order-8 moments, merged closure schedule; trained on P_39 runs "
+                   "over 8 seeded 512x512 random media; held-out media 100.. ; error = rel-L2 of R_0^0 vs P_39",
+                   "train_samples": data.count, "train_steps": tr.steps, "final_train_loss": tr.losses[-1],
+                   "generate_s": t1 - t0, "train_s": t2 - t1, "matched_N": ev["matched_N"],
+                   "closure": ev["closure"], "plain": ev["plain"], "gain_vs_p7": ev["gain_vs_p7"],
+                   "l2_flush": "none"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "closure evaluation (features + mma.sync MLP + nodes)",
+                     "flops_per_launch": flops, "launch_ms": eval_ms, "peak_kind": f"{pk_kind} bf16_tflops"},
+        "e2e": None,
+        "gpu_launches": None,
+        "clocks": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,6 +546,10 @@ def main():
         raise SystemExit("at least 3 warm-up steps are required")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched_256":
+        return run_batch(args)
+    if args.workload == "closure_p7":
+        return run_closure(args)
     return run_native(args)
 
 
