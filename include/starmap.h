@@ -80,7 +80,10 @@ extern "C" {
 /* Kernel selection for the half-step passes. */
 #define STARMAP_KERNEL_AUTO    0  /* tiled kernel where supported, else gather */
 #define STARMAP_KERNEL_GATHER  1  /* one thread per point, CSR loop over moments */
-#define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N, N <= 63) */
+#define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N, N <= 63);
+                                     tile height chosen by N */
+#define STARMAP_KERNEL_TILED_TALL  3  /* tiled, 64 x 10 tiles, one CTA per SM */
+#define STARMAP_KERNEL_TILED_SHORT 4  /* tiled, 64 x 5 tiles, two CTAs per SM */
 
 /* Closure of the moment hierarchy.  NONE: the P_N truncation of section 3
  * (moments of order N+1 are zero).  MLP8: not in the paper (its outlook,
@@ -159,7 +162,8 @@ int    starmap_num_moments(const starmap_t* h);
 double starmap_dt(const starmap_t* h);
 double starmap_time(const starmap_t* h);
 long   starmap_steps_done(const starmap_t* h);
-/* Kernel actually used for the passes (STARMAP_KERNEL_GATHER or _TILED). */
+/* Kernel actually used for the passes (STARMAP_KERNEL_GATHER, _TILED_TALL or
+ * _TILED_SHORT). */
 int    starmap_kernel(const starmap_t* h);
 /* Component j: order l, index m (>= 0), is_imag (1 for I_l^m), grid 0..3,
  * and the size nx x ny of its grid.  Any output pointer may be NULL. */

@@ -23,7 +23,7 @@ PERIODIC, EXTRAPOLATION = 0, 1
 PN2D, SLAB = 0, 1
 FP64, FP32 = 0, 1
 SCHEDULE_LITERAL, SCHEDULE_MERGED = 0, 1
-KERNEL_AUTO, KERNEL_GATHER, KERNEL_TILED = 0, 1, 2
+KERNEL_AUTO, KERNEL_GATHER, KERNEL_TILED, KERNEL_TILED_TALL, KERNEL_TILED_SHORT = 0, 1, 2, 3, 4
 CLOSURE_NONE, CLOSURE_MLP8 = 0, 1
 MLP_INPUTS, MLP_HIDDEN, MLP_OUTPUTS, MLP_PARAMS = 38, 128, 9, 22665
 
@@ -205,7 +205,8 @@ def make_config(N: int, ax, n, bc=("periodic", "periodic"), cn: float = 0.5, pre
     c.dt = float(dt)
     c.precision = {"fp64": FP64, "fp32": FP32}[precision]
     c.schedule = {"literal": SCHEDULE_LITERAL, "merged": SCHEDULE_MERGED}[schedule]
-    c.kernel = {"auto": KERNEL_AUTO, "gather": KERNEL_GATHER, "tiled": KERNEL_TILED}[kernel]
+    c.kernel = {"auto": KERNEL_AUTO, "gather": KERNEL_GATHER, "tiled": KERNEL_TILED, "tiled_tall": KERNEL_TILED_TALL,
+                "tiled_short": KERNEL_TILED_SHORT}[kernel]
     c.cuda_stream = stream
     c.closure = {"none": CLOSURE_NONE, "mlp8": CLOSURE_MLP8}[closure]
     return c
@@ -275,7 +276,13 @@ class Stepper:
 
     @property
     def kernel(self) -> str:
-        return {KERNEL_GATHER: "gather", KERNEL_TILED: "tiled"}[self._L.starmap_kernel(self._h)]
+        """"gather" or "tiled" (either tile height)."""
+        return "gather" if self._L.starmap_kernel(self._h) == KERNEL_GATHER else "tiled"
+
+    @property
+    def tile_rows(self) -> int:
+        """Rows of the tiled kernel's tiles (10 or 5; 0 for the gather kernel)."""
+        return {KERNEL_GATHER: 0, KERNEL_TILED_TALL: 10, KERNEL_TILED_SHORT: 5}[self._L.starmap_kernel(self._h)]
 
     def moment_info(self, j: int):
         v = [ctypes.c_int() for _ in range(6)]

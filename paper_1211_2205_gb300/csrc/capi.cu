@@ -77,6 +77,7 @@ struct starmap_batch_s {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int schedule = STARMAP_SCHEDULE_MERGED;
+    int variant = 1;                       // tile height of every instance (see starmap_batch_create)
     std::vector<starmap_t*> inst;
     std::vector<unsigned long> uploaded;   // parameter version of each instance on the device
     std::vector<char> staging;             // host copy of the parameter blocks
@@ -264,7 +265,7 @@ int fill_ghosts_all(starmap_t* h) {
 // even: G11, G22.  which: 0 half-step coefficients, 1 full-step.
 template <class T>
 int run_pass(starmap_t* h, bool odd, int which) {
-    if (h->kernel_used == STARMAP_KERNEL_TILED) {
+    if (h->kernel_used != STARMAP_KERNEL_GATHER) {
         int rc = tiled_pass(h->tiled, odd, which, h->stream);
         if (rc) return fail(h, rc, tiled_error(h->tiled));
         return STARMAP_OK;
@@ -506,7 +507,7 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
     if (c.precision != STARMAP_FP64 && c.precision != STARMAP_FP32) return fail(nullptr, STARMAP_E_ARG, "unknown precision");
     if (c.schedule != STARMAP_SCHEDULE_LITERAL && c.schedule != STARMAP_SCHEDULE_MERGED)
         return fail(nullptr, STARMAP_E_ARG, "unknown schedule");
-    if (c.kernel < STARMAP_KERNEL_AUTO || c.kernel > STARMAP_KERNEL_TILED) return fail(nullptr, STARMAP_E_ARG, "unknown kernel");
+    if (c.kernel < STARMAP_KERNEL_AUTO || c.kernel > STARMAP_KERNEL_TILED_SHORT) return fail(nullptr, STARMAP_E_ARG, "unknown kernel");
     if (c.closure != STARMAP_CLOSURE_NONE && c.closure != STARMAP_CLOSURE_MLP8)
         return fail(nullptr, STARMAP_E_ARG, "unknown closure");
     if (c.closure == STARMAP_CLOSURE_MLP8) {
@@ -570,12 +571,16 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
     }
     // kernel choice
     bool tiled_ok = tiled_supported(c.system, h->nsys, c.precision);
-    if (c.kernel == STARMAP_KERNEL_TILED && !tiled_ok) {
+    const bool want_tiled = c.kernel >= STARMAP_KERNEL_TILED;
+    if (want_tiled && !tiled_ok) {
         delete h;
         return fail(nullptr, STARMAP_E_UNSUPPORTED, "tiled kernel needs FP32, the 2D P_N system, N <= 63 and TMA support");
     }
-    h->kernel_used = (c.kernel == STARMAP_KERNEL_TILED || (c.kernel == STARMAP_KERNEL_AUTO && tiled_ok))
-                         ? STARMAP_KERNEL_TILED : STARMAP_KERNEL_GATHER;
+    int variant = tiled_default_variant(h->nsys);
+    if (c.kernel == STARMAP_KERNEL_TILED_TALL) variant = 0;
+    if (c.kernel == STARMAP_KERNEL_TILED_SHORT) variant = 1;
+    h->kernel_used = (want_tiled || (c.kernel == STARMAP_KERNEL_AUTO && tiled_ok))
+                         ? (variant ? STARMAP_KERNEL_TILED_SHORT : STARMAP_KERNEL_TILED_TALL) : STARMAP_KERNEL_GATHER;
 
     // device resources
     cudaError_t e;
@@ -601,13 +606,14 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc reduction"));
     e = cudaMalloc(&h->result, 4 * sizeof(double));
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc reduction"));
-    if (h->kernel_used == STARMAP_KERNEL_TILED) {
+    if (h->kernel_used != STARMAP_KERNEL_GATHER) {
         TiledGeometry geo;
         for (int g = 0; g < 4; ++g) {
             geo.base[g] = h->base[g]; geo.cstride[g] = h->cstride[g];
             geo.nx[g] = h->nxg[g]; geo.ny[g] = h->nyg[g]; geo.K[g] = h->Kg[g];
         }
         geo.pitch = h->pitch; geo.rows = h->rows; geo.p[0] = h->p[0]; geo.p[1] = h->p[1]; geo.N = h->nsys;
+        geo.variant = h->kernel_used == STARMAP_KERNEL_TILED_SHORT ? 1 : 0;
         int rc = tiled_create(geo, &h->tiled);
         if (rc) { std::string m = h->tiled ? tiled_error(h->tiled) : "tiled kernel setup failed"; return bail(fail(h, rc, m)); }
     }
@@ -1040,7 +1046,7 @@ int batch_sync_params(starmap_batch_t* b) {
 // The pass launches of one starmap_batch_step(b, n) (same schedules as do_steps).
 int batch_issue(starmap_batch_t* b, long n) {
     auto pass = [&](int P, int w) {
-        return tiled_batch_pass(b->dev_params, b->dev_items, b->nitems, P, w, b->grid, b->smem, b->stream);
+        return tiled_batch_pass(b->dev_params, b->dev_items, b->nitems, P, w, b->grid, b->smem, b->variant, b->stream);
     };
     if (b->schedule == STARMAP_SCHEDULE_MERGED) {
         if (pass(1, 0)) return STARMAP_E_CUDA;
@@ -1080,14 +1086,18 @@ int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t*
         if (e != cudaSuccess) return bail(bfail(b, STARMAP_E_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
         b->own_stream = true;
     }
-    struct Item { int inst, tile, cost; };
-    std::vector<Item> items;
+    struct Inst { int tiles, cost; };       // tiles and per-tile cost (stages of both parities)
+    std::vector<Inst> shapes;
+    // one tile height for all instances: the default of the largest order
+    int maxN = 1;
+    for (int i = 0; i < count; ++i) maxN = std::max(maxN, cfgs[i].N);
+    b->variant = tiled_default_variant(maxN);
     for (int i = 0; i < count; ++i) {
         starmap_config c = cfgs[i];
         if (c.system != STARMAP_PN2D || c.precision != STARMAP_FP32 || c.closure != STARMAP_CLOSURE_NONE)
             return bail(bfail(b, STARMAP_E_UNSUPPORTED, "batch instance " + std::to_string(i) +
                                                             ": batches hold FP32 2D P_N instances without closure"));
-        c.kernel = STARMAP_KERNEL_TILED;
+        c.kernel = b->variant ? STARMAP_KERNEL_TILED_SHORT : STARMAP_KERNEL_TILED_TALL;
         c.schedule = b->schedule;
         c.cuda_stream = b->stream;
         starmap_t* h = nullptr;
@@ -1096,28 +1106,43 @@ int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t*
         b->inst.push_back(h);
         int tx = 0, ty = 0;
         tiled_tile_grid(h->tiled, &tx, &ty);
-        const int cost = tiled_stage_count(h->tiled, 0) + tiled_stage_count(h->tiled, 1);
-        for (int t = 0; t < tx * ty; ++t) items.push_back({i, t, cost});
+        shapes.push_back({tx * ty, tiled_stage_count(h->tiled, 0) + tiled_stage_count(h->tiled, 1)});
         b->smem = std::max(b->smem, std::max(tiled_smem_bytes(h->tiled, 0), tiled_smem_bytes(h->tiled, 1)));
     }
-    // heaviest tiles first: CTA k takes items k, k + grid, ... of this order
-    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& c) { return a.cost > c.cost; });
-    if (items.size() > 0x7fffffffu) return bail(bfail(b, STARMAP_E_ARG, "too many tiles in one batch"));
-    b->nitems = (int)items.size();
-    std::vector<int2> it(items.size());
-    for (size_t k = 0; k < items.size(); ++k) it[k] = make_int2(items[k].inst, items[k].tile);
-    int rc = tiled_batch_prepare(b->smem);
-    if (rc) return bail(bfail(b, rc, "batch kernel needs more shared memory than the device offers"));
+    // Items: runs of consecutive tiles of one instance, each about 1/4 of a
+    // CTA's fair share of the work (so a run streams through one pipeline,
+    // and the heaviest-first round robin still balances), heaviest first:
+    // CTA k takes items k, k + grid, ...
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->grid = std::max(1, std::min(b->nitems, sms));
+    double total = 0;
+    for (const Inst& x : shapes) total += (double)x.tiles * x.cost;
+    const int slots = sms * tiled_ctas_per_sm(b->variant);     // resident CTAs of the persistent grid
+    const double target = std::max(1.0, total / (4.0 * slots));
+    struct Item { int inst, first, count; double cost; };
+    std::vector<Item> items;
+    for (int i = 0; i < count; ++i) {
+        const int per = std::max(1, std::min(shapes[i].tiles, (int)std::lround(target / std::max(1, shapes[i].cost))));
+        for (int t = 0; t < shapes[i].tiles; t += per) {
+            const int c = std::min(per, shapes[i].tiles - t);
+            items.push_back({i, t, c, (double)c * shapes[i].cost});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& c) { return a.cost > c.cost; });
+    if (items.size() > 0x7fffffffu) return bail(bfail(b, STARMAP_E_ARG, "too many tiles in one batch"));
+    b->nitems = (int)items.size();
+    std::vector<int4> it(items.size());
+    for (size_t k = 0; k < items.size(); ++k) it[k] = make_int4(items[k].inst, items[k].first, items[k].count, 0);
+    int rc = tiled_batch_prepare(b->smem, b->variant);
+    if (rc) return bail(bfail(b, rc, "batch kernel needs more shared memory than the device offers"));
+    b->grid = std::max(1, std::min(b->nitems, slots));
     b->staging.assign((size_t)count * 4 * tiled_params_bytes(), 0);
     b->uploaded.assign(count, ~0ul);
     e = cudaMalloc(&b->dev_params, b->staging.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int4));
     if (e == cudaSuccess && !it.empty())
-        e = cudaMemcpyAsync(b->dev_items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
+        e = cudaMemcpyAsync(b->dev_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bail(bfail(b, e == cudaErrorMemoryAllocation ? STARMAP_E_NOMEM : STARMAP_E_CUDA,
                                             std::string("batch setup: ") + cudaGetErrorString(e)));

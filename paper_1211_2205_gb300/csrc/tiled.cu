@@ -10,11 +10,22 @@
 #include <cstring>
 
 #include "tiled.h"
+// the kernels, once per tile height (namespaces tiled: 10 rows, tiled5: 5 rows)
+#include "tiled_kernel.cuh"
+#undef STARMAP_TILED_NS
+#undef STARMAP_TILED_TY
+#undef STARMAP_TILED_MINB
+#define STARMAP_TILED_NS tiled5
+#define STARMAP_TILED_TY 5
+#define STARMAP_TILED_MINB 2
 #include "tiled_kernel.cuh"
 
 namespace starmap {
 
-using namespace tiled;
+using namespace tiled;   // constants and types common to both tile heights
+
+static_assert(sizeof(tiled::Params) == sizeof(tiled5::Params), "both tile heights share the parameter layout");
+static_assert(tiled::TX == tiled5::TX && tiled::BX == tiled5::BX, "both tile heights share the tile width");
 
 namespace {
 
@@ -71,6 +82,16 @@ struct PassTables {
     int nin = 0;
 };
 
+// Orders up to this use the 5-row tiles by default (few stages per tile:
+// two CTAs per SM hide each other's setup, fill and drain).
+constexpr int SHORT_TILE_MAX_N = 21;
+
+// Per tile height: rows, input box rows, threads, consumer threads, end of the ring.
+struct Variant { int ty, byi, threads, consumers, ring_end; };
+const Variant kVariant[2] = {
+    {tiled::TY, tiled::BYI, tiled::THREADS, tiled::CONSUMERS, tiled::RING_OFF + tiled::NSTAGES * tiled::STAGE_BYTES},
+    {tiled5::TY, tiled5::BYI, tiled5::THREADS, tiled5::CONSUMERS, tiled5::RING_OFF + tiled5::NSTAGES * tiled5::STAGE_BYTES}};
+
 }  // namespace
 
 struct TiledPlan {
@@ -87,6 +108,8 @@ struct TiledPlan {
     void* dev_fin[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     void* dev_src = nullptr;
     int tiles_x = 0, tiles_y = 0;
+    int variant = 0;                      // 0: 10-row tiles, 1: 5-row tiles
+    int sms = 1;
     int smem_bytes[2] = {0, 0};
     Params prm[2][2];                     // [P][which]
     bool ready = false;
@@ -239,9 +262,11 @@ int tiled_create(const TiledGeometry& geo, TiledPlan** out) {
     pl->N = geo.N;
     *out = pl;
     if (geo.N < 1 || geo.N > MAXN) { pl->err = "tiled kernel supports 1 <= N <= 63"; return -8; }
+    pl->variant = geo.variant == 1 ? 1 : 0;
+    const Variant& V = kVariant[pl->variant];
     for (int g = 0; g < 4; ++g) {
-        if (!encode_grid_map(&pl->maps_in[g], geo.base[g], geo.pitch, geo.rows, geo.K[g], BX, BYI) ||
-            !encode_grid_map(&pl->maps_out[g], geo.base[g], geo.pitch, geo.rows, geo.K[g], TX, TY)) {
+        if (!encode_grid_map(&pl->maps_in[g], geo.base[g], geo.pitch, geo.rows, geo.K[g], BX, V.byi) ||
+            !encode_grid_map(&pl->maps_out[g], geo.base[g], geo.pitch, geo.rows, geo.K[g], TX, V.ty)) {
             pl->err = "cuTensorMapEncodeTiled failed";
             return -4;
         }
@@ -249,7 +274,12 @@ int tiled_create(const TiledGeometry& geo, TiledPlan** out) {
     int nxmax = 0, nymax = 0;
     for (int g = 0; g < 4; ++g) { nxmax = std::max(nxmax, geo.nx[g]); nymax = std::max(nymax, geo.ny[g]); }
     pl->tiles_x = (nxmax + TX - 1) / TX;
-    pl->tiles_y = (nymax + TY - 1) / TY;
+    pl->tiles_y = (nymax + V.ty - 1) / V.ty;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || pl->sms < 1) pl->sms = 1;
+    }
     if (cudaMalloc(&pl->err_dev, sizeof(int)) != cudaSuccess || cudaMemset(pl->err_dev, 0, sizeof(int)) != cudaSuccess) {
         pl->err = "cudaMalloc error flag failed";
         return -4;
@@ -306,7 +336,8 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             return -4;
         }
         // shared memory: barriers, ring, coefficient rows, finalise events, partial sums
-        int off = RING_OFF + NSTAGES * STAGE_BYTES;
+        const Variant& V = kVariant[pl->variant];
+        int off = V.ring_end;
         int coef_off[2], fin_off[2];
         for (int K = 0; K < 2; ++K) {
             coef_off[K] = off;
@@ -320,14 +351,17 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
         off += (int)(t.stages.size() * sizeof(int4));
         off = (off + 15) & ~15;
         const int part_off = off;
-        off += (nq_of(pl->N) + 1) * PP * CONSUMERS * 8;   // PP pairs of partial sums per consumer thread and q
+        off += (nq_of(pl->N) + 1) * PP * V.consumers * 8;   // PP pairs of partial sums per consumer thread and q
         pl->smem_bytes[P] = off;
         int dev = 0, maxsm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (off > maxsm) { pl->err = "tiled kernel needs more shared memory than the device offers"; return -8; }
         const int need = std::max(pl->smem_bytes[0], pl->smem_bytes[1]);
-        if (cudaFuncSetAttribute(k_tiled_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, need) != cudaSuccess) {
+        const cudaError_t fe = pl->variant
+            ? cudaFuncSetAttribute(tiled5::k_tiled_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, need)
+            : cudaFuncSetAttribute(tiled::k_tiled_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        if (fe != cudaSuccess) {
             pl->err = "cudaFuncSetAttribute failed";
             return -4;
         }
@@ -390,7 +424,14 @@ void tiled_set_coef(TiledPlan* pl, int g, void* coef, int nclasses) {
 int tiled_pass(TiledPlan* pl, bool odd, int which, void* stream) {
     if (!pl->ready) { pl->err = "tiled tables not built"; return -7; }
     const int P = odd ? 1 : 0;
-    k_tiled_pass<<<pl->tiles_x * pl->tiles_y, THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(pl->prm[P][which]);
+    const int ntiles = pl->tiles_x * pl->tiles_y;
+    if (pl->variant) {
+        tiled5::Params q;
+        std::memcpy(&q, &pl->prm[P][which], sizeof(q));
+        tiled5::k_tiled_pass<<<ntiles, tiled5::THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(q, ntiles);
+    } else {
+        tiled::k_tiled_pass<<<ntiles, tiled::THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(pl->prm[P][which], ntiles);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         pl->err = std::string("tiled pass launch: ") + cudaGetErrorString(e);
@@ -435,20 +476,32 @@ void tiled_tile_grid(TiledPlan* pl, int* tx, int* ty) {
 
 int tiled_stage_count(TiledPlan* pl, int P) { return pl ? (int)pl->tab[P].stages.size() : 0; }
 
-int tiled_batch_prepare(int smem_bytes) {
+int tiled_variant(TiledPlan* pl) { return pl ? pl->variant : 0; }
+
+int tiled_default_variant(int N) { return N <= SHORT_TILE_MAX_N ? 1 : 0; }
+
+int tiled_ctas_per_sm(int variant) { return variant ? tiled5::MINB : tiled::MINB; }
+
+int tiled_batch_prepare(int smem_bytes, int variant) {
     int dev = 0, maxsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem_bytes + (int)sizeof(Params) > maxsm) return -8;
-    return cudaFuncSetAttribute(k_tiled_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) == cudaSuccess
-               ? 0 : -4;
+    const cudaError_t e = variant
+        ? cudaFuncSetAttribute(tiled5::k_tiled_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes)
+        : cudaFuncSetAttribute(tiled::k_tiled_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    return e == cudaSuccess ? 0 : -4;
 }
 
 int tiled_batch_pass(const void* params, const void* items, int nitems, int P, int which, int grid, int smem_bytes,
-                     void* stream) {
+                     int variant, void* stream) {
     if (nitems <= 0) return 0;
-    k_tiled_batch<<<grid, THREADS, smem_bytes, (cudaStream_t)stream>>>(
-        static_cast<const Params*>(params), static_cast<const int2*>(items), nitems, P, which);
+    if (variant)
+        tiled5::k_tiled_batch<<<grid, tiled5::THREADS, smem_bytes, (cudaStream_t)stream>>>(
+            static_cast<const tiled5::Params*>(params), static_cast<const int4*>(items), nitems, P, which);
+    else
+        tiled::k_tiled_batch<<<grid, tiled::THREADS, smem_bytes, (cudaStream_t)stream>>>(
+            static_cast<const tiled::Params*>(params), static_cast<const int4*>(items), nitems, P, which);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 

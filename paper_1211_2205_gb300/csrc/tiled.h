@@ -16,7 +16,11 @@ struct TiledGeometry {
     long pitch, rows;
     int p[2];
     int N;
+    int variant = 0;                   // tile height: 0 = 10 rows (one CTA per SM), 1 = 5 rows (two per SM)
 };
+
+// Tile height the tiled kernel uses for order N when nothing else decides.
+int tiled_default_variant(int N);
 
 bool tiled_supported(int system, int N, int precision);
 int tiled_create(const TiledGeometry& geo, TiledPlan** out);
@@ -38,11 +42,15 @@ int tiled_export_params(TiledPlan* plan, void* host4);
 int tiled_smem_bytes(TiledPlan* plan, int P);
 void tiled_tile_grid(TiledPlan* plan, int* tiles_x, int* tiles_y);
 int tiled_stage_count(TiledPlan* plan, int P);
-// Allow the batch kernel smem_bytes of dynamic shared memory.
-int tiled_batch_prepare(int smem_bytes);
-// items: device array of (instance, tile); params: device array of
+int tiled_variant(TiledPlan* plan);
+// Resident CTAs per SM the kernels of a tile height are built for.
+int tiled_ctas_per_sm(int variant);
+// Allow the batch kernel of the given tile height smem_bytes of dynamic shared memory.
+int tiled_batch_prepare(int smem_bytes, int variant);
+// items: device array of int4 (instance, first tile, tile count, 0), each a
+// run of consecutive tiles of one instance; params: device array of
 // 4 * instances parameter blocks (instance i, parity P, which at 4 i + 2 P + which).
 int tiled_batch_pass(const void* params, const void* items, int nitems, int P, int which, int grid, int smem_bytes,
-                     void* stream);
+                     int variant, void* stream);
 
 }  // namespace starmap

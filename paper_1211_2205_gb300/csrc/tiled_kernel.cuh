@@ -34,18 +34,30 @@
 // which the finalising thread writes with each boundary value.  Every wait
 // is bounded: on expiry the kernel raises an error flag, waits (bounded) for
 // its copies in flight, and returns.
-#pragma once
+//
+// The file is compiled once per tile height: STARMAP_TILED_NS names the
+// namespace, STARMAP_TILED_TY the tile height and STARMAP_TILED_MINB the
+// CTAs per SM the launch bounds ask for (10 rows, one CTA per SM, for large
+// N; 5 rows, two CTAs per SM, so that one CTA's setup, fill and drain
+// overlap the other's streaming when a tile has few stages).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
+#ifndef STARMAP_TILED_NS
+#define STARMAP_TILED_NS tiled
+#define STARMAP_TILED_TY 10
+#define STARMAP_TILED_MINB 1
+#endif
+
 namespace starmap {
-namespace tiled {
+namespace STARMAP_TILED_NS {
 
 constexpr int PP = 1;                   // point pairs per consumer thread (along x)
 constexpr int TX = 64 * PP;             // tile width: pair j of lane l covers x0 + 64 j + 2 l, +1
-constexpr int TY = 10;                  // tile height
+constexpr int TY = STARMAP_TILED_TY;    // tile height
+constexpr int MINB = STARMAP_TILED_MINB;
 constexpr int VEC = 4;                  // 16 bytes of FP32: TMA x alignment
 constexpr int BX = TX + VEC;            // input box width (halo + alignment)
 constexpr int BYI = TY + 1;             // input box height (halo)
@@ -218,11 +230,17 @@ __device__ __forceinline__ f2 diff_x(const float* row, int c, bool c_even) {
     return f2_sub(f2_make(hi, Q), P);
 }
 
-// One tile of one pass.  maps: the pass's four tensor maps (in parameter or
-// global memory: TMA reads them from there); prm: everything else.
-// first_tile: the CTA's first tile (later tiles of a persistent CTA invalidate and
-// re-initialise the barriers; the caller synchronises the CTA in between).
-__device__ __forceinline__ void tiled_tile(const Params& prm, const CUtensorMap* maps, int tile, bool first_tile) {
+// Tiles t0, t0 + tstride, ... < tend of one pass, through one continuous
+// pipeline: the producers walk a global stage index over all of them (the
+// first stages of the next tile are in flight while the consumers finish
+// the current one), the consumers step through the tiles in the same order.
+// maps: the pass's four tensor maps (in parameter or global memory: TMA
+// reads them from there); prm: everything else.  first_call: the CTA's
+// first call (a later call invalidates and re-initialises the barriers; the
+// caller synchronises the CTA in between).
+static_assert(STEPS_PER_STAGE == 1, "the cross-tile pipeline assumes one consumer step per stage");
+__device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap* maps, int t0, int tstride, int tend,
+                                            bool first_call) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + NSTAGES;
@@ -233,12 +251,11 @@ __device__ __forceinline__ void tiled_tile(const Params& prm, const CUtensorMap*
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int x0 = (tile % prm.tiles_x) * TX;
-    const int y0 = (tile / prm.tiles_x) * TY;
+    const int ntl = t0 < tend ? (tend - t0 + tstride - 1) / tstride : 0;
 
     if (tid == 0) {
         for (int r = 0; r < NSTAGES; ++r) {
-            if (!first_tile) {
+            if (!first_call) {
                 mbar_inval(&full[r]);
                 mbar_inval(&empty[r]);
             }
@@ -266,48 +283,61 @@ __device__ __forceinline__ void tiled_tile(const Params& prm, const CUtensorMap*
     input_shift(prm.P, 1, prm.p[0], prm.p[1], sxI, syI);
 
     // --------------------------------------------------------- producer
-    // Producer warp pw owns the stages k = pw (mod PRODUCER_WARPS); stage k
-    // holds the consumer steps 2k and 2k + 1.  Lane 0 waits for the stage to
-    // drain and arms its barrier with the byte count; lanes 0..7 then issue
-    // the (up to) eight boxes, lane = 4 * (step in stage) + slot.
+    // Producer warp pw owns the global stages G = pw (mod PRODUCER_WARPS)
+    // over all of the CTA's tiles (stage k of tile t is G = t * nstages + k,
+    // ring slot G mod NSTAGES).  Lane 0 waits for the slot to drain and arms
+    // its barrier with the byte count; lanes 0..3 then issue the (up to) four
+    // boxes, lane = slot.
     if (warp >= CONSUMER_WARPS) {
         const int pw = warp - CONSUMER_WARPS;
         const int slot = lane & 3;
-        const int bxR = x0 + (sxR == 0 ? 0 : VEC), byR = y0 + (syR == 0 ? -1 : 0) + 1;
-        const int bxI = x0 + (sxI == 0 ? 0 : VEC), byI = y0 + (syI == 0 ? -1 : 0) + 1;
-        // box origin of this lane's slot (tensor coordinates x' = x + VEC, row = y + 1)
-        const int bx = slot == 0 ? bxR : slot == 1 ? bxI : x0 + VEC;
-        const int by = slot == 0 ? byR : slot == 1 ? byI : y0 + 1;
         const CUtensorMap* map = maps + slot;
-        const int nst = (prm.nstages + STEPS_PER_STAGE - 1) / STEPS_PER_STAGE;
+        const int nst = prm.nstages;
+        const int total = ntl * nst;        // the host keeps this below 2^31
         int last = -1;
         bool ok = true;
-        for (int k = pw; k < nst; k += PRODUCER_WARPS) {
-            const int r = k % NSTAGES;
-            const int step = STEPS_PER_STAGE * k + (lane >> 2);
+        // G = pw, pw + PRODUCER_WARPS, ...: stage k of local tile tl, ring
+        // slot r, ring round u (all advanced incrementally)
+        int k = pw, tl = 0, r = pw, u = 0;
+        while (k >= nst && nst > 0) { k -= nst; ++tl; }
+        int tile_at = -1, bx = 0, by = 0;
+        for (int G = pw; G < total; G += PRODUCER_WARPS) {
+            if (tl != tile_at) {
+                // box origin of this lane's slot in tile tl (tensor coordinates x' = x + VEC, row = y + 1)
+                tile_at = tl;
+                const int tile = t0 + tl * tstride;
+                const int x0 = (tile % prm.tiles_x) * TX, y0 = (tile / prm.tiles_x) * TY;
+                const int bxR = x0 + (sxR == 0 ? 0 : VEC), byR = y0 + (syR == 0 ? -1 : 0) + 1;
+                const int bxI = x0 + (sxI == 0 ? 0 : VEC), byI = y0 + (syI == 0 ? -1 : 0) + 1;
+                bx = slot == 0 ? bxR : slot == 1 ? bxI : x0 + VEC;
+                by = slot == 0 ? byR : slot == 1 ? byI : y0 + 1;
+            }
             int4 st = make_int4(-1, -1, -1, -1);
-            if (lane < 4 * STEPS_PER_STAGE && step < prm.nstages) st = s_stages[step];
+            if (lane < 4) st = s_stages[k];
             const int comp = slot == 0 ? st.x : slot == 1 ? st.y : slot == 2 ? st.z : st.w;
-            const uint32_t mine = lane < 4 * STEPS_PER_STAGE && comp >= 0 ? (slot < 2 ? IN_BYTES : OUT_BYTES) : 0u;
+            const uint32_t mine = lane < 4 && comp >= 0 ? (slot < 2 ? IN_BYTES : OUT_BYTES) : 0u;
             uint32_t bytes = mine;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
             if (lane == 0) {
-                if (k >= NSTAGES && !wait_bounded(&empty[r], ((k / NSTAGES) - 1) & 1, abort_flag, prm.err)) ok = false;
+                if (u > 0 && !wait_bounded(&empty[r], (u - 1) & 1, abort_flag, prm.err)) ok = false;
                 if (ok) mbar_expect_tx(&full[r], bytes);
             }
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
-            if (mine != 0u)
-                tma_load_3d(ring + r * STAGE_BYTES + (lane >> 2) * STEP_BYTES + slot * SLOT, map, bx, by, comp, &full[r]);
-            last = k;
+            if (mine != 0u) tma_load_3d(ring + r * STAGE_BYTES + slot * SLOT, map, bx, by, comp, &full[r]);
+            last = G;
+            k += PRODUCER_WARPS;
+            while (k >= nst) { k -= nst; ++tl; }
+            r += PRODUCER_WARPS;
+            if (r >= NSTAGES) { r -= NSTAGES; ++u; }
         }
         if (!ok && lane == 0) {
             // aborted: wait (bounded) for this warp's copies still in flight
-            for (int k = last; k >= 0 && k > last - NSTAGES; k -= PRODUCER_WARPS) {
-                const unsigned long long t0 = global_ns();
-                while (!mbar_try_wait(&full[k % NSTAGES], (k / NSTAGES) & 1))
-                    if (global_ns() - t0 > WAIT_NS) break;
+            for (int G = last; G >= 0 && G > last - NSTAGES; G -= PRODUCER_WARPS) {
+                const unsigned long long tw = global_ns();
+                while (!mbar_try_wait(&full[G % NSTAGES], (G / NSTAGES) & 1))
+                    if (global_ns() - tw > WAIT_NS) break;
             }
         }
         return;
@@ -321,250 +351,264 @@ __device__ __forceinline__ void tiled_tile(const Params& prm, const CUtensorMap*
     // the other kind (through My).
     const int K = warp / TY;
     const int row = warp % TY;
-    const int gy = y0 + row;
-    // float offsets, inside a step, of the difference operands of pair 0
-    // (pair j sits 64 j floats further): d_x from the input of kind K (slot
-    // K), d_y from the input of kind 1 - K (slot 1 - K)
-    int rx, cx, uy;
-    bool ev;
-    {
-        const int sxK = K == 0 ? sxR : sxI;
-        const int syO = K == 0 ? syI : syR;
-        const int syK = K == 0 ? syR : syI;
-        const int sxO = K == 0 ? sxI : sxR;
-        const int bxsK = sxK == 0 ? -VEC : 0, oyK = syK == 0 ? -1 : 0;
-        const int bxsO = sxO == 0 ? -VEC : 0, oyO = syO == 0 ? -1 : 0;
-        rx = K * (SLOT / 4) + (row - oyK) * BX;
-        cx = 2 * lane + sxK - bxsK;
-        ev = (cx & 1) == 0;
-        uy = (1 - K) * (SLOT / 4) + (row + syO - oyO) * BX + (2 * lane - bxsO);
-    }
-    // the output grid of kind K
-    const OutGrid& G = prm.out[K];
-    const int gK = prm.P == 1 ? (K == 0 ? 1 : 2) : (K == 0 ? 0 : 3);
-    const bool xnode = gK & 1, ynode = gK & 2;
-    const long plane = (long)G.nx * G.ny;
-    int gxA[PP];
-    bool inA[PP], inB[PP], fast[PP];
-    float* pptr[PP];          // point A_j in component 0
-    long cidxA[PP];
-    f2 ca2[PP][2], cb2[PP][2];  // decay pairs by class (isotropic)
-#pragma unroll
-    for (int j = 0; j < PP; ++j) {
-        gxA[j] = x0 + 64 * j + 2 * lane;
-        inA[j] = gxA[j] < G.nx && gy < G.ny;
-        inB[j] = gxA[j] + 1 < G.nx && gy < G.ny;
-        pptr[j] = G.base + (long)(gy + 1) * prm.pitch + gxA[j];
-        cidxA[j] = (long)gy * G.nx + gxA[j];
-        bool bnd = false;
-        for (int pt = 0; pt < 2; ++pt) {
-            const int gx = gxA[j] + pt;
-            if (prm.p[0]) bnd |= (gx == G.nx - 1) || (gx == 0);
-            else if (!xnode) bnd |= (gx == 0) || (gx == G.nx - 1);
-            if (prm.p[1]) bnd |= (gy == G.ny - 1) || (gy == 0);
-            else if (!ynode) bnd |= (gy == 0) || (gy == G.ny - 1);
-        }
-        fast[j] = inA[j] && inB[j] && !bnd;
-        for (int c = 0; c < 2; ++c) {
-            float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
-            if (prm.nclasses == 2 && G.coef != nullptr) {
-                const float* cf = G.coef + (long)c * 4 * plane + cidxA[j];
-                if (inA[j]) { a[0] = __ldg(cf + 2 * prm.which * plane); b[0] = __ldg(cf + (2 * prm.which + 1) * plane); }
-                if (inB[j]) { a[1] = __ldg(cf + 2 * prm.which * plane + 1); b[1] = __ldg(cf + (2 * prm.which + 1) * plane + 1); }
-            }
-            ca2[j][c] = f2_make(a[0], a[1]);
-            cb2[j][c] = f2_make(b[0], b[1]);
-        }
-    }
-
-    // walking pointers into this kind's tables and this thread's partial sums
-    const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(smem + prm.smem_coef_off[K]);
-    const int2* fp = reinterpret_cast<const int2*>(smem + prm.smem_fin_off[K]);
-    f2* const pp = s_part + tid;            // entry (q, j) at pp[(q * PP + j) * CONSUMERS]
-    const int uoff = (2 + K) * (SLOT / 4) + row * TX + 2 * lane;    // old value of pair 0 inside a step
-    int s = 0;
+    int s = 0;                  // global consumer step (= stage) over the CTA's tiles
     bool alive = true;
-    // consumer step s lives in stage s / STEPS_PER_STAGE; the stage's barrier
-    // is awaited at its first step and released after its last step
-    const int last_step = prm.nstages - 1;
-    auto stage_ptr = [&]() -> const float* {
-        const int k = s / STEPS_PER_STAGE;
-        const int r = k % NSTAGES;
-        if (s % STEPS_PER_STAGE == 0 && alive) alive = wait_bounded(&full[r], (k / NSTAGES) & 1, abort_flag, prm.err);
-        return reinterpret_cast<const float*>(ring + r * STAGE_BYTES + (s % STEPS_PER_STAGE) * STEP_BYTES);
-    };
-    auto stage_done = [&]() {
-        if (s % STEPS_PER_STAGE == STEPS_PER_STAGE - 1 || s == last_step) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[(s / STEPS_PER_STAGE) % NSTAGES]);
+    for (int tl = 0; tl < ntl && alive; ++tl) {
+        const int tile = t0 + tl * tstride;
+        const int x0 = (tile % prm.tiles_x) * TX, y0 = (tile / prm.tiles_x) * TY;
+        const int gy = y0 + row;
+        // float offsets, inside a step, of the difference operands of pair 0
+        // (pair j sits 64 j floats further): d_x from the input of kind K (slot
+        // K), d_y from the input of kind 1 - K (slot 1 - K)
+        int rx, cx, uy;
+        bool ev;
+        {
+            const int sxK = K == 0 ? sxR : sxI;
+            const int syO = K == 0 ? syI : syR;
+            const int syK = K == 0 ? syR : syI;
+            const int sxO = K == 0 ? sxI : sxR;
+            const int bxsK = sxK == 0 ? -VEC : 0, oyK = syK == 0 ? -1 : 0;
+            const int bxsO = sxO == 0 ? -VEC : 0, oyO = syO == 0 ? -1 : 0;
+            rx = K * (SLOT / 4) + (row - oyK) * BX;
+            cx = 2 * lane + sxK - bxsK;
+            ev = (cx & 1) == 0;
+            uy = (1 - K) * (SLOT / 4) + (row + syO - oyO) * BX + (2 * lane - bxsO);
         }
-        ++s;
-    };
-    // write one point (and its boundary copies)
-    auto store_point = [&](float* dst, int gx, float v) {
-        *dst = v;
-        int xa = -2, xb = -2, ya = -2, yb = -2;
-        if (prm.p[0]) { if (gx == G.nx - 1) xa = -1; if (gx == 0) xb = G.nx; }
-        else if (!xnode) { if (gx == 0) xa = -1; if (gx == G.nx - 1) xb = G.nx; }
-        if (prm.p[1]) { if (gy == G.ny - 1) ya = -1; if (gy == 0) yb = G.ny; }
-        else if (!ynode) { if (gy == 0) ya = -1; if (gy == G.ny - 1) yb = G.ny; }
-        float* rw = dst - gx;
-        if (xa != -2) rw[xa] = v;
-        if (xb != -2) rw[xb] = v;
-        float* col = dst - (long)(gy + 1) * prm.pitch;
-        if (ya != -2) col[(long)(ya + 1) * prm.pitch] = v;
-        if (yb != -2) col[(long)(yb + 1) * prm.pitch] = v;
-    };
-    // decay pairs (a, b) of the outputs of order L
-    f2 aL[PP], bL[PP];
-    auto set_order = [&](int L) {
-#pragma unroll
+        // the output grid of kind K
+        const OutGrid& G = prm.out[K];
+        const int gK = prm.P == 1 ? (K == 0 ? 1 : 2) : (K == 0 ? 0 : 3);
+        const bool xnode = gK & 1, ynode = gK & 2;
+        const long plane = (long)G.nx * G.ny;
+        int gxA[PP];
+        bool inA[PP], inB[PP], fast[PP];
+        float* pptr[PP];          // point A_j in component 0
+        long cidxA[PP];
+        f2 ca2[PP][2], cb2[PP][2];  // decay pairs by class (isotropic)
+    #pragma unroll
         for (int j = 0; j < PP; ++j) {
-            if (prm.nclasses == 2) {
-                aL[j] = L == 0 ? ca2[j][0] : ca2[j][1];
-                bL[j] = L == 0 ? cb2[j][0] : cb2[j][1];
-            } else {
-                const float* cf = G.coef + (long)L * 4 * plane + cidxA[j];
-                const float a0 = inA[j] ? __ldg(cf + 2 * prm.which * plane) : 0.f;
-                const float b0 = inA[j] ? __ldg(cf + (2 * prm.which + 1) * plane) : 0.f;
-                const float a1 = inB[j] ? __ldg(cf + 2 * prm.which * plane + 1) : 0.f;
-                const float b1 = inB[j] ? __ldg(cf + (2 * prm.which + 1) * plane + 1) : 0.f;
-                aL[j] = f2_make(a0, a1);
-                bL[j] = f2_make(b0, b1);
+            gxA[j] = x0 + 64 * j + 2 * lane;
+            inA[j] = gxA[j] < G.nx && gy < G.ny;
+            inB[j] = gxA[j] + 1 < G.nx && gy < G.ny;
+            pptr[j] = G.base + (long)(gy + 1) * prm.pitch + gxA[j];
+            cidxA[j] = (long)gy * G.nx + gxA[j];
+            bool bnd = false;
+            for (int pt = 0; pt < 2; ++pt) {
+                const int gx = gxA[j] + pt;
+                if (prm.p[0]) bnd |= (gx == G.nx - 1) || (gx == 0);
+                else if (!xnode) bnd |= (gx == 0) || (gx == G.nx - 1);
+                if (prm.p[1]) bnd |= (gy == G.ny - 1) || (gy == 0);
+                else if (!ynode) bnd |= (gy == 0) || (gy == G.ny - 1);
+            }
+            fast[j] = inA[j] && inB[j] && !bnd;
+            for (int c = 0; c < 2; ++c) {
+                float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
+                if (prm.nclasses == 2 && G.coef != nullptr) {
+                    const float* cf = G.coef + (long)c * 4 * plane + cidxA[j];
+                    if (inA[j]) { a[0] = __ldg(cf + 2 * prm.which * plane); b[0] = __ldg(cf + (2 * prm.which + 1) * plane); }
+                    if (inB[j]) { a[1] = __ldg(cf + 2 * prm.which * plane + 1); b[1] = __ldg(cf + (2 * prm.which + 1) * plane + 1); }
+                }
+                ca2[j][c] = f2_make(a[0], a[1]);
+                cb2[j][c] = f2_make(b[0], b[1]);
             }
         }
-    };
-    // finalise this warp's output of the current finalising step (slot 2 + K)
-    auto finalize = [&](const float* t, const f2 (&W)[PP]) {
-        const int2 f = *fp;
-        fp += 1;
-#pragma unroll
-        for (int j = 0; j < PP; ++j) {
-            const f2 u = lds2(t + uoff + 64 * j);
-            f2 w = W[j];
-            if (f.y >= 0) {
-                const float* qs = prm.srcs[f.y];
-                const float q0 = inA[j] ? __ldg(qs + cidxA[j]) : 0.f;
-                const float q1 = inB[j] ? __ldg(qs + cidxA[j] + 1) : 0.f;
-                w = f2_add(w, f2_make(q0, q1));
-            }
-            const f2 v = f2_fma(aL[j], u, f2_mul(bL[j], w));
-            if (f.x < 0 || !alive) continue;
-            float* dst = pptr[j] + f.x;
-            if (fast[j]) {
-                *reinterpret_cast<f2*>(dst) = v;
-            } else {
-                float v0, v1;
-                f2_split(v, v0, v1);
-                if (inA[j]) store_point(dst, gxA[j], v0);
-                if (inB[j]) store_point(dst + 1, gxA[j] + 1, v1);
-            }
-        }
-    };
-    // accumulate a q step into the four targets of kind K in reach: d_x of
-    // the input of kind K (slot K), d_y of the other input (slot 1 - K);
-    // a missing I input has zero coefficients and its differences masked
-    auto accumulate = [&](const float* t, bool inI, f2 (&Pc)[PP], f2 (&Pn)[PP], f2 (&Nc)[PP], f2 (&Nn)[PP]) {
-        const ulonglong2 xa = cp[0], xb = cp[1], ya = cp[2], yb = cp[3];
-        cp += 4;
-#pragma unroll
-        for (int j = 0; j < PP; ++j) {
-            f2 dx = diff_x(t + rx + 64 * j, cx, ev);
-            f2 dy = f2_sub(lds2(t + uy + 64 * j), lds2(t + uy + 64 * j - BX));
-            if (!inI) {
-                if (K == 1) dx = zero2(); else dy = zero2();
-            }
-            Pc[j] = f2_fma(xa.x, dx, Pc[j]);
-            Pn[j] = f2_fma(xa.y, dx, Pn[j]);
-            Nc[j] = f2_fma(xb.x, dx, Nc[j]);
-            Nn[j] = f2_fma(xb.y, dx, Nn[j]);
-            Pc[j] = f2_fma(ya.x, dy, Pc[j]);
-            Pn[j] = f2_fma(ya.y, dy, Pn[j]);
-            Nc[j] = f2_fma(yb.x, dy, Nc[j]);
-            Nn[j] = f2_fma(yb.y, dy, Nn[j]);
-        }
-    };
 
-    const int N = prm.N;
-    const int first = 1 - prm.P;              // first input order: even l' for the odd pass
-    int last_in = first;
-    for (int lp = first; lp <= N && alive; lp += 2) {
-        last_in = lp;
-        const int nq = nq_of(lp);
-        const int nqp = nq_of(lp - 1);                    // previous-order targets
-        const int nqn = lp + 1 <= N ? nq_of(lp + 1) : 0;  // next-order targets
-        const int nqload = lp > first ? nqp : 0;          // previous-order partial sums exist once order lp - 2 passed
-        set_order(lp - 1);
-        f2 Pc[PP], Nc[PP], Pn[PP], Nn[PP];
-#pragma unroll
-        for (int j = 0; j < PP; ++j) { Pc[j] = zero2(); Nc[j] = zero2(); }
-        // one q step: (Pc, Nc) carried in, (Pn, Nn) started here
-        auto qstep = [&](int q, f2 (&Pc_)[PP], f2 (&Nc_)[PP], f2 (&Pn_)[PP], f2 (&Nn_)[PP]) {
-#pragma unroll
-            for (int j = 0; j < PP; ++j) {
-                Pn_[j] = q < nqload ? pp[(q * PP + j) * CONSUMERS] : zero2();
-                Nn_[j] = zero2();
+        // walking pointers into this kind's tables and this thread's partial sums
+        const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(smem + prm.smem_coef_off[K]);
+        const int2* fp = reinterpret_cast<const int2*>(smem + prm.smem_fin_off[K]);
+        f2* const pp = s_part + tid;            // entry (q, j) at pp[(q * PP + j) * CONSUMERS]
+        const int uoff = (2 + K) * (SLOT / 4) + row * TX + 2 * lane;    // old value of pair 0 inside a step
+        // consumer step s lives in stage s / STEPS_PER_STAGE; the stage's barrier
+        // is awaited at its first step and released after its last step
+        const int last_step = prm.nstages - 1;
+        auto stage_ptr = [&]() -> const float* {
+            const int k = s / STEPS_PER_STAGE;
+            const int r = k % NSTAGES;
+            if (s % STEPS_PER_STAGE == 0 && alive) alive = wait_bounded(&full[r], (k / NSTAGES) & 1, abort_flag, prm.err);
+            return reinterpret_cast<const float*>(ring + r * STAGE_BYTES + (s % STEPS_PER_STAGE) * STEP_BYTES);
+        };
+        auto stage_done = [&]() {
+            if (s % STEPS_PER_STAGE == STEPS_PER_STAGE - 1 || s == last_step) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(s / STEPS_PER_STAGE) % NSTAGES]);
             }
-            const float* t = stage_ptr();
-            accumulate(t, has_imag(lp, q), Pc_, Pn_, Nc_, Nn_);
-            if (q >= 1 && q - 1 < nqp) finalize(t, Pc_);
-            stage_done();
-            if (q < nqn) {
-#pragma unroll
-                for (int j = 0; j < PP; ++j) pp[(q * PP + j) * CONSUMERS] = Nc_[j];
+            ++s;
+        };
+        // write one point (and its boundary copies)
+        auto store_point = [&](float* dst, int gx, float v) {
+            *dst = v;
+            int xa = -2, xb = -2, ya = -2, yb = -2;
+            if (prm.p[0]) { if (gx == G.nx - 1) xa = -1; if (gx == 0) xb = G.nx; }
+            else if (!xnode) { if (gx == 0) xa = -1; if (gx == G.nx - 1) xb = G.nx; }
+            if (prm.p[1]) { if (gy == G.ny - 1) ya = -1; if (gy == 0) yb = G.ny; }
+            else if (!ynode) { if (gy == 0) ya = -1; if (gy == G.ny - 1) yb = G.ny; }
+            float* rw = dst - gx;
+            if (xa != -2) rw[xa] = v;
+            if (xb != -2) rw[xb] = v;
+            float* col = dst - (long)(gy + 1) * prm.pitch;
+            if (ya != -2) col[(long)(ya + 1) * prm.pitch] = v;
+            if (yb != -2) col[(long)(yb + 1) * prm.pitch] = v;
+        };
+        // decay pairs (a, b) of the outputs of order L
+        f2 aL[PP], bL[PP];
+        auto set_order = [&](int L) {
+    #pragma unroll
+            for (int j = 0; j < PP; ++j) {
+                if (prm.nclasses == 2) {
+                    aL[j] = L == 0 ? ca2[j][0] : ca2[j][1];
+                    bL[j] = L == 0 ? cb2[j][0] : cb2[j][1];
+                } else {
+                    const float* cf = G.coef + (long)L * 4 * plane + cidxA[j];
+                    const float a0 = inA[j] ? __ldg(cf + 2 * prm.which * plane) : 0.f;
+                    const float b0 = inA[j] ? __ldg(cf + (2 * prm.which + 1) * plane) : 0.f;
+                    const float a1 = inB[j] ? __ldg(cf + 2 * prm.which * plane + 1) : 0.f;
+                    const float b1 = inB[j] ? __ldg(cf + (2 * prm.which + 1) * plane + 1) : 0.f;
+                    aL[j] = f2_make(a0, a1);
+                    bL[j] = f2_make(b0, b1);
+                }
             }
         };
-        int q = 0;
-        for (; q + 1 < nq && alive; q += 2) {
-            qstep(q, Pc, Nc, Pn, Nn);
-            qstep(q + 1, Pn, Nn, Pc, Nc);
+        // finalise this warp's output of the current finalising step (slot 2 + K)
+        auto finalize = [&](const float* t, const f2 (&W)[PP]) {
+            const int2 f = *fp;
+            fp += 1;
+    #pragma unroll
+            for (int j = 0; j < PP; ++j) {
+                const f2 u = lds2(t + uoff + 64 * j);
+                f2 w = W[j];
+                if (f.y >= 0) {
+                    const float* qs = prm.srcs[f.y];
+                    const float q0 = inA[j] ? __ldg(qs + cidxA[j]) : 0.f;
+                    const float q1 = inB[j] ? __ldg(qs + cidxA[j] + 1) : 0.f;
+                    w = f2_add(w, f2_make(q0, q1));
+                }
+                const f2 v = f2_fma(aL[j], u, f2_mul(bL[j], w));
+                if (f.x < 0 || !alive) continue;
+                float* dst = pptr[j] + f.x;
+                if (fast[j]) {
+                    *reinterpret_cast<f2*>(dst) = v;
+                } else {
+                    float v0, v1;
+                    f2_split(v, v0, v1);
+                    if (inA[j]) store_point(dst, gxA[j], v0);
+                    if (inB[j]) store_point(dst + 1, gxA[j] + 1, v1);
+                }
+            }
+        };
+        // accumulate a q step into the four targets of kind K in reach: d_x of
+        // the input of kind K (slot K), d_y of the other input (slot 1 - K);
+        // a missing I input has zero coefficients and its differences masked
+        auto accumulate = [&](const float* t, bool inI, f2 (&Pc)[PP], f2 (&Pn)[PP], f2 (&Nc)[PP], f2 (&Nn)[PP]) {
+            const ulonglong2 xa = cp[0], xb = cp[1], ya = cp[2], yb = cp[3];
+            cp += 4;
+    #pragma unroll
+            for (int j = 0; j < PP; ++j) {
+                f2 dx = diff_x(t + rx + 64 * j, cx, ev);
+                f2 dy = f2_sub(lds2(t + uy + 64 * j), lds2(t + uy + 64 * j - BX));
+                if (!inI) {
+                    if (K == 1) dx = zero2(); else dy = zero2();
+                }
+                Pc[j] = f2_fma(xa.x, dx, Pc[j]);
+                Pn[j] = f2_fma(xa.y, dx, Pn[j]);
+                Nc[j] = f2_fma(xb.x, dx, Nc[j]);
+                Nn[j] = f2_fma(xb.y, dx, Nn[j]);
+                Pc[j] = f2_fma(ya.x, dy, Pc[j]);
+                Pn[j] = f2_fma(ya.y, dy, Pn[j]);
+                Nc[j] = f2_fma(yb.x, dy, Nc[j]);
+                Nn[j] = f2_fma(yb.y, dy, Nn[j]);
+            }
+        };
+
+        const int N = prm.N;
+        const int first = 1 - prm.P;              // first input order: even l' for the odd pass
+        int last_in = first;
+        for (int lp = first; lp <= N && alive; lp += 2) {
+            last_in = lp;
+            const int nq = nq_of(lp);
+            const int nqp = nq_of(lp - 1);                    // previous-order targets
+            const int nqn = lp + 1 <= N ? nq_of(lp + 1) : 0;  // next-order targets
+            const int nqload = lp > first ? nqp : 0;          // previous-order partial sums exist once order lp - 2 passed
+            set_order(lp - 1);
+            f2 Pc[PP], Nc[PP], Pn[PP], Nn[PP];
+    #pragma unroll
+            for (int j = 0; j < PP; ++j) { Pc[j] = zero2(); Nc[j] = zero2(); }
+            // one q step: (Pc, Nc) carried in, (Pn, Nn) started here
+            auto qstep = [&](int q, f2 (&Pc_)[PP], f2 (&Nc_)[PP], f2 (&Pn_)[PP], f2 (&Nn_)[PP]) {
+    #pragma unroll
+                for (int j = 0; j < PP; ++j) {
+                    Pn_[j] = q < nqload ? pp[(q * PP + j) * CONSUMERS] : zero2();
+                    Nn_[j] = zero2();
+                }
+                const float* t = stage_ptr();
+                accumulate(t, has_imag(lp, q), Pc_, Pn_, Nc_, Nn_);
+                if (q >= 1 && q - 1 < nqp) finalize(t, Pc_);
+                stage_done();
+                if (q < nqn) {
+    #pragma unroll
+                    for (int j = 0; j < PP; ++j) pp[(q * PP + j) * CONSUMERS] = Nc_[j];
+                }
+            };
+            int q = 0;
+            for (; q + 1 < nq && alive; q += 2) {
+                qstep(q, Pc, Nc, Pn, Nn);
+                qstep(q + 1, Pn, Nn, Pc, Nc);
+            }
+            if (q < nq && alive) {
+                qstep(q, Pc, Nc, Pn, Nn);
+    #pragma unroll
+                for (int j = 0; j < PP; ++j) { Pc[j] = Pn[j]; Nc[j] = Nn[j]; }
+            }
+            if (alive && nq - 1 < nqp) {
+                // tail step: the last previous-order target
+                const float* t = stage_ptr();
+                finalize(t, Pc);
+                stage_done();
+            }
+            if (nq < nqn) {
+    #pragma unroll
+                for (int j = 0; j < PP; ++j) pp[(nq * PP + j) * CONSUMERS] = Nc[j];
+            }
         }
-        if (q < nq && alive) {
-            qstep(q, Pc, Nc, Pn, Nn);
-#pragma unroll
-            for (int j = 0; j < PP; ++j) { Pc[j] = Pn[j]; Nc[j] = Nn[j]; }
+        // outputs of the order above the last input order have no further inputs
+        const int L = last_in + 1;
+        if (L <= N) {
+            set_order(L);
+            for (int q = 0; q < nq_of(L) && alive; ++q) {
+                f2 W[PP];
+    #pragma unroll
+                for (int j = 0; j < PP; ++j) W[j] = pp[(q * PP + j) * CONSUMERS];
+                const float* t = stage_ptr();
+                finalize(t, W);
+                stage_done();
+            }
         }
-        if (alive && nq - 1 < nqp) {
-            // tail step: the last previous-order target
-            const float* t = stage_ptr();
-            finalize(t, Pc);
-            stage_done();
-        }
-        if (nq < nqn) {
-#pragma unroll
-            for (int j = 0; j < PP; ++j) pp[(nq * PP + j) * CONSUMERS] = Nc[j];
-        }
-    }
-    // outputs of the order above the last input order have no further inputs
-    const int L = last_in + 1;
-    if (L <= N) {
-        set_order(L);
-        for (int q = 0; q < nq_of(L) && alive; ++q) {
-            f2 W[PP];
-#pragma unroll
-            for (int j = 0; j < PP; ++j) W[j] = pp[(q * PP + j) * CONSUMERS];
-            const float* t = stage_ptr();
-            finalize(t, W);
-            stage_done();
+        // every tile consumes exactly the stages the producers issue for it
+        if (alive && s != (tl + 1) * prm.nstages) {
+            alive = false;
+            atomicExch(prm.err, 1);
         }
     }
 }
 
-__global__ void __launch_bounds__(THREADS, 1) k_tiled_pass(const __grid_constant__ Params prm) {
-    tiled_tile(prm, prm.maps, blockIdx.x, true);
+// Single-instance pass: one tile per CTA (the hardware's CTA scheduler
+// balances the SMs; measured faster than a persistent grid with a static
+// tile order on this two-die part).
+__global__ void __launch_bounds__(THREADS, MINB) k_tiled_pass(const __grid_constant__ Params prm, int ntiles) {
+    tiled_tiles(prm, prm.maps, blockIdx.x, 1, min(ntiles, (int)blockIdx.x + 1), true);
 }
 
-// Batched pass: a persistent grid walks the (instance, tile) items of all
-// instances (items sorted by decreasing cost, CTA b takes items b, b + grid,
-// ...).  Instance i's parameters for parity P and coefficient set `which`
-// are prms[(2 i + P) * 2 + which] in global memory; the CTA copies them to
-// shared memory and hands TMA the tensor maps of the global copy.
-__global__ void __launch_bounds__(THREADS, 1) k_tiled_batch(const Params* __restrict__ prms,
-                                                            const int2* __restrict__ items, int nitems, int P,
+// Batched pass: a persistent grid walks the items of all instances (items
+// sorted by decreasing cost, CTA b takes items b, b + grid, ...); an item
+// is a run of consecutive tiles of one instance, (instance, first tile,
+// tile count), streamed through one pipeline.  Instance i's parameters for
+// parity P and coefficient set `which` are prms[(2 i + P) * 2 + which] in
+// global memory; the CTA copies them to shared memory and hands TMA the
+// tensor maps of the global copy.
+__global__ void __launch_bounds__(THREADS, MINB) k_tiled_batch(const Params* __restrict__ prms,
+                                                            const int4* __restrict__ items, int nitems, int P,
                                                             int which) {
     __shared__ Params s_prm;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int2 item = items[it];
+        const int4 item = items[it];
         const Params* g = prms + (2 * item.x + P) * 2 + which;
         if (it != (int)blockIdx.x) __syncthreads();          // previous tile done with s_prm and the barriers
         {
@@ -573,9 +617,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_tiled_batch(const Params* __rest
             for (int i = threadIdx.x; i < (int)(sizeof(Params) / 16); i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
-        tiled_tile(s_prm, g->maps, item.y, it == (int)blockIdx.x);
+        tiled_tiles(s_prm, g->maps, item.y, 1, item.y + item.z, it == (int)blockIdx.x);
     }
 }
 
-}  // namespace tiled
+}  // namespace STARMAP_TILED_NS
 }  // namespace starmap

@@ -15,18 +15,30 @@ pytestmark = pytest.mark.gpu
 FP32_TOL = 1e-5
 
 
+@pytest.mark.parametrize("kernel", ["tiled_tall", "tiled_short"])
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 8, 13])
 @pytest.mark.parametrize("bc", [("periodic", "periodic"), ("extrapolation", "extrapolation"),
                                 ("periodic", "extrapolation"), ("extrapolation", "periodic")])
-def test_tiled_vs_oracle_ragged(N, bc):
-    """70 x 45 grid: three 32-wide tile columns (ragged), six 8-high tile
-    rows (ragged), every boundary combination."""
+def test_tiled_vs_oracle_ragged(N, bc, kernel):
+    """70 x 45 grid: two 64-wide tile columns (the second ragged) and 5 or
+    9 tile rows (the last ragged), every boundary combination, both tile
+    heights."""
     p = _random_problem(N, (70, 45), bc, "fp32", 300 + N, 7)
     for sched in ("literal", "merged"):
-        s, got = gpu_run(p, schedule=sched, kernel="tiled")
-        assert s.kernel == "tiled"
+        s, got = gpu_run(p, schedule=sched, kernel=kernel)
+        assert s.kernel == "tiled" and s.tile_rows == (10 if kernel == "tiled_tall" else 5)
         o, ref = oracle_run(p, dt=s.dt)
         assert rel_l2(got, ref) <= FP32_TOL, sched
+
+
+@pytest.mark.parametrize("N", [3, 9, 22])
+def test_tile_heights_agree(N):
+    """Both tile heights compute the same arithmetic per point: bit for bit."""
+    p = _random_problem(N, (83, 37), ("periodic", "extrapolation"), "fp32", 500 + N, 5)
+    a, ga = gpu_run(p, kernel="tiled_tall", schedule="merged")
+    b, gb = gpu_run(p, kernel="tiled_short", schedule="merged")
+    for x, y in zip(ga, gb):
+        assert np.array_equal(x, y)
 
 
 def test_tiled_anisotropic():
