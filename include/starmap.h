@@ -319,6 +319,15 @@ int starmap_set_closure(starmap_t* h, const float* params, size_t count);
  * stream. */
 int starmap_closure_samples(starmap_t* h, float* X, float* scale, float* targets, size_t count);
 
+/* Tensor-core path of the network's inference: MMA_SYNC (warp-level
+ * mma.sync, BF16 -> FP32, activations in registers) or TCGEN05 (5th-gen
+ * tensor cores: tcgen05.mma from shared-memory operands into a TMEM
+ * accumulator).  Same arithmetic per element up to the FP32 summation
+ * order.  Default MMA_SYNC.  Training always uses the mma.sync kernels. */
+#define STARMAP_MLP_ENGINE_MMA_SYNC 0
+#define STARMAP_MLP_ENGINE_TCGEN05  1
+int starmap_set_closure_engine(starmap_t* h, int engine);
+
 /* Network object for inference and training on the device.  All X, Y, T,
  * grad, loss and idx pointers are caller-owned device pointers; work is
  * queued on the object's stream (cuda_stream, or a library stream if NULL)
@@ -374,6 +383,8 @@ int  starmap_batch_step(starmap_batch_t* b, long nsteps);
  * instance (E_TIMEOUT). */
 int  starmap_batch_sync(starmap_batch_t* b);
 
+/* Inference engine of starmap_mlp_forward (STARMAP_MLP_ENGINE_*). */
+int  starmap_mlp_set_engine(starmap_mlp_t* net, int engine);
 /* Number of Adam steps taken since creation or the last set_params. */
 long starmap_mlp_steps(const starmap_mlp_t* net);
 int  starmap_mlp_sync(starmap_mlp_t* net);

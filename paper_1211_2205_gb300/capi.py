@@ -25,6 +25,7 @@ FP64, FP32 = 0, 1
 SCHEDULE_LITERAL, SCHEDULE_MERGED = 0, 1
 KERNEL_AUTO, KERNEL_GATHER, KERNEL_TILED, KERNEL_TILED_TALL, KERNEL_TILED_SHORT = 0, 1, 2, 3, 4
 CLOSURE_NONE, CLOSURE_MLP8 = 0, 1
+ENGINE_MMA_SYNC, ENGINE_TCGEN05 = 0, 1
 MLP_INPUTS, MLP_HIDDEN, MLP_OUTPUTS, MLP_PARAMS = 38, 128, 9, 22665
 
 
@@ -127,6 +128,8 @@ def lib():
         "starmap_mlp_train_step": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.c_size_t, ctypes.c_float, ctypes.c_void_p]),
         "starmap_mlp_steps": (ctypes.c_long, [H]),
+        "starmap_mlp_set_engine": (ctypes.c_int, [H, ctypes.c_int]),
+        "starmap_set_closure_engine": (ctypes.c_int, [H, ctypes.c_int]),
         "starmap_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(H)]),
         "starmap_batch_destroy": (None, [H]),
         "starmap_batch_last_error": (ctypes.c_char_p, [H]),
@@ -397,6 +400,11 @@ class Stepper:
         a = _params32(params)
         self._check(self._L.starmap_set_closure(self._h, a.ctypes.data_as(_fp), a.size))
 
+    def set_closure_engine(self, engine: str):
+        """"mma_sync" or "tcgen05": tensor-core path of the closure network."""
+        self._check(self._L.starmap_set_closure_engine(self._h, {"mma_sync": ENGINE_MMA_SYNC,
+                                                                 "tcgen05": ENGINE_TCGEN05}[engine]))
+
     def closure_samples(self, X, scale, targets=None):
         """Network inputs X [M, 38], scales s [M] and (optionally) the
         order-8 moments divided by s, targets [M, 9], of the current state,
@@ -482,6 +490,11 @@ class Network:
     @property
     def steps(self) -> int:
         return self._L.starmap_mlp_steps(self._h)
+
+    def set_engine(self, engine: str):
+        """"mma_sync" or "tcgen05" for forward()."""
+        self._check(self._L.starmap_mlp_set_engine(self._h, {"mma_sync": ENGINE_MMA_SYNC,
+                                                             "tcgen05": ENGINE_TCGEN05}[engine]))
 
     def forward(self, X, M: int, Y):
         self._check(self._L.starmap_mlp_forward(self._h, _addr(X), int(M), _addr(Y)))

@@ -69,6 +69,8 @@ struct starmap_s {
     float* ctr = nullptr;                  // closure scratch (input fragments, scales, I_8 centre values)
     float* lsig = nullptr;                 // log(1 + sigma_a), log(1 + sigma_s0) at the cell centres
     bool lsig_dirty = true;
+    int engine = mlp::ENGINE_MMA_SYNC;     // tensor-core path of the closure network
+    int* closure_err = nullptr;            // bounded-wait flag of the tcgen05 network
     unsigned long version = 0;             // bumped whenever the tiled pass parameters change
     std::string err;
 };
@@ -103,8 +105,19 @@ int cuda_fail(starmap_t* h, cudaError_t e, const char* what) {
 
 #define CK(call, what) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail(h, e_, what); } while (0)
 
-// Surface a bounded-wait failure of the tiled kernel (synchronises the stream).
+// Surface a bounded-wait failure of the tiled kernel or of the tcgen05
+// closure network (synchronises the stream).
 int poll_kernel(starmap_t* h) {
+    if (h->closure_err) {
+        int flag = 0;
+        if (cudaMemcpyAsync(&flag, h->closure_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return fail(h, STARMAP_E_CUDA, "reading the closure error flag failed");
+        if (flag) {
+            cudaMemsetAsync(h->closure_err, 0, sizeof(int), h->stream);
+            return fail(h, STARMAP_E_TIMEOUT, "a bounded wait in the closure network gave up");
+        }
+    }
     if (!h->tiled) return STARMAP_OK;
     int rc = tiled_poll(h->tiled, h->stream);
     if (rc == -6) return fail(h, STARMAP_E_TIMEOUT, tiled_error(h->tiled));
@@ -341,7 +354,12 @@ int run_closure(starmap_t* h) {
     const size_t M = (size_t)h->nxg[0] * h->nyg[0];
     if (!h->ctr) CK(cudaMalloc(&h->ctr, std::max<size_t>(1, (size_t)mlp::closure_scratch_floats((long)M)) * sizeof(float)),
                     "cudaMalloc closure scratch");
-    if (mlp::closure<T>(closure_args<T>(h), h->net, h->ctr, h->stream)) return cuda_fail(h, cudaGetLastError(), "closure");
+    if (!h->closure_err) {
+        CK(cudaMalloc(&h->closure_err, sizeof(int)), "cudaMalloc closure flag");
+        CK(cudaMemsetAsync(h->closure_err, 0, sizeof(int), h->stream), "closure flag");
+    }
+    if (mlp::closure<T>(closure_args<T>(h), h->net, h->ctr, h->engine, h->closure_err, h->stream))
+        return cuda_fail(h, cudaGetLastError(), "closure");
     return STARMAP_OK;
 }
 
@@ -441,6 +459,7 @@ void release(starmap_t* h) {
     if (h->net) cudaFree(h->net);
     if (h->ctr) cudaFree(h->ctr);
     if (h->lsig) cudaFree(h->lsig);
+    if (h->closure_err) cudaFree(h->closure_err);
     if (h->tiled) tiled_destroy(h->tiled);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -982,6 +1001,14 @@ int starmap_set_closure(starmap_t* h, const float* params, size_t count) {
     if (mlp::pack(h->net_params, h->net, h->stream)) return cuda_fail(h, cudaGetLastError(), "pack closure");
     CK(cudaStreamSynchronize(h->stream), "set_closure");
     h->net_ready = true;
+    return STARMAP_OK;
+}
+
+int starmap_set_closure_engine(starmap_t* h, int engine) {
+    if (!h) return STARMAP_E_ARG;
+    if (engine != STARMAP_MLP_ENGINE_MMA_SYNC && engine != STARMAP_MLP_ENGINE_TCGEN05)
+        return fail(h, STARMAP_E_ARG, "unknown network engine");
+    h->engine = engine == STARMAP_MLP_ENGINE_TCGEN05 ? mlp::ENGINE_TCGEN05 : mlp::ENGINE_MMA_SYNC;
     return STARMAP_OK;
 }
 

@@ -667,8 +667,10 @@ __global__ void __launch_bounds__(256) k_samples(const ClosureArgs<T> A, float* 
     }
 }
 
+constexpr int PAD_ROWS_F = 128;         // input rows are written up to a whole number of 128-row tiles
+
 // Closure inputs of every cell as padded BF16 rows xg[m][LDX] (columns 38..
-// LDX-1 zero; rows up to a whole number of 32-row tiles) and the scale
+// LDX-1 zero; rows up to a whole number of 128-row tiles) and the scale
 // sc[m]: one thread per cell, exactly the features of k_samples (the
 // training samples), rounded to BF16.
 template <class T>
@@ -679,7 +681,7 @@ __global__ void __launch_bounds__(256) k_closure_features(const ClosureArgs<T> A
     __syncthreads();
     const int nx = A.nx, ny = A.ny;
     const int M = nx * ny;
-    const int Mpad = (M + IROWS - 1) / IROWS * IROWS;
+    const int Mpad = (M + PAD_ROWS_F - 1) / PAD_ROWS_F * PAD_ROWS_F;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < Mpad; m += gridDim.x * blockDim.x) {
         const bool ok = m < M;
         const int ix = ok ? m % nx : 0, iy = ok ? m / nx : 0;
@@ -879,31 +881,38 @@ int samples(const ClosureArgs<T>& A, float* X, float* scale, float* tgt, void* s
     return status(cudaGetLastError());
 }
 
+// input rows are padded to whole 128-row tiles (the tcgen05 network's M)
+constexpr int PAD_ROWS = 128;
+
 long closure_scratch_floats(long M) {
-    const long Mpad = (M + IROWS - 1) / IROWS * IROWS;
+    const long Mpad = (M + PAD_ROWS - 1) / PAD_ROWS * PAD_ROWS;
     return Mpad * LDX / 2 + Mpad + (long)NOUT * M;      // BF16 input rows, scales, I_8 centre values
 }
 
 template <class T>
-int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, void* stream) {
+int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine, int* err, void* stream) {
     static bool attr = false;
     if (set_smem(k_closure_mlp<T>, sizeof(ClosureSmem), attr)) return -4;
     const long M = (long)A.nx * A.ny;
     if (M <= 0) return 0;
     if (M > 0x7fff0000L) return -8;
     const long tiles = (M + IROWS - 1) / IROWS;
-    const long Mpad = tiles * IROWS;
+    const long Mpad = (M + PAD_ROWS - 1) / PAD_ROWS * PAD_ROWS;
     __nv_bfloat16* xg = reinterpret_cast<__nv_bfloat16*>(scratch);
     float* sc = scratch + Mpad * LDX / 2;
     float* ctr = sc + Mpad;
-    long fb = (Mpad + 255) / 256;
+    long fb = (Mpad + 255) / 256;      // the features kernel covers the padded rows too
     if (fb > 32L * sm_count()) fb = 32L * sm_count();
     k_closure_features<T><<<(unsigned)fb, 256, 0, (cudaStream_t)stream>>>(A, xg, sc);
     if (cudaGetLastError() != cudaSuccess) return -4;
-    long blocks = (tiles + IW - 1) / IW;
-    if (blocks > sm_count()) blocks = sm_count();
-    k_closure_mlp<T><<<(unsigned)blocks, ITHREADS, sizeof(ClosureSmem), (cudaStream_t)stream>>>(A, P, xg, sc, ctr);
-    if (cudaGetLastError() != cudaSuccess) return -4;
+    if (engine == ENGINE_TCGEN05) {
+        if (closure_mlp_tc<T>(A, P, xg, sc, ctr, err, stream)) return -4;
+    } else {
+        long blocks = (tiles + IW - 1) / IW;
+        if (blocks > sm_count()) blocks = sm_count();
+        k_closure_mlp<T><<<(unsigned)blocks, ITHREADS, sizeof(ClosureSmem), (cudaStream_t)stream>>>(A, P, xg, sc, ctr);
+        if (cudaGetLastError() != cudaSuccess) return -4;
+    }
     if (A.g[3].nx > 0 && A.g[3].ny > 0) {
         const dim3 grid((A.g[3].nx + 255) / 256, A.g[3].ny < 65535 ? A.g[3].ny : 65535);
         k_closure_nodes<T><<<grid, 256, 0, (cudaStream_t)stream>>>(A, ctr);
@@ -913,8 +922,8 @@ int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, void* stre
 
 template int samples<float>(const ClosureArgs<float>&, float*, float*, float*, void*);
 template int samples<double>(const ClosureArgs<double>&, float*, float*, float*, void*);
-template int closure<float>(const ClosureArgs<float>&, const Packed*, float*, void*);
-template int closure<double>(const ClosureArgs<double>&, const Packed*, float*, void*);
+template int closure<float>(const ClosureArgs<float>&, const Packed*, float*, int, int*, void*);
+template int closure<double>(const ClosureArgs<double>&, const Packed*, float*, int, int*, void*);
 
 }  // namespace mlp
 }  // namespace starmap

@@ -68,9 +68,20 @@ int adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1
 template <class T> int samples(const ClosureArgs<T>& A, float* X, float* scale, float* tgt, void* stream);
 // Closure evaluation (features, network, order-8 moments written to G11 and
 // G22); scratch holds closure_scratch_floats(n_x n_y) floats; n_x n_y must
-// stay below 2^31 (else -8).
+// stay below 2^31 (else -8).  engine: ENGINE_MMA_SYNC or ENGINE_TCGEN05;
+// err: device flag raised by a bounded wait of the tcgen05 kernel.
+constexpr int ENGINE_MMA_SYNC = 0;
+constexpr int ENGINE_TCGEN05 = 1;
 long closure_scratch_floats(long M);
-template <class T> int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, void* stream);
+template <class T>
+int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine, int* err, void* stream);
+
+// tcgen05 network (mlp_tc.cu)
+size_t tc_smem_bytes();
+int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void* stream);
+template <class T>
+int closure_mlp_tc(const ClosureArgs<T>& A, const Packed* P, const __nv_bfloat16* xg, const float* sc, float* ctr,
+                   int* err, void* stream);
 
 }  // namespace mlp
 }  // namespace starmap

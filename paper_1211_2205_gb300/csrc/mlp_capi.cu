@@ -26,6 +26,8 @@ struct starmap_mlp_s {
     float* part = nullptr;         // per-tile partial gradients
     long part_tiles = 0;
     long steps = 0;
+    int engine = mlp::ENGINE_MMA_SYNC;
+    int* flag = nullptr;           // bounded-wait flag of the tcgen05 network
     std::string err;
 };
 
@@ -51,6 +53,7 @@ void mrelease(starmap_mlp_t* n) {
     cudaFree(n->grad);
     cudaFree(n->packed);
     cudaFree(n->part);
+    cudaFree(n->flag);
     if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
 }
 
@@ -118,6 +121,9 @@ int starmap_mlp_create(const float* params, size_t count, void* cuda_stream, sta
     }
     e = cudaMalloc(&net->packed, sizeof(mlp::Packed));
     if (e != cudaSuccess) return bail(mfail(net, STARMAP_E_NOMEM, "cudaMalloc packed weights"));
+    e = cudaMalloc(&net->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(net->flag, 0, sizeof(int));
+    if (e != cudaSuccess) return bail(mfail(net, STARMAP_E_NOMEM, "cudaMalloc error flag"));
     if (int rc = load(net, params)) return bail(rc);
     *out = net;
     return STARMAP_OK;
@@ -152,7 +158,9 @@ int starmap_mlp_forward(starmap_mlp_t* net, const float* X, size_t M, float* Y) 
     if (!net) return STARMAP_E_ARG;
     if (M == 0) return STARMAP_OK;
     if (!X || !Y) return mfail(net, STARMAP_E_ARG, "X and Y must be device pointers");
-    if (mlp::forward(X, (long)M, net->packed, Y, net->stream)) MCK(cudaGetLastError(), "forward");
+    const int rc = net->engine == mlp::ENGINE_TCGEN05 ? mlp::forward_tc(X, (long)M, net->packed, Y, net->flag, net->stream)
+                                                      : mlp::forward(X, (long)M, net->packed, Y, net->stream);
+    if (rc) MCK(cudaGetLastError(), "forward");
     return STARMAP_OK;
 }
 
@@ -183,6 +191,20 @@ long starmap_mlp_steps(const starmap_mlp_t* net) { return net ? net->steps : 0; 
 int starmap_mlp_sync(starmap_mlp_t* net) {
     if (!net) return STARMAP_E_ARG;
     MCK(cudaStreamSynchronize(net->stream), "sync");
+    int flag = 0;
+    MCK(cudaMemcpy(&flag, net->flag, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+    if (flag) {
+        cudaMemset(net->flag, 0, sizeof(int));
+        return mfail(net, STARMAP_E_TIMEOUT, "a bounded wait in the tcgen05 network gave up");
+    }
+    return STARMAP_OK;
+}
+
+int starmap_mlp_set_engine(starmap_mlp_t* net, int engine) {
+    if (!net) return STARMAP_E_ARG;
+    if (engine != STARMAP_MLP_ENGINE_MMA_SYNC && engine != STARMAP_MLP_ENGINE_TCGEN05)
+        return mfail(net, STARMAP_E_ARG, "unknown network engine");
+    net->engine = engine == STARMAP_MLP_ENGINE_TCGEN05 ? mlp::ENGINE_TCGEN05 : mlp::ENGINE_MMA_SYNC;
     return STARMAP_OK;
 }
 

@@ -160,7 +160,7 @@ def test_training_fits_a_teacher_network():
 
 # ----------------------------------------------------------- closure in the step
 def _closure_problem(n=(37, 29), bc=("periodic", "extrapolation"), precision="fp64", N=7, seed=31, nsteps=4):
-    ax = (0.0, 1.1, 0.0, 0.9)
+    ax = (0.0, 1.1, 0.0, 1.1 * n[1] / n[0])
     rng = inputs.SplitMix64(seed)
     ncomp = (N + 1) * (N + 2) // 2
     ic = []
@@ -291,3 +291,70 @@ def test_closure_errors():
     with pytest.raises(capi.StarmapError) as e:
         plain.set_closure(_params(1))
     assert e.value.code == capi.E_STATE
+
+
+# ----------------------------------------------------------- tcgen05 engine
+@pytest.mark.parametrize("M", [1, 127, 1000, 40000])
+def test_tcgen05_forward_matches_oracle_and_mma_sync(M):
+    """The tcgen05 network (TMEM accumulators, shared-memory operands) against
+    the oracle with the same BF16 weights and inputs, and against the
+    mma.sync network: the same per-element arithmetic up to the FP32
+    summation order (an occasional hidden activation may round to the
+    neighbouring BF16 value)."""
+    rng = np.random.default_rng(100 + M)
+    X = rng.normal(size=(M, C.N_IN)).astype(np.float32)
+    params = _params(8)
+    net = capi.Network(params)
+    Xd = _dev(X)
+    Yt = torch.full((M * C.N_OUT,), float("nan"), device="cuda")
+    Ym = torch.full((M * C.N_OUT,), float("nan"), device="cuda")
+    torch.cuda.synchronize()
+    net.set_engine("tcgen05")
+    net.forward(Xd, M, Yt)
+    net.sync()
+    net.set_engine("mma_sync")
+    net.forward(Xd, M, Ym)
+    net.sync()
+    yt = Yt.cpu().numpy().reshape(M, C.N_OUT)
+    ym = Ym.cpu().numpy().reshape(M, C.N_OUT)
+    ref, _ = _oracle_mlp(params).forward(bf16(X).astype(np.float64))
+    assert np.isfinite(yt).all()
+    assert _rel(yt, ref) <= BF16_TOL
+    assert _rel(yt, ym) <= 2e-3
+
+
+@pytest.mark.parametrize("bc", [("periodic", "periodic"), ("extrapolation", "periodic")])
+def test_tcgen05_closure_prediction_matches_oracle_hook(bc):
+    p = _closure_problem(bc=bc, nsteps=3, n=(150, 90))
+    params = _params(43, scale_out=0.6)
+    s = capi.Stepper.from_problem(p, kernel="gather", closure="mlp8")
+    s.set_closure(params)
+    s.set_closure_engine("tcgen05")
+    s.step(3)
+    before = _state(s)
+    s.run_pass(1, 0)
+    after = _state(s)
+    s.sync()
+    o = C.closed_solver(p, _oracle_mlp(params), dt=s.dt)
+    for j in range(45):
+        o.U[j] = before[j].T.copy()
+    o.pre_odd(o)
+    ref = [o.U[j].T for j in range(36, 45)]
+    assert rel_l2(after[36:], ref) <= 2 * BF16_TOL
+
+
+def test_tcgen05_closed_run_matches_mma_sync_run():
+    p = _closure_problem(precision="fp32", nsteps=6, n=(130, 70))
+    params = _params(44, scale_out=0.6)
+    runs = []
+    for engine in ("mma_sync", "tcgen05"):
+        s = capi.Stepper.from_problem(p, kernel="tiled", closure="mlp8", schedule="merged")
+        s.set_closure(params)
+        s.set_closure_engine(engine)
+        s.step(p.nsteps)
+        s.sync()
+        runs.append(_state(s))
+    plain = O.solver_from_problem(p, dt=s.dt)
+    plain.run(p.nsteps)
+    effect = rel_l2([u.T for u in plain.U], runs[0][:36])
+    assert rel_l2(runs[1][:36], runs[0][:36]) <= 0.05 * effect
