@@ -323,7 +323,8 @@ int starmap_closure_samples(starmap_t* h, float* X, float* scale, float* targets
  * mma.sync, BF16 -> FP32, activations in registers) or TCGEN05 (5th-gen
  * tensor cores: tcgen05.mma from shared-memory operands into a TMEM
  * accumulator).  Same arithmetic per element up to the FP32 summation
- * order.  Default MMA_SYNC.  Training always uses the mma.sync kernels. */
+ * order.  Default for the stepper: TCGEN05; for starmap_mlp_forward:
+ * MMA_SYNC.  Training always uses the mma.sync kernels. */
 #define STARMAP_MLP_ENGINE_MMA_SYNC 0
 #define STARMAP_MLP_ENGINE_TCGEN05  1
 int starmap_set_closure_engine(starmap_t* h, int engine);

@@ -69,7 +69,7 @@ struct starmap_s {
     float* ctr = nullptr;                  // closure scratch (input fragments, scales, I_8 centre values)
     float* lsig = nullptr;                 // log(1 + sigma_a), log(1 + sigma_s0) at the cell centres
     bool lsig_dirty = true;
-    int engine = mlp::ENGINE_MMA_SYNC;     // tensor-core path of the closure network
+    int engine = mlp::ENGINE_TCGEN05;      // tensor-core path of the closure network
     int* closure_err = nullptr;            // bounded-wait flag of the tcgen05 network
     unsigned long version = 0;             // bumped whenever the tiled pass parameters change
     std::string err;

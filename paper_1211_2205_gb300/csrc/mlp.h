@@ -79,9 +79,9 @@ int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine
 // tcgen05 network (mlp_tc.cu)
 size_t tc_smem_bytes();
 int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void* stream);
+// fused features + network + order-8 output on tcgen05 (I_8 centre values to ctr)
 template <class T>
-int closure_mlp_tc(const ClosureArgs<T>& A, const Packed* P, const __nv_bfloat16* xg, const float* sc, float* ctr,
-                   int* err, void* stream);
+int closure_tc(const ClosureArgs<T>& A, const Packed* P, float* ctr, int* err, void* stream);
 
 }  // namespace mlp
 }  // namespace starmap

@@ -1,15 +1,17 @@
 // The closure network on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// One CTA (8 warps) owns 128 samples at a time.  Operands live in shared
+// One CTA per SM: four independent groups of 4 warps, each owning a tile of
+// 128 samples at a time (its own TMEM columns, operand buffers, mbarrier and
+// named barrier; the weights are shared).  Operands live in shared
 // memory in the canonical K-major layout without swizzle: 8-row x 16-byte
 // core matrices; an M x K (or N x K) operand stores element (r, k) at
 //     (k / 8) * LBO + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2  bytes,
 // LBO = (rows / 8) * 128 (core matrices adjacent along M/N are 128 bytes
 // apart = SBO, along K LBO apart).  One elected thread issues the layer's
-// tcgen05.mma (M = 128, K = 16 per instruction, BF16 x BF16 -> FP32) into a
-// 128-column TMEM accumulator and commits it to an mbarrier; all 8 warps
-// then read the accumulator with tcgen05.ld (warp w: lanes 32 (w % 4)..,
-// columns 64 (w / 4)..), add the bias, apply the shared activation
+// tcgen05.mma (M = 128, K = 16 per instruction, BF16 x BF16 -> FP32) into the
+// group's 128-column TMEM accumulator and commits it to the group's
+// mbarrier; the group's 4 warps then read the accumulator with tcgen05.ld
+// (thread = row = TMEM lane), add the bias, apply the shared activation
 // (tanh.approx.bf16x2 of the BF16-rounded pre-activation) and write the
 // next layer's operand back to shared memory.  Layers: 38(48) -> 128
 // (3 MMAs), 128 -> 128 (8 MMAs), 128 -> 16 (9 used, 8 MMAs with N = 16).
@@ -20,6 +22,7 @@
 
 #include <cstdint>
 
+#include "closure_features.cuh"
 #include "internal.h"
 #include "mlp.h"
 
@@ -29,34 +32,34 @@ namespace mlp {
 namespace {
 
 constexpr int TM = 128;                  // samples per tile (MMA M)
-constexpr int TC_THREADS = 256;
+constexpr int GROUPS = 4;                // independent 4-warp groups per CTA, one tile each
+constexpr int GWARPS = 4;
+constexpr int GTHREADS = GWARPS * 32;    // one thread per tile row (= TMEM lane)
+constexpr int TC_THREADS = GROUPS * GTHREADS;
 constexpr int KX_TC = 48;                // input width padded to the MMA K step
 constexpr int XC_BYTES = (KX_TC / 8) * (TM / 8) * 128;       // 12288
 constexpr int W1_BYTES = (KX_TC / 8) * (HID / 8) * 128;      // 12288
 constexpr int W2_BYTES = (HID / 8) * (HID / 8) * 128;        // 32768
 constexpr int W3_BYTES = (HID / 8) * (OUTP / 8) * 128;       // 4096
 constexpr int H_BYTES = (HID / 8) * (TM / 8) * 128;          // 32768
-// TMEM columns per CTA and CTAs per SM.  Sized generously: an operand
-// descriptor read with leading and stride offsets swapped would span up to
-// 15 * 2048 + 256 bytes past its start; the shared layout below keeps that
-// inside this CTA's allocation (OVERREAD), and 512 columns cover any N.
-constexpr int TMEM_COLS = 512;
-constexpr int TC_MINB = 1;
-constexpr int OVERREAD = 15 * 2048 + 256;
+constexpr int TMEM_COLS = 512;           // 128 accumulator columns per group
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
+struct TcGroup {
+    alignas(128) unsigned char x[XC_BYTES];
+    alignas(128) unsigned char h[H_BYTES];
+};
 struct TcSmem {
     alignas(1024) unsigned char w1[W1_BYTES];
     alignas(128) unsigned char w2[W2_BYTES];
     alignas(128) unsigned char w3[W3_BYTES];
-    alignas(128) unsigned char x[2][XC_BYTES];
-    alignas(128) unsigned char h[H_BYTES];
+    TcGroup grp[GROUPS];
     float b1[HID], b2[HID], b3[OUTP];
-    alignas(8) uint64_t mbar;
+    alignas(8) uint64_t mbar[GROUPS];
     uint32_t tmem;
-    int abort;
-    unsigned char guard[OVERREAD];       // never accessed by the kernel's own code
+    int abort[GROUPS];
 };
+static_assert(sizeof(TcSmem) <= 227 * 1024, "tile groups must fit in shared memory");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -90,12 +93,32 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// barrier of one 128-thread group (ids 1..GROUPS; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(GTHREADS) : "memory"); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+// 64 consecutive columns of this warp's 32 lanes in one load
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+          "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
+          "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
+          "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+          "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -140,91 +163,106 @@ __device__ __forceinline__ void cp_async16_tc(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
 }
 
-// Weights (row-major padded BF16 of Packed) into the canonical layouts.
+// Weights (row-major padded BF16 of Packed) into the canonical layouts,
+// 16-byte pieces by cp.async (no register round trip); the caller waits.
 __device__ void load_weights_tc(TcSmem& S, const Packed* P) {
+    const uint32_t w1 = su32(S.w1), w2 = su32(S.w2), w3 = su32(S.w3);
     for (int i = threadIdx.x; i < HID * (KX_TC / 8); i += TC_THREADS) {         // W1: 128 rows x 6 chunks
         const int n = i / (KX_TC / 8), c = i % (KX_TC / 8);
-        *reinterpret_cast<uint4*>(S.w1 + canon(n, 8 * c, HID)) = *reinterpret_cast<const uint4*>(P->W1 + n * LDX + 8 * c);
+        cp_async16_tc(w1 + canon(n, 8 * c, HID), P->W1 + n * LDX + 8 * c);
     }
     for (int i = threadIdx.x; i < HID * (HID / 8); i += TC_THREADS) {           // W2: 128 rows x 16 chunks
         const int n = i / (HID / 8), c = i % (HID / 8);
-        *reinterpret_cast<uint4*>(S.w2 + canon(n, 8 * c, HID)) = *reinterpret_cast<const uint4*>(P->W2 + n * LDH + 8 * c);
+        cp_async16_tc(w2 + canon(n, 8 * c, HID), P->W2 + n * LDH + 8 * c);
     }
     for (int i = threadIdx.x; i < OUTP * (HID / 8); i += TC_THREADS) {          // W3: 16 rows x 16 chunks
         const int n = i / (HID / 8), c = i % (HID / 8);
-        *reinterpret_cast<uint4*>(S.w3 + canon(n, 8 * c, OUTP)) = *reinterpret_cast<const uint4*>(P->W3 + n * LDH + 8 * c);
+        cp_async16_tc(w3 + canon(n, 8 * c, OUTP), P->W3 + n * LDH + 8 * c);
     }
     for (int i = threadIdx.x; i < HID; i += TC_THREADS) { S.b1[i] = P->b1[i]; S.b2[i] = P->b2[i]; }
     for (int i = threadIdx.x; i < OUTP; i += TC_THREADS) S.b3[i] = P->b3[i];
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// The three layers of the tile whose inputs sit in S.x[buf]; on return the
-// output accumulator (columns 0..15) is in TMEM and `ph` has advanced.
-// Returns false if a wait expired.
-__device__ bool tile_network(TcSmem& S, int buf, uint32_t& ph, int* err) {
+// Per-thread view of its group: group g, row (TMEM lane) and TMEM base.
+struct GroupCtx {
+    int g, row;
+    uint32_t tacc;                      // this thread's lane quarter, the group's columns
+    bool leader;
+};
+
+__device__ __forceinline__ GroupCtx group_ctx(const TcSmem& S) {
+    GroupCtx c;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = 32 * (warp & 3) + lane;            // TMEM lane = sample row of this thread
-    const int col0 = 64 * (warp >> 2);                  // this warp's column half
-    const uint32_t tm = S.tmem;
-    const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+    c.g = warp / GWARPS;
+    c.row = 32 * (warp % GWARPS) + lane;
+    c.tacc = S.tmem + ((uint32_t)(32 * (warp % GWARPS)) << 16) + (uint32_t)(128 * c.g);
+    c.leader = (threadIdx.x % GTHREADS) == 0;
+    return c;
+}
+
+// The three layers of the group's tile (inputs in its x buffer); on return
+// the output accumulator (columns 0..15 of the group) is in TMEM.  Returns
+// false if a wait expired.
+__device__ bool tile_network(TcSmem& S, const GroupCtx& c, uint32_t& ph, int* err) {
+    TcGroup& G = S.grp[c.g];
+    const uint32_t dcol = S.tmem + (uint32_t)(128 * c.g);     // lane 0 of the group's accumulator
     const uint32_t id128 = idesc(TM, HID), id16 = idesc(TM, OUTP);
     for (int layer = 0; layer < 3; ++layer) {
-        // issue the layer
-        if (threadIdx.x == 0) {
+        if (c.leader) {
             fence_after();
             if (layer == 0) {
-                const uint32_t a0 = su32(S.x[buf]), b0 = su32(S.w1);
+                const uint32_t a0 = su32(G.x), b0 = su32(S.w1);
                 for (int kk = 0; kk < KX_TC / 16; ++kk)
-                    mma_f16(tm, sdesc(a0 + kk * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
-                            sdesc(b0 + kk * 2 * (HID / 8) * 128, (HID / 8) * 128, 128), id128, kk > 0);
-            } else if (layer == 1) {
-                const uint32_t a0 = su32(S.h), b0 = su32(S.w2);
-                for (int kk = 0; kk < HID / 16; ++kk)
-                    mma_f16(tm, sdesc(a0 + kk * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
+                    mma_f16(dcol, sdesc(a0 + kk * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
                             sdesc(b0 + kk * 2 * (HID / 8) * 128, (HID / 8) * 128, 128), id128, kk > 0);
             } else {
-                const uint32_t a0 = su32(S.h), b0 = su32(S.w3);
+                const uint32_t a0 = su32(G.h), b0 = su32(layer == 1 ? S.w2 : S.w3);
+                const int nb = layer == 1 ? HID : OUTP;
                 for (int kk = 0; kk < HID / 16; ++kk)
-                    mma_f16(tm, sdesc(a0 + kk * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
-                            sdesc(b0 + kk * 2 * (OUTP / 8) * 128, (OUTP / 8) * 128, 128), id16, kk > 0);
+                    mma_f16(dcol, sdesc(a0 + kk * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
+                            sdesc(b0 + kk * 2 * (nb / 8) * 128, (nb / 8) * 128, 128), layer == 1 ? id128 : id16,
+                            kk > 0);
             }
-            mma_commit(&S.mbar);
+            mma_commit(&S.mbar[c.g]);
+            if (!mbar_wait(&S.mbar[c.g], ph & 1, err)) S.abort[c.g] = 1;
         }
-        const bool ok = mbar_wait(&S.mbar, ph & 1, err);
         ++ph;
-        if (!ok) S.abort = 1;
-        __syncthreads();
-        if (S.abort) return false;
+        group_sync(c.g);
+        if (S.abort[c.g]) return false;
         fence_after();
         if (layer == 2) return true;
-        // bias + activation: accumulator -> next layer's A operand in S.h
+        // bias + activation: accumulator -> next layer's A operand in G.h
         const float* bias = layer == 0 ? S.b1 : S.b2;
 #pragma unroll
-        for (int cb = 0; cb < 64; cb += 16) {
-            uint32_t v[16];
-            tmem_ld16(tm + tlane + (uint32_t)(col0 + cb), v);
+        for (int half = 0; half < 2; ++half) {
+            uint32_t v[64];
+            tmem_ld64(c.tacc + (uint32_t)(64 * half), v);
             tmem_wait_ld();
-            uint32_t w[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int c = col0 + cb + 2 * e;
-                w[e] = act2_tc(__uint_as_float(v[2 * e]) + bias[c], __uint_as_float(v[2 * e + 1]) + bias[c + 1]);
+            for (int cb = 0; cb < 64; cb += 16) {
+                uint32_t w[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int col = 64 * half + cb + 2 * e;
+                    w[e] = act2_tc(__uint_as_float(v[cb + 2 * e]) + bias[col],
+                                   __uint_as_float(v[cb + 2 * e + 1]) + bias[col + 1]);
+                }
+                *reinterpret_cast<uint4*>(G.h + canon(c.row, 64 * half + cb, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(G.h + canon(c.row, 64 * half + cb + 8, TM)) = make_uint4(w[4], w[5], w[6], w[7]);
             }
-            *reinterpret_cast<uint4*>(S.h + canon(row, col0 + cb, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<uint4*>(S.h + canon(row, col0 + cb + 8, TM)) = make_uint4(w[4], w[5], w[6], w[7]);
         }
         fence_async_smem();
         fence_before();
-        __syncthreads();
+        group_sync(c.g);
     }
     return true;
 }
 
-// Output of the tile (warps 0..3; thread = row): y[0..15] from TMEM + b3.
-__device__ __forceinline__ void tile_output(const TcSmem& S, float (&y)[16]) {
-    const int warp = threadIdx.x >> 5;
+// Output of the group's tile (thread = row): y[0..15] from TMEM + b3.
+__device__ __forceinline__ void tile_output(const TcSmem& S, const GroupCtx& c, float (&y)[16]) {
     uint32_t v[16];
-    tmem_ld16(S.tmem + ((uint32_t)(32 * (warp & 3)) << 16), v);
+    tmem_ld16(c.tacc, v);
     tmem_wait_ld();
 #pragma unroll
     for (int o = 0; o < 16; ++o) y[o] = __uint_as_float(v[o]) + S.b3[o];
@@ -232,17 +270,18 @@ __device__ __forceinline__ void tile_output(const TcSmem& S, float (&y)[16]) {
 
 __device__ void tc_setup(TcSmem& S, const Packed* P) {
     const int warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.mbar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        S.abort = 0;
+    if (threadIdx.x < GROUPS) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.mbar[threadIdx.x])) : "memory");
+        S.abort[threadIdx.x] = 0;
     }
+    if (threadIdx.x == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem)),
                      "r"(TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     load_weights_tc(S, P);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     fence_async_smem();
     fence_before();
     __syncthreads();
@@ -258,97 +297,104 @@ __device__ void tc_teardown(TcSmem& S) {
     }
 }
 
-// Input rows (BF16, LDX per row) of tile t into S.x[buf] (canonical), cp.async.
-__device__ __forceinline__ void issue_rows(TcSmem& S, int buf, const __nv_bfloat16* xg, long row0) {
-    const uint32_t base = su32(S.x[buf]);
-    for (int i = threadIdx.x; i < TM * (KX_TC / 8); i += TC_THREADS) {
-        const int r = i / (KX_TC / 8), c = i % (KX_TC / 8);
-        cp_async16_tc(base + canon(r, 8 * c, TM), xg + (row0 + r) * LDX + 8 * c);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
+// Fused closure evaluation: four groups per CTA work on their own tiles of
+// 128 cells (tile = 4 * CTA + group, then stepping by 4 * grid).  Each
+// thread of a group gathers the inputs of its cell (exactly the features
+// of the training sampler) into the group's operand buffer, the group runs
+// the network, and the thread writes s * y: R_8^m straight to G11 (with
+// their ghost copies), the centre values of I_8^m to ctr[o][M] for the node
+// averaging.  While one group gathers or waits for its MMAs, the others
+// run their epilogues, so load, tensor and MUFU latencies overlap.
 template <class T>
-__global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_closure_mlp_tc(const ClosureArgs<T> A, const Packed* __restrict__ P,
-                                                                  const __nv_bfloat16* __restrict__ xg,
-                                                                  const float* __restrict__ sc,
-                                                                  float* __restrict__ ctr, int* __restrict__ err) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_closure_tc(const ClosureArgs<T> A, const Packed* __restrict__ P,
+                                                              float* __restrict__ ctr, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(raw);
-    tc_setup(S, P);
+    __shared__ const T* colp[NMOM];
+    column_table(A, colp, NMOM);
+    tc_setup(S, P);                         // ends with a CTA barrier: colp is visible
+    const GroupCtx c = group_ctx(S);
     const int nx = A.nx, ny = A.ny;
     const int M = nx * ny;
     const int tiles = (M + TM - 1) / TM;
     const long Pp = A.pitch;
     uint32_t ph = 0;
-    int buf = 0;
-    int tile = blockIdx.x;
-    if (tile < tiles) issue_rows(S, 0, xg, (long)tile * TM);
-    for (; tile < tiles; tile += gridDim.x, buf ^= 1) {
-        if (tile + (int)gridDim.x < tiles) issue_rows(S, buf ^ 1, xg, (long)(tile + gridDim.x) * TM);
-        else asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        fence_async_smem();
-        __syncthreads();
-        if (!tile_network(S, buf, ph, err)) break;
-        if (threadIdx.x < TM) {
-            float y[16];
-            tile_output(S, y);
-            const int m = tile * TM + threadIdx.x;
-            if (m < M) {
-                const float s = sc[m];
-                const int ix = m % nx, iy = m / nx;
+    for (int tile = blockIdx.x * GROUPS + c.g; tile < tiles; tile += gridDim.x * GROUPS) {
+        TcGroup& G = S.grp[c.g];
+        const int m = tile * TM + c.row;
+        const bool ok = m < M;
+        const int ix = ok ? m % nx : 0, iy = ok ? m / nx : 0;
+        float f[NMOM], s, inv;
+        features36<T>(colp, stencil(ix, iy, nx, ny, A.p[0], A.p[1], Pp), ok, f, s, inv);
+        {
+            const float la = ok ? A.lsa[m] : 0.f, ls = ok ? A.lss[m] : 0.f;
+            uint32_t w[KX_TC / 2];
 #pragma unroll
-                for (int o = 0; o < NOUT; ++o) {
-                    const float val = s * y[o];
-                    if (A.slot[NMOM + o].x != 0) { ctr[(long)o * M + m] = val; continue; }
-                    T* c = A.g[0].base + (long)A.slot[NMOM + o].y * A.g[0].cstride;
-                    const T tv = (T)val;
-                    c[(long)(iy + 1) * Pp + ix] = tv;
-                    if (ix == (A.p[0] ? nx - 1 : 0)) c[(long)(iy + 1) * Pp - 1] = tv;
-                    if (ix == (A.p[0] ? 0 : nx - 1)) c[(long)(iy + 1) * Pp + nx] = tv;
-                    if (iy == (A.p[1] ? ny - 1 : 0)) c[ix] = tv;
-                    if (iy == (A.p[1] ? 0 : ny - 1)) c[(long)(ny + 1) * Pp + ix] = tv;
-                }
+            for (int q = 0; q < NMOM / 2; ++q) w[q] = pack_bf16_tc(f[2 * q], f[2 * q + 1]);
+            w[NMOM / 2] = pack_bf16_tc(la, ls);
+#pragma unroll
+            for (int q = NMOM / 2 + 1; q < KX_TC / 2; ++q) w[q] = 0u;
+#pragma unroll
+            for (int q = 0; q < KX_TC / 8; ++q)
+                *reinterpret_cast<uint4*>(G.x + canon(c.row, 8 * q, TM)) =
+                    make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
+        fence_async_smem();
+        group_sync(c.g);
+        if (!tile_network(S, c, ph, err)) break;
+        float y[16];
+        tile_output(S, c, y);
+        if (ok) {
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) {
+                const float val = s * y[o];
+                if (A.slot[NMOM + o].x != 0) { ctr[(long)o * M + m] = val; continue; }
+                T* cc = A.g[0].base + (long)A.slot[NMOM + o].y * A.g[0].cstride;
+                const T tv = (T)val;
+                cc[(long)(iy + 1) * Pp + ix] = tv;
+                if (ix == (A.p[0] ? nx - 1 : 0)) cc[(long)(iy + 1) * Pp - 1] = tv;
+                if (ix == (A.p[0] ? 0 : nx - 1)) cc[(long)(iy + 1) * Pp + nx] = tv;
+                if (iy == (A.p[1] ? ny - 1 : 0)) cc[ix] = tv;
+                if (iy == (A.p[1] ? 0 : ny - 1)) cc[(long)(ny + 1) * Pp + ix] = tv;
             }
         }
         fence_before();
-        __syncthreads();
+        group_sync(c.g);
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
     tc_teardown(S);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_forward_tc(const float* __restrict__ X, long M,
+__global__ void __launch_bounds__(TC_THREADS, 1) k_forward_tc(const float* __restrict__ X, long M,
                                                               const Packed* __restrict__ P, float* __restrict__ Y,
                                                               int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(raw);
     tc_setup(S, P);
+    const GroupCtx c = group_ctx(S);
+    const int t = threadIdx.x % GTHREADS;
     const long tiles = (M + TM - 1) / TM;
     uint32_t ph = 0;
-    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        // FP32 rows -> BF16 canonical (two columns per thread step)
-        for (int i = threadIdx.x; i < TM * (KX_TC / 2); i += TC_THREADS) {
-            const int r = i / (KX_TC / 2), c = 2 * (i % (KX_TC / 2));
+    for (long tile = (long)blockIdx.x * GROUPS + c.g; tile < tiles; tile += (long)gridDim.x * GROUPS) {
+        TcGroup& G = S.grp[c.g];
+        // FP32 rows -> BF16 canonical (two columns per step)
+        for (int i = t; i < TM * (KX_TC / 2); i += GTHREADS) {
+            const int r = i / (KX_TC / 2), col = 2 * (i % (KX_TC / 2));
             const long m = tile * TM + r;
             float a = 0.f, b = 0.f;
-            if (m < M && c < NIN) { a = X[m * NIN + c]; b = X[m * NIN + c + 1]; }
-            *reinterpret_cast<uint32_t*>(S.x[0] + canon(r, c, TM)) = pack_bf16_tc(a, b);
+            if (m < M && col < NIN) { a = X[m * NIN + col]; b = X[m * NIN + col + 1]; }
+            *reinterpret_cast<uint32_t*>(G.x + canon(r, col, TM)) = pack_bf16_tc(a, b);
         }
         fence_async_smem();
-        __syncthreads();
-        if (!tile_network(S, 0, ph, err)) break;
-        if (threadIdx.x < TM) {
-            float y[16];
-            tile_output(S, y);
-            const long m = tile * TM + threadIdx.x;
-            if (m < M)
+        group_sync(c.g);
+        if (!tile_network(S, c, ph, err)) break;
+        float y[16];
+        tile_output(S, c, y);
+        const long m = tile * TM + c.row;
+        if (m < M)
 #pragma unroll
-                for (int o = 0; o < NOUT; ++o) Y[m * NOUT + o] = y[o];
-        }
+            for (int o = 0; o < NOUT; ++o) Y[m * NOUT + o] = y[o];
         fence_before();
-        __syncthreads();
+        group_sync(c.g);
     }
     tc_teardown(S);
 }
@@ -380,29 +426,26 @@ int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void
     if (M <= 0) return 0;
     static bool attr = false;
     if (smem_attr(k_forward_tc, attr)) return -4;
-    long blocks = (M + TM - 1) / TM;
-    if (blocks > (long)TC_MINB * sms_tc()) blocks = (long)TC_MINB * sms_tc();
+    long blocks = (M + TM * GROUPS - 1) / (TM * GROUPS);
+    if (blocks > sms_tc()) blocks = sms_tc();
     k_forward_tc<<<(unsigned)blocks, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(X, M, P, Y, err);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
 template <class T>
-int closure_mlp_tc(const ClosureArgs<T>& A, const Packed* P, const __nv_bfloat16* xg, const float* sc, float* ctr,
-                   int* err, void* stream) {
+int closure_tc(const ClosureArgs<T>& A, const Packed* P, float* ctr, int* err, void* stream) {
     static bool attr = false;
-    if (smem_attr(k_closure_mlp_tc<T>, attr)) return -4;
+    if (smem_attr(k_closure_tc<T>, attr)) return -4;
     const long M = (long)A.nx * A.ny;
     if (M <= 0) return 0;
-    long blocks = (M + TM - 1) / TM;
-    if (blocks > (long)TC_MINB * sms_tc()) blocks = (long)TC_MINB * sms_tc();
-    k_closure_mlp_tc<T><<<(unsigned)blocks, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(A, P, xg, sc, ctr, err);
+    long blocks = (M + TM * GROUPS - 1) / (TM * GROUPS);
+    if (blocks > sms_tc()) blocks = sms_tc();
+    k_closure_tc<T><<<(unsigned)blocks, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(A, P, ctr, err);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
-template int closure_mlp_tc<float>(const ClosureArgs<float>&, const Packed*, const __nv_bfloat16*, const float*, float*,
-                                   int*, void*);
-template int closure_mlp_tc<double>(const ClosureArgs<double>&, const Packed*, const __nv_bfloat16*, const float*,
-                                    float*, int*, void*);
+template int closure_tc<float>(const ClosureArgs<float>&, const Packed*, float*, int*, void*);
+template int closure_tc<double>(const ClosureArgs<double>&, const Packed*, float*, int*, void*);
 
 }  // namespace mlp
 }  // namespace starmap
