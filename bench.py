@@ -521,7 +521,7 @@ def run_closure(args):
                    "closure": ev["closure"], "plain": ev["plain"], "gain_vs_p7": ev["gain_vs_p7"],
                    "l2_flush": "none"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "closure evaluation (features + mma.sync MLP + nodes)",
+                     "frac": achieved / peak, "traffic": None, "kernel": "closure evaluation (fused features + tcgen05 network, node averaging)",
                      "flops_per_launch": flops, "launch_ms": eval_ms, "peak_kind": f"{pk_kind} bf16_tflops"},
         "e2e": None,
         "gpu_launches": None,
