@@ -266,6 +266,9 @@ def run_native(args):
     from paper_1211_2205_gb300 import capi
 
     problem, desc = workload(args.workload)
+    if args.grid > 0:
+        problem = inputs.Problem(**{**problem.__dict__, "n": (args.grid, args.grid)})
+        desc += f" (grid overridden to {args.grid}x{args.grid})"
     esize = 4 if problem.precision == "fp32" else 8
     # a dedicated stream: the legacy default stream has handle 0, which the
     # library would read as "use your own stream"
@@ -312,7 +315,7 @@ def run_native(args):
     achieved = alg_bytes / (pass_times[dom] / 1e3) / 1e9
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
-    traffic = measured_traffic(s.kernel, args.workload, dom)
+    traffic = measured_traffic(s.kernel, args.workload, dom) if args.grid <= 0 else None
 
     # end to end through the C ABI with host buffers: zero the state on the
     # device, upload the initial moments from the host, K steps, read back
@@ -474,7 +477,8 @@ def run_closure(args):
     t0 = time.perf_counter()
     data = closure.generate(list(range(8)), n=512, N_ref=39, snapshots=8, t_final=0.5)
     t1 = time.perf_counter()
-    tr = closure.train(data, steps=6000, batch=8192)
+    tr = closure.train(data, steps=args.train_steps, batch=8192) if args.train_steps > 0 else \
+        closure.TrainResult(params=closure.init_params(0), losses=[float("nan")], steps=0)
     t2 = time.perf_counter()
     media = max(1, min(args.steps, 4))
     ev = closure.evaluate(tr.params, [100 + k for k in range(media)], n=512, repeats=2)
@@ -541,6 +545,11 @@ def main():
     ap.add_argument("--workload", default="random_p39")
     ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "tiled"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="override the cells per axis of a single-instance workload (profiling captures of a "
+                         "smaller case of the same kernel)")
+    ap.add_argument("--train-steps", type=int, default=6000,
+                    help="closure_p7: Adam steps (0: time the untrained network, for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps are required")
