@@ -758,7 +758,8 @@ int starmap_set_source(starmap_t* h, int j, const double* q, size_t count) {
         return rebuild_tables(h);
     }
     if (count != np) return fail(h, STARMAP_E_ARG, "source size does not match the grid of the component");
-    if (h->src_slot[j] < 0) {
+    const bool new_slot = h->src_slot[j] < 0;
+    if (new_slot) {
         void* d = nullptr;
         CK(cudaMalloc(&d, np * h->esize), "cudaMalloc source");
         h->src_slot[j] = (int)h->src_dev.size();
@@ -771,7 +772,8 @@ int starmap_set_source(starmap_t* h, int j, const double* q, size_t count) {
     } else {
         CK(cudaMemcpy(d, q, np * 8, cudaMemcpyHostToDevice), "upload source");
     }
-    return rebuild_tables(h);
+    // the pass tables only change when a component gains a source
+    return new_slot ? rebuild_tables(h) : STARMAP_OK;
 }
 
 int starmap_set_moment(starmap_t* h, int j, const double* u, size_t count) {
