@@ -281,6 +281,15 @@ int starmap_set_state(starmap_t* h, const void* buf, size_t bytes);
 /* Wait for all queued work of the handle. */
 int starmap_sync(starmap_t* h);
 
+/* Failure-detection self-test (no counterpart in the paper).  Runs one CTA
+ * that waits, with the same bounded wait the pass kernels use (2 s limit),
+ * for an mbarrier phase that nothing completes.  The wait must give up,
+ * raise the error flag and return; the call then returns STARMAP_E_TIMEOUT
+ * (the expected outcome; the CUDA context stays usable).  STARMAP_E_STATE
+ * if the wait did not give up, STARMAP_E_CUDA if the kernel could not run.
+ * Synchronous (legacy default stream), about 2 s. */
+int starmap_selftest_bounded_wait(void);
+
 /* ------------------------------------------------------ learned closure
  * Not in the paper.  The network maps 38 inputs to the 9 order-8 moments:
  *   inputs  x = (u_0 .. u_35) / s, log(1 + sigma_a), log(1 + sigma_s0), the

@@ -111,6 +111,7 @@ def lib():
         "starmap_get_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t]),
         "starmap_set_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t]),
         "starmap_sync": (ctypes.c_int, [H]),
+        "starmap_selftest_bounded_wait": (ctypes.c_int, []),
         "starmap_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                        ctypes.c_int, ctypes.c_long, ctypes.c_long, ctypes.c_long,
                                                        ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
@@ -180,6 +181,11 @@ def host_matrices(system: int, N: int):
     if rc != OK:
         raise StarmapError(rc, L.starmap_last_error(None).decode())
     return Mx, My, grid, order, lam.value
+
+
+def selftest_bounded_wait() -> int:
+    """Status of the bounded-wait self-test (E_TIMEOUT is the expected outcome)."""
+    return lib().starmap_selftest_bounded_wait()
 
 
 def host_expm1div(c) -> np.ndarray:

@@ -478,6 +478,38 @@ int tiled_stage_count(TiledPlan* pl, int P) { return pl ? (int)pl->tab[P].stages
 
 int tiled_variant(TiledPlan* pl) { return pl ? pl->variant : 0; }
 
+namespace {
+// One CTA waits, through the passes' own bounded wait, for the phase of an
+// mbarrier that nothing arrives at: the wait must give up and raise the flag.
+__global__ void k_wait_selftest(int* err, int* result) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *result = wait_bounded(&bar, 0, &abort_flag, err) ? 1 : 0;
+}
+}  // namespace
+
+int tiled_wait_selftest(int* gave_up) {
+    int *d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return -4;
+    int h[2] = {0, -1};
+    cudaError_t e = cudaMemcpy(d, h, 2 * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>(d, d + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return -4;
+    *gave_up = (h[0] == 1 && h[1] == 0) ? 1 : 0;
+    return 0;
+}
+
 int tiled_default_variant(int N) { return N <= SHORT_TILE_MAX_N ? 1 : 0; }
 
 int tiled_ctas_per_sm(int variant) { return variant ? tiled5::MINB : tiled::MINB; }

@@ -43,6 +43,9 @@ int tiled_smem_bytes(TiledPlan* plan, int P);
 void tiled_tile_grid(TiledPlan* plan, int* tiles_x, int* tiles_y);
 int tiled_stage_count(TiledPlan* plan, int P);
 int tiled_variant(TiledPlan* plan);
+// Self-test of the bounded wait (an mbarrier nothing arrives at); *gave_up = 1
+// when the wait expired and raised the flag as it must.
+int tiled_wait_selftest(int* gave_up);
 // Resident CTAs per SM the kernels of a tile height are built for.
 int tiled_ctas_per_sm(int variant);
 // Allow the batch kernel of the given tile height smem_bytes of dynamic shared memory.
