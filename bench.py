@@ -445,6 +445,8 @@ def run_batch(args):
         "config": {"workload": "batched_256", "description": desc, "instances": len(inst),
                    "updates_per_step": updates_per_step, "state_bytes": state_bytes, "schedule": "merged",
                    "kernel": "tiled_batch (persistent, CUDA graph)",
+                   "tile_rows_autotuned": b.tile_rows()[0],
+                   "autotune_ms_per_step": {"rows10": b.tile_rows()[1], "rows5": b.tile_rows()[2]},
                    "l2_flush": "none: state larger than L2", "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "tiled_batch", "algorithmic_bytes_per_launch": alg_total / launches,

@@ -374,8 +374,13 @@ int starmap_mlp_train_step(starmap_mlp_t* net, const float* X, const float* T, c
  * all instances (heaviest first) with each instance's own tables; the
  * pass sequence of a step count is captured once and replayed.  The
  * schedule is cfgs[0].schedule for all; cfgs[0].cuda_stream (if not NULL)
- * must be a non-default stream (graphs are captured on it).  Errors:
- * E_UNSUPPORTED for an FP64, slab or closure instance, else as
+ * must be a non-default stream (graphs are captured on it).  Tile shape:
+ * cfgs[0].kernel = STARMAP_KERNEL_TILED_TALL or _TILED_SHORT forces 64 x 10
+ * or 64 x 5 tiles; anything else runs the autotuner, which builds the batch
+ * with both, times two steps of each on the fresh all-zero state (left
+ * zero; time and step counters are reset) and keeps the faster -- creation
+ * then takes both builds and needs twice the state memory meanwhile.
+ * Errors: E_UNSUPPORTED for an FP64, slab or closure instance, else as
  * starmap_create (the message names the instance). */
 typedef struct starmap_batch_s starmap_batch_t;
 int  starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t** out);
@@ -386,6 +391,9 @@ int  starmap_batch_count(const starmap_batch_t* b);
  * the problem-data, read-out and diagnostics entry points.  Stepping an
  * instance alone with starmap_step is allowed.  NULL if i is out of range. */
 starmap_t* starmap_batch_instance(starmap_batch_t* b, int i);
+/* Rows of the tiles the batch uses (10 or 5) and the autotuner's ms per
+ * step for each (-1 where it did not time them).  Outputs may be NULL. */
+int  starmap_batch_tile_rows(const starmap_batch_t* b, double* ms_tall, double* ms_short);
 /* Kernel launches of one starmap_batch_step(b, nsteps) (inside its graph). */
 long starmap_batch_launches(const starmap_batch_t* b, long nsteps);
 int  starmap_batch_step(starmap_batch_t* b, long nsteps);

@@ -138,6 +138,7 @@ def lib():
         "starmap_batch_instance": (H, [H, ctypes.c_int]),
         "starmap_batch_launches": (ctypes.c_long, [H, ctypes.c_long]),
         "starmap_batch_step": (ctypes.c_int, [H, ctypes.c_long]),
+        "starmap_batch_tile_rows": (ctypes.c_int, [H, _dp, _dp]),
         "starmap_batch_sync": (ctypes.c_int, [H]),
         "starmap_mlp_sync": (ctypes.c_int, [H]),
     }
@@ -558,8 +559,11 @@ class Batch:
         self._inst = [Stepper._borrow(self._L.starmap_batch_instance(h, i), "fp32") for i in range(len(configs))]
 
     @classmethod
-    def from_problems(cls, problems, schedule: str = "merged", stream: Optional[int] = None) -> "Batch":
-        cfgs = [dict(N=p.N, ax=p.ax, n=p.n, bc=p.bc, cn=p.cn, precision="fp32", schedule=schedule) for p in problems]
+    def from_problems(cls, problems, schedule: str = "merged", stream: Optional[int] = None,
+                      kernel: str = "auto") -> "Batch":
+        """kernel: "auto" (autotuned tile height), "tiled_tall" or "tiled_short"."""
+        cfgs = [dict(N=p.N, ax=p.ax, n=p.n, bc=p.bc, cn=p.cn, precision="fp32", schedule=schedule,
+                     kernel=kernel) for p in problems]
         b = cls(cfgs, stream=stream)
         for inst, p in zip(b.instances, problems):
             inst.load_problem(p)
@@ -588,6 +592,12 @@ class Batch:
 
     def __len__(self):
         return len(self._inst)
+
+    def tile_rows(self):
+        """(rows of the batch's tiles, autotuner ms/step with 10-row tiles, with 5-row tiles)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        rows = self._L.starmap_batch_tile_rows(self._h, ctypes.byref(a), ctypes.byref(b))
+        return rows, a.value, b.value
 
     def launches(self, nsteps: int) -> int:
         return self._L.starmap_batch_launches(self._h, int(nsteps))

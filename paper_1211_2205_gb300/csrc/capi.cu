@@ -80,6 +80,7 @@ struct starmap_batch_s {
     bool own_stream = false;
     int schedule = STARMAP_SCHEDULE_MERGED;
     int variant = 1;                       // tile height of every instance (see starmap_batch_create)
+    double tuned_ms[2] = {-1.0, -1.0};     // autotuner: ms per step with 10-row / 5-row tiles (-1: not timed)
     std::vector<starmap_t*> inst;
     std::vector<unsigned long> uploaded;   // parameter version of each instance on the device
     std::vector<char> staging;             // host copy of the parameter blocks
@@ -1098,8 +1099,9 @@ int batch_issue(starmap_batch_t* b, long n) {
 }
 }  // namespace
 
-int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t** out) {
-    if (!out) return bfail(nullptr, STARMAP_E_ARG, "out is NULL");
+namespace {
+// Build a batch whose instances use tile height `variant` (0: 10 rows, 1: 5 rows).
+int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batch_t** out) {
     *out = nullptr;
     if (!cfgs || count < 1) return bfail(nullptr, STARMAP_E_ARG, "a batch needs at least one configuration");
     starmap_batch_t* b = new (std::nothrow) starmap_batch_t();
@@ -1124,10 +1126,7 @@ int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t*
     }
     struct Inst { int tiles, cost; };       // tiles and per-tile cost (stages of both parities)
     std::vector<Inst> shapes;
-    // one tile height for all instances: the default of the largest order
-    int maxN = 1;
-    for (int i = 0; i < count; ++i) maxN = std::max(maxN, cfgs[i].N);
-    b->variant = tiled_default_variant(maxN);
+    b->variant = variant;
     for (int i = 0; i < count; ++i) {
         starmap_config c = cfgs[i];
         if (c.system != STARMAP_PN2D || c.precision != STARMAP_FP32 || c.closure != STARMAP_CLOSURE_NONE)
@@ -1186,6 +1185,74 @@ int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t*
     if (rc) return bail(rc);
     *out = b;
     return STARMAP_OK;
+}
+
+// Device time of `steps` batched steps (CUDA events on the batch stream).
+int batch_time(starmap_batch_t* b, long steps, double* ms) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return STARMAP_E_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return STARMAP_E_CUDA; }
+    int rc = starmap_batch_step(b, 1);                     // warm-up: graph capture and first touch
+    if (!rc) rc = cudaEventRecord(e0, b->stream) == cudaSuccess ? 0 : STARMAP_E_CUDA;
+    if (!rc) rc = starmap_batch_step(b, steps);
+    if (!rc) rc = cudaEventRecord(e1, b->stream) == cudaSuccess ? 0 : STARMAP_E_CUDA;
+    if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? 0 : STARMAP_E_CUDA;
+    float t = 0.f;
+    if (!rc) rc = cudaEventElapsedTime(&t, e0, e1) == cudaSuccess ? 0 : STARMAP_E_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) rc = starmap_batch_sync(b);
+    *ms = t / (double)steps;
+    return rc;
+}
+
+// Back to t = 0, step 0 (the tuning steps ran on the zero state).
+void batch_reset_clock(starmap_batch_t* b) {
+    for (starmap_t* h : b->inst) {
+        h->t = 0.0;
+        h->steps = 0;
+        h->have_output = false;
+    }
+}
+}  // namespace
+
+int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t** out) {
+    if (!out) return bfail(nullptr, STARMAP_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfgs || count < 1) return bfail(nullptr, STARMAP_E_ARG, "a batch needs at least one configuration");
+    const int k = cfgs[0].kernel;
+    if (k == STARMAP_KERNEL_TILED_TALL || k == STARMAP_KERNEL_TILED_SHORT)
+        return batch_build(cfgs, count, k == STARMAP_KERNEL_TILED_SHORT ? 1 : 0, out);
+    // Autotuner: build the batch with each tile height, time two steps of
+    // each on the freshly created (all-zero, source-free, vacuum) state --
+    // which the steps leave zero -- and keep the faster.
+    starmap_batch_t* cand[2] = {nullptr, nullptr};
+    double ms[2] = {-1.0, -1.0};
+    int rc = STARMAP_OK;
+    for (int v = 0; v < 2 && rc == STARMAP_OK; ++v) {
+        rc = batch_build(cfgs, count, v, &cand[v]);
+        if (rc == STARMAP_OK) rc = batch_time(cand[v], 2, &ms[v]);
+        if (rc != STARMAP_OK && cand[v]) g_batch_create_error = cand[v]->err;
+    }
+    if (rc != STARMAP_OK) {
+        for (starmap_batch_t* c : cand) starmap_batch_destroy(c);
+        return rc;
+    }
+    const int best = ms[1] < ms[0] ? 1 : 0;
+    starmap_batch_destroy(cand[1 - best]);
+    starmap_batch_t* b = cand[best];
+    b->tuned_ms[0] = ms[0];
+    b->tuned_ms[1] = ms[1];
+    batch_reset_clock(b);
+    *out = b;
+    return STARMAP_OK;
+}
+
+int starmap_batch_tile_rows(const starmap_batch_t* b, double* ms_tall, double* ms_short) {
+    if (!b) return 0;
+    if (ms_tall) *ms_tall = b->tuned_ms[0];
+    if (ms_short) *ms_short = b->tuned_ms[1];
+    return b->variant ? 5 : 10;
 }
 
 void starmap_batch_destroy(starmap_batch_t* b) {

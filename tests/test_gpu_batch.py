@@ -124,3 +124,22 @@ def test_batch_rejects_unsupported_instances():
     with pytest.raises(capi.StarmapError) as e:
         capi.Batch([dict(ok, system="slab", n=(32, 1))])
     assert e.value.code == capi.E_UNSUPPORTED
+
+
+def test_autotuner_times_both_tile_heights_and_leaves_state_zero():
+    probs = [_instance(k) for k in range(6)]
+    b = capi.Batch.from_problems(probs)                  # kernel "auto": tuned
+    rows, tall, short = b.tile_rows()
+    assert rows in (5, 10) and tall > 0 and short > 0
+    assert (rows == 5) == (short < tall)
+    for inst in b.instances:
+        assert inst.steps_done == 0 and inst.time == 0.0
+    # the tuning steps left the state as loaded (zero before the problem data)
+    alone = capi.Stepper.from_problem(probs[2], kernel="tiled", schedule="merged")
+    b.step(3)
+    alone.step(3)
+    b.sync()
+    for j in range(alone.ncomp):
+        assert np.array_equal(b.instances[2].moments(j), alone.moments(j)), j
+    forced = capi.Batch.from_problems(probs[:2], kernel="tiled_tall")
+    assert forced.tile_rows() == (10, -1.0, -1.0)
