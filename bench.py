@@ -181,10 +181,9 @@ def peaks():
 # CPU oracle sample (cpu_baseline and --impl reference)
 # --------------------------------------------------------------------------
 
-def oracle_sample(problem, cells: int, steps: int):
-    """Time the FP64 oracle on a cells x cells window of the workload with the
-    same spacing and material (periodic wrap at the window edges), `steps`
-    full steps.  Returns (updates/s, description)."""
+def window_problem(problem, cells: int):
+    """The cells x cells window at the centre of the workload with the same
+    spacing and material (periodic wrap at the window edges), and its dt."""
     from oracle import pn_oracle as O
     x0, x1, y0, y1 = problem.ax
     hx = (x1 - x0) / problem.n[0]
@@ -195,13 +194,41 @@ def oracle_sample(problem, cells: int, steps: int):
     Mx, My, order = O.system_matrices(problem.system, problem.N)
     dt = O.time_step(Mx, problem.ax, problem.n, problem.cn)
     sub = inputs.Problem(**{**problem.__dict__, "ax": ax, "n": (cells, cells), "bc": ("periodic", "periodic")})
+    return sub, dt
+
+
+def oracle_sample(problem, cells: int, steps: int, keep: bool = False):
+    """Time the FP64 oracle on a cells x cells window of the workload,
+    `steps` full steps after one untimed.  Returns (updates/s, description,
+    seconds[, the oracle's moments after the 1 + steps steps])."""
+    from oracle import pn_oracle as O
+    sub, dt = window_problem(problem, cells)
     s = O.solver_from_problem(sub, dt=dt)
     s.step()  # materials evaluated in the first step: exclude from timing
     t0 = time.perf_counter()
     s.run(steps)
     el = time.perf_counter() - t0
     updates = sum(u.size for u in s.U) * steps
-    return updates / el, f"oracle (numpy FP64) on a {cells}x{cells} window of the workload, {steps} steps after 1 untimed", el
+    desc = f"oracle (numpy FP64) on a {cells}x{cells} window of the workload, {steps} steps after 1 untimed"
+    if keep:
+        return updates / el, desc, el, [u.T.copy() for u in s.U]
+    return updates / el, desc, el
+
+
+def window_error(problem, cells: int, steps: int, ref, kernel: str):
+    """Relative L2 error over all moments of the GPU path (the workload's
+    precision and kernel) against the FP64 oracle on the oracle sample's
+    window after the same 1 + steps steps."""
+    from paper_1211_2205_gb300 import capi
+    sub, dt = window_problem(problem, cells)
+    g = capi.Stepper.from_problem(sub, dt=dt, kernel=kernel, schedule="merged")
+    g.step(1 + steps)
+    got = [g.moments(j) for j in range(g.ncomp)]
+    g.close()
+    num = sum(float(np.sum((a - b) ** 2)) for a, b in zip(got, ref))
+    den = sum(float(np.sum(b ** 2)) for b in ref)
+    return {"rel_l2_vs_fp64_oracle": math.sqrt(num / den) if den > 0 else math.sqrt(num),
+            "window": f"{cells}x{cells}", "steps": 1 + steps, "dtype": problem.precision}
 
 
 def run_reference(args):
@@ -361,8 +388,9 @@ def run_native(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cells, nst = {"random_p39": (192, 4), "checkerboard_p13": (256, 8), "gaussian_p5": (64, 100)}[args.workload]
-        v, sample, el = oracle_sample(problem, cells, nst)
+        v, sample, el, sol = oracle_sample(problem, cells, nst, keep=True)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+        line["precision"] = window_error(problem, cells, nst, sol, args.kernel)
     s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -458,7 +486,7 @@ def run_batch(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         small = min(problems, key=lambda p: p.n[0] * (p.N + 1) ** 2)
-        v, sample, el = oracle_sample(small, 64, 6)
+        v, sample, el = oracle_sample(small, 64, 6)[:3]
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
                                 "sample": sample + f" (instance {small.name})"}
     b.close()
