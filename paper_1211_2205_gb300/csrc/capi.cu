@@ -282,6 +282,15 @@ int run_pass(starmap_t* h, bool odd, int which) {
     if (h->kernel_used != STARMAP_KERNEL_GATHER) {
         int rc = tiled_pass(h->tiled, odd, which, h->stream);
         if (rc) return fail(h, rc, tiled_error(h->tiled));
+        // the tiled pass leaves the boundary copies to this refresh (scattered
+        // single-value stores would otherwise gate the boundary tiles)
+        GhostPassArgs<T> ga;
+        const int go[2] = {odd ? 1 : 0, odd ? 2 : 3};
+        for (int q = 0; q < 2; ++q) { ga.g[q] = grid_dev<T>(h, go[q]); ga.grid[q] = go[q]; }
+        ga.pitch = h->pitch;
+        ga.p[0] = h->p[0];
+        ga.p[1] = h->p[1];
+        if (launch_fill_ghosts_pass<T>(ga, h->stream)) return cuda_fail(h, cudaGetLastError(), "ghost refresh");
         return STARMAP_OK;
     }
     const int gl[2] = {odd ? 1 : 0, odd ? 2 : 3};

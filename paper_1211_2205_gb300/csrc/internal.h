@@ -63,6 +63,15 @@ struct GhostArgs {
     int kbegin, kend;             // components to refresh
 };
 
+// Boundary copies of every component of the two output grids of a pass.
+template <class T>
+struct GhostPassArgs {
+    GridDev<T> g[2];
+    int grid[2];                  // grid numbers (their x / y type)
+    long pitch;
+    int p[2];
+};
+
 template <class T>
 struct ReduceArgs {
     GridDev<T> g[4];
@@ -73,6 +82,7 @@ struct ReduceArgs {
 // launchers (kernels_gather.cu)
 template <class T> int launch_gather_pass(const GatherArgs<T>& a, void* stream);
 template <class T> int launch_fill_ghosts(const GhostArgs<T>& a, void* stream);
+template <class T> int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream);
 template <class T> int launch_reduce(const ReduceArgs<T>& a, double* partials, int nblocks,
                                      double* result, void* stream);
 template <class T> int launch_axpby(T* out, const T* x, const T* y, double alpha, double beta,

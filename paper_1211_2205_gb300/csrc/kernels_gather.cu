@@ -9,6 +9,8 @@
 // or a merged odd pair).  It serves FP64 runs, the slab system and any N.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace starmap {
@@ -93,6 +95,30 @@ __global__ void k_fill_ghosts(const GhostArgs<T> A) {
         T* comp = G.base + (long)k * G.cstride;
         const T v = comp[(long)(y + 1) * A.pitch + x];
         store_point(comp, A.pitch, x, y, G.nx, G.ny, xnode, ynode, A.p[0], A.p[1], v);
+    }
+}
+
+// Boundary copies after a pass whose kernel left them out: blockIdx.y runs
+// over the components of both output grids, threads over the four
+// boundary lines of the component (rows y = 0 and ny - 1, columns x = 0
+// and nx - 1), each point re-stored with its copies (store_point).
+template <class T>
+__global__ void k_fill_ghosts_pass(const GhostPassArgs<T> A) {
+    const int c = blockIdx.y;
+    const int which = c < A.g[0].K ? 0 : 1;
+    const GridDev<T>& G = A.g[which];
+    const int k = which ? c - A.g[0].K : c;
+    const bool xnode = (A.grid[which] & 1) != 0, ynode = (A.grid[which] & 2) != 0;
+    T* comp = G.base + (long)k * G.cstride;
+    const int nx = G.nx, ny = G.ny;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < 2 * (nx + ny); r += gridDim.x * blockDim.x) {
+        int x, y;
+        if (r < nx) { x = r; y = 0; }
+        else if (r < 2 * nx) { x = r - nx; y = ny - 1; }
+        else if (r < 2 * nx + ny) { x = 0; y = r - 2 * nx; }
+        else { x = nx - 1; y = r - 2 * nx - ny; }
+        const T v = comp[(long)(y + 1) * A.pitch + x];
+        store_point(comp, A.pitch, x, y, nx, ny, xnode, ynode, A.p[0], A.p[1], v);
     }
 }
 
@@ -182,6 +208,16 @@ int launch_fill_ghosts(const GhostArgs<T>& a, void* stream) {
 }
 
 template <class T>
+int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream) {
+    const int K = a.g[0].K + a.g[1].K;
+    if (K <= 0) return 0;
+    const int len = 2 * std::max(a.g[0].nx + a.g[0].ny, a.g[1].nx + a.g[1].ny);
+    const dim3 grid((len + 255) / 256, K);
+    k_fill_ghosts_pass<T><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    return status_of(cudaGetLastError());
+}
+
+template <class T>
 int launch_reduce(const ReduceArgs<T>& a, double* partials, int nblocks, double* result, void* stream) {
     k_reduce_partials<T><<<nblocks, 256, 0, (cudaStream_t)stream>>>(a, partials);
     cudaError_t e = cudaGetLastError();
@@ -203,6 +239,8 @@ template int launch_gather_pass<float>(const GatherArgs<float>&, void*);
 template int launch_gather_pass<double>(const GatherArgs<double>&, void*);
 template int launch_fill_ghosts<float>(const GhostArgs<float>&, void*);
 template int launch_fill_ghosts<double>(const GhostArgs<double>&, void*);
+template int launch_fill_ghosts_pass<float>(const GhostPassArgs<float>&, void*);
+template int launch_fill_ghosts_pass<double>(const GhostPassArgs<double>&, void*);
 template int launch_reduce<float>(const ReduceArgs<float>&, double*, int, double*, void*);
 template int launch_reduce<double>(const ReduceArgs<double>&, double*, int, double*, void*);
 template int launch_axpby<float>(float*, const float*, const float*, double, double, size_t, void*);

@@ -84,7 +84,7 @@ struct PassTables {
 
 // Orders up to this use the 5-row tiles by default (few stages per tile:
 // two CTAs per SM hide each other's setup, fill and drain).
-constexpr int SHORT_TILE_MAX_N = 21;
+constexpr int SHORT_TILE_MAX_N = 3;
 
 // Per tile height: rows, input box rows, threads, consumer threads, end of the ring.
 struct Variant { int ty, byi, threads, consumers, ring_end; };
@@ -399,6 +399,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             prm.srcs = (const float* const*)pl->dev_src;
             prm.err = pl->err_dev;
             prm.smem_part_off = part_off;
+            prm.ghosts = 0;                     // single-instance passes: the handle refreshes ghosts
             prm.smem_stage_off = stage_off;
         }
     }
@@ -463,7 +464,10 @@ int tiled_export_params(TiledPlan* pl, void* host4) {
     if (!pl || !pl->ready) return -7;
     Params* d = static_cast<Params*>(host4);
     for (int P = 0; P < 2; ++P)
-        for (int w = 0; w < 2; ++w) d[2 * P + w] = pl->prm[P][w];
+        for (int w = 0; w < 2; ++w) {
+            d[2 * P + w] = pl->prm[P][w];
+            d[2 * P + w].ghosts = 1;          // batched passes write the boundary copies themselves
+        }
     return 0;
 }
 

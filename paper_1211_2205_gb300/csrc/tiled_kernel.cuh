@@ -102,6 +102,8 @@ struct Params {
                                 // component, or -1 if absent; source slot or -1)
     const float* const* srcs;   // source arrays by slot
     int* err;                   // bounded-wait failure flag
+    int ghosts;                 // 1: write the boundary copies of boundary points here; 0: the
+                                // caller refreshes them after the pass (off the critical path)
     int smem_coef_off[2], smem_fin_off[2], smem_part_off, smem_stage_off;   // byte offsets in dynamic smem
 };
 
@@ -253,6 +255,9 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
     const int warp = tid >> 5, lane = tid & 31;
     const int ntl = t0 < tend ? (tend - t0 + tstride - 1) / tstride : 0;
 
+    // warm the TMA descriptor cache while the barriers and tables are set up
+    if (warp == CONSUMER_WARPS && lane < 4)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(maps + lane)) : "memory");
     if (tid == 0) {
         for (int r = 0; r < NSTAGES; ++r) {
             if (!first_call) {
@@ -380,7 +385,7 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
         const bool xnode = gK & 1, ynode = gK & 2;
         const long plane = (long)G.nx * G.ny;
         int gxA[PP];
-        bool inA[PP], inB[PP], fast[PP];
+        bool inA[PP], inB[PP], pair[PP], bndj[PP];
         float* pptr[PP];          // point A_j in component 0
         long cidxA[PP];
         f2 ca2[PP][2], cb2[PP][2];  // decay pairs by class (isotropic)
@@ -399,7 +404,8 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
                 if (prm.p[1]) bnd |= (gy == G.ny - 1) || (gy == 0);
                 else if (!ynode) bnd |= (gy == 0) || (gy == G.ny - 1);
             }
-            fast[j] = inA[j] && inB[j] && !bnd;
+            pair[j] = inA[j] && inB[j];
+            bndj[j] = bnd && prm.ghosts;
             for (int c = 0; c < 2; ++c) {
                 float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
                 if (prm.nclasses == 2 && G.coef != nullptr) {
@@ -433,9 +439,9 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
             }
             ++s;
         };
-        // write one point (and its boundary copies)
-        auto store_point = [&](float* dst, int gx, float v) {
-            *dst = v;
+        // boundary copies of one point (section 4.2): the value itself is
+        // stored by the caller
+        auto ghost_copies = [&](float* dst, int gx, float v) {
             int xa = -2, xb = -2, ya = -2, yb = -2;
             if (prm.p[0]) { if (gx == G.nx - 1) xa = -1; if (gx == 0) xb = G.nx; }
             else if (!xnode) { if (gx == 0) xa = -1; if (gx == G.nx - 1) xb = G.nx; }
@@ -484,13 +490,21 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
                 const f2 v = f2_fma(aL[j], u, f2_mul(bL[j], w));
                 if (f.x < 0 || !alive) continue;
                 float* dst = pptr[j] + f.x;
-                if (fast[j]) {
+                // the pair with one 8-byte store; only a ragged right edge
+                // stores A alone, and only boundary points add their copies
+                // (so one boundary lane does not send its warp down a slow path)
+                if (pair[j]) {
                     *reinterpret_cast<f2*>(dst) = v;
-                } else {
+                } else if (inA[j]) {
                     float v0, v1;
                     f2_split(v, v0, v1);
-                    if (inA[j]) store_point(dst, gxA[j], v0);
-                    if (inB[j]) store_point(dst + 1, gxA[j] + 1, v1);
+                    *dst = v0;
+                }
+                if (bndj[j]) {
+                    float v0, v1;
+                    f2_split(v, v0, v1);
+                    if (inA[j]) ghost_copies(dst, gxA[j], v0);
+                    if (inB[j]) ghost_copies(dst + 1, gxA[j] + 1, v1);
                 }
             }
         };
