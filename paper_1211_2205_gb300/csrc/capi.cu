@@ -87,6 +87,8 @@ struct starmap_batch_s {
     void* dev_params = nullptr;
     void* dev_items = nullptr;
     int nitems = 0;
+    GhostJob* dev_ghosts[2] = {nullptr, nullptr};   // boundary refresh after even / odd passes
+    int nghosts[2] = {0, 0};
     int smem = 0;
     int grid = 0;
     std::vector<std::pair<long, cudaGraphExec_t>> graphs;   // captured step sequences by step count
@@ -1068,6 +1070,7 @@ void batch_release(starmap_batch_t* b) {
     b->inst.clear();
     if (b->dev_params) cudaFree(b->dev_params);
     if (b->dev_items) cudaFree(b->dev_items);
+    for (GhostJob* g : b->dev_ghosts) if (g) cudaFree(g);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -1078,7 +1081,8 @@ int batch_sync_params(starmap_batch_t* b) {
     for (size_t i = 0; i < b->inst.size(); ++i) {
         starmap_t* h = b->inst[i];
         if (b->uploaded[i] == h->version) continue;
-        if (tiled_export_params(h->tiled, b->staging.data() + i * pb)) return bfail(b, STARMAP_E_STATE, "instance tables not built");
+        if (tiled_export_params(h->tiled, b->staging.data() + i * pb, 0))
+            return bfail(b, STARMAP_E_STATE, "instance tables not built");
         b->uploaded[i] = h->version;
         any = true;
     }
@@ -1092,7 +1096,8 @@ int batch_sync_params(starmap_batch_t* b) {
 // The pass launches of one starmap_batch_step(b, n) (same schedules as do_steps).
 int batch_issue(starmap_batch_t* b, long n) {
     auto pass = [&](int P, int w) {
-        return tiled_batch_pass(b->dev_params, b->dev_items, b->nitems, P, w, b->grid, b->smem, b->variant, b->stream);
+        return tiled_batch_pass(b->dev_params, b->dev_items, b->nitems, P, w, b->grid, b->smem, b->variant, b->stream) ||
+               launch_fill_ghosts_jobs(b->dev_ghosts[P], b->nghosts[P], b->stream);
     };
     if (b->schedule == STARMAP_SCHEDULE_MERGED) {
         if (pass(1, 0)) return STARMAP_E_CUDA;
@@ -1183,10 +1188,27 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
     b->grid = std::max(1, std::min(b->nitems, slots));
     b->staging.assign((size_t)count * 4 * tiled_params_bytes(), 0);
     b->uploaded.assign(count, ~0ul);
+    // Boundary refresh after a pass of parity P: every component of its two
+    // output grids (even: G11, G22; odd: G21, G12) of every instance.
+    std::vector<GhostJob> jobs[2];
+    for (int P = 0; P < 2; ++P)
+        for (starmap_t* h : b->inst)
+            for (int g : {P ? 1 : 0, P ? 2 : 3})
+                for (int k = 0; k < h->Kg[g]; ++k)
+                    jobs[P].push_back(GhostJob{(float*)h->base[g] + (long)k * h->cstride[g], h->pitch, h->nxg[g],
+                                               h->nyg[g], g, h->p[0], h->p[1], 0});
     e = cudaMalloc(&b->dev_params, b->staging.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int4));
     if (e == cudaSuccess && !it.empty())
         e = cudaMemcpyAsync(b->dev_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+    for (int P = 0; P < 2 && e == cudaSuccess; ++P) {
+        if (jobs[P].size() > 0x7fffffffu) return bail(bfail(b, STARMAP_E_ARG, "too many components in one batch"));
+        b->nghosts[P] = (int)jobs[P].size();
+        e = cudaMalloc(&b->dev_ghosts[P], std::max<size_t>(1, jobs[P].size()) * sizeof(GhostJob));
+        if (e == cudaSuccess && !jobs[P].empty())
+            e = cudaMemcpyAsync(b->dev_ghosts[P], jobs[P].data(), jobs[P].size() * sizeof(GhostJob),
+                                cudaMemcpyHostToDevice, b->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bail(bfail(b, e == cudaErrorMemoryAllocation ? STARMAP_E_NOMEM : STARMAP_E_CUDA,
                                             std::string("batch setup: ") + cudaGetErrorString(e)));
@@ -1282,7 +1304,8 @@ starmap_t* starmap_batch_instance(starmap_batch_t* b, int i) {
 
 long starmap_batch_launches(const starmap_batch_t* b, long nsteps) {
     if (!b || nsteps <= 0) return 0;
-    return b->schedule == STARMAP_SCHEDULE_MERGED ? 2 * nsteps + 1 : 3 * nsteps;
+    // two launches per pass: the batched pass and the boundary refresh
+    return 2 * (b->schedule == STARMAP_SCHEDULE_MERGED ? 2 * nsteps + 1 : 3 * nsteps);
 }
 
 int starmap_batch_step(starmap_batch_t* b, long nsteps) {

@@ -72,6 +72,17 @@ struct GhostPassArgs {
     int p[2];
 };
 
+// Boundary copies of one FP32 component, one entry of a batched refresh
+// (comp points at the component's first interior value, as GridDev::base).
+struct GhostJob {
+    float* comp;
+    long pitch;
+    int nx, ny;
+    int grid;                     // grid number (its x / y type)
+    int px, py;                   // periodic in x / y
+    int pad;
+};
+
 template <class T>
 struct ReduceArgs {
     GridDev<T> g[4];
@@ -83,6 +94,7 @@ struct ReduceArgs {
 template <class T> int launch_gather_pass(const GatherArgs<T>& a, void* stream);
 template <class T> int launch_fill_ghosts(const GhostArgs<T>& a, void* stream);
 template <class T> int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream);
+int launch_fill_ghosts_jobs(const GhostJob* jobs, int njobs, void* stream);
 template <class T> int launch_reduce(const ReduceArgs<T>& a, double* partials, int nblocks,
                                      double* result, void* stream);
 template <class T> int launch_axpby(T* out, const T* x, const T* y, double alpha, double beta,

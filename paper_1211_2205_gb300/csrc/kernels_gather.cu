@@ -122,6 +122,23 @@ __global__ void k_fill_ghosts_pass(const GhostPassArgs<T> A) {
     }
 }
 
+// Batched refresh: block b re-stores the boundary points of component
+// jobs[b] with their copies.
+__global__ void k_fill_ghosts_jobs(const GhostJob* __restrict__ jobs) {
+    const GhostJob J = jobs[blockIdx.x];
+    const bool xnode = (J.grid & 1) != 0, ynode = (J.grid & 2) != 0;
+    const int nx = J.nx, ny = J.ny;
+    for (int r = threadIdx.x; r < 2 * (nx + ny); r += blockDim.x) {
+        int x, y;
+        if (r < nx) { x = r; y = 0; }
+        else if (r < 2 * nx) { x = r - nx; y = ny - 1; }
+        else if (r < 2 * nx + ny) { x = 0; y = r - 2 * nx; }
+        else { x = nx - 1; y = r - 2 * nx - ny; }
+        const float v = J.comp[(long)(y + 1) * J.pitch + x];
+        store_point(J.comp, J.pitch, x, y, nx, ny, xnode, ynode, J.px, J.py, v);
+    }
+}
+
 // Deterministic FP64 reduction: per-block partials (mass, sum of squares,
 // non-finite count) over all rows of all grids, then one block sums them in
 // a fixed order.
@@ -214,6 +231,12 @@ int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream) {
     const int len = 2 * std::max(a.g[0].nx + a.g[0].ny, a.g[1].nx + a.g[1].ny);
     const dim3 grid((len + 255) / 256, K);
     k_fill_ghosts_pass<T><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    return status_of(cudaGetLastError());
+}
+
+int launch_fill_ghosts_jobs(const GhostJob* jobs, int njobs, void* stream) {
+    if (njobs <= 0) return 0;
+    k_fill_ghosts_jobs<<<njobs, 256, 0, (cudaStream_t)stream>>>(jobs);
     return status_of(cudaGetLastError());
 }
 

@@ -460,13 +460,13 @@ const char* tiled_error(TiledPlan* p) { return p ? p->err.c_str() : "tiled kerne
 
 size_t tiled_params_bytes() { return sizeof(Params); }
 
-int tiled_export_params(TiledPlan* pl, void* host4) {
+int tiled_export_params(TiledPlan* pl, void* host4, int ghosts) {
     if (!pl || !pl->ready) return -7;
     Params* d = static_cast<Params*>(host4);
     for (int P = 0; P < 2; ++P)
         for (int w = 0; w < 2; ++w) {
             d[2 * P + w] = pl->prm[P][w];
-            d[2 * P + w].ghosts = 1;          // batched passes write the boundary copies themselves
+            d[2 * P + w].ghosts = ghosts;
         }
     return 0;
 }

@@ -37,8 +37,10 @@ void tiled_destroy(TiledPlan* plan);
 
 // Batched passes over several plans (one persistent launch per pass).
 size_t tiled_params_bytes();
-// Copy the plan's four pass parameter blocks (index 2 P + which) to host4.
-int tiled_export_params(TiledPlan* plan, void* host4);
+// Copy the plan's four pass parameter blocks (index 2 P + which) to host4;
+// ghosts = 1: the batched pass also stores the boundary copies of its
+// boundary points, 0: a separate refresh does.
+int tiled_export_params(TiledPlan* plan, void* host4, int ghosts);
 int tiled_smem_bytes(TiledPlan* plan, int P);
 void tiled_tile_grid(TiledPlan* plan, int* tiles_x, int* tiles_y);
 int tiled_stage_count(TiledPlan* plan, int P);
