@@ -87,6 +87,7 @@ struct starmap_batch_s {
     void* dev_params = nullptr;
     void* dev_items = nullptr;
     int nitems = 0;
+    int* dev_ticket = nullptr;             // item counter of the batched pass
     GhostJob* dev_ghosts[2] = {nullptr, nullptr};   // boundary refresh after even / odd passes
     int nghosts[2] = {0, 0};
     int smem = 0;
@@ -1071,6 +1072,7 @@ void batch_release(starmap_batch_t* b) {
     if (b->dev_params) cudaFree(b->dev_params);
     if (b->dev_items) cudaFree(b->dev_items);
     for (GhostJob* g : b->dev_ghosts) if (g) cudaFree(g);
+    if (b->dev_ticket) cudaFree(b->dev_ticket);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -1081,7 +1083,7 @@ int batch_sync_params(starmap_batch_t* b) {
     for (size_t i = 0; i < b->inst.size(); ++i) {
         starmap_t* h = b->inst[i];
         if (b->uploaded[i] == h->version) continue;
-        if (tiled_export_params(h->tiled, b->staging.data() + i * pb, 0))
+        if (tiled_export_params(h->tiled, b->staging.data() + i * pb))
             return bfail(b, STARMAP_E_STATE, "instance tables not built");
         b->uploaded[i] = h->version;
         any = true;
@@ -1096,7 +1098,8 @@ int batch_sync_params(starmap_batch_t* b) {
 // The pass launches of one starmap_batch_step(b, n) (same schedules as do_steps).
 int batch_issue(starmap_batch_t* b, long n) {
     auto pass = [&](int P, int w) {
-        return tiled_batch_pass(b->dev_params, b->dev_items, b->nitems, P, w, b->grid, b->smem, b->variant, b->stream) ||
+        return tiled_batch_pass(b->dev_params, b->dev_items, b->nitems, P, w, b->grid, b->smem, b->variant,
+                                b->dev_ticket, b->stream) ||
                launch_fill_ghosts_jobs(b->dev_ghosts[P], b->nghosts[P], b->stream);
     };
     if (b->schedule == STARMAP_SCHEDULE_MERGED) {
@@ -1159,9 +1162,9 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
         b->smem = std::max(b->smem, std::max(tiled_smem_bytes(h->tiled, 0), tiled_smem_bytes(h->tiled, 1)));
     }
     // Items: runs of consecutive tiles of one instance, each about 1/4 of a
-    // CTA's fair share of the work (so a run streams through one pipeline,
-    // and the heaviest-first round robin still balances), heaviest first:
-    // CTA k takes items k, k + grid, ...
+    // CTA's fair share of the work (so a run streams through one pipeline),
+    // heaviest first: CTA k starts with item k and then claims the next
+    // unclaimed one (greedy longest-first balancing).
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1198,6 +1201,7 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
                     jobs[P].push_back(GhostJob{(float*)h->base[g] + (long)k * h->cstride[g], h->pitch, h->nxg[g],
                                                h->nyg[g], g, h->p[0], h->p[1], 0});
     e = cudaMalloc(&b->dev_params, b->staging.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->dev_ticket, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int4));
     if (e == cudaSuccess && !it.empty())
         e = cudaMemcpyAsync(b->dev_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);

@@ -10,14 +10,17 @@
 #include <cstring>
 
 #include "tiled.h"
-// the kernels, once per tile height (namespaces tiled: 10 rows, tiled5: 5 rows)
+// the kernels, once per tile height (namespaces tiled: 10 rows, two per
+// consumer warp; tiled5: 5 rows, one per consumer warp)
 #include "tiled_kernel.cuh"
 #undef STARMAP_TILED_NS
 #undef STARMAP_TILED_TY
 #undef STARMAP_TILED_MINB
+#undef STARMAP_TILED_RW
 #define STARMAP_TILED_NS tiled5
 #define STARMAP_TILED_TY 5
 #define STARMAP_TILED_MINB 2
+#define STARMAP_TILED_RW 1
 #include "tiled_kernel.cuh"
 
 namespace starmap {
@@ -86,11 +89,14 @@ struct PassTables {
 // two CTAs per SM hide each other's setup, fill and drain).
 constexpr int SHORT_TILE_MAX_N = 3;
 
-// Per tile height: rows, input box rows, threads, consumer threads, end of the ring.
-struct Variant { int ty, byi, threads, consumers, ring_end; };
+// Per tile height: rows, input box rows, threads, consumer threads, point
+// pairs per consumer thread, end of the ring.
+struct Variant { int ty, byi, threads, consumers, pp, ring_end; };
 const Variant kVariant[2] = {
-    {tiled::TY, tiled::BYI, tiled::THREADS, tiled::CONSUMERS, tiled::RING_OFF + tiled::NSTAGES * tiled::STAGE_BYTES},
-    {tiled5::TY, tiled5::BYI, tiled5::THREADS, tiled5::CONSUMERS, tiled5::RING_OFF + tiled5::NSTAGES * tiled5::STAGE_BYTES}};
+    {tiled::TY, tiled::BYI, tiled::THREADS, tiled::CONSUMERS, tiled::PP,
+     tiled::RING_OFF + tiled::NSTAGES * tiled::STAGE_BYTES},
+    {tiled5::TY, tiled5::BYI, tiled5::THREADS, tiled5::CONSUMERS, tiled5::PP,
+     tiled5::RING_OFF + tiled5::NSTAGES * tiled5::STAGE_BYTES}};
 
 }  // namespace
 
@@ -351,7 +357,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
         off += (int)(t.stages.size() * sizeof(int4));
         off = (off + 15) & ~15;
         const int part_off = off;
-        off += (nq_of(pl->N) + 1) * PP * V.consumers * 8;   // PP pairs of partial sums per consumer thread and q
+        off += (nq_of(pl->N) + 1) * V.pp * V.consumers * 8;   // pp pairs of partial sums per consumer thread and q
         pl->smem_bytes[P] = off;
         int dev = 0, maxsm = 0;
         cudaGetDevice(&dev);
@@ -399,7 +405,6 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             prm.srcs = (const float* const*)pl->dev_src;
             prm.err = pl->err_dev;
             prm.smem_part_off = part_off;
-            prm.ghosts = 0;                     // single-instance passes: the handle refreshes ghosts
             prm.smem_stage_off = stage_off;
         }
     }
@@ -460,14 +465,11 @@ const char* tiled_error(TiledPlan* p) { return p ? p->err.c_str() : "tiled kerne
 
 size_t tiled_params_bytes() { return sizeof(Params); }
 
-int tiled_export_params(TiledPlan* pl, void* host4, int ghosts) {
+int tiled_export_params(TiledPlan* pl, void* host4) {
     if (!pl || !pl->ready) return -7;
     Params* d = static_cast<Params*>(host4);
     for (int P = 0; P < 2; ++P)
-        for (int w = 0; w < 2; ++w) {
-            d[2 * P + w] = pl->prm[P][w];
-            d[2 * P + w].ghosts = ghosts;
-        }
+        for (int w = 0; w < 2; ++w) d[2 * P + w] = pl->prm[P][w];
     return 0;
 }
 
@@ -530,14 +532,15 @@ int tiled_batch_prepare(int smem_bytes, int variant) {
 }
 
 int tiled_batch_pass(const void* params, const void* items, int nitems, int P, int which, int grid, int smem_bytes,
-                     int variant, void* stream) {
+                     int variant, int* ticket, void* stream) {
     if (nitems <= 0) return 0;
+    if (cudaMemsetAsync(ticket, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess) return -4;
     if (variant)
         tiled5::k_tiled_batch<<<grid, tiled5::THREADS, smem_bytes, (cudaStream_t)stream>>>(
-            static_cast<const tiled5::Params*>(params), static_cast<const int4*>(items), nitems, P, which);
+            static_cast<const tiled5::Params*>(params), static_cast<const int4*>(items), nitems, P, which, ticket);
     else
         tiled::k_tiled_batch<<<grid, tiled::THREADS, smem_bytes, (cudaStream_t)stream>>>(
-            static_cast<const tiled::Params*>(params), static_cast<const int4*>(items), nitems, P, which);
+            static_cast<const tiled::Params*>(params), static_cast<const int4*>(items), nitems, P, which, ticket);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 

@@ -37,10 +37,9 @@ void tiled_destroy(TiledPlan* plan);
 
 // Batched passes over several plans (one persistent launch per pass).
 size_t tiled_params_bytes();
-// Copy the plan's four pass parameter blocks (index 2 P + which) to host4;
-// ghosts = 1: the batched pass also stores the boundary copies of its
-// boundary points, 0: a separate refresh does.
-int tiled_export_params(TiledPlan* plan, void* host4, int ghosts);
+// Copy the plan's four pass parameter blocks (index 2 P + which) to host4
+// (the passes leave the boundary copies to a separate refresh).
+int tiled_export_params(TiledPlan* plan, void* host4);
 int tiled_smem_bytes(TiledPlan* plan, int P);
 void tiled_tile_grid(TiledPlan* plan, int* tiles_x, int* tiles_y);
 int tiled_stage_count(TiledPlan* plan, int P);
@@ -54,8 +53,10 @@ int tiled_ctas_per_sm(int variant);
 int tiled_batch_prepare(int smem_bytes, int variant);
 // items: device array of int4 (instance, first tile, tile count, 0), each a
 // run of consecutive tiles of one instance; params: device array of
-// 4 * instances parameter blocks (instance i, parity P, which at 4 i + 2 P + which).
+// 4 * instances parameter blocks (instance i, parity P, which at 4 i + 2 P + which);
+// ticket: one device int, zeroed on the stream before the launch, from which
+// the CTAs claim items after their first.
 int tiled_batch_pass(const void* params, const void* items, int nitems, int P, int which, int grid, int smem_bytes,
-                     int variant, void* stream);
+                     int variant, int* ticket, void* stream);
 
 }  // namespace starmap

@@ -1,7 +1,8 @@
 // Tiled half-step pass for the 2D real P_N system in FP32 (sm_103a).
 //
 // One CTA owns a TX x TY tile of point indices, shared by the four staggered
-// grids (section 4.1); each consumer thread owns PP pairs of points of one row.  A
+// grids (section 4.1); each consumer thread owns a pair of points in each of
+// RW rows of the tile.  A
 // pass updates the components of one parity (odd l: grids G21 (R) and G12
 // (I); even l: G11 (R) and G22 (I)) from the half-grid differences
 // (eq. central_differences) of the other parity, weighted by -Mx/dx and
@@ -30,16 +31,19 @@
 // one arrival per consumer warp).  A stage is one step of the consumer loop:
 // slots for the R and I input of (l', q') and the R and I output finalised
 // there.  Input boxes are BX x (TY+1) (one-point halo, x start aligned to 16
-// bytes); output boxes TX x TY.  Boundary conditions live in ghost cells,
-// which the finalising thread writes with each boundary value.  Every wait
-// is bounded: on expiry the kernel raises an error flag, waits (bounded) for
-// its copies in flight, and returns.
+// bytes); output boxes TX x TY.  Boundary conditions live in ghost cells
+// (section 4.2), which a separate refresh kernel rewrites after the pass
+// (the boundary tiles would otherwise wait on scattered single-value
+// stores).  Every wait is bounded: on expiry the kernel raises an error
+// flag, waits (bounded) for its copies in flight, and returns.
 //
 // The file is compiled once per tile height: STARMAP_TILED_NS names the
-// namespace, STARMAP_TILED_TY the tile height and STARMAP_TILED_MINB the
-// CTAs per SM the launch bounds ask for (10 rows, one CTA per SM, for large
-// N; 5 rows, two CTAs per SM, so that one CTA's setup, fill and drain
-// overlap the other's streaming when a tile has few stages).
+// namespace, STARMAP_TILED_TY the tile height, STARMAP_TILED_RW the rows per
+// consumer warp and STARMAP_TILED_MINB the CTAs per SM the launch bounds ask
+// for (10 rows, two per warp, one CTA per SM, for large N: a warp's fixed
+// cost per step (barrier wait, table reads, release) is spread over four
+// points; 5 rows, one per warp, two CTAs per SM, so that one CTA's setup,
+// fill and drain overlap the other's streaming when a tile has few stages).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -49,14 +53,20 @@
 #define STARMAP_TILED_NS tiled
 #define STARMAP_TILED_TY 10
 #define STARMAP_TILED_MINB 1
+#define STARMAP_TILED_RW 2
 #endif
 
 namespace starmap {
 namespace STARMAP_TILED_NS {
 
-constexpr int PP = 1;                   // point pairs per consumer thread (along x)
-constexpr int TX = 64 * PP;             // tile width: pair j of lane l covers x0 + 64 j + 2 l, +1
+constexpr int PX = 1;                   // point pairs per consumer thread along x
+constexpr int TX = 64 * PX;             // tile width
 constexpr int TY = STARMAP_TILED_TY;    // tile height
+constexpr int RW = STARMAP_TILED_RW;    // tile rows per consumer warp
+constexpr int RSTEP = TY / RW;          // rows between the rows of one warp
+constexpr int PP = PX * RW;             // point pairs per consumer thread: pair j of lane l covers
+                                        // x = x0 + 64 (j % PX) + 2 l, +1 in row row0 + RSTEP (j / PX)
+static_assert(TY % RW == 0, "the rows of a tile split evenly over the warps");
 constexpr int MINB = STARMAP_TILED_MINB;
 constexpr int VEC = 4;                  // 16 bytes of FP32: TMA x alignment
 constexpr int BX = TX + VEC;            // input box width (halo + alignment)
@@ -69,7 +79,7 @@ constexpr int STEPS_PER_STAGE = 1;      // consumer steps sharing one mbarrier s
 constexpr int STEP_BYTES = SLOT * SLOTS_PER_STEP;
 constexpr int STAGE_BYTES = STEP_BYTES * STEPS_PER_STAGE;
 constexpr int NSTAGES = 6;              // stages in the ring
-constexpr int CONSUMER_WARPS = 2 * TY;  // one warp per tile row and output kind (R, I)
+constexpr int CONSUMER_WARPS = 2 * RSTEP;   // per output kind (R, I), one warp per RW rows
 constexpr int CONSUMERS = CONSUMER_WARPS * 32;
 constexpr int PRODUCER_WARPS = 2;       // independent TMA issue streams (stage s mod 2)
 constexpr int THREADS = CONSUMERS + 32 * PRODUCER_WARPS;
@@ -102,8 +112,6 @@ struct Params {
                                 // component, or -1 if absent; source slot or -1)
     const float* const* srcs;   // source arrays by slot
     int* err;                   // bounded-wait failure flag
-    int ghosts;                 // 1: write the boundary copies of boundary points here; 0: the
-                                // caller refreshes them after the pass (off the critical path)
     int smem_coef_off[2], smem_fin_off[2], smem_part_off, smem_stage_off;   // byte offsets in dynamic smem
 };
 
@@ -213,6 +221,10 @@ __device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
 }
 __device__ __forceinline__ f2 lds2(const float* p) { return *reinterpret_cast<const f2*>(p); }
 __device__ __forceinline__ f2 zero2() { return 0ull; }
+
+// float offsets of point pair j from pair 0 inside an input box / an output box
+__host__ __device__ constexpr int in_off(int j) { return (j / PX) * RSTEP * BX + 64 * (j % PX); }
+__host__ __device__ constexpr int out_off(int j) { return (j / PX) * RSTEP * TX + 64 * (j % PX); }
 
 // x-differences of points A (column c) and B (column c + 1) of one box row:
 // right operands at columns c, c + 1, left operands at c - 1, c.  The pair
@@ -349,21 +361,23 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
     }
 
     // --------------------------------------------------------- consumers
-    // Warp w handles tile row w % TY for the targets of kind K = w / TY
-    // (0: R outputs, 1: I outputs), at the point pairs j = 0..PP-1:
-    // A_j = (x0 + 64 j + 2 lane, y), B_j = A_j + (1, 0).  Targets of kind K
+    // Warp w handles the tile rows row0 + RSTEP i (row0 = w % RSTEP, i < RW)
+    // for the targets of kind K = w / RSTEP (0: R outputs, 1: I outputs), at
+    // the point pairs j = 0..PP-1: A_j = (x0 + 64 (j % PX) + 2 lane,
+    // y0 + row0 + RSTEP (j / PX)), B_j = A_j + (1, 0).  Targets of kind K
     // take d_x of the inputs of kind K (through Mx) and d_y of the inputs of
     // the other kind (through My).
-    const int K = warp / TY;
-    const int row = warp % TY;
+    const int K = warp / RSTEP;
+    const int row = warp % RSTEP;
     int s = 0;                  // global consumer step (= stage) over the CTA's tiles
+    int ring_r = 0;             // its ring slot and barrier phase
+    uint32_t ring_ph = 0;
     bool alive = true;
     for (int tl = 0; tl < ntl && alive; ++tl) {
         const int tile = t0 + tl * tstride;
         const int x0 = (tile % prm.tiles_x) * TX, y0 = (tile / prm.tiles_x) * TY;
-        const int gy = y0 + row;
         // float offsets, inside a step, of the difference operands of pair 0
-        // (pair j sits 64 j floats further): d_x from the input of kind K (slot
+        // (pair j sits in_off(j) floats further): d_x from the input of kind K (slot
         // K), d_y from the input of kind 1 - K (slot 1 - K)
         int rx, cx, uy;
         bool ev;
@@ -381,31 +395,20 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
         }
         // the output grid of kind K
         const OutGrid& G = prm.out[K];
-        const int gK = prm.P == 1 ? (K == 0 ? 1 : 2) : (K == 0 ? 0 : 3);
-        const bool xnode = gK & 1, ynode = gK & 2;
         const long plane = (long)G.nx * G.ny;
-        int gxA[PP];
-        bool inA[PP], inB[PP], pair[PP], bndj[PP];
+        bool inA[PP], inB[PP], pair[PP];
         float* pptr[PP];          // point A_j in component 0
         long cidxA[PP];
         f2 ca2[PP][2], cb2[PP][2];  // decay pairs by class (isotropic)
     #pragma unroll
         for (int j = 0; j < PP; ++j) {
-            gxA[j] = x0 + 64 * j + 2 * lane;
-            inA[j] = gxA[j] < G.nx && gy < G.ny;
-            inB[j] = gxA[j] + 1 < G.nx && gy < G.ny;
-            pptr[j] = G.base + (long)(gy + 1) * prm.pitch + gxA[j];
-            cidxA[j] = (long)gy * G.nx + gxA[j];
-            bool bnd = false;
-            for (int pt = 0; pt < 2; ++pt) {
-                const int gx = gxA[j] + pt;
-                if (prm.p[0]) bnd |= (gx == G.nx - 1) || (gx == 0);
-                else if (!xnode) bnd |= (gx == 0) || (gx == G.nx - 1);
-                if (prm.p[1]) bnd |= (gy == G.ny - 1) || (gy == 0);
-                else if (!ynode) bnd |= (gy == 0) || (gy == G.ny - 1);
-            }
+            const int gx = x0 + 64 * (j % PX) + 2 * lane;
+            const int gy = y0 + row + RSTEP * (j / PX);
+            inA[j] = gx < G.nx && gy < G.ny;
+            inB[j] = gx + 1 < G.nx && gy < G.ny;
+            pptr[j] = G.base + (long)(gy + 1) * prm.pitch + gx;
+            cidxA[j] = (long)gy * G.nx + gx;
             pair[j] = inA[j] && inB[j];
-            bndj[j] = bnd && prm.ghosts;
             for (int c = 0; c < 2; ++c) {
                 float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
                 if (prm.nclasses == 2 && G.coef != nullptr) {
@@ -423,36 +426,17 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
         const int2* fp = reinterpret_cast<const int2*>(smem + prm.smem_fin_off[K]);
         f2* const pp = s_part + tid;            // entry (q, j) at pp[(q * PP + j) * CONSUMERS]
         const int uoff = (2 + K) * (SLOT / 4) + row * TX + 2 * lane;    // old value of pair 0 inside a step
-        // consumer step s lives in stage s / STEPS_PER_STAGE; the stage's barrier
-        // is awaited at its first step and released after its last step
-        const int last_step = prm.nstages - 1;
+        // consumer step s is stage s (ring slot ring_r, phase ring_ph): its
+        // barrier is awaited before the step and released after it
         auto stage_ptr = [&]() -> const float* {
-            const int k = s / STEPS_PER_STAGE;
-            const int r = k % NSTAGES;
-            if (s % STEPS_PER_STAGE == 0 && alive) alive = wait_bounded(&full[r], (k / NSTAGES) & 1, abort_flag, prm.err);
-            return reinterpret_cast<const float*>(ring + r * STAGE_BYTES + (s % STEPS_PER_STAGE) * STEP_BYTES);
+            if (alive) alive = wait_bounded(&full[ring_r], ring_ph, abort_flag, prm.err);
+            return reinterpret_cast<const float*>(ring + ring_r * STAGE_BYTES);
         };
         auto stage_done = [&]() {
-            if (s % STEPS_PER_STAGE == STEPS_PER_STAGE - 1 || s == last_step) {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[(s / STEPS_PER_STAGE) % NSTAGES]);
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[ring_r]);
             ++s;
-        };
-        // boundary copies of one point (section 4.2): the value itself is
-        // stored by the caller
-        auto ghost_copies = [&](float* dst, int gx, float v) {
-            int xa = -2, xb = -2, ya = -2, yb = -2;
-            if (prm.p[0]) { if (gx == G.nx - 1) xa = -1; if (gx == 0) xb = G.nx; }
-            else if (!xnode) { if (gx == 0) xa = -1; if (gx == G.nx - 1) xb = G.nx; }
-            if (prm.p[1]) { if (gy == G.ny - 1) ya = -1; if (gy == 0) yb = G.ny; }
-            else if (!ynode) { if (gy == 0) ya = -1; if (gy == G.ny - 1) yb = G.ny; }
-            float* rw = dst - gx;
-            if (xa != -2) rw[xa] = v;
-            if (xb != -2) rw[xb] = v;
-            float* col = dst - (long)(gy + 1) * prm.pitch;
-            if (ya != -2) col[(long)(ya + 1) * prm.pitch] = v;
-            if (yb != -2) col[(long)(yb + 1) * prm.pitch] = v;
+            if (++ring_r == NSTAGES) { ring_r = 0; ring_ph ^= 1u; }
         };
         // decay pairs (a, b) of the outputs of order L
         f2 aL[PP], bL[PP];
@@ -479,7 +463,7 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
             fp += 1;
     #pragma unroll
             for (int j = 0; j < PP; ++j) {
-                const f2 u = lds2(t + uoff + 64 * j);
+                const f2 u = lds2(t + uoff + out_off(j));
                 f2 w = W[j];
                 if (f.y >= 0) {
                     const float* qs = prm.srcs[f.y];
@@ -491,20 +475,13 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
                 if (f.x < 0 || !alive) continue;
                 float* dst = pptr[j] + f.x;
                 // the pair with one 8-byte store; only a ragged right edge
-                // stores A alone, and only boundary points add their copies
-                // (so one boundary lane does not send its warp down a slow path)
+                // stores A alone
                 if (pair[j]) {
                     *reinterpret_cast<f2*>(dst) = v;
                 } else if (inA[j]) {
                     float v0, v1;
                     f2_split(v, v0, v1);
                     *dst = v0;
-                }
-                if (bndj[j]) {
-                    float v0, v1;
-                    f2_split(v, v0, v1);
-                    if (inA[j]) ghost_copies(dst, gxA[j], v0);
-                    if (inB[j]) ghost_copies(dst + 1, gxA[j] + 1, v1);
                 }
             }
         };
@@ -516,8 +493,8 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
             cp += 4;
     #pragma unroll
             for (int j = 0; j < PP; ++j) {
-                f2 dx = diff_x(t + rx + 64 * j, cx, ev);
-                f2 dy = f2_sub(lds2(t + uy + 64 * j), lds2(t + uy + 64 * j - BX));
+                f2 dx = diff_x(t + rx + in_off(j), cx, ev);
+                f2 dy = f2_sub(lds2(t + uy + in_off(j)), lds2(t + uy + in_off(j) - BX));
                 if (!inI) {
                     if (K == 1) dx = zero2(); else dy = zero2();
                 }
@@ -613,25 +590,34 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tiled_pass(const __grid_const
 // Batched pass: a persistent grid walks the items of all instances (items
 // sorted by decreasing cost, CTA b takes items b, b + grid, ...); an item
 // is a run of consecutive tiles of one instance, (instance, first tile,
-// tile count), streamed through one pipeline.  Instance i's parameters for
+// tile count), streamed through one pipeline.  CTA b starts with item b and
+// then claims item gridDim.x + atomicAdd(ticket, 1) (ticket zero at launch).  Instance i's parameters for
 // parity P and coefficient set `which` are prms[(2 i + P) * 2 + which] in
 // global memory; the CTA copies them to shared memory and hands TMA the
 // tensor maps of the global copy.
 __global__ void __launch_bounds__(THREADS, MINB) k_tiled_batch(const Params* __restrict__ prms,
                                                             const int4* __restrict__ items, int nitems, int P,
-                                                            int which) {
+                                                            int which, int* __restrict__ ticket) {
     __shared__ Params s_prm;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    __shared__ int s_next;
+    int it = blockIdx.x;
+    bool first = true;
+    while (it < nitems) {
         const int4 item = items[it];
         const Params* g = prms + (2 * item.x + P) * 2 + which;
-        if (it != (int)blockIdx.x) __syncthreads();          // previous tile done with s_prm and the barriers
         {
             const uint4* src = reinterpret_cast<const uint4*>(g);
             uint4* dst = reinterpret_cast<uint4*>(&s_prm);
             for (int i = threadIdx.x; i < (int)(sizeof(Params) / 16); i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
-        tiled_tiles(s_prm, g->maps, item.y, 1, item.y + item.z, it == (int)blockIdx.x);
+        tiled_tiles(s_prm, g->maps, item.y, 1, item.y + item.z, first);
+        first = false;
+        __syncthreads();                  // run done with s_prm and the barriers
+        // claim the next item (heaviest first): greedy dynamic balancing
+        if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(ticket, 1);
+        __syncthreads();
+        it = s_next;
     }
 }
 
