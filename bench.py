@@ -411,6 +411,9 @@ def run_batch(args):
     from paper_1211_2205_gb300 import capi
 
     problems, desc = workload("batched_256")
+    if 0 < args.instances < len(problems):
+        problems = problems[:args.instances]
+        desc += f" (first {args.instances} instances only)"
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     b = capi.Batch.from_problems(problems, schedule="merged", stream=stream.cuda_stream)
@@ -581,6 +584,9 @@ def main():
     ap.add_argument("--grid", type=int, default=0,
                     help="override the cells per axis of a single-instance workload (profiling captures of a "
                          "smaller case of the same kernel)")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="batched_256: keep only the first K instances (profiling captures of a smaller case of "
+                         "the same kernel)")
     ap.add_argument("--train-steps", type=int, default=6000,
                     help="closure_p7: Adam steps (0: time the untrained network, for profiling captures)")
     args = ap.parse_args()

@@ -85,9 +85,8 @@ struct starmap_batch_s {
     std::vector<unsigned long> uploaded;   // parameter version of each instance on the device
     std::vector<char> staging;             // host copy of the parameter blocks
     void* dev_params = nullptr;
-    void* dev_items = nullptr;
-    int nitems = 0;
-    int* dev_ticket = nullptr;             // item counter of the batched pass
+    void* dev_items = nullptr;             // per CTA: strided runs (instance, first tile, count, stride)
+    int* dev_off = nullptr;                // CTA b's runs: items[off[b]] .. items[off[b + 1] - 1]
     GhostJob* dev_ghosts[2] = {nullptr, nullptr};   // boundary refresh after even / odd passes
     int nghosts[2] = {0, 0};
     int smem = 0;
@@ -1072,7 +1071,7 @@ void batch_release(starmap_batch_t* b) {
     if (b->dev_params) cudaFree(b->dev_params);
     if (b->dev_items) cudaFree(b->dev_items);
     for (GhostJob* g : b->dev_ghosts) if (g) cudaFree(g);
-    if (b->dev_ticket) cudaFree(b->dev_ticket);
+    if (b->dev_off) cudaFree(b->dev_off);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -1098,8 +1097,8 @@ int batch_sync_params(starmap_batch_t* b) {
 // The pass launches of one starmap_batch_step(b, n) (same schedules as do_steps).
 int batch_issue(starmap_batch_t* b, long n) {
     auto pass = [&](int P, int w) {
-        return tiled_batch_pass(b->dev_params, b->dev_items, b->nitems, P, w, b->grid, b->smem, b->variant,
-                                b->dev_ticket, b->stream) ||
+        return tiled_batch_pass(b->dev_params, b->dev_items, b->dev_off, P, w, b->grid, b->smem, b->variant,
+                                b->stream) ||
                launch_fill_ghosts_jobs(b->dev_ghosts[P], b->nghosts[P], b->stream);
     };
     if (b->schedule == STARMAP_SCHEDULE_MERGED) {
@@ -1141,7 +1140,7 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
         if (e != cudaSuccess) return bail(bfail(b, STARMAP_E_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
         b->own_stream = true;
     }
-    struct Inst { int tiles, cost; };       // tiles and per-tile cost (stages of both parities)
+    struct Inst { int tiles, cost; };       // tiles and per-tile cost (stages of the longer parity)
     std::vector<Inst> shapes;
     b->variant = variant;
     for (int i = 0; i < count; ++i) {
@@ -1158,37 +1157,85 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
         b->inst.push_back(h);
         int tx = 0, ty = 0;
         tiled_tile_grid(h->tiled, &tx, &ty);
-        shapes.push_back({tx * ty, tiled_stage_count(h->tiled, 0) + tiled_stage_count(h->tiled, 1)});
+        const int cost = std::max(tiled_stage_count(h->tiled, 0), tiled_stage_count(h->tiled, 1));
+        if ((long long)tx * ty * cost > 0x7fffffffll)
+            return bail(bfail(b, STARMAP_E_ARG, "batch instance " + std::to_string(i) + ": too many pipeline stages"));
+        shapes.push_back({tx * ty, cost});
         b->smem = std::max(b->smem, std::max(tiled_smem_bytes(h->tiled, 0), tiled_smem_bytes(h->tiled, 1)));
     }
-    // Items: runs of consecutive tiles of one instance, each about 1/4 of a
-    // CTA's fair share of the work (so a run streams through one pipeline),
-    // heaviest first: CTA k starts with item k and then claims the next
-    // unclaimed one (greedy longest-first balancing).
+    // Work units of all instances (heaviest instance first) form one list
+    // dealt round robin to the resident CTAs: unit e goes to CTA e mod grid,
+    // so every CTA gets about the same work and at any time the CTAs work on
+    // one contiguous band of the list (x-neighbouring units run side by
+    // side and share their halo columns in L2).  A unit is
+    //  * for short tiles (few stages): a strip of consecutive tiles in y,
+    //    STRIP_STAGES stages long, streamed through one pipeline (the next
+    //    tile's halo row is still in L2; setup, fill and drain are paid once
+    //    per strip);
+    //  * for long tiles: one tile; a CTA's tiles of one instance are then a
+    //    single run with stride grid (the band of tiles moves down the grid
+    //    in lockstep, so vertical neighbours also share halo rows in L2).
+    // Items are (instance, first tile, tile count, tile stride).
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    double total = 0;
-    for (const Inst& x : shapes) total += (double)x.tiles * x.cost;
+    constexpr int STRIP_MAX_STAGES = 48;     // tiles up to this long go in strips
     const int slots = sms * tiled_ctas_per_sm(b->variant);     // resident CTAs of the persistent grid
-    const double target = std::max(1.0, total / (4.0 * slots));
-    struct Item { int inst, first, count; double cost; };
-    std::vector<Item> items;
-    for (int i = 0; i < count; ++i) {
-        const int per = std::max(1, std::min(shapes[i].tiles, (int)std::lround(target / std::max(1, shapes[i].cost))));
-        for (int t = 0; t < shapes[i].tiles; t += per) {
-            const int c = std::min(per, shapes[i].tiles - t);
-            items.push_back({i, t, c, (double)c * shapes[i].cost});
+    // stages per strip: 192, halved while the list would hold fewer than
+    // four units per CTA (a few small instances must still fill the GPU)
+    std::vector<int> strip(count, 1);
+    long long total_units = 0;
+    for (int strip_stages = 192;; strip_stages /= 2) {
+        total_units = 0;
+        for (int i = 0; i < count; ++i) {
+            int tx = 0, ty = 0;
+            tiled_tile_grid(b->inst[i]->tiled, &tx, &ty);
+            const int c = std::max(1, shapes[i].cost);
+            strip[i] = c <= STRIP_MAX_STAGES ? std::max(1, std::min(ty, (strip_stages + c - 1) / c)) : 1;
+            total_units += strip[i] > 1 ? (long long)tx * ((ty + strip[i] - 1) / strip[i]) : shapes[i].tiles;
+        }
+        if (total_units >= 4LL * slots || strip_stages <= 1) break;
+    }
+    const int grid = (int)std::max(1LL, std::min<long long>(total_units, slots));
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (double)shapes[a].tiles * shapes[a].cost > (double)shapes[c].tiles * shapes[c].cost;
+    });
+    std::vector<std::vector<int4>> per(grid);
+    long long cum = 0;                        // list position of the instance's first unit
+    for (int i : order) {
+        int tx = 0, ty = 0;
+        tiled_tile_grid(b->inst[i]->tiled, &tx, &ty);
+        if (strip[i] > 1) {
+            const int S = strip[i];
+            long long u = 0;
+            for (int y0 = 0; y0 < ty; y0 += S)
+                for (int x = 0; x < tx; ++x, ++u)
+                    per[(cum + u) % grid].push_back(make_int4(i, y0 * tx + x, std::min(S, ty - y0), tx));
+            cum += u;
+        } else {
+            const int tiles = shapes[i].tiles;
+            for (int cta = 0; cta < grid; ++cta) {
+                const long long first = ((cta - cum) % grid + grid) % grid;
+                if (first >= tiles) continue;
+                const int n = (int)((tiles - 1 - first) / grid) + 1;
+                per[cta].push_back(make_int4(i, (int)first, n, grid));
+            }
+            cum += tiles;
         }
     }
-    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& c) { return a.cost > c.cost; });
-    if (items.size() > 0x7fffffffu) return bail(bfail(b, STARMAP_E_ARG, "too many tiles in one batch"));
-    b->nitems = (int)items.size();
-    std::vector<int4> it(items.size());
-    for (size_t k = 0; k < items.size(); ++k) it[k] = make_int4(items[k].inst, items[k].first, items[k].count, 0);
+    std::vector<int4> it;
+    std::vector<int> off(grid + 1, 0);
+    for (int cta = 0; cta < grid; ++cta) {
+        off[cta] = (int)it.size();
+        it.insert(it.end(), per[cta].begin(), per[cta].end());
+        if (it.size() > 0x7fffffffu) return bail(bfail(b, STARMAP_E_ARG, "too many tiles in one batch"));
+    }
+    off[grid] = (int)it.size();
     int rc = tiled_batch_prepare(b->smem, b->variant);
     if (rc) return bail(bfail(b, rc, "batch kernel needs more shared memory than the device offers"));
-    b->grid = std::max(1, std::min(b->nitems, slots));
+    b->grid = grid;
     b->staging.assign((size_t)count * 4 * tiled_params_bytes(), 0);
     b->uploaded.assign(count, ~0ul);
     // Boundary refresh after a pass of parity P: every component of its two
@@ -1201,7 +1248,9 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
                     jobs[P].push_back(GhostJob{(float*)h->base[g] + (long)k * h->cstride[g], h->pitch, h->nxg[g],
                                                h->nyg[g], g, h->p[0], h->p[1], 0});
     e = cudaMalloc(&b->dev_params, b->staging.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->dev_ticket, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dev_off, off.size() * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dev_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int4));
     if (e == cudaSuccess && !it.empty())
         e = cudaMemcpyAsync(b->dev_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);

@@ -431,12 +431,19 @@ int tiled_pass(TiledPlan* pl, bool odd, int which, void* stream) {
     if (!pl->ready) { pl->err = "tiled tables not built"; return -7; }
     const int P = odd ? 1 : 0;
     const int ntiles = pl->tiles_x * pl->tiles_y;
+    if (ntiles <= 0) return 0;
+    // persistent grid: every resident CTA slot, at most one per tile
+    const int grid = std::min(ntiles, pl->sms * tiled_ctas_per_sm(pl->variant));
+    if ((long long)((ntiles + grid - 1) / grid) * pl->prm[P][which].nstages > 0x7fffffffll) {
+        pl->err = "too many pipeline stages per CTA for the tiled kernel";
+        return -8;
+    }
     if (pl->variant) {
         tiled5::Params q;
         std::memcpy(&q, &pl->prm[P][which], sizeof(q));
-        tiled5::k_tiled_pass<<<ntiles, tiled5::THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(q, ntiles);
+        tiled5::k_tiled_pass<<<grid, tiled5::THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(q, ntiles);
     } else {
-        tiled::k_tiled_pass<<<ntiles, tiled::THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(pl->prm[P][which], ntiles);
+        tiled::k_tiled_pass<<<grid, tiled::THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(pl->prm[P][which], ntiles);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -531,16 +538,15 @@ int tiled_batch_prepare(int smem_bytes, int variant) {
     return e == cudaSuccess ? 0 : -4;
 }
 
-int tiled_batch_pass(const void* params, const void* items, int nitems, int P, int which, int grid, int smem_bytes,
-                     int variant, int* ticket, void* stream) {
-    if (nitems <= 0) return 0;
-    if (cudaMemsetAsync(ticket, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess) return -4;
+int tiled_batch_pass(const void* params, const void* items, const int* off, int P, int which, int grid,
+                     int smem_bytes, int variant, void* stream) {
+    if (grid <= 0) return 0;
     if (variant)
         tiled5::k_tiled_batch<<<grid, tiled5::THREADS, smem_bytes, (cudaStream_t)stream>>>(
-            static_cast<const tiled5::Params*>(params), static_cast<const int4*>(items), nitems, P, which, ticket);
+            static_cast<const tiled5::Params*>(params), static_cast<const int4*>(items), off, P, which);
     else
         tiled::k_tiled_batch<<<grid, tiled::THREADS, smem_bytes, (cudaStream_t)stream>>>(
-            static_cast<const tiled::Params*>(params), static_cast<const int4*>(items), nitems, P, which, ticket);
+            static_cast<const tiled::Params*>(params), static_cast<const int4*>(items), off, P, which);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 

@@ -51,12 +51,12 @@ int tiled_wait_selftest(int* gave_up);
 int tiled_ctas_per_sm(int variant);
 // Allow the batch kernel of the given tile height smem_bytes of dynamic shared memory.
 int tiled_batch_prepare(int smem_bytes, int variant);
-// items: device array of int4 (instance, first tile, tile count, 0), each a
-// run of consecutive tiles of one instance; params: device array of
-// 4 * instances parameter blocks (instance i, parity P, which at 4 i + 2 P + which);
-// ticket: one device int, zeroed on the stream before the launch, from which
-// the CTAs claim items after their first.
-int tiled_batch_pass(const void* params, const void* items, int nitems, int P, int which, int grid, int smem_bytes,
-                     int variant, int* ticket, void* stream);
+// items: device array of int4 (instance, first tile, tile count, stride),
+// each the tiles first, first + stride, ... of one instance; CTA b runs
+// items off[b] .. off[b + 1] - 1 (off: grid + 1 device ints); params: device array
+// of 4 * instances parameter blocks (instance i, parity P, which at
+// 4 i + 2 P + which).
+int tiled_batch_pass(const void* params, const void* items, const int* off, int P, int which, int grid,
+                     int smem_bytes, int variant, void* stream);
 
 }  // namespace starmap

@@ -373,6 +373,9 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
     int ring_r = 0;             // its ring slot and barrier phase
     uint32_t ring_ph = 0;
     bool alive = true;
+    // the output grid of kind K
+    const OutGrid& G = prm.out[K];
+    const long plane = (long)G.nx * G.ny;
     for (int tl = 0; tl < ntl && alive; ++tl) {
         const int tile = t0 + tl * tstride;
         const int x0 = (tile % prm.tiles_x) * TX, y0 = (tile / prm.tiles_x) * TY;
@@ -393,9 +396,6 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
             ev = (cx & 1) == 0;
             uy = (1 - K) * (SLOT / 4) + (row + syO - oyO) * BX + (2 * lane - bxsO);
         }
-        // the output grid of kind K
-        const OutGrid& G = prm.out[K];
-        const long plane = (long)G.nx * G.ny;
         bool inA[PP], inB[PP], pair[PP];
         float* pptr[PP];          // point A_j in component 0
         long cidxA[PP];
@@ -580,44 +580,36 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
     }
 }
 
-// Single-instance pass: one tile per CTA (the hardware's CTA scheduler
-// balances the SMs; measured faster than a persistent grid with a static
-// tile order on this two-die part).
+// Single-instance pass: a persistent grid; CTA b takes tiles b, b + gridDim.x,
+// ... (raster order).  The CTAs then work on one contiguous band of tiles
+// at any time, so the halo rows that vertically adjacent tiles share come
+// from DRAM once, and each CTA's pipeline runs on across its tiles.
 __global__ void __launch_bounds__(THREADS, MINB) k_tiled_pass(const __grid_constant__ Params prm, int ntiles) {
-    tiled_tiles(prm, prm.maps, blockIdx.x, 1, min(ntiles, (int)blockIdx.x + 1), true);
+    tiled_tiles(prm, prm.maps, blockIdx.x, gridDim.x, ntiles, true);
 }
 
-// Batched pass: a persistent grid walks the items of all instances (items
-// sorted by decreasing cost, CTA b takes items b, b + grid, ...); an item
-// is a run of consecutive tiles of one instance, (instance, first tile,
-// tile count), streamed through one pipeline.  CTA b starts with item b and
-// then claims item gridDim.x + atomicAdd(ticket, 1) (ticket zero at launch).  Instance i's parameters for
-// parity P and coefficient set `which` are prms[(2 i + P) * 2 + which] in
-// global memory; the CTA copies them to shared memory and hands TMA the
-// tensor maps of the global copy.
+// Batched pass: CTA b runs items[off[b]] .. items[off[b + 1] - 1], each a
+// strided run of tiles of one instance, (instance, first tile, tile count,
+// tile stride), streamed through one pipeline.  Instance i's
+// parameters for parity P and coefficient set `which` are
+// prms[(2 i + P) * 2 + which] in global memory; the CTA copies them to
+// shared memory and hands TMA the tensor maps of the global copy.
 __global__ void __launch_bounds__(THREADS, MINB) k_tiled_batch(const Params* __restrict__ prms,
-                                                            const int4* __restrict__ items, int nitems, int P,
-                                                            int which, int* __restrict__ ticket) {
+                                                            const int4* __restrict__ items,
+                                                            const int* __restrict__ off, int P, int which) {
     __shared__ Params s_prm;
-    __shared__ int s_next;
-    int it = blockIdx.x;
-    bool first = true;
-    while (it < nitems) {
+    const int begin = off[blockIdx.x], end = off[blockIdx.x + 1];
+    for (int it = begin; it < end; ++it) {
         const int4 item = items[it];
         const Params* g = prms + (2 * item.x + P) * 2 + which;
+        if (it != begin) __syncthreads();             // previous run done with s_prm and the barriers
         {
             const uint4* src = reinterpret_cast<const uint4*>(g);
             uint4* dst = reinterpret_cast<uint4*>(&s_prm);
             for (int i = threadIdx.x; i < (int)(sizeof(Params) / 16); i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
-        tiled_tiles(s_prm, g->maps, item.y, 1, item.y + item.z, first);
-        first = false;
-        __syncthreads();                  // run done with s_prm and the barriers
-        // claim the next item (heaviest first): greedy dynamic balancing
-        if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(ticket, 1);
-        __syncthreads();
-        it = s_next;
+        tiled_tiles(s_prm, g->maps, item.y, item.w, item.y + (item.z - 1) * item.w + 1, it == begin);
     }
 }
 
