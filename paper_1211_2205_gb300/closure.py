@@ -224,8 +224,10 @@ def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
 
 def evaluate(params: np.ndarray, seeds: Sequence[int], n: int = 512, orders: Sequence[int] = (7, 9, 11, 13, 15),
              N_ref: int = 39, t_final: float = 0.5, repeats: int = 1,
-             closure_schedules: Sequence[str] = ("merged",)) -> Dict:
-    """Errors of R_0^0 against P_{N_ref} and device times, per held-out medium."""
+             closure_schedules: Sequence[str] = ("merged",), compare: Optional[Sequence[int]] = None) -> Dict:
+    """Errors of R_0^0 against P_{N_ref} and device times, per held-out
+    medium; the error-matched speedup is taken among the orders `compare`
+    (default: all of `orders`) and among all of `orders` ("strict")."""
     cases = []
     for seed in seeds:
         p = inputs.closure_medium(seed, n=n, N=N_ref, t_final=t_final)
@@ -240,19 +242,27 @@ def evaluate(params: np.ndarray, seeds: Sequence[int], n: int = 512, orders: Seq
             r = run_case(p, N_BASE, dt, nsteps, params=params, repeats=repeats, closure_schedule=sched)
             row["closure" if k == 0 else "closure_" + sched] = {"err": rel_l2(r.R00, ref.R00), "ms": r.ms}
         cases.append(row)
-    return summarize(cases, orders)
+    return summarize(cases, orders, compare)
 
 
-def summarize(cases: List[Dict], orders: Sequence[int]) -> Dict:
+def summarize(cases: List[Dict], orders: Sequence[int], compare: Optional[Sequence[int]] = None) -> Dict:
     """Mean error and time per method over the cases, and the error-matched
     speedup of the closure against the lowest plain order at least as
-    accurate on average."""
+    accurate on average: among `compare` (default: all evaluated orders) and,
+    as "strict", among all evaluated orders."""
     plain = {N: {"err": float(np.mean([c["plain"][N]["err"] for c in cases])),
                  "ms": float(np.mean([c["plain"][N]["ms"] for c in cases]))} for N in orders}
     cl = {"err": float(np.mean([c["closure"]["err"] for c in cases])),
           "ms": float(np.mean([c["closure"]["ms"] for c in cases]))}
-    match = next((N for N in sorted(orders) if plain[N]["err"] <= cl["err"]), None)
-    out = {"cases": cases, "plain": plain, "closure": cl, "matched_N": match,
-           "error_matched_speedup": (plain[match]["ms"] / cl["ms"]) if match is not None else None,
+
+    def matched(candidates):
+        N = next((N for N in sorted(candidates) if plain[N]["err"] <= cl["err"]), None)
+        return N, (plain[N]["ms"] / cl["ms"]) if N is not None else None
+
+    cmp = sorted(compare) if compare is not None else sorted(orders)
+    match, speedup = matched(cmp)
+    strict_N, strict = matched(orders)
+    out = {"cases": cases, "plain": plain, "closure": cl, "compare_orders": cmp, "matched_N": match,
+           "error_matched_speedup": speedup, "strict_matched_N": strict_N, "strict_error_matched_speedup": strict,
            "gain_vs_p7": plain[N_BASE]["err"] / cl["err"] if N_BASE in plain and cl["err"] > 0 else None}
     return out

@@ -146,8 +146,8 @@ bool upload(void** dst, const std::vector<V>& v) {
 }
 
 // Walk the consumer loop of pass P and emit its tables.
-bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>& comp_class, int P, double dx,
-                double dy, PassTables& t, std::string& err) {
+bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>& comp_class,
+                const std::vector<char>& frozen, int P, double dx, double dy, PassTables& t, std::string& err) {
     const int N = pl->N, n = sys.ncomp;
     t = PassTables();
     const int gin[2] = {P == 1 ? 0 : 1, P == 1 ? 3 : 2};
@@ -188,8 +188,9 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
     auto emit_fin = [&](int L, int q, int imag) -> bool {
         int local;
         if (!local_of(L, q, imag, gout[imag], local)) return false;
-        if (imag) cur.w = local; else cur.z = local;
         const int j = comp_index(L, L - 2 * q, imag);
+        // a frozen output is not finalised: its old value is not loaded either
+        if (!frozen[j]) { if (imag) cur.w = local; else cur.z = local; }
         t.fin.push_back(make_int2(local, comp_class[j]));
         t.fin_comp.push_back(j);
         return true;
@@ -307,7 +308,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
     const int gout[2][2] = {{0, 3}, {1, 2}};
     for (int P = 0; P < 2; ++P) {
         PassTables& t = pl->tab[P];
-        if (!build_pass(pl, sys, comp_class, P, dx, dy, t, pl->err)) return -8;
+        if (!build_pass(pl, sys, comp_class, frozen, P, dx, dy, t, pl->err)) return -8;
         // per output kind K: coefficient rows (x part of the kind-K input,
         // y part of the other input) and finalise entries (offset, source slot)
         const size_t nsteps = t.coef.size() / 32;

@@ -57,3 +57,24 @@ def test_reference_arm_prints_contract_line():
     assert line["impl"] == "reference"
     assert line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_closure_summary_matches_lowest_accurate_order():
+    """The error-matched speedup takes the lowest plain order at least as
+    accurate as the closure, among the comparison set and among all orders."""
+    sys.path.insert(0, ROOT)
+    from paper_1211_2205_gb300 import closure
+    errs = {7: 0.29, 9: 0.15, 11: 0.072, 13: 0.035, 15: 0.018}
+    ms = {7: 13.7, 9: 17.4, 11: 22.6, 13: 27.9, 15: 33.6}
+    case = {"plain": {N: {"err": errs[N], "ms": ms[N]} for N in errs}, "closure": {"err": 0.055, "ms": 29.8}}
+    out = closure.summarize([case, case], list(errs), compare=(7, 11, 15))
+    assert out["matched_N"] == 15 and out["strict_matched_N"] == 13
+    assert out["error_matched_speedup"] == pytest.approx(33.6 / 29.8)
+    assert out["strict_error_matched_speedup"] == pytest.approx(27.9 / 29.8)
+    assert out["gain_vs_p7"] == pytest.approx(0.29 / 0.055)
+    worse = {"plain": case["plain"], "closure": {"err": 0.5, "ms": 1.0}}
+    out = closure.summarize([worse], list(errs))
+    assert out["matched_N"] == 7 and out["compare_orders"] == sorted(errs)
+    none = {"plain": case["plain"], "closure": {"err": 0.001, "ms": 1.0}}
+    out = closure.summarize([none], list(errs))
+    assert out["matched_N"] is None and out["error_matched_speedup"] is None
