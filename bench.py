@@ -54,7 +54,7 @@ KERNEL_SOURCES = {
     "gather": ["paper_1211_2205_gb300/csrc/kernels_gather.cu"],
     # a tiled pass is the tile kernel plus the boundary refresh (kernels_gather.cu)
     "tiled": ["paper_1211_2205_gb300/csrc/tiled.cu", "paper_1211_2205_gb300/csrc/tiled_kernel.cuh",
-              "paper_1211_2205_gb300/csrc/kernels_gather.cu"],
+              "paper_1211_2205_gb300/csrc/kernels_gather.cu", "paper_1211_2205_gb300/csrc/pdl.h"],
 }
 
 

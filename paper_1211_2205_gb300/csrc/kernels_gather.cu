@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "pdl.h"
 
 namespace starmap {
 
@@ -104,6 +105,8 @@ __global__ void k_fill_ghosts(const GhostArgs<T> A) {
 // and nx - 1), each point re-stored with its copies (store_point).
 template <class T>
 __global__ void k_fill_ghosts_pass(const GhostPassArgs<T> A) {
+    pdl_trigger();
+    pdl_wait();                         // the pass that wrote these components is done
     const int c = blockIdx.y;
     const int which = c < A.g[0].K ? 0 : 1;
     const GridDev<T>& G = A.g[which];
@@ -230,8 +233,8 @@ int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream) {
     if (K <= 0) return 0;
     const int len = 2 * std::max(a.g[0].nx + a.g[0].ny, a.g[1].nx + a.g[1].ny);
     const dim3 grid((len + 255) / 256, K);
-    k_fill_ghosts_pass<T><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-    return status_of(cudaGetLastError());
+    const cudaError_t e = launch_pdl(k_fill_ghosts_pass<T>, grid, dim3(256), 0, (cudaStream_t)stream, a);
+    return status_of(e != cudaSuccess ? e : cudaGetLastError());
 }
 
 int launch_fill_ghosts_jobs(const GhostJob* jobs, int njobs, void* stream) {

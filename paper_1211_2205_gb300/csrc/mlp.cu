@@ -28,6 +28,7 @@
 #include "closure_features.cuh"
 #include "internal.h"
 #include "mlp.h"
+#include "pdl.h"
 
 namespace starmap {
 namespace mlp {
@@ -712,6 +713,8 @@ __global__ void __launch_bounds__(ITHREADS, 1) k_closure_mlp(const ClosureArgs<T
 // Rows of G22 by blockIdx.y, points along x by threads.
 template <class T>
 __global__ void k_closure_nodes(const ClosureArgs<T> A, const float* __restrict__ ctr) {
+    pdl_trigger();
+    pdl_wait();                         // the centre values are written
     const GridDev<T>& G = A.g[3];
     const int nx = A.nx, ny = A.ny;
     const long M = (long)nx * ny;
@@ -843,7 +846,9 @@ int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine
     }
     if (A.g[3].nx > 0 && A.g[3].ny > 0) {
         const dim3 grid((A.g[3].nx + 255) / 256, A.g[3].ny < 65535 ? A.g[3].ny : 65535);
-        k_closure_nodes<T><<<grid, 256, 0, (cudaStream_t)stream>>>(A, ctr);
+        if (launch_pdl(k_closure_nodes<T>, grid, dim3(256), 0, (cudaStream_t)stream, A, (const float*)ctr) !=
+            cudaSuccess)
+            return -4;
     }
     return status(cudaGetLastError());
 }

@@ -25,6 +25,7 @@
 #include "closure_features.cuh"
 #include "internal.h"
 #include "mlp.h"
+#include "pdl.h"
 
 namespace starmap {
 namespace mlp {
@@ -313,6 +314,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_closure_tc(const ClosureArgs<
     __shared__ const T* colp[NMOM];
     column_table(A, colp, NMOM);
     tc_setup(S, P);                         // ends with a CTA barrier: colp is visible
+    // weights, TMEM and the column table come from host-written data; the
+    // state is read below, after the previous kernel of the stream is done
+    pdl_trigger();
+    pdl_wait();
     const GroupCtx c = group_ctx(S);
     const int nx = A.nx, ny = A.ny;
     const int M = nx * ny;
@@ -440,8 +445,9 @@ int closure_tc(const ClosureArgs<T>& A, const Packed* P, float* ctr, int* err, v
     if (M <= 0) return 0;
     long blocks = (M + TM * GROUPS - 1) / (TM * GROUPS);
     if (blocks > sms_tc()) blocks = sms_tc();
-    k_closure_tc<T><<<(unsigned)blocks, TC_THREADS, sizeof(TcSmem), (cudaStream_t)stream>>>(A, P, ctr, err);
-    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+    const cudaError_t e = launch_pdl(k_closure_tc<T>, dim3((unsigned)blocks), dim3(TC_THREADS), sizeof(TcSmem),
+                                     (cudaStream_t)stream, A, P, ctr, err);
+    return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
 template int closure_tc<float>(const ClosureArgs<float>&, const Packed*, float*, int*, void*);

@@ -439,14 +439,19 @@ int tiled_pass(TiledPlan* pl, bool odd, int which, void* stream) {
         pl->err = "too many pipeline stages per CTA for the tiled kernel";
         return -8;
     }
+    // programmatic dependent launch: the CTAs stage their tables while the
+    // previous kernel of the stream finishes
+    cudaError_t e;
     if (pl->variant) {
         tiled5::Params q;
         std::memcpy(&q, &pl->prm[P][which], sizeof(q));
-        tiled5::k_tiled_pass<<<grid, tiled5::THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(q, ntiles);
+        e = launch_pdl(tiled5::k_tiled_pass, dim3(grid), dim3(tiled5::THREADS), (size_t)pl->smem_bytes[P],
+                       (cudaStream_t)stream, q, ntiles);
     } else {
-        tiled::k_tiled_pass<<<grid, tiled::THREADS, pl->smem_bytes[P], (cudaStream_t)stream>>>(pl->prm[P][which], ntiles);
+        e = launch_pdl(tiled::k_tiled_pass, dim3(grid), dim3(tiled::THREADS), (size_t)pl->smem_bytes[P],
+                       (cudaStream_t)stream, pl->prm[P][which], ntiles);
     }
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         pl->err = std::string("tiled pass launch: ") + cudaGetErrorString(e);
         return -4;

@@ -49,6 +49,8 @@
 
 #include <cstdint>
 
+#include "pdl.h"
+
 #ifndef STARMAP_TILED_NS
 #define STARMAP_TILED_NS tiled
 #define STARMAP_TILED_TY 10
@@ -294,6 +296,12 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
         for (int i = tid; i < prm.nstages; i += THREADS) st[i] = __ldg(prm.stages + i);
     }
     __syncthreads();
+    if (first_call) {
+        // everything above reads host-written data only; the state is read
+        // and written below, after the previous kernel of the stream is done
+        pdl_trigger();
+        pdl_wait();
+    }
 
     int sxR, syR, sxI, syI;
     input_shift(prm.P, 0, prm.p[0], prm.p[1], sxR, syR);
