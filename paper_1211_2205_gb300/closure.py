@@ -112,6 +112,7 @@ def generate(seeds: Sequence[int], n: int = 512, N_ref: int = 39, snapshots: int
             s.step(mk - done)
             done = mk
             s.closure_samples(X[off:off + M], scale, T[off:off + M])
+            s.sync()                     # the samples are written on the stepper's stream
             sc = scale.cpu().numpy()
             keep.append(off + np.nonzero(sc >= rel_floor * sc.max())[0].astype(np.int64))
             off += M

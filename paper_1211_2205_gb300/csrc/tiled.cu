@@ -83,6 +83,7 @@ struct PassTables {
     std::vector<int2> fin;                // (local, class)
     std::vector<int> fin_comp;            // global component per finalise event
     int nin = 0;
+    int top = 0;                          // highest output order finalised
 };
 
 // Orders up to this use the 5-row tiles by default (few stages per tile:
@@ -150,6 +151,11 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
                 const std::vector<char>& frozen, int P, double dx, double dy, PassTables& t, std::string& err) {
     const int N = pl->N, n = sys.ncomp;
     t = PassTables();
+    // a frozen top order has no finalising stages at all (no data, no work)
+    bool top_frozen = true;
+    for (int j = 0; j < n; ++j)
+        if (sys.moms[j].l == N && !frozen[j]) top_frozen = false;
+    t.top = top_frozen ? N - 1 : N;
     const int gin[2] = {P == 1 ? 0 : 1, P == 1 ? 3 : 2};
     const int gout[2] = {P == 1 ? 1 : 0, P == 1 ? 2 : 3};
     auto local_of = [&](int L, int q, int imag, int grid_expected, int& local) -> bool {
@@ -232,7 +238,7 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
         }
     }
     const int L = last_in + 1;
-    if (ok && L <= N)
+    if (ok && L <= t.top)
         for (int q = 0; q < nq_of(L) && ok; ++q) {
             ok = ok && emit_fin_pair(L, q);
             close_stage();
@@ -240,7 +246,7 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
     if (!ok) { err = "moment placement differs from the tiled kernel's"; return false; }
     // every component of the output parity is finalised exactly once
     long nout = 0;
-    for (int j = 0; j < n; ++j) nout += (sys.moms[j].l % 2 == P);
+    for (int j = 0; j < n; ++j) nout += (sys.moms[j].l % 2 == P && sys.moms[j].l <= t.top);
     long nreal = 0;
     for (int c : t.fin_comp) nreal += c >= 0;
     if (nreal != nout) { err = "tiled schedule does not cover every output"; return false; }
@@ -396,6 +402,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             prm.nstages = (int)t.stages.size();
             prm.nin = (int)nsteps;
             prm.nfin = (int)fk[0].size();
+            prm.top = t.top;
             prm.stages = (const int4*)pl->dev_stages[P];
             for (int K = 0; K < 2; ++K) {
                 prm.coef[K] = (const float4*)pl->dev_coef[P][K];

@@ -106,6 +106,8 @@ struct Params {
     int which;                  // 0 half-step coefficients, 1 full-step
     int nclasses;               // 2 = isotropic (class 0: l = 0, 1: l >= 1), else class = l
     int nstages, nin, nfin;
+    int top;                    // highest output order finalised: N, or N - 1 when every order-N
+                                // component is frozen (a closure sets them)
     const int4* stages;         // per stage: component (in its grid) of slot 0..3, -1 if absent
     const float4* coef[2];      // per output kind K, per q step: (cx Pm, cx P0, cx N0, cx Np) of the
                                 // input of kind K and (cy Pm, cy P0, cy N0, cy Np) of the other
@@ -569,7 +571,7 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
         }
         // outputs of the order above the last input order have no further inputs
         const int L = last_in + 1;
-        if (L <= N) {
+        if (L <= prm.top) {
             set_order(L);
             for (int q = 0; q < nq_of(L) && alive; ++q) {
                 f2 W[PP];
