@@ -371,8 +371,11 @@ int starmap_mlp_train_step(starmap_mlp_t* net, const float* X, const float* T, c
  * closure), each a full handle with its own state, material and sources.
  * starmap_batch_step advances every instance by nsteps of its own dt with
  * one CUDA graph launch: per pass, one persistent kernel walks the tiles of
- * all instances (heaviest first) with each instance's own tables; the
- * pass sequence of a step count is captured once and replayed.  The
+ * all instances with each instance's own tables (work units of all
+ * instances dealt round robin to the CTAs: strips of consecutive tiles in y
+ * for short tiles, single tiles for long ones), then one kernel refreshes
+ * the boundary copies of every instance; the pass sequence of a step count
+ * is captured once and replayed.  The
  * schedule is cfgs[0].schedule for all; cfgs[0].cuda_stream (if not NULL)
  * must be a non-default stream (graphs are captured on it).  Tile shape:
  * cfgs[0].kernel = STARMAP_KERNEL_TILED_TALL or _TILED_SHORT forces 64 x 10

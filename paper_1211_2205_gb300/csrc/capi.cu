@@ -292,7 +292,8 @@ int run_pass(starmap_t* h, bool odd, int which) {
         ga.pitch = h->pitch;
         ga.p[0] = h->p[0];
         ga.p[1] = h->p[1];
-        if (launch_fill_ghosts_pass<T>(ga, h->stream)) return cuda_fail(h, cudaGetLastError(), "ghost refresh");
+        if (launch_fill_ghosts_pass<T>(ga, h->stream, tiled_overlap(h->tiled, odd)))
+            return cuda_fail(h, cudaGetLastError(), "ghost refresh");
         return STARMAP_OK;
     }
     const int gl[2] = {odd ? 1 : 0, odd ? 2 : 3};

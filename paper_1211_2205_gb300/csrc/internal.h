@@ -93,7 +93,8 @@ struct ReduceArgs {
 // launchers (kernels_gather.cu)
 template <class T> int launch_gather_pass(const GatherArgs<T>& a, void* stream);
 template <class T> int launch_fill_ghosts(const GhostArgs<T>& a, void* stream);
-template <class T> int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream);
+// overlap: programmatic dependent launch (after a short tiled pass)
+template <class T> int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream, bool overlap);
 int launch_fill_ghosts_jobs(const GhostJob* jobs, int njobs, void* stream);
 template <class T> int launch_reduce(const ReduceArgs<T>& a, double* partials, int nblocks,
                                      double* result, void* stream);

@@ -228,12 +228,12 @@ int launch_fill_ghosts(const GhostArgs<T>& a, void* stream) {
 }
 
 template <class T>
-int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream) {
+int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream, bool overlap) {
     const int K = a.g[0].K + a.g[1].K;
     if (K <= 0) return 0;
     const int len = 2 * std::max(a.g[0].nx + a.g[0].ny, a.g[1].nx + a.g[1].ny);
     const dim3 grid((len + 255) / 256, K);
-    const cudaError_t e = launch_pdl(k_fill_ghosts_pass<T>, grid, dim3(256), 0, (cudaStream_t)stream, a);
+    const cudaError_t e = launch_pdl(k_fill_ghosts_pass<T>, grid, dim3(256), 0, (cudaStream_t)stream, overlap, a);
     return status_of(e != cudaSuccess ? e : cudaGetLastError());
 }
 
@@ -265,8 +265,8 @@ template int launch_gather_pass<float>(const GatherArgs<float>&, void*);
 template int launch_gather_pass<double>(const GatherArgs<double>&, void*);
 template int launch_fill_ghosts<float>(const GhostArgs<float>&, void*);
 template int launch_fill_ghosts<double>(const GhostArgs<double>&, void*);
-template int launch_fill_ghosts_pass<float>(const GhostPassArgs<float>&, void*);
-template int launch_fill_ghosts_pass<double>(const GhostPassArgs<double>&, void*);
+template int launch_fill_ghosts_pass<float>(const GhostPassArgs<float>&, void*, bool);
+template int launch_fill_ghosts_pass<double>(const GhostPassArgs<double>&, void*, bool);
 template int launch_reduce<float>(const ReduceArgs<float>&, double*, int, double*, void*);
 template int launch_reduce<double>(const ReduceArgs<double>&, double*, int, double*, void*);
 template int launch_axpby<float>(float*, const float*, const float*, double, double, size_t, void*);

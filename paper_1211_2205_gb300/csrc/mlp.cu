@@ -846,7 +846,7 @@ int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine
     }
     if (A.g[3].nx > 0 && A.g[3].ny > 0) {
         const dim3 grid((A.g[3].nx + 255) / 256, A.g[3].ny < 65535 ? A.g[3].ny : 65535);
-        if (launch_pdl(k_closure_nodes<T>, grid, dim3(256), 0, (cudaStream_t)stream, A, (const float*)ctr) !=
+        if (launch_pdl(k_closure_nodes<T>, grid, dim3(256), 0, (cudaStream_t)stream, true, A, (const float*)ctr) !=
             cudaSuccess)
             return -4;
     }

@@ -446,7 +446,7 @@ int closure_tc(const ClosureArgs<T>& A, const Packed* P, float* ctr, int* err, v
     long blocks = (M + TM * GROUPS - 1) / (TM * GROUPS);
     if (blocks > sms_tc()) blocks = sms_tc();
     const cudaError_t e = launch_pdl(k_closure_tc<T>, dim3((unsigned)blocks), dim3(TC_THREADS), sizeof(TcSmem),
-                                     (cudaStream_t)stream, A, P, ctr, err);
+                                     (cudaStream_t)stream, true, A, P, ctr, err);
     return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 

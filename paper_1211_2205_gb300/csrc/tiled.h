@@ -30,6 +30,10 @@ int tiled_update(TiledPlan* plan, const SystemMatrices& sys, const std::vector<i
                  const std::vector<char>& frozen, double dx, double dy);
 void tiled_set_coef(TiledPlan* plan, int g, void* coef, int nclasses);
 int tiled_pass(TiledPlan* plan, bool odd, int which, void* stream);
+// Whether the pass is launched with programmatic dependent launch (so its
+// boundary refresh should be too): only for short passes, where the kernel
+// boundary is a visible share of the pass.
+bool tiled_overlap(TiledPlan* plan, bool odd);
 // Read and clear the bounded-wait failure flag (synchronises the stream).
 int tiled_poll(TiledPlan* plan, void* stream);
 const char* tiled_error(TiledPlan* plan);
