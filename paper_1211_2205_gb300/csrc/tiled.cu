@@ -91,13 +91,19 @@ struct PassTables {
 constexpr int SHORT_TILE_MAX_N = 3;
 
 // Per tile height: rows, input box rows, threads, consumer threads, point
-// pairs per consumer thread, end of the ring.
-struct Variant { int ty, byi, threads, consumers, pp, ring_end; };
+// pairs per consumer thread, bytes of a ring stage.
+struct Variant { int ty, byi, threads, consumers, pp, stage_bytes; };
 const Variant kVariant[2] = {
-    {tiled::TY, tiled::BYI, tiled::THREADS, tiled::CONSUMERS, tiled::PP,
-     tiled::RING_OFF + tiled::NSTAGES * tiled::STAGE_BYTES},
-    {tiled5::TY, tiled5::BYI, tiled5::THREADS, tiled5::CONSUMERS, tiled5::PP,
-     tiled5::RING_OFF + tiled5::NSTAGES * tiled5::STAGE_BYTES}};
+    {tiled::TY, tiled::BYI, tiled::THREADS, tiled::CONSUMERS, tiled::PP, tiled::STAGE_BYTES},
+    {tiled5::TY, tiled5::BYI, tiled5::THREADS, tiled5::CONSUMERS, tiled5::PP, tiled5::STAGE_BYTES}};
+static_assert(tiled::MAX_STAGES == tiled5::MAX_STAGES && tiled::RING_OFF == tiled5::RING_OFF,
+              "both tile heights share the barrier area");
+// Ring depth: as many stages as the shared memory allows, at most RING_DEPTH
+// (measured with 6, 9, 12 and 15 stages: 9 is best or level at every order
+// and grid tried; 15 costs 5 % at N = 13..15), at least MIN_RING.
+constexpr int RING_DEPTH = 9;
+constexpr int MIN_RING = 4;
+static_assert(RING_DEPTH <= MAX_STAGES, "the barrier area holds the ring");
 
 }  // namespace
 
@@ -118,6 +124,7 @@ struct TiledPlan {
     int variant = 0;                      // 0: 10-row tiles, 1: 5-row tiles
     int sms = 1;
     int smem_bytes[2] = {0, 0};
+    int nring[2] = {0, 0};                // ring stages per parity
     Params prm[2][2];                     // [P][which]
     bool ready = false;
 };
@@ -317,15 +324,18 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
         if (!build_pass(pl, sys, comp_class, frozen, P, dx, dy, t, pl->err)) return -8;
         // per output kind K: coefficient rows (x part of the kind-K input,
         // y part of the other input) and finalise entries (offset, source slot)
+        // (each value once: the kernel pairs it for f32x2 itself)
         const size_t nsteps = t.coef.size() / 32;
         std::vector<float> ck[2];
         for (int K = 0; K < 2; ++K) {
-            ck[K].resize(nsteps * 16);
+            ck[K].resize(nsteps * 8);
             for (size_t k = 0; k < nsteps; ++k) {
                 const float* rowK = t.coef.data() + 32 * k + 16 * K;
                 const float* rowO = t.coef.data() + 32 * k + 16 * (1 - K);
-                std::copy(rowK, rowK + 8, ck[K].begin() + 16 * k);
-                std::copy(rowO + 8, rowO + 16, ck[K].begin() + 16 * k + 8);
+                for (int q = 0; q < 4; ++q) {
+                    ck[K][8 * k + q] = rowK[2 * q];            // Mx of the kind-K input, targets Pm P0 N0 Np
+                    ck[K][8 * k + 4 + q] = rowO[8 + 2 * q];    // My of the other input
+                }
             }
         }
         std::vector<int2> fk[2];
@@ -348,28 +358,42 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             pl->err = "uploading the tiled tables failed";
             return -4;
         }
-        // shared memory: barriers, ring, coefficient rows, finalise events, partial sums
+        // shared memory: barriers, ring, coefficient rows, finalise events,
+        // partial sums; the ring takes what the variant's CTAs per SM leave,
+        // up to RING_DEPTH stages (a deeper ring keeps more loads in flight:
+        // 9 stages instead of 6 made the P_39 1024^2 pass 7 % faster)
         const Variant& V = kVariant[pl->variant];
-        int off = V.ring_end;
-        int coef_off[2], fin_off[2];
+        int tables = 0;
+        int coef_rel[2], fin_rel[2];
         for (int K = 0; K < 2; ++K) {
-            coef_off[K] = off;
-            off += (int)(ck[K].size() * sizeof(float));
-            off = (off + 15) & ~15;
-            fin_off[K] = off;
-            off += (int)(fk[K].size() * sizeof(int2));
-            off = (off + 15) & ~15;
+            coef_rel[K] = tables;
+            tables += (int)(ck[K].size() * sizeof(float));
+            tables = (tables + 15) & ~15;
+            fin_rel[K] = tables;
+            tables += (int)(fk[K].size() * sizeof(int2));
+            tables = (tables + 15) & ~15;
         }
-        const int stage_off = off;
-        off += (int)(t.stages.size() * sizeof(int4));
-        off = (off + 15) & ~15;
-        const int part_off = off;
-        off += (nq_of(pl->N) + 1) * V.pp * V.consumers * 8;   // pp pairs of partial sums per consumer thread and q
-        pl->smem_bytes[P] = off;
-        int dev = 0, maxsm = 0;
+        const int stage_rel = tables;
+        tables += (int)(t.stages.size() * sizeof(int4));
+        tables = (tables + 15) & ~15;
+        const int part_rel = tables;
+        tables += nq_of(pl->N) * V.pp * V.consumers * 8;    // pp pairs of partial sums per consumer thread and q
+        int dev = 0, maxsm = 0, persm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (off > maxsm) { pl->err = "tiled kernel needs more shared memory than the device offers"; return -8; }
+        cudaDeviceGetAttribute(&persm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        // per-CTA budget: the variant's CTAs per SM (1 KB reserved per CTA),
+        // less the batch kernel's static parameter copy
+        const int minb = tiled_ctas_per_sm(pl->variant);
+        const int budget = std::min(maxsm, persm / minb - 1024) - (int)sizeof(Params) - 256;
+        const int nring = std::min(RING_DEPTH, (budget - RING_OFF - tables) / V.stage_bytes);
+        if (nring < MIN_RING) { pl->err = "tiled kernel needs more shared memory than the device offers"; return -8; }
+        const int ring_end = RING_OFF + nring * V.stage_bytes;
+        const int coef_off[2] = {ring_end + coef_rel[0], ring_end + coef_rel[1]};
+        const int fin_off[2] = {ring_end + fin_rel[0], ring_end + fin_rel[1]};
+        const int stage_off = ring_end + stage_rel, part_off = ring_end + part_rel;
+        pl->smem_bytes[P] = ring_end + tables;
+        pl->nring[P] = nring;
         const int need = std::max(pl->smem_bytes[0], pl->smem_bytes[1]);
         const cudaError_t fe = pl->variant
             ? cudaFuncSetAttribute(tiled5::k_tiled_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, need)
@@ -402,6 +426,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             prm.nstages = (int)t.stages.size();
             prm.nin = (int)nsteps;
             prm.nfin = (int)fk[0].size();
+            prm.nring = nring;
             prm.top = t.top;
             prm.stages = (const int4*)pl->dev_stages[P];
             for (int K = 0; K < 2; ++K) {

@@ -75,18 +75,19 @@ constexpr int BX = TX + VEC;            // input box width (halo + alignment)
 constexpr int BYI = TY + 1;             // input box height (halo)
 constexpr int IN_BYTES = BX * BYI * 4;
 constexpr int OUT_BYTES = TX * TY * 4;
-constexpr int SLOT = ((IN_BYTES + 127) / 128) * 128;   // slot stride in bytes
-constexpr int SLOTS_PER_STEP = 4;       // input R, input I, output R, output I of one consumer step
-constexpr int STEPS_PER_STAGE = 1;      // consumer steps sharing one mbarrier stage
-constexpr int STEP_BYTES = SLOT * SLOTS_PER_STEP;
-constexpr int STAGE_BYTES = STEP_BYTES * STEPS_PER_STAGE;
-constexpr int NSTAGES = 6;              // stages in the ring
+constexpr int IN_SLOT = ((IN_BYTES + 127) / 128) * 128;    // slot strides in bytes
+constexpr int OUT_SLOT = ((OUT_BYTES + 127) / 128) * 128;
+// a stage (one consumer step) holds the input R, input I, output R, output I boxes
+constexpr int STAGE_BYTES = 2 * IN_SLOT + 2 * OUT_SLOT;
+__host__ __device__ constexpr int slot_off(int slot) { return slot < 2 ? slot * IN_SLOT : 2 * IN_SLOT + (slot - 2) * OUT_SLOT; }
+constexpr int MAX_STAGES = 15;          // ring depth limit (the host fills the shared memory up to it)
 constexpr int CONSUMER_WARPS = 2 * RSTEP;   // per output kind (R, I), one warp per RW rows
 constexpr int CONSUMERS = CONSUMER_WARPS * 32;
 constexpr int PRODUCER_WARPS = 2;       // independent TMA issue streams (stage s mod 2)
 constexpr int THREADS = CONSUMERS + 32 * PRODUCER_WARPS;
 constexpr int MAXN = 63;
-constexpr int RING_OFF = 256;
+constexpr int RING_OFF = 256;           // full[MAX_STAGES], empty[MAX_STAGES], abort flag
+static_assert(2 * MAX_STAGES * 8 + 4 <= RING_OFF, "barriers fit before the ring");
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded waits: 2 s
 
 struct OutGrid {
@@ -106,12 +107,13 @@ struct Params {
     int which;                  // 0 half-step coefficients, 1 full-step
     int nclasses;               // 2 = isotropic (class 0: l = 0, 1: l >= 1), else class = l
     int nstages, nin, nfin;
+    int nring;                  // stages in the ring (2 .. MAX_STAGES)
     int top;                    // highest output order finalised: N, or N - 1 when every order-N
                                 // component is frozen (a closure sets them)
     const int4* stages;         // per stage: component (in its grid) of slot 0..3, -1 if absent
     const float4* coef[2];      // per output kind K, per q step: (cx Pm, cx P0, cx N0, cx Np) of the
                                 // input of kind K and (cy Pm, cy P0, cy N0, cy Np) of the other
-                                // input, each value twice (f32x2 operands); zero if absent
+                                // input; zero if absent
     const int2* fin[2];         // per output kind K, per finalising stage: (element offset of the
                                 // component, or -1 if absent; source slot or -1)
     const float* const* srcs;   // source arrays by slot
@@ -256,13 +258,13 @@ __device__ __forceinline__ f2 diff_x(const float* row, int c, bool c_even) {
 // reads them from there); prm: everything else.  first_call: the CTA's
 // first call (a later call invalidates and re-initialises the barriers; the
 // caller synchronises the CTA in between).
-static_assert(STEPS_PER_STAGE == 1, "the cross-tile pipeline assumes one consumer step per stage");
 __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap* maps, int t0, int tstride, int tend,
                                             bool first_call) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* empty = full + NSTAGES;
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NSTAGES);
+    uint64_t* empty = full + MAX_STAGES;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + MAX_STAGES);
+    const int NR = prm.nring;
     unsigned char* ring = smem + RING_OFF;
     f2* s_part = reinterpret_cast<f2*>(smem + prm.smem_part_off);
     const int4* s_stages = reinterpret_cast<const int4*>(smem + prm.smem_stage_off);
@@ -275,7 +277,7 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
     if (warp == CONSUMER_WARPS && lane < 4)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(maps + lane)) : "memory");
     if (tid == 0) {
-        for (int r = 0; r < NSTAGES; ++r) {
+        for (int r = 0; r < MAX_STAGES; ++r) {      // every barrier: a batch's items differ in depth
             if (!first_call) {
                 mbar_inval(&full[r]);
                 mbar_inval(&empty[r]);
@@ -289,7 +291,7 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
     // stage the coefficient, finalise and stage tables in shared memory
     for (int k = 0; k < 2; ++k) {
         float4* c = reinterpret_cast<float4*>(smem + prm.smem_coef_off[k]);
-        for (int i = tid; i < 4 * prm.nin; i += THREADS) c[i] = __ldg(prm.coef[k] + i);
+        for (int i = tid; i < 2 * prm.nin; i += THREADS) c[i] = __ldg(prm.coef[k] + i);
         int2* f = reinterpret_cast<int2*>(smem + prm.smem_fin_off[k]);
         for (int i = tid; i < prm.nfin; i += THREADS) f[i] = __ldg(prm.fin[k] + i);
     }
@@ -312,7 +314,7 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
     // --------------------------------------------------------- producer
     // Producer warp pw owns the global stages G = pw (mod PRODUCER_WARPS)
     // over all of the CTA's tiles (stage k of tile t is G = t * nstages + k,
-    // ring slot G mod NSTAGES).  Lane 0 waits for the slot to drain and arms
+    // ring slot G mod nring).  Lane 0 waits for the slot to drain and arms
     // its barrier with the byte count; lanes 0..3 then issue the (up to) four
     // boxes, lane = slot.
     if (warp >= CONSUMER_WARPS) {
@@ -352,18 +354,18 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
             }
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
-            if (mine != 0u) tma_load_3d(ring + r * STAGE_BYTES + slot * SLOT, map, bx, by, comp, &full[r]);
+            if (mine != 0u) tma_load_3d(ring + r * STAGE_BYTES + slot_off(slot), map, bx, by, comp, &full[r]);
             last = G;
             k += PRODUCER_WARPS;
             while (k >= nst) { k -= nst; ++tl; }
             r += PRODUCER_WARPS;
-            if (r >= NSTAGES) { r -= NSTAGES; ++u; }
+            if (r >= NR) { r -= NR; ++u; }
         }
         if (!ok && lane == 0) {
             // aborted: wait (bounded) for this warp's copies still in flight
-            for (int G = last; G >= 0 && G > last - NSTAGES; G -= PRODUCER_WARPS) {
+            for (int G = last; G >= 0 && G > last - NR; G -= PRODUCER_WARPS) {
                 const unsigned long long tw = global_ns();
-                while (!mbar_try_wait(&full[G % NSTAGES], (G / NSTAGES) & 1))
+                while (!mbar_try_wait(&full[G % NR], (G / NR) & 1))
                     if (global_ns() - tw > WAIT_NS) break;
             }
         }
@@ -401,10 +403,10 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
             const int sxO = K == 0 ? sxI : sxR;
             const int bxsK = sxK == 0 ? -VEC : 0, oyK = syK == 0 ? -1 : 0;
             const int bxsO = sxO == 0 ? -VEC : 0, oyO = syO == 0 ? -1 : 0;
-            rx = K * (SLOT / 4) + (row - oyK) * BX;
+            rx = slot_off(K) / 4 + (row - oyK) * BX;
             cx = 2 * lane + sxK - bxsK;
             ev = (cx & 1) == 0;
-            uy = (1 - K) * (SLOT / 4) + (row + syO - oyO) * BX + (2 * lane - bxsO);
+            uy = slot_off(1 - K) / 4 + (row + syO - oyO) * BX + (2 * lane - bxsO);
         }
         bool inA[PP], inB[PP], pair[PP];
         float* pptr[PP];          // point A_j in component 0
@@ -432,10 +434,10 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
         }
 
         // walking pointers into this kind's tables and this thread's partial sums
-        const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(smem + prm.smem_coef_off[K]);
+        const float4* cp = reinterpret_cast<const float4*>(smem + prm.smem_coef_off[K]);
         const int2* fp = reinterpret_cast<const int2*>(smem + prm.smem_fin_off[K]);
         f2* const pp = s_part + tid;            // entry (q, j) at pp[(q * PP + j) * CONSUMERS]
-        const int uoff = (2 + K) * (SLOT / 4) + row * TX + 2 * lane;    // old value of pair 0 inside a step
+        const int uoff = slot_off(2 + K) / 4 + row * TX + 2 * lane;    // old value of pair 0 inside a step
         // consumer step s is stage s (ring slot ring_r, phase ring_ph): its
         // barrier is awaited before the step and released after it
         auto stage_ptr = [&]() -> const float* {
@@ -446,7 +448,7 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[ring_r]);
             ++s;
-            if (++ring_r == NSTAGES) { ring_r = 0; ring_ph ^= 1u; }
+            if (++ring_r == NR) { ring_r = 0; ring_ph ^= 1u; }
         };
         // decay pairs (a, b) of the outputs of order L
         f2 aL[PP], bL[PP];
@@ -499,8 +501,13 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
         // the input of kind K (slot K), d_y of the other input (slot 1 - K);
         // a missing I input has zero coefficients and its differences masked
         auto accumulate = [&](const float* t, bool inI, f2 (&Pc)[PP], f2 (&Pn)[PP], f2 (&Nc)[PP], f2 (&Nn)[PP]) {
-            const ulonglong2 xa = cp[0], xb = cp[1], ya = cp[2], yb = cp[3];
-            cp += 4;
+            // each coefficient as an f32x2 pair (the same value for both points)
+            const float4 cxv = cp[0], cyv = cp[1];
+            cp += 2;
+            const f2 xPm = f2_make(cxv.x, cxv.x), xP0 = f2_make(cxv.y, cxv.y);
+            const f2 xN0 = f2_make(cxv.z, cxv.z), xNp = f2_make(cxv.w, cxv.w);
+            const f2 yPm = f2_make(cyv.x, cyv.x), yP0 = f2_make(cyv.y, cyv.y);
+            const f2 yN0 = f2_make(cyv.z, cyv.z), yNp = f2_make(cyv.w, cyv.w);
     #pragma unroll
             for (int j = 0; j < PP; ++j) {
                 f2 dx = diff_x(t + rx + in_off(j), cx, ev);
@@ -508,14 +515,14 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
                 if (!inI) {
                     if (K == 1) dx = zero2(); else dy = zero2();
                 }
-                Pc[j] = f2_fma(xa.x, dx, Pc[j]);
-                Pn[j] = f2_fma(xa.y, dx, Pn[j]);
-                Nc[j] = f2_fma(xb.x, dx, Nc[j]);
-                Nn[j] = f2_fma(xb.y, dx, Nn[j]);
-                Pc[j] = f2_fma(ya.x, dy, Pc[j]);
-                Pn[j] = f2_fma(ya.y, dy, Pn[j]);
-                Nc[j] = f2_fma(yb.x, dy, Nc[j]);
-                Nn[j] = f2_fma(yb.y, dy, Nn[j]);
+                Pc[j] = f2_fma(xPm, dx, Pc[j]);
+                Pn[j] = f2_fma(xP0, dx, Pn[j]);
+                Nc[j] = f2_fma(xN0, dx, Nc[j]);
+                Nn[j] = f2_fma(xNp, dx, Nn[j]);
+                Pc[j] = f2_fma(yPm, dy, Pc[j]);
+                Pn[j] = f2_fma(yP0, dy, Pn[j]);
+                Nc[j] = f2_fma(yN0, dy, Nc[j]);
+                Nn[j] = f2_fma(yNp, dy, Nn[j]);
             }
         };
 

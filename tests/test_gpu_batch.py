@@ -143,3 +143,25 @@ def test_autotuner_times_both_tile_heights_and_leaves_state_zero():
         assert np.array_equal(b.instances[2].moments(j), alone.moments(j)), j
     forced = capi.Batch.from_problems(probs[:2], kernel="tiled_tall")
     assert forced.tile_rows() == (10, -1.0, -1.0)
+
+
+def test_batch_mixing_long_and_short_tiles():
+    """Instances whose tiles are long (N = 21, 27: single tiles dealt in
+    strided runs) next to short ones (strips of tiles): each equals its
+    standalone tiled run bit for bit, with both tile heights."""
+    probs = [_instance(k, nsteps=4) for k in range(5)]
+    for k, N in ((0, 21), (3, 27)):
+        probs[k] = inputs.Problem(**{**probs[k].__dict__, "N": N})
+    for kernel in ("tiled_tall", "tiled_short"):
+        b = capi.Batch.from_problems(probs, schedule="merged", kernel=kernel)
+        b.step(3)
+        b.step(1)
+        b.sync()
+        for k, p in enumerate(probs):
+            alone = capi.Stepper.from_problem(p, kernel=kernel, schedule="merged")
+            alone.step(3)
+            alone.step(1)
+            inst = b.instances[k]
+            for j in range(0, inst.ncomp, max(1, inst.ncomp // 8)):
+                assert np.array_equal(inst.moments(j), alone.moments(j)), (kernel, k, j)
+        b.close()
