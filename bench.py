@@ -384,7 +384,11 @@ def run_native(args):
                      "frac": achieved / peak, "traffic": traffic, "kernel": f"{s.kernel}:{dom}",
                      "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": pass_times[dom],
                      "pass_ms": pass_times, "timed": "update kernel + boundary refresh",
-                     "peak_kind": f"{pk_kind} hbm_gbs"},
+                     "peak_kind": f"{pk_kind} hbm_gbs",
+                     # measured DRAM bytes of the pass over its time, and the schedule floor
+                     # (every value read and written once per step) over the step time
+                     "dram_frac": (traffic / (pass_times[dom] / 1e3) / 1e9 / peak) if traffic else None,
+                     "floor_frac": 2.0 * updates_per_step * esize / (ms_max / args.steps / 1e3) / 1e9 / peak},
         "e2e": {"value": e2e_value, "unit": "updates/s",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": r00_bytes / args.steps},
         "gpu_launches": launches,
