@@ -115,3 +115,39 @@ def test_full_size_random_p39_sampled(nsteps):
         sub_u = o.U[j].T                       # (ny, nx) on the window grid
         ref.append(sub_u[halo: halo + w, halo: halo + w])
     assert rel_l2(got, ref) <= FP32_TOL
+
+
+def test_full_size_random_p39_sampled_across_periodic_edge():
+    """The bench configuration again, with the sampled window straddling the
+    periodic x boundary at mid height (the boundary copies refreshed after
+    every pass at full size): the window sub-problem continues past x = 1
+    with its fields evaluated at the wrapped points; the pulse's tail there
+    (~1e-22) is well inside FP32's normal range."""
+    p = inputs.random_p39()
+    nsteps = 4
+    s = capi.Stepper.from_problem(p, kernel="tiled", schedule="merged")
+    s.step(nsteps)
+    halo = int(math.ceil(1.5 * nsteps)) + 3
+    w = 16
+    i0, j0 = p.n[0] - w // 2 - halo, p.n[1] // 2 - halo
+    x0, x1, y0, y1 = p.ax
+
+    def wrapped(f):
+        # f at the point of the periodic domain that (x, y) stands for
+        return lambda t, x, y: f(t, x0 + np.mod(x - x0, x1 - x0), y0 + np.mod(y - y0, y1 - y0))
+
+    sub = _window_problem(p, i0, j0, w + 2 * halo, s.dt)
+    sub = inputs.Problem(**{**sub.__dict__, "sigma_a": wrapped(p.sigma_a), "sigma_s0": wrapped(p.sigma_s0),
+                            "ic": [(k, wrapped(f)) for k, f in p.ic]})
+    o = O.solver_from_problem(sub, dt=s.dt)
+    o.run(nsteps)
+    xa = i0 + halo                          # first window column on the full grid
+    left = p.n[0] - xa                      # columns before the wrap
+    got, ref = [], []
+    for j in range(s.ncomp):
+        a = s.moments_window(j, xa, j0 + halo, left, w)
+        b = s.moments_window(j, 0, j0 + halo, w - left, w)
+        got.append(np.concatenate([a, b], axis=1))
+        ref.append(o.U[j].T[halo: halo + w, halo: halo + w])
+    assert min(np.abs(r).max() for r in ref[:1]) > 1e-30
+    assert rel_l2(got, ref) <= FP32_TOL
