@@ -23,7 +23,7 @@ order and notation, with no blocking, fusion or reordering:
   even differences computed once (section 5.8), material and sources at the
   half-step time, output by linear interpolation in time (section 5.8).
 
-Readings where the paper is silent or garbled (also listed in the design doc):
+Readings where the paper is silent or garbled:
 
 * time step: dt = cn * min(dx, dy) / lambda_max(Mx); cn already contains the
   2D factor 1/2 of section 4.5;
