@@ -151,3 +151,32 @@ def test_full_size_random_p39_sampled_across_periodic_edge():
         ref.append(o.U[j].T[halo: halo + w, halo: halo + w])
     assert min(np.abs(r).max() for r in ref[:1]) > 1e-30
     assert rel_l2(got, ref) <= FP32_TOL
+
+
+def test_full_size_checkerboard_p13_sampled():
+    """The P_13 checkerboard workload at full size (512 x 512, FP32,
+    extrapolation boundaries, source block, tiled kernel, merged schedule):
+    a 16 x 16 window across the source block's edge at x = 4 against the
+    oracle on the window plus a halo.  The window problem wraps
+    periodically, so on a grid with nodes along an axis its node k lies
+    between full cells i0 + k and i0 + k + 1, which is node i0 + k + 1 of
+    the full grid (extrapolation: node m lies between cells m - 1 and m)."""
+    p = inputs.checkerboard_p13()
+    nsteps = 4
+    s = capi.Stepper.from_problem(p, kernel="tiled", schedule="merged")
+    s.step(nsteps)
+    halo = int(math.ceil(1.5 * nsteps)) + 3
+    w = 16
+    i0, j0 = 285 - halo, 250 - halo
+    sub = _window_problem(p, i0, j0, w + 2 * halo, s.dt)
+    o = O.solver_from_problem(sub, dt=s.dt)
+    o.run(nsteps)
+    got, ref = [], []
+    for j in range(s.ncomp):
+        g = s.moment_info(j)["grid"]
+        xo = i0 + halo + (1 if g & 1 else 0)
+        yo = j0 + halo + (1 if g & 2 else 0)
+        got.append(s.moments_window(j, xo, yo, w, w))
+        ref.append(o.U[j].T[halo: halo + w, halo: halo + w])
+    assert np.abs(ref[0]).max() > 1e-3
+    assert rel_l2(got, ref) <= FP32_TOL
