@@ -348,6 +348,16 @@ class Stepper:
     def step(self, n: int = 1):
         self._check(self._L.starmap_step(self._h, int(n)))
 
+    def step_time_dependent(self, problem, n: int = 1):
+        """n steps of a problem whose material or sources change in time.
+        The method freezes them at each step's midpoint (section 5.5): before
+        every step they are sampled at t + dt/2 on the host and uploaded (the
+        library recomputes the decay coefficients); one step per call is the
+        literal schedule O_1/2 E E O_1/2 whatever the handle's schedule."""
+        for _ in range(int(n)):
+            self.load_problem(problem, self.time + 0.5 * self.dt, ic=False, factors=False)
+            self.step(1)
+
     def run_pass(self, parity: int, which: int):
         self._check(self._L.starmap_pass(self._h, int(parity), int(which)))
 
@@ -430,10 +440,11 @@ class Stepper:
         s.load_problem(problem, t_eval)
         return s
 
-    def load_problem(self, problem, t_eval: float = 0.0, ic: bool = True):
+    def load_problem(self, problem, t_eval: float = 0.0, ic: bool = True, factors: bool = True):
         """Sample material, sources and initial conditions of a Problem at
-        the points of each grid and upload them."""
-        if problem.sigma_sl_factor is not None:
+        the points of each grid and upload them (factors: also the
+        per-order scattering factors)."""
+        if factors and problem.sigma_sl_factor is not None:
             self.set_scattering_factors(problem.sigma_sl_factor)
         for g in range(4):
             nx, ny, *_ = self.grid_info(g)
