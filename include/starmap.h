@@ -141,6 +141,18 @@ int starmap_host_matrices(int system, int N, int ncomp_capacity,
                           double* Mx, double* My, int* grid, int* order,
                           double* lambda_max);
 
+/* Moments of a unit beam: the real spherical harmonic of every component
+ * of the 2D system (section 3: orthonormal, without the Condon-Shortley
+ * phase, so that R_1^1 ~ Omega_x and I_1^1 ~ Omega_y; R_l^m ~ sqrt2 N_l^m
+ * P_l^m(mu) cos(m phi), I_l^m ~ sqrt2 N_l^m P_l^m(mu) sin(m phi), R_l^0 ~
+ * N_l^0 P_l(mu)) at the direction Omega = (sqrt(1-mu^2) cos phi,
+ * sqrt(1-mu^2) sin phi, mu), in the component order of starmap_host_matrices.
+ * A source q(x, Omega) = qbar(x) delta(Omega - Omega_0) (the beam of
+ * section 6) has the moments qbar(x) * out[j].  out holds count >= ncomp
+ * doubles.  Host function.  Errors: E_ARG (slab system, N out of range,
+ * |mu| > 1, short out). */
+int starmap_direction_moments(int system, int N, double mu, double phi, double* out, size_t count);
+
 /* E(c) = (exp(c) - 1)/c, section 5.6 (series for |c| <= 2e-4), applied to
  * count values in place.  Host function, for tests. */
 int starmap_host_expm1div(double* c, size_t count);

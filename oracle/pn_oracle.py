@@ -83,6 +83,46 @@ def real_moments(N: int) -> List[Tuple[str, int, int]]:
     return out
 
 
+def _legendre_derivative(l: int, m: int, x):
+    """d^m/dx^m P_l(x), exact in rationals, from the explicit sum
+    P_l(x) = 2^-l sum_k (-1)^k C(l, k) C(2l - 2k, l) x^(l - 2k)."""
+    from fractions import Fraction
+    total = Fraction(0)
+    for k in range(l // 2 + 1):
+        p = l - 2 * k
+        if p < m:
+            continue
+        coef = Fraction((-1) ** k * math.comb(l, k) * math.comb(2 * l - 2 * k, l), 2 ** l)
+        total += coef * Fraction(math.factorial(p), math.factorial(p - m)) * x ** (p - m)
+    return total
+
+
+def direction_moments(N: int, mu: float, phi: float) -> np.ndarray:
+    """The real harmonic of every real moment (order of real_moments) at the
+    direction (sqrt(1-mu^2) cos phi, sqrt(1-mu^2) sin phi, mu): the moments
+    of a unit beam q = delta(Omega - Omega_0) (the beam test of section 6).
+    Orthonormal, without the Condon-Shortley phase (R_1^1 ~ Omega_x, I_1^1 ~
+    Omega_y, as the real moments of section 3):
+        N_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),
+        P_l^m(mu) = (1 - mu^2)^(m/2) d^m/dmu^m P_l(mu)   (derivative exact),
+        R_l^m = sqrt2 N_l^m P_l^m cos(m phi), I_l^m = sqrt2 N_l^m P_l^m sin(m phi),
+        R_l^0 = N_l^0 P_l(mu)."""
+    from fractions import Fraction
+    x = Fraction(mu)
+    st = math.sqrt(max(0.0, 1.0 - mu * mu))
+    out = []
+    for kind, l, m in real_moments(N):
+        norm = math.sqrt((2 * l + 1) / (4 * math.pi) * float(Fraction(math.factorial(l - m), math.factorial(l + m))))
+        P = st ** m * float(_legendre_derivative(l, m, x))
+        if m == 0:
+            out.append(norm * P)
+        elif kind == "R":
+            out.append(math.sqrt(2.0) * norm * P * math.cos(m * phi))
+        else:
+            out.append(math.sqrt(2.0) * norm * P * math.sin(m * phi))
+    return np.array(out)
+
+
 def complex_flux_matrices(N: int) -> Tuple[np.ndarray, np.ndarray]:
     """M_x^complex and M_y^complex of section 3 (including the 1/2 and i/2),
     read off eq. Pncomplex; terms of order N+1 are dropped (P_N closure)."""

@@ -81,6 +81,8 @@ def lib():
         "starmap_config_default": (None, [ctypes.POINTER(Config)]),
         "starmap_host_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _ip, _ip, _dp]),
         "starmap_host_expm1div": (ctypes.c_int, [_dp, ctypes.c_size_t]),
+        "starmap_direction_moments": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                     _dp, ctypes.c_size_t]),
         "starmap_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(H)]),
         "starmap_destroy": (None, [H]),
         "starmap_last_error": (ctypes.c_char_p, [H]),
@@ -182,6 +184,18 @@ def host_matrices(system: int, N: int):
     if rc != OK:
         raise StarmapError(rc, L.starmap_last_error(None).decode())
     return Mx, My, grid, order, lam.value
+
+
+def direction_moments(N: int, mu: float, phi: float) -> np.ndarray:
+    """Moments of a unit beam in the direction (mu, phi): the real harmonic
+    of every component of the 2D system (host math)."""
+    L = lib()
+    n = (N + 1) * (N + 2) // 2
+    out = np.zeros(n)
+    rc = L.starmap_direction_moments(PN2D, int(N), float(mu), float(phi), _dptr(out), n)
+    if rc != OK:
+        raise StarmapError(rc, L.starmap_last_error(None).decode())
+    return out
 
 
 def selftest_bounded_wait() -> int:

@@ -517,6 +517,15 @@ int starmap_host_matrices(int system, int N, int cap, double* Mx, double* My, in
     return STARMAP_OK;
 }
 
+int starmap_direction_moments(int system, int N, double mu, double phi, double* out, size_t count) {
+    std::vector<double> v;
+    std::string err;
+    if (!direction_moments(system, N, mu, phi, v, err)) return fail(nullptr, STARMAP_E_ARG, err);
+    if (!out || count < v.size()) return fail(nullptr, STARMAP_E_ARG, "out needs ncomp doubles");
+    std::copy(v.begin(), v.end(), out);
+    return STARMAP_OK;
+}
+
 int starmap_host_expm1div(double* c, size_t count) {
     if (!c && count) return STARMAP_E_ARG;
     for (size_t i = 0; i < count; ++i) c[i] = expm1div(c[i]);

@@ -298,4 +298,41 @@ bool build_system(int system, int N, SystemMatrices& out, std::string& err) {
     return true;
 }
 
+// The real harmonic of every component at the direction (mu, phi): the
+// orthonormal associated Legendre functions N_l^m P_l^m(mu) without the
+// Condon-Shortley phase (so R_1^1 ~ Omega_x, I_1^1 ~ Omega_y, the convention
+// of the real moments of section 3), by the standard three-term recurrence
+// in l at fixed m, started from N_m^m P_m^m = sqrt(1/(4 pi)) prod_k
+// sqrt((2k+1)/(2k)) (1 - mu^2)^(m/2); then R_l^m = sqrt2 Ybar cos(m phi),
+// I_l^m = sqrt2 Ybar sin(m phi), R_l^0 = Ybar.
+bool direction_moments(int system, int N, double mu, double phi, std::vector<double>& out, std::string& err) {
+    if (system != 0) { err = "direction moments are defined for the 2D system"; return false; }
+    if (!(mu >= -1.0 && mu <= 1.0)) { err = "mu must lie in [-1, 1]"; return false; }
+    SystemMatrices sys;
+    if (!build_system(system, N, sys, err)) return false;
+    const double pi = std::acos(-1.0);
+    const double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+    // ybar[m][l]: orthonormal associated Legendre values
+    std::vector<std::vector<double>> ybar(N + 1, std::vector<double>(N + 1, 0.0));
+    double ymm = std::sqrt(1.0 / (4.0 * pi));
+    for (int m = 0; m <= N; ++m) {
+        if (m > 0) ymm *= std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * st;
+        ybar[m][m] = ymm;
+        if (m + 1 <= N) ybar[m][m + 1] = std::sqrt(2.0 * m + 3.0) * mu * ymm;
+        for (int l = m + 2; l <= N; ++l) {
+            const double a = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+            const double b = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+            ybar[m][l] = a * (mu * ybar[m][l - 1] - b * ybar[m][l - 2]);
+        }
+    }
+    out.assign(sys.ncomp, 0.0);
+    for (int j = 0; j < sys.ncomp; ++j) {
+        const Moment& mo = sys.moms[j];
+        const double y = ybar[mo.m][mo.l];
+        if (mo.m == 0) out[j] = y;
+        else out[j] = std::sqrt(2.0) * y * (mo.imag ? std::sin(mo.m * phi) : std::cos(mo.m * phi));
+    }
+    return true;
+}
+
 }  // namespace starmap

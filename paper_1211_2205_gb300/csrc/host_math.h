@@ -27,6 +27,10 @@ struct SystemMatrices {
 // Returns false with a message in err on failure.
 bool build_system(int system, int N, SystemMatrices& out, std::string& err);
 
+// Real harmonic of every component (section 3) at the direction with
+// cosine mu to the z axis and azimuth phi (the moments of a unit beam).
+bool direction_moments(int system, int N, double mu, double phi, std::vector<double>& out, std::string& err);
+
 // E(c) = (exp(c) - 1)/c, section 5.6.
 double expm1div(double c);
 

@@ -256,6 +256,46 @@ def closure_medium(seed: int, n: int = 512, N: int = 39, t_final: float = 0.5,
         precision=precision, sigma_a=sigma_a, sigma_s0=sigma_s0, ic=[(0, ic0)], t_final=t_final)
 
 
+BEAM_ANGLE = math.pi / 6
+BEAM_INTERFACE = 0.3
+
+
+def beam(moments: Sequence[float], n: int = 150, t_final: float = 0.6, g: float = 0.85,
+         precision: str = "fp32", interface: float = BEAM_INTERFACE) -> Problem:
+    """The beam of section 6: a continuous source qbar(x) delta(Omega -
+    Omega_0), Omega_0 in the plane at the angle pi/6 to the x axis, qbar the
+    line source's Gaussian (pseudo-time 3.2e-4, unit mass) at the origin, on
+    [-0.6, 0.6]^2 with extrapolation boundaries; void for x < 0.3, for
+    x >= 0.3 no absorption and Henyey-Greenstein scattering
+    Sigma_sl = 100 g^l.  `moments` are the beam direction's moments of the
+    components (their real harmonics at Omega_0, one per component: the
+    order N is len(moments) = (N+1)(N+2)/2).  `interface` moves the medium's
+    edge (beyond 0.6: all void)."""
+    ncomp = len(moments)
+    N = int(round((math.sqrt(8 * ncomp + 1) - 3) / 2))
+    if (N + 1) * (N + 2) // 2 != ncomp:
+        raise ValueError("moments must hold one value per component of a 2D system")
+    qbar = gaussian_paper(3.2e-4)
+
+    def medium(x):
+        return np.asarray(x) >= interface
+
+    def sigma_a(t, x, y):
+        return 0.0 * np.asarray(x) + 0.0 * np.asarray(y)
+
+    def sigma_s0(t, x, y):
+        return np.where(medium(x), 100.0, 0.0) + 0.0 * np.asarray(y)
+
+    def scaled(c):
+        return lambda t, x, y: c * qbar(t, x, y)
+
+    sources = [(j, scaled(float(c))) for j, c in enumerate(moments) if abs(c) > 1e-14]
+    return Problem(name=f"beam_p{N}_{n}" + ("" if interface == BEAM_INTERFACE else "_void"), N=N, ax=(-0.6, 0.6, -0.6, 0.6), n=(n, n),
+                   bc=("extrapolation", "extrapolation"), cn=0.5, precision=precision,
+                   sigma_a=sigma_a, sigma_s0=sigma_s0, sigma_sl_factor=[g ** l for l in range(N + 1)],
+                   sources=sources, ic=[], t_final=t_final)
+
+
 def batched_instance(k: int, nsteps: int = 100) -> Problem:
     """Instance k of the batched workload (seed 12112205 + k)."""
     rng = SplitMix64(12112205 + k)
