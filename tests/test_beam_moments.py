@@ -14,6 +14,13 @@ from paper_1211_2205_gb300 import capi
 DIRS = [(0.0, math.pi / 6), (0.3, 1.1), (-0.8, 4.0), (0.999, 2.5)]
 
 
+@pytest.fixture(scope="module")
+def built():
+    """The library's host functions need libstarmap.so (compiled here, no GPU needed)."""
+    import __graft_entry__
+    __graft_entry__.build()
+
+
 @pytest.mark.parametrize("mu,phi", DIRS)
 def test_first_moments_closed_form(mu, phi):
     y = O.direction_moments(3, mu, phi)
@@ -47,11 +54,11 @@ def test_flux_matrices_reproduce_the_direction(N, mu, phi):
 
 @pytest.mark.parametrize("N", [3, 9, 39])
 @pytest.mark.parametrize("mu,phi", DIRS)
-def test_library_matches_oracle(N, mu, phi):
+def test_library_matches_oracle(built, N, mu, phi):
     np.testing.assert_allclose(capi.direction_moments(N, mu, phi), O.direction_moments(N, mu, phi), atol=1e-14)
 
 
-def test_library_rejects_bad_arguments():
+def test_library_rejects_bad_arguments(built):
     with pytest.raises(capi.StarmapError) as e:
         capi.direction_moments(3, 1.5, 0.0)
     assert e.value.code == capi.E_ARG
