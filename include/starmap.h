@@ -78,10 +78,12 @@ extern "C" {
 #define STARMAP_SCHEDULE_MERGED  1
 
 /* Kernel selection for the half-step passes. */
-#define STARMAP_KERNEL_AUTO    0  /* tiled kernel where supported, else gather */
+#define STARMAP_KERNEL_AUTO    0  /* tiled kernel where supported and its tables fit in
+                                     shared memory (FP32 2D P_N up to N ~ 50), else gather */
 #define STARMAP_KERNEL_GATHER  1  /* one thread per point, CSR loop over moments */
-#define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N, N <= 63);
-                                     tile height chosen by N */
+#define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N,
+                                     N <= 63 where the tables fit in shared memory, else
+                                     E_UNSUPPORTED); tile height chosen by N */
 #define STARMAP_KERNEL_TILED_TALL  3  /* tiled, 64 x 10 tiles, one CTA per SM */
 #define STARMAP_KERNEL_TILED_SHORT 4  /* tiled, 64 x 5 tiles, two CTAs per SM */
 
@@ -379,7 +381,8 @@ int starmap_mlp_train_step(starmap_mlp_t* net, const float* X, const float* T, c
                            size_t B, float lr, float* loss);
 /* ------------------------------------------------------------- batches
  * Not in the paper: many independent problems advanced together.  A batch
- * holds `count` FP32 2D P_N instances (any N <= 63, any grid size, without
+ * holds `count` FP32 2D P_N instances (any grid size, N up to the order at
+ * which the tiled kernel's tables still fit in shared memory -- about 50 --, without
  * closure), each a full handle with its own state, material and sources.
  * starmap_batch_step advances every instance by nsteps of its own dt with
  * one CUDA graph launch: per pass, one persistent kernel walks the tiles of

@@ -662,6 +662,15 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
     if (rc) return bail(rc);
     if (h->tiled) { for (int g = 0; g < 4; ++g) tiled_set_coef(h->tiled, g, h->coef[g], h->nclasses); }
     rc = rebuild_tables(h);
+    if (rc == STARMAP_E_UNSUPPORTED && h->tiled && c.kernel == STARMAP_KERNEL_AUTO) {
+        // at the highest orders the tiled kernel's partial sums and tables
+        // leave no room for its ring in shared memory: the gather kernel
+        tiled_destroy(h->tiled);
+        h->tiled = nullptr;
+        h->kernel_used = STARMAP_KERNEL_GATHER;
+        h->err.clear();
+        rc = rebuild_tables(h);
+    }
     if (rc) return bail(rc);
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "create"));

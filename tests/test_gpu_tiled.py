@@ -180,3 +180,23 @@ def test_full_size_checkerboard_p13_sampled():
         ref.append(o.U[j].T[halo: halo + w, halo: halo + w])
     assert np.abs(ref[0]).max() > 1e-3
     assert rel_l2(got, ref) <= FP32_TOL
+
+
+def test_highest_orders_fall_back_to_gather():
+    """At N = 61 the tiled kernel's partial sums and tables leave no room for
+    its ring in shared memory: kernel "auto" runs the gather kernel (and
+    matches the oracle), an explicit "tiled" request is refused."""
+    p = inputs.Problem(name="p61", N=61, ax=(0.0, 1.0, 0.0, 1.0), n=(12, 10), bc=("periodic", "extrapolation"),
+                       precision="fp32", sigma_a=lambda t, x, y: 0.3 + 0 * x,
+                       sigma_s0=lambda t, x, y: 1.0 + 0.5 * np.sin(6 * x) * np.cos(4 * y),
+                       ic=[(0, inputs.gaussian_std(0.5, 0.45, 0.15))], nsteps=2)
+    s = capi.Stepper.from_problem(p, schedule="merged")
+    assert s.kernel == "gather"
+    s.step(2)
+    got = [s.moments(j) for j in range(s.ncomp)]
+    o = O.solver_from_problem(p, dt=s.dt)
+    o.run(2)
+    assert rel_l2(got, [u.T for u in o.U]) <= 1e-5
+    with pytest.raises(capi.StarmapError) as e:
+        capi.Stepper.from_problem(p, kernel="tiled")
+    assert e.value.code == capi.E_UNSUPPORTED
