@@ -78,13 +78,15 @@ extern "C" {
 #define STARMAP_SCHEDULE_MERGED  1
 
 /* Kernel selection for the half-step passes. */
-#define STARMAP_KERNEL_AUTO    0  /* tiled kernel where supported and its tables fit in
-                                     shared memory (FP32 2D P_N up to N ~ 50), else gather */
+#define STARMAP_KERNEL_AUTO    0  /* tiled kernel where supported (FP32 2D P_N, N <= 63),
+                                     else gather */
 #define STARMAP_KERNEL_GATHER  1  /* one thread per point, CSR loop over moments */
 #define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N,
-                                     N <= 63 where the tables fit in shared memory, else
-                                     E_UNSUPPORTED); tile height chosen by N */
-#define STARMAP_KERNEL_TILED_TALL  3  /* tiled, 64 x 10 tiles, one CTA per SM */
+                                     N <= 63); tile height chosen by N, and 5-row tiles at
+                                     one CTA per SM where the tables of the 10-row tiles
+                                     leave no room for their ring (N >= 56 or so) */
+#define STARMAP_KERNEL_TILED_TALL  3  /* tiled, 64 x 10 tiles, one CTA per SM (E_UNSUPPORTED where
+                                         their tables do not fit, N >= 56 or so) */
 #define STARMAP_KERNEL_TILED_SHORT 4  /* tiled, 64 x 5 tiles, two CTAs per SM */
 
 /* Closure of the moment hierarchy.  NONE: the P_N truncation of section 3

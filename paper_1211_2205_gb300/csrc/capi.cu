@@ -662,9 +662,29 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
     if (rc) return bail(rc);
     if (h->tiled) { for (int g = 0; g < 4; ++g) tiled_set_coef(h->tiled, g, h->coef[g], h->nclasses); }
     rc = rebuild_tables(h);
+    if (rc == STARMAP_E_UNSUPPORTED && h->tiled && h->kernel_used == STARMAP_KERNEL_TILED_TALL &&
+        (c.kernel == STARMAP_KERNEL_AUTO || c.kernel == STARMAP_KERNEL_TILED)) {
+        // at the highest orders the partial sums and tables of the 10-row
+        // tiles leave no room for a ring: the 5-row tiles (half the partial
+        // sums, one CTA per SM where needed)
+        tiled_destroy(h->tiled);
+        h->tiled = nullptr;
+        h->err.clear();
+        TiledGeometry geo;
+        for (int g = 0; g < 4; ++g) {
+            geo.base[g] = h->base[g]; geo.cstride[g] = h->cstride[g];
+            geo.nx[g] = h->nxg[g]; geo.ny[g] = h->nyg[g]; geo.K[g] = h->Kg[g];
+        }
+        geo.pitch = h->pitch; geo.rows = h->rows; geo.p[0] = h->p[0]; geo.p[1] = h->p[1]; geo.N = h->nsys;
+        geo.variant = 1;
+        rc = tiled_create(geo, &h->tiled);
+        if (rc) return bail(fail(h, rc, h->tiled ? tiled_error(h->tiled) : "tiled kernel setup failed"));
+        h->kernel_used = STARMAP_KERNEL_TILED_SHORT;
+        for (int g = 0; g < 4; ++g) tiled_set_coef(h->tiled, g, h->coef[g], h->nclasses);
+        rc = rebuild_tables(h);
+    }
     if (rc == STARMAP_E_UNSUPPORTED && h->tiled && c.kernel == STARMAP_KERNEL_AUTO) {
-        // at the highest orders the tiled kernel's partial sums and tables
-        // leave no room for its ring in shared memory: the gather kernel
+        // beyond that the gather kernel
         tiled_destroy(h->tiled);
         h->tiled = nullptr;
         h->kernel_used = STARMAP_KERNEL_GATHER;

@@ -123,6 +123,7 @@ struct TiledPlan {
     int tiles_x = 0, tiles_y = 0;
     int variant = 0;                      // 0: 10-row tiles, 1: 5-row tiles
     int sms = 1;
+    int ctas_per_sm = 1;                  // resident CTAs per SM the tables allow (<= the variant's)
     int smem_bytes[2] = {0, 0};
     int nring[2] = {0, 0};                // ring stages per parity
     Params prm[2][2];                     // [P][which]
@@ -383,11 +384,20 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
         cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaDeviceGetAttribute(&persm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         // per-CTA budget: the variant's CTAs per SM (1 KB reserved per CTA),
-        // less the batch kernel's static parameter copy
-        const int minb = tiled_ctas_per_sm(pl->variant);
-        const int budget = std::min(maxsm, persm / minb - 1024) - (int)sizeof(Params) - 256;
-        const int nring = std::min(RING_DEPTH, (budget - RING_OFF - tables) / V.stage_bytes);
+        // less the batch kernel's static parameter copy; where the tables of
+        // a high order do not leave room for the ring, one CTA per SM
+        auto ring_for = [&](int minb) {
+            const int budget = std::min(maxsm, persm / minb - 1024) - (int)sizeof(Params) - 256;
+            return std::min(RING_DEPTH, (budget - RING_OFF - tables) / V.stage_bytes);
+        };
+        int minb = tiled_ctas_per_sm(pl->variant);
+        int nring = ring_for(minb);
+        if (nring < MIN_RING && minb > 1) {
+            minb = 1;
+            nring = ring_for(1);
+        }
         if (nring < MIN_RING) { pl->err = "tiled kernel needs more shared memory than the device offers"; return -8; }
+        pl->ctas_per_sm = P == 0 ? minb : std::min(pl->ctas_per_sm, minb);
         const int ring_end = RING_OFF + nring * V.stage_bytes;
         const int coef_off[2] = {ring_end + coef_rel[0], ring_end + coef_rel[1]};
         const int fin_off[2] = {ring_end + fin_rel[0], ring_end + fin_rel[1]};
@@ -469,7 +479,7 @@ constexpr long long OVERLAP_MAX_STAGES = 1000;
 bool tiled_overlap(TiledPlan* pl, bool odd) {
     if (!pl || !pl->ready) return false;
     const int ntiles = pl->tiles_x * pl->tiles_y;
-    const int grid = std::max(1, std::min(ntiles, pl->sms * tiled_ctas_per_sm(pl->variant)));
+    const int grid = std::max(1, std::min(ntiles, pl->sms * pl->ctas_per_sm));
     return (long long)((ntiles + grid - 1) / grid) * pl->prm[odd ? 1 : 0][0].nstages < OVERLAP_MAX_STAGES;
 }
 
@@ -479,7 +489,7 @@ int tiled_pass(TiledPlan* pl, bool odd, int which, void* stream) {
     const int ntiles = pl->tiles_x * pl->tiles_y;
     if (ntiles <= 0) return 0;
     // persistent grid: every resident CTA slot, at most one per tile
-    const int grid = std::min(ntiles, pl->sms * tiled_ctas_per_sm(pl->variant));
+    const int grid = std::min(ntiles, pl->sms * pl->ctas_per_sm);
     if ((long long)((ntiles + grid - 1) / grid) * pl->prm[P][which].nstages > 0x7fffffffll) {
         pl->err = "too many pipeline stages per CTA for the tiled kernel";
         return -8;

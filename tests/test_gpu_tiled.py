@@ -182,21 +182,22 @@ def test_full_size_checkerboard_p13_sampled():
     assert rel_l2(got, ref) <= FP32_TOL
 
 
-def test_highest_orders_fall_back_to_gather():
-    """At N = 61 the tiled kernel's partial sums and tables leave no room for
-    its ring in shared memory: kernel "auto" runs the gather kernel (and
-    matches the oracle), an explicit "tiled" request is refused."""
+@pytest.mark.parametrize("kernel", ["auto", "tiled"])
+def test_highest_orders_run_on_short_tiles(kernel):
+    """At N = 61 the partial sums and tables of the 10-row tiles leave no
+    room for a ring: kernel "auto" and "tiled" run the 5-row tiles at one
+    CTA per SM (and match the oracle), an explicit "tiled_tall" is refused."""
     p = inputs.Problem(name="p61", N=61, ax=(0.0, 1.0, 0.0, 1.0), n=(12, 10), bc=("periodic", "extrapolation"),
                        precision="fp32", sigma_a=lambda t, x, y: 0.3 + 0 * x,
                        sigma_s0=lambda t, x, y: 1.0 + 0.5 * np.sin(6 * x) * np.cos(4 * y),
                        ic=[(0, inputs.gaussian_std(0.5, 0.45, 0.15))], nsteps=2)
-    s = capi.Stepper.from_problem(p, schedule="merged")
-    assert s.kernel == "gather"
+    s = capi.Stepper.from_problem(p, schedule="merged", kernel=kernel)
+    assert s.kernel == "tiled" and s.tile_rows == 5
     s.step(2)
     got = [s.moments(j) for j in range(s.ncomp)]
     o = O.solver_from_problem(p, dt=s.dt)
     o.run(2)
     assert rel_l2(got, [u.T for u in o.U]) <= 1e-5
     with pytest.raises(capi.StarmapError) as e:
-        capi.Stepper.from_problem(p, kernel="tiled")
+        capi.Stepper.from_problem(p, kernel="tiled_tall")
     assert e.value.code == capi.E_UNSUPPORTED
