@@ -9,12 +9,16 @@ steps.  A bench step is one full time step dt of every moment at every grid
 point; the metric is moment-cell updates per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                  [--workload random_p39|checkerboard_p13|gaussian_p5|batched_256|closure_p7]
+                  [--workload random_p39|checkerboard_p13|gaussian_p5|paper_p5|batched_256|closure_p7]
                   [--kernel auto|gather|tiled]
 
 batched_256: 256 independent FP32 instances (grids 64^2..512^2, N in
 {3,..,15}, random piecewise-constant media, Gaussian sources) advanced by
 one graph launch per step call; same metric over all instances.
+paper_p5: the one run the paper times (section 6.3: P_5 checkerboard,
+100x100, extrapolation, to t = 3.2, in about 1.5 s of Matlab on a 2008
+laptop, about 1.2e7 moment-cell updates/s); FP64 as Matlab; the line adds
+the time to t = 3.2 and vs_baseline against that figure.
 closure_p7: the learned order-8 closure of P_7, trained on the GPU from
 P_39 runs on 512x512 random media; the line reports the error-matched
 speedup against plain P_N on held-out media (a bench step is one held-out
@@ -49,6 +53,9 @@ import numpy as np  # noqa: E402
 from paper_1211_2205_gb300 import inputs  # noqa: E402
 
 METRIC = "moment-cell updates/s"
+# the paper's one timing (section 6.3): 18.3e6 degrees of freedom (space x
+# angle x time) of the P_5 checkerboard run in about 1.5 s
+PAPER_UPDATES_PER_S = 18.3e6 / 1.5
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 KERNEL_SOURCES = {
     "gather": ["paper_1211_2205_gb300/csrc/kernels_gather.cu"],
@@ -65,6 +72,9 @@ def workload(name: str):
         return inputs.checkerboard_p13(), "2D P_13 FP32 512x512 checkerboard, extrapolation, source"
     if name == "gaussian_p5":
         return inputs.gaussian_p5(), "2D P_5 FP64 64x64 periodic Gaussian"
+    if name == "paper_p5":
+        return (inputs.checkerboard_p13(n=100, N=5, precision="fp64"),
+                "the run the paper times (section 6.3): 2D P_5 FP64 100x100 checkerboard, extrapolation, to t = 3.2")
     if name == "batched_256":
         return ([inputs.batched_instance(k) for k in range(256)],
                 "256 independent 2D P_N FP32 instances, grids 64^2-512^2, N in {3..15}, piecewise-constant media, "
@@ -185,8 +195,12 @@ def peaks():
 
 def window_problem(problem, cells: int):
     """The cells x cells window at the centre of the workload with the same
-    spacing and material (periodic wrap at the window edges), and its dt."""
+    spacing and material (periodic wrap at the window edges), and its dt;
+    the workload itself when the window is the whole grid."""
     from oracle import pn_oracle as O
+    if problem.n == (cells, cells):
+        Mx, My, order = O.system_matrices(problem.system, problem.N)
+        return problem, O.time_step(Mx, problem.ax, problem.n, problem.cn)
     x0, x1, y0, y1 = problem.ax
     hx = (x1 - x0) / problem.n[0]
     hy = (y1 - y0) / problem.n[1]
@@ -211,7 +225,8 @@ def oracle_sample(problem, cells: int, steps: int, keep: bool = False):
     s.run(steps)
     el = time.perf_counter() - t0
     updates = sum(u.size for u in s.U) * steps
-    desc = f"oracle (numpy FP64) on a {cells}x{cells} window of the workload, {steps} steps after 1 untimed"
+    where = "the whole workload" if sub is problem else f"a {cells}x{cells} window of the workload"
+    desc = f"oracle (numpy FP64) on {where}, {steps} steps after 1 untimed"
     if keep:
         return updates / el, desc, el, [u.T.copy() for u in s.U]
     return updates / el, desc, el
@@ -245,7 +260,8 @@ def run_reference(args):
     if args.workload == "batched_256":
         problem = min(problem, key=lambda p: p.n[0] * (p.N + 1) ** 2)
         desc += f"; oracle sample from the smallest instance ({problem.name})"
-    cells = {"random_p39": 48, "checkerboard_p13": 96, "gaussian_p5": 64, "batched_256": 64}[args.workload]
+    cells = {"random_p39": 48, "checkerboard_p13": 96, "gaussian_p5": 64, "paper_p5": 100,
+             "batched_256": 64}[args.workload]
     vals = []
     for _ in range(args.warmup):
         oracle_sample(problem, cells, 1)
@@ -391,6 +407,7 @@ def run_native(args):
     assert np.isfinite(r00).all()
 
     clocks = clk.summary()
+    steps_to_final = math.ceil(problem.t_final / s.dt - 1e-9) if problem.t_final else 0
     # every pass is the update kernel plus the ghost-cell refresh
     launches = (2 * args.steps + 1) * 2
     line = {
@@ -417,8 +434,16 @@ def run_native(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if args.workload == "paper_p5":
+        # context: the paper's Matlab run of the same problem (another machine)
+        line["vs_baseline"] = value / PAPER_UPDATES_PER_S
+        line["paper"] = {"updates_per_s": PAPER_UPDATES_PER_S, "seconds_to_t_final": 1.5,
+                         "hardware": "2008 Lenovo W500 laptop, Matlab (section 6.3)"}
+        line["time_to_t_final_ms"] = steps_to_final * ms_max / args.steps
+        line["config"]["steps_to_t_final"] = steps_to_final
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cells, nst = {"random_p39": (192, 4), "checkerboard_p13": (256, 8), "gaussian_p5": (64, 100)}[args.workload]
+        cells, nst = {"random_p39": (192, 4), "checkerboard_p13": (256, 8), "gaussian_p5": (64, 100),
+                      "paper_p5": (100, steps_to_final - 1)}[args.workload]
         v, sample, el, sol = oracle_sample(problem, cells, nst, keep=True)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
         line["precision"] = window_error(problem, cells, nst, sol, args.kernel)

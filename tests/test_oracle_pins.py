@@ -335,6 +335,36 @@ def test_mass_decays_exactly_with_uniform_absorption():
     assert abs(s.mass() - m0 * math.exp(-sa * 25 * s.dt)) <= 1e-13 * abs(m0)
 
 
+@pytest.mark.parametrize("n", [(1, 1), (4, 3)])
+@pytest.mark.parametrize("aniso", [False, True])
+def test_homogeneous_state_follows_the_relaxation_ode(n, aniso):
+    """A spatially constant state in a constant medium on a periodic grid
+    (down to a single cell) has no differences, so every moment obeys its
+    own relaxation ODE u' = -c_l u + q (section 2: c_0 = sigma_a, c_l =
+    sigma_a + sigma_s0 - sigma_sl), whose exact solution the exponential
+    sub-steps (eq. sub_step_solution) must reproduce after any number of
+    steps: u(t) = e^(-c t) u(0) + q (1 - e^(-c t)) / c."""
+    N = 4
+    Mx, My, order = O.system_matrices("pn2d", N)
+    sa, s0 = 0.8, 1.7
+    fac = [0.6 ** l for l in range(N + 1)] if aniso else None
+    rng = inputs.SplitMix64(41)
+    u0 = rng.uniforms(len(order)) * 2 - 1
+    q = {0: 0.9, 2: -0.4, 7: 0.25}
+    s = O.StaggeredSolver(Mx, My, order, (0, 1, 0, 1), n, ("periodic", "periodic"),
+                          sigma_a=lambda t, x, y: sa + 0 * x, sigma_s0=lambda t, x, y: s0 + 0 * x,
+                          sl_factor=fac, sources=[(j, (lambda v: lambda t, x, y: v + 0 * x)(v)) for j, v in q.items()],
+                          ic=[(j, (lambda v: lambda t, x, y: v + 0 * x)(u0[j])) for j in range(len(order))])
+    s.run(7)
+    t = 7 * s.dt
+    for j in range(len(order)):
+        l = int(order[j])
+        c = sa if l == 0 else sa + s0 - (s0 * fac[l] if aniso else 0.0)
+        e = math.exp(-c * t)
+        want = e * u0[j] + q.get(j, 0.0) * (1.0 - e) / c
+        np.testing.assert_allclose(s.U[j], want, rtol=1e-13, atol=1e-15)
+
+
 def test_symmetry_of_centred_gaussian():
     p = inputs.gaussian_p5(n=32, nsteps=20)
     s = O.solver_from_problem(p)
