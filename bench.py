@@ -391,13 +391,22 @@ def run_native(args):
     for j, f in problem.ic:
         X, Y = s.grid_coords(s.moment_info(j)["grid"])
         ic_host.append((j, np.ascontiguousarray(np.broadcast_to(f(0.0, X, Y), X.shape), dtype=np.float64)))
-    h2d = sum(a.nbytes for _, a in ic_host)
+    # a workload that starts from zero (checkerboard) has its source as the input
+    src_host = {}
+    if not problem.ic:
+        for j, f in problem.sources:
+            X, Y = s.grid_coords(s.moment_info(j)["grid"])
+            v = np.broadcast_to(f(0.0, X, Y), X.shape).astype(np.float64)
+            src_host[j] = src_host[j] + v if j in src_host else np.ascontiguousarray(v)
+    h2d = sum(a.nbytes for _, a in ic_host) + sum(a.nbytes for a in src_host.values())
     r00_bytes = s.moment_info(0)["nx"] * s.moment_info(0)["ny"] * 8
     barrier()
     t0 = time.perf_counter()
     s.clear()
     for j, a in ic_host:
         s.set_moment(j, a)
+    for j, a in src_host.items():
+        s.set_source(j, a)
     s.step(args.steps)
     r00 = s.moments(0)
     barrier()
@@ -573,7 +582,8 @@ def run_closure(args):
     media = max(1, min(args.steps, 4))
     # the headline compares with plain P_7 / P_11 / P_15 (the workload's comparison set); the
     # line also reports the stricter comparison with every odd order 7..15
-    ev = closure.evaluate(tr.params, [100 + k for k in range(media)], n=512, repeats=2, compare=(7, 11, 15))
+    with ClockSampler(local) as clk:
+        ev = closure.evaluate(tr.params, [100 + k for k in range(media)], n=512, repeats=2, compare=(7, 11, 15))
     # cost of one closure evaluation: closure + odd pass minus the same odd pass without closure
     p = inputs.closure_medium(100, n=512, N=7)
     dt = closure.common_dt(p, 39)
@@ -621,9 +631,15 @@ def run_closure(args):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "closure evaluation (fused features + tcgen05 network, node averaging)",
                      "flops_per_launch": flops, "launch_ms": eval_ms, "peak_kind": f"{pk_kind} bf16_tflops"},
-        "e2e": None,
-        "gpu_launches": None,
-        "clocks": None,
+        # the same ratio on the host clock: initial moments uploaded from host
+        # arrays, the steps, R_0^0 read back, for the closed run and the matched plain run
+        "e2e": {"value": ev["e2e_error_matched_speedup"], "unit": "x",
+                "h2d_bytes_per_step": ev["cases"][0]["closure"]["h2d_bytes"] / ev["cases"][0]["steps"],
+                "d2h_bytes_per_step": ev["cases"][0]["closure"]["d2h_bytes"] / ev["cases"][0]["steps"]},
+        # one medium: the closed run (2n + 1 passes of tile kernel + refresh, n + 1
+        # closure evaluations of network + node averaging) and the matched plain run
+        "gpu_launches": 10 * ev["cases"][0]["steps"] + 6,
+        "clocks": clk.summary(),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -25,6 +25,7 @@ Workflow
 from __future__ import annotations
 
 import math
+import time
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional, Sequence
 
@@ -184,13 +185,18 @@ class RunResult:
     R00: np.ndarray
     ms: float
     steps: int
+    e2e_ms: float = float("nan")      # host clock: initial moments uploaded, steps, R_0^0 read back
+    h2d_bytes: int = 0
+    d2h_bytes: int = 0
 
 
 def run_case(problem: inputs.Problem, N: int, dt: float, nsteps: int, params: Optional[np.ndarray] = None,
              repeats: int = 1, closure_schedule: str = "merged") -> RunResult:
     """Run P_N (params None) or P_7 with the closure network from the
     problem's initial condition for nsteps steps of size dt; device time of
-    the stepping (after one untimed warm-up run) on a dedicated stream."""
+    the stepping (after one untimed warm-up run) on a dedicated stream, and
+    the same run end to end on the host clock: state cleared, initial
+    moments uploaded from host arrays, the steps, R_0^0 read back."""
     torch = _torch()
     stream = torch.cuda.Stream()
     closure = params is not None
@@ -200,10 +206,15 @@ def run_case(problem: inputs.Problem, N: int, dt: float, nsteps: int, params: Op
                                   closure="mlp8" if closure else "none")
     if closure:
         s.set_closure(params)
-    times = []
+    ic_host = []
+    for j, f in q.ic:
+        X, Y = s.grid_coords(s.moment_info(j)["grid"])
+        ic_host.append((j, np.ascontiguousarray(np.broadcast_to(f(0.0, X, Y), X.shape), dtype=np.float64)))
+    times, e2e = [], []
     for r in range(repeats + 1):
         s.clear()
-        _set_ic(s, q)
+        for j, a0 in ic_host:
+            s.set_moment(j, a0)
         s.sync()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
@@ -214,9 +225,19 @@ def run_case(problem: inputs.Problem, N: int, dt: float, nsteps: int, params: Op
         b.synchronize()
         if r > 0:
             times.append(a.elapsed_time(b))
+    for r in range(repeats):
+        t0 = time.perf_counter()
+        s.clear()
+        for j, a0 in ic_host:
+            s.set_moment(j, a0)
+        s.step(nsteps)
+        R00 = s.moments(0)
+        e2e.append((time.perf_counter() - t0) * 1e3)
     R00 = s.moments(0)
     s.close()
-    return RunResult(N=N, closure=closure, R00=R00, ms=float(np.median(times)), steps=nsteps)
+    return RunResult(N=N, closure=closure, R00=R00, ms=float(np.median(times)), steps=nsteps,
+                     e2e_ms=float(np.median(e2e)) if e2e else float("nan"),
+                     h2d_bytes=sum(a0.nbytes for _, a0 in ic_host), d2h_bytes=R00.size * 8)
 
 
 def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
@@ -238,10 +259,13 @@ def evaluate(params: np.ndarray, seeds: Sequence[int], n: int = 512, orders: Seq
         row = {"seed": seed, "dt": dt, "steps": nsteps, "ref_ms": ref.ms, "plain": {}}
         for N in orders:
             r = run_case(p, N, dt, nsteps, repeats=repeats)
-            row["plain"][N] = {"err": rel_l2(r.R00, ref.R00), "ms": r.ms}
+            row["plain"][N] = {"err": rel_l2(r.R00, ref.R00), "ms": r.ms, "e2e_ms": r.e2e_ms,
+                               "h2d_bytes": r.h2d_bytes, "d2h_bytes": r.d2h_bytes}
         for k, sched in enumerate(closure_schedules):
             r = run_case(p, N_BASE, dt, nsteps, params=params, repeats=repeats, closure_schedule=sched)
-            row["closure" if k == 0 else "closure_" + sched] = {"err": rel_l2(r.R00, ref.R00), "ms": r.ms}
+            row["closure" if k == 0 else "closure_" + sched] = {
+                "err": rel_l2(r.R00, ref.R00), "ms": r.ms, "e2e_ms": r.e2e_ms,
+                "h2d_bytes": r.h2d_bytes, "d2h_bytes": r.d2h_bytes}
         cases.append(row)
     return summarize(cases, orders, compare)
 
@@ -251,19 +275,23 @@ def summarize(cases: List[Dict], orders: Sequence[int], compare: Optional[Sequen
     speedup of the closure against the lowest plain order at least as
     accurate on average: among `compare` (default: all evaluated orders) and,
     as "strict", among all evaluated orders."""
-    plain = {N: {"err": float(np.mean([c["plain"][N]["err"] for c in cases])),
-                 "ms": float(np.mean([c["plain"][N]["ms"] for c in cases]))} for N in orders}
-    cl = {"err": float(np.mean([c["closure"]["err"] for c in cases])),
-          "ms": float(np.mean([c["closure"]["ms"] for c in cases]))}
+    def mean(rows, key):
+        vals = [r[key] for r in rows if key in r]
+        return float(np.mean(vals)) if vals else float("nan")
 
-    def matched(candidates):
+    plain = {N: {k: mean([c["plain"][N] for c in cases], k) for k in ("err", "ms", "e2e_ms")} for N in orders}
+    cl = {k: mean([c["closure"] for c in cases], k) for k in ("err", "ms", "e2e_ms")}
+
+    def matched(candidates, key="ms"):
         N = next((N for N in sorted(candidates) if plain[N]["err"] <= cl["err"]), None)
-        return N, (plain[N]["ms"] / cl["ms"]) if N is not None else None
+        return N, (plain[N][key] / cl[key]) if N is not None else None
 
     cmp = sorted(compare) if compare is not None else sorted(orders)
     match, speedup = matched(cmp)
     strict_N, strict = matched(orders)
+    e2e = matched(cmp, "e2e_ms")[1]
     out = {"cases": cases, "plain": plain, "closure": cl, "compare_orders": cmp, "matched_N": match,
            "error_matched_speedup": speedup, "strict_matched_N": strict_N, "strict_error_matched_speedup": strict,
+           "e2e_error_matched_speedup": e2e if e2e is None or math.isfinite(e2e) else None,
            "gain_vs_p7": plain[N_BASE]["err"] / cl["err"] if N_BASE in plain and cl["err"] > 0 else None}
     return out

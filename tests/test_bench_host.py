@@ -75,6 +75,11 @@ def test_closure_summary_matches_lowest_accurate_order():
     worse = {"plain": case["plain"], "closure": {"err": 0.5, "ms": 1.0}}
     out = closure.summarize([worse], list(errs))
     assert out["matched_N"] == 7 and out["compare_orders"] == sorted(errs)
+    # the end-to-end ratio takes the same matched order, on the host-clock times
+    timed = {"plain": {N: {"err": errs[N], "ms": ms[N], "e2e_ms": 2 * ms[N]} for N in errs},
+             "closure": {"err": 0.055, "ms": 29.8, "e2e_ms": 40.0}}
+    out = closure.summarize([timed], list(errs), compare=(7, 11, 15))
+    assert out["e2e_error_matched_speedup"] == pytest.approx(2 * 33.6 / 40.0)
     none = {"plain": case["plain"], "closure": {"err": 0.001, "ms": 1.0}}
     out = closure.summarize([none], list(errs))
     assert out["matched_N"] is None and out["error_matched_speedup"] is None
