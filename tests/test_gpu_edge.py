@@ -70,3 +70,35 @@ def test_homogeneous_state_follows_the_relaxation_ode(kernel, precision, tol):
             want = e * u0[j] + q.get(j, 0.0) * (1.0 - e) / c
             assert np.max(np.abs(got[j] - want)) <= tol * max(1.0, abs(want)), (sched, j)
         s.close()
+
+
+@pytest.mark.parametrize("kernel,precision", [("gather", "fp64"), ("tiled_tall", "fp32"), ("tiled_short", "fp32")])
+@pytest.mark.parametrize("schedule", ["literal", "merged"])
+def test_finite_speed_gives_exact_zeros(kernel, precision, schedule):
+    """A source in one cell and a zero initial state: information moves at
+    most two cells per step (odd half, even pair, odd half), so after 6 steps
+    every moment is exactly 0 further than 13 cells from the source (one
+    more for the node grids) -- no halo, ghost or out-of-range box value may
+    leak in.  Scaling the source scales the result (linearity)."""
+    n = 40
+    cell = 1.0 / n
+
+    def problem(alpha):
+        box = lambda t, x, y: alpha * ((np.abs(x - 0.5 - 0.5 * cell) < 0.4 * cell) &  # noqa: E731
+                                       (np.abs(y - 0.5 - 0.5 * cell) < 0.4 * cell)).astype(float)
+        return inputs.Problem(name="point", N=3, ax=(0.0, 1.0, 0.0, 1.0), n=(n, n), bc=("extrapolation", "periodic"),
+                              precision=precision, sigma_a=lambda t, x, y: 0 * x,
+                              sigma_s0=lambda t, x, y: 0.5 + 0 * x, sources=[(0, box)], ic=[], nsteps=6)
+
+    s, got = gpu_run(problem(1.0), schedule=schedule, kernel=kernel)
+    s.close()
+    s2, scaled = gpu_run(problem(-3.5), schedule=schedule, kernel=kernel)
+    s2.close()
+    assert got[0][n // 2, n // 2] != 0
+    jj, ii = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")   # (y, x) like the moments
+    far = np.maximum(np.abs(ii - n // 2), np.abs(jj - n // 2)) > 14
+    tol = 1e-14 if precision == "fp64" else 2e-6
+    for j, (u, v) in enumerate(zip(got, scaled)):
+        assert np.all(u[far[:u.shape[0], :u.shape[1]]] == 0.0), j
+        scale = float(np.max(np.abs(u))) + 1e-300
+        assert np.max(np.abs(v + 3.5 * u)) <= tol * 3.5 * scale, j
