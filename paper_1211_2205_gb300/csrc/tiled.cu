@@ -344,10 +344,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             for (int K = 0; K < 2; ++K) {
                 const int comp = t.fin_comp[e + K];
                 if (comp < 0 || frozen[comp]) { fk[K].push_back(make_int2(-1, -1)); continue; }
-                const int g = gout[P][K];
-                const long long off = (long long)t.fin[e + K].x * pl->geo.cstride[g];
-                if (off > 0x7fffffffll) { pl->err = "state too large for the tiled kernel's 32-bit offsets"; return -8; }
-                fk[K].push_back(make_int2((int)off, src_slot[comp]));
+                fk[K].push_back(make_int2(t.fin[e + K].x, src_slot[comp]));   // component in its grid
             }
         }
         for (int K = 0; K < 2; ++K)

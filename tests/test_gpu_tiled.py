@@ -153,6 +153,51 @@ def test_full_size_random_p39_sampled_across_periodic_edge():
     assert rel_l2(got, ref) <= FP32_TOL
 
 
+def test_state_beyond_32bit_offsets():
+    """P_39 FP32 on 3300 x 3300: every grid holds more than 2^31 values, so
+    the highest components of G11, G21 and G12 start beyond 32-bit element
+    offsets from their grid's base (36 GB of state).  Each component from
+    local index 186 up gets its own bump next to the bench pulse; a 16 x 16
+    window of all 820 moments after 2 steps against the oracle on the window
+    plus a halo, and the high components on their own."""
+    n, nsteps = 3300, 2
+    p = inputs.random_p39(n=n, nsteps=nsteps)
+    s = capi.Stepper.from_problem(p, kernel="tiled", schedule="merged")
+    assert s.kernel == "tiled"
+    assert s.state_bytes() // 4 > 4 * 2 ** 31            # more than 2^31 values per grid on average
+    h = (p.ax[1] - p.ax[0]) / n
+    halo = int(math.ceil(1.5 * nsteps)) + 3
+    w = 16
+    i0, j0 = n // 2 + 200 - halo, n // 2 - 100 - halo
+    xc, yc = p.ax[0] + (i0 + halo + w / 2) * h, p.ax[2] + (j0 + halo + w / 2) * h
+    rng = inputs.SplitMix64(3300)
+    seen, high, bumps = [0, 0, 0, 0], [], []
+    for j in range(s.ncomp):
+        g = s.moment_info(j)["grid"]
+        if seen[g] >= 186:
+            c = rng.uniforms(3)
+            sd = (4 + 4 * c[2]) * h
+            f = inputs.gaussian_std(xc + (c[0] - 0.5) * 8 * h, yc + (c[1] - 0.5) * 8 * h, sd,
+                                    mass=(-1) ** j * 2 * math.pi * sd * sd)
+            X, Y = s.grid_coords(g)
+            s.set_moment(j, f(0.0, X, Y))
+            high.append(j)
+            bumps.append((j, f))
+        seen[g] += 1
+    assert len(high) >= 60
+    s.step(nsteps)
+    sub = _window_problem(p, i0, j0, w + 2 * halo, s.dt)
+    sub = inputs.Problem(**{**sub.__dict__, "ic": list(p.ic) + bumps})
+    o = O.solver_from_problem(sub, dt=s.dt)
+    o.run(nsteps)
+    got = [s.moments_window(j, i0 + halo, j0 + halo, w, w) for j in range(s.ncomp)]
+    ref = [o.U[j].T[halo: halo + w, halo: halo + w] for j in range(s.ncomp)]
+    s.close()
+    assert min(float(np.abs(ref[j]).max()) for j in high) > 1e-3
+    assert rel_l2(got, ref) <= FP32_TOL
+    assert rel_l2([got[j] for j in high], [ref[j] for j in high]) <= FP32_TOL
+
+
 def test_full_size_checkerboard_p13_sampled():
     """The P_13 checkerboard workload at full size (512 x 512, FP32,
     extrapolation boundaries, source block, tiled kernel, merged schedule):
