@@ -344,7 +344,15 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             for (int K = 0; K < 2; ++K) {
                 const int comp = t.fin_comp[e + K];
                 if (comp < 0 || frozen[comp]) { fk[K].push_back(make_int2(-1, -1)); continue; }
-                fk[K].push_back(make_int2(t.fin[e + K].x, src_slot[comp]));   // component in its grid
+                // the component's element offset in units of 32 (pitch, and so the
+                // component stride, is a multiple of 32): 2^36 values per grid
+                const int g = gout[P][K];
+                const long long off = (long long)t.fin[e + K].x * pl->geo.cstride[g];
+                if (pl->geo.cstride[g] % 32 != 0 || off / 32 > 0x7fffffffll) {
+                    pl->err = "state too large for the tiled kernel's offsets";
+                    return -8;
+                }
+                fk[K].push_back(make_int2((int)(off / 32), src_slot[comp]));
             }
         }
         for (int K = 0; K < 2; ++K)

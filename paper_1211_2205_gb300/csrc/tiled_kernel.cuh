@@ -114,8 +114,8 @@ struct Params {
     const float4* coef[2];      // per output kind K, per q step: (cx Pm, cx P0, cx N0, cx Np) of the
                                 // input of kind K and (cy Pm, cy P0, cy N0, cy Np) of the other
                                 // input; zero if absent
-    const int2* fin[2];         // per output kind K, per finalising stage: (the component in its
-                                // grid, or -1 if absent; source slot or -1)
+    const int2* fin[2];         // per output kind K, per finalising stage: (element offset of the
+                                // component / 32, or -1 if absent; source slot or -1)
     const float* const* srcs;   // source arrays by slot
     int* err;                   // bounded-wait failure flag
     int smem_coef_off[2], smem_fin_off[2], smem_part_off, smem_stage_off;   // byte offsets in dynamic smem
@@ -485,7 +485,7 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
                 }
                 const f2 v = f2_fma(aL[j], u, f2_mul(bL[j], w));
                 if (f.x < 0 || !alive) continue;
-                float* dst = pptr[j] + (long)f.x * G.cstride;     // 64-bit: states beyond 2^31 values
+                float* dst = pptr[j] + 32 * (long)f.x;            // 64-bit: states beyond 2^31 values
                 // the pair with one 8-byte store; only a ragged right edge
                 // stores A alone
                 if (pair[j]) {
