@@ -84,7 +84,8 @@ extern "C" {
 #define STARMAP_KERNEL_TILED   2  /* TMA-staged tiles, moments streamed by order (FP32, 2D P_N,
                                      N <= 63); tile height chosen by N, and 5-row tiles at
                                      one CTA per SM where the tables of the 10-row tiles
-                                     leave no room for their ring (N >= 56 or so) */
+                                     leave no room for their ring (N >= 56 or so); up to
+                                     2^36 values per staggered grid */
 #define STARMAP_KERNEL_TILED_TALL  3  /* tiled, 64 x 10 tiles, one CTA per SM (E_UNSUPPORTED where
                                          their tables do not fit, N >= 56 or so) */
 #define STARMAP_KERNEL_TILED_SHORT 4  /* tiled, 64 x 5 tiles, two CTAs per SM */
