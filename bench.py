@@ -232,6 +232,100 @@ def oracle_sample(problem, cells: int, steps: int, keep: bool = False):
     return updates / el, desc, el
 
 
+def _workload_problem(spec):
+    """A workload's problem rebuilt from (name, grid override, smallest
+    instance of a batch): the fields are closures, so worker processes
+    build their own."""
+    name, grid = spec
+    problem, _ = workload(name)
+    if name == "batched_256":
+        problem = min(problem, key=lambda p: p.n[0] * (p.N + 1) ** 2)
+    if grid > 0:
+        problem = inputs.Problem(**{**problem.__dict__, "n": (grid, grid)})
+    return problem
+
+
+def _oracle_proc(spec, cells, warm, steps, barrier, out):
+    """One worker of oracle_all_cores: its own oracle on the same window,
+    `warm` untimed steps, then `steps` timed ones started together with the
+    other workers."""
+    try:
+        from oracle import pn_oracle as O
+        sub, dt = window_problem(_workload_problem(spec), cells)
+        s = O.solver_from_problem(sub, dt=dt)
+        s.run(warm)
+        barrier.wait(timeout=900)
+        t0 = time.perf_counter()
+        s.run(steps)
+        el = time.perf_counter() - t0
+        out.put((sum(u.size for u in s.U) * steps, el, None))
+    except Exception as e:  # reported to the parent, which raises
+        out.put((0, 0.0, repr(e)))
+
+
+def _host_memory_available() -> int:
+    """Bytes this process may still allocate on the host: MemAvailable,
+    lowered to the cgroup's remaining limit where there is one."""
+    avail = None
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    avail = int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    try:
+        with open("/sys/fs/cgroup/memory.max") as f:
+            lim = f.read().strip()
+        with open("/sys/fs/cgroup/memory.current") as f:
+            cur = int(f.read().strip())
+        if lim.isdigit():
+            left = int(lim) - cur
+            avail = left if avail is None else min(avail, left)
+    except OSError:
+        pass
+    return avail if avail is not None else 8 * 2 ** 30
+
+
+def oracle_all_cores(spec, cells: int, warm: int, steps: int, workers: int = 0):
+    """The oracle on every host core at once: one spawned process per core
+    (no fork after CUDA is up), each running the same window; they start the
+    timed steps together at a barrier.  Returns (updates/s summed over the
+    workers, processes, seconds of the slowest)."""
+    import multiprocessing
+    if not workers:
+        # one process per core, as many as half the free host memory holds
+        # (a worker peaks near five times its window's state)
+        problem = _workload_problem(spec)
+        ncomp = (problem.N + 1) * (problem.N + 2) // 2 if problem.system == "pn2d" else problem.N + 1
+        per = 6 * ncomp * (cells + 1) ** 2 * 8
+        workers = max(1, min(os.cpu_count() or 1, 64, _host_memory_available() // 2 // per))
+    ctx = multiprocessing.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_proc, args=(spec, cells, warm, steps, barrier, out)) for _ in range(workers)]
+    # one thread per process: the children's numpy reads these at import
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({k: "1" for k in saved})
+    try:
+        for pr in procs:
+            pr.start()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    res = [out.get(timeout=1800) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+    errs = [r[2] for r in res if r[2]]
+    if errs:
+        raise RuntimeError(f"oracle worker failed: {errs[0]}")
+    el = max(r[1] for r in res)
+    return sum(r[0] for r in res) / el, workers, el
+
+
 def window_error(problem, cells: int, steps: int, ref, kernel: str):
     """Relative L2 error over all moments of the GPU path (the workload's
     precision and kernel) against the FP64 oracle on the oracle sample's
@@ -262,22 +356,20 @@ def run_reference(args):
         desc += f"; oracle sample from the smallest instance ({problem.name})"
     cells = {"random_p39": 48, "checkerboard_p13": 96, "gaussian_p5": 64, "paper_p5": 100,
              "batched_256": 64}[args.workload]
-    vals = []
-    for _ in range(args.warmup):
-        oracle_sample(problem, cells, 1)
-    el_total = 0.0
-    for _ in range(args.steps):
-        v, sample, el = oracle_sample(problem, cells, 1)
-        vals.append(v)
-        el_total += el
-    value = statistics.median(vals)
+    # every host core runs the oracle on the same window, W untimed and K
+    # timed steps, started together; one core alone for comparison
+    value, workers, el = oracle_all_cores((args.workload, 0), cells, args.warmup, args.steps)
+    v1, sample, el1 = oracle_sample(problem, cells, args.steps)
+    sample = sample.replace(f"{args.steps} steps after 1 untimed",
+                            f"{args.steps} steps after {args.warmup} untimed, in each of {workers} processes at once")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": el_total / max(1, args.steps) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": el / max(1, args.steps) * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "sample": f"{cells}x{cells} window"},
-        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": workers, "kind": "oracle", "sample": sample,
+                         "single_core": v1},
         "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -454,7 +546,9 @@ def run_native(args):
         cells, nst = {"random_p39": (192, 4), "checkerboard_p13": (256, 8), "gaussian_p5": (64, 100),
                       "paper_p5": (100, steps_to_final - 1)}[args.workload]
         v, sample, el, sol = oracle_sample(problem, cells, nst, keep=True)
-        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+        va, workers, _ = oracle_all_cores((args.workload, args.grid), cells, 1, nst)
+        line["cpu_baseline"] = {"value": va, "unit": "updates/s", "cores": workers, "kind": "oracle",
+                                "sample": sample + f", in each of {workers} processes at once", "single_core": v}
         line["precision"] = window_error(problem, cells, nst, sol, args.kernel)
     s.close()
     if rank == 0:
@@ -556,8 +650,10 @@ def run_batch(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         small = min(problems, key=lambda p: p.n[0] * (p.N + 1) ** 2)
         v, sample, el = oracle_sample(small, 64, 6)[:3]
-        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                                "sample": sample + f" (instance {small.name})"}
+        va, workers, _ = oracle_all_cores(("batched_256", 0), 64, 1, 6)
+        line["cpu_baseline"] = {"value": va, "unit": "updates/s", "cores": workers, "kind": "oracle",
+                                "sample": sample + f" (instance {small.name}), in each of {workers} processes at once",
+                                "single_core": v}
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -57,6 +57,9 @@ def test_reference_arm_prints_contract_line():
     assert line["impl"] == "reference"
     assert line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+    # every host core runs the oracle at once; the single-core figure is beside it
+    assert 1 <= line["cpu_baseline"]["cores"] <= (os.cpu_count() or 1)
+    assert line["cpu_baseline"]["single_core"] > 0
 
 
 def test_closure_summary_matches_lowest_accurate_order():
