@@ -382,6 +382,16 @@ int starmap_mlp_loss_grad(starmap_mlp_t* net, const float* X, const float* T, co
  * step. */
 int starmap_mlp_train_step(starmap_mlp_t* net, const float* X, const float* T, const int32_t* idx,
                            size_t B, float lr, float* loss);
+/* Training-input noise (not in the paper; a regulariser of the closure's
+ * training): Xn[m][c] = X[m][c] + sigma * g for c < cols, Xn[m][c] = X[m][c]
+ * for cols <= c < 38, over M rows of 38 floats.  g is a standard normal
+ * drawn from a counter-based stream (the SplitMix64 finaliser of
+ * seed * 0x9e3779b97f4a7c15 + the element's index, Box-Muller), so the same
+ * seed gives the same noise.  X and Xn are caller-owned device pointers
+ * (distinct or equal); queued on the network's stream.  E_ARG for cols
+ * outside [0, 38] or a negative or non-finite sigma. */
+int starmap_mlp_perturb_inputs(starmap_mlp_t* net, const float* X, float* Xn, size_t M, int cols, float sigma,
+                               unsigned long long seed);
 /* ------------------------------------------------------------- batches
  * Not in the paper: many independent problems advanced together.  A batch
  * holds `count` FP32 2D P_N instances (any grid size, N up to the order at

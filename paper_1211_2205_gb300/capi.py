@@ -130,6 +130,8 @@ def lib():
                                                  ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
         "starmap_mlp_train_step": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.c_size_t, ctypes.c_float, ctypes.c_void_p]),
+        "starmap_mlp_perturb_inputs": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                                      ctypes.c_int, ctypes.c_float, ctypes.c_ulonglong]),
         "starmap_mlp_steps": (ctypes.c_long, [H]),
         "starmap_mlp_set_engine": (ctypes.c_int, [H, ctypes.c_int]),
         "starmap_set_closure_engine": (ctypes.c_int, [H, ctypes.c_int]),
@@ -538,6 +540,11 @@ class Network:
     def train_step(self, X, T, B: int, lr: float, loss=None, idx=None):
         self._check(self._L.starmap_mlp_train_step(self._h, _addr(X), _addr(T), _addr(idx), int(B), float(lr),
                                                    _addr(loss)))
+
+    def perturb_inputs(self, X, Xn, M: int, cols: int, sigma: float, seed: int):
+        """Xn = X plus N(0, sigma^2) noise on the first cols inputs of each row."""
+        self._check(self._L.starmap_mlp_perturb_inputs(self._h, _addr(X), _addr(Xn), int(M), int(cols),
+                                                       float(sigma), int(seed) & 0xFFFFFFFFFFFFFFFF))
 
     def sync(self):
         self._check(self._L.starmap_mlp_sync(self._h))

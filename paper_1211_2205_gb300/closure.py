@@ -132,9 +132,13 @@ class TrainResult:
     steps: int = 0
 
 
-def train(data: SampleSet, steps: int = 6000, batch: int = 8192, lr0: float = 2e-3, lr1: float = 2e-5,
-          seed: int = 0, log_every: int = 200) -> TrainResult:
-    """Minibatch Adam with cosine decay from lr0 to lr1."""
+def train(data: SampleSet, steps: int = 48000, batch: int = 8192, lr0: float = 2e-3, lr1: float = 2e-5,
+          seed: int = 0, log_every: int = 200, noise: float = 0.05) -> TrainResult:
+    """Minibatch Adam with cosine decay from lr0 to lr1.  noise: standard
+    deviation of Gaussian noise added to the 36 normalised moment inputs,
+    drawn afresh for every pass over the samples (the closed run feeds the
+    network states with errors of its own; noise in training makes it
+    tolerate them)."""
     torch = _torch()
     net = capi.Network(init_params(seed))
     rng = np.random.default_rng(seed)
@@ -142,14 +146,20 @@ def train(data: SampleSet, steps: int = 6000, batch: int = 8192, lr0: float = 2e
     res = TrainResult(params=np.empty(0))
     idx = None
     pos = data.count
+    X = torch.empty_like(data.X) if noise > 0 else data.X
+    epoch = 0
     torch.cuda.synchronize()
     for it in range(steps):
         if pos + batch > data.count:
             idx = torch.from_numpy(data.index[rng.permutation(data.count)]).cuda()
+            if noise > 0:
+                net.perturb_inputs(data.X, X, data.X.shape[0], capi.MLP_INPUTS - 2, noise,
+                                   (seed << 20) + epoch)
+            epoch += 1
             torch.cuda.synchronize()
             pos = 0
         lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * it / max(1, steps - 1)))
-        net.train_step(data.X, data.T, batch, lr, loss=loss if (it % log_every == 0) else None,
+        net.train_step(X, data.T, batch, lr, loss=loss if (it % log_every == 0) else None,
                        idx=idx[pos:pos + batch])
         pos += batch
         if it % log_every == 0:

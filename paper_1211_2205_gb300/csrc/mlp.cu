@@ -749,6 +749,32 @@ __global__ void k_closure_nodes(const ClosureArgs<T> A, const float* __restrict_
     }
 }
 
+// Training-input noise: Xn[m][c] = X[m][c] + sigma g(seed, m NIN + c) for
+// c < cols, a copy of X[m][c] otherwise.  g is a standard normal from a
+// counter-based stream: the SplitMix64 finaliser (Steele, Lea & Flood 2014)
+// of seed * golden + counter gives two 32-bit uniforms in (0, 1), turned
+// into one normal by the Box-Muller transform (Box & Muller 1958).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_perturb(const float* X, float* Xn, long total, int cols, float sigma,
+                          unsigned long long seed) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        float v = X[e];
+        if ((int)(e % NIN) < cols) {
+            const unsigned long long z = splitmix64(seed * 0x9e3779b97f4a7c15ull + (unsigned long long)e);
+            const float u1 = ((float)(unsigned)(z >> 32) + 0.5f) * 2.3283064365386963e-10f;   // (0, 1)
+            const float u2 = ((float)(unsigned)(z & 0xffffffffu) + 0.5f) * 2.3283064365386963e-10f;
+            v += sigma * sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+        }
+        Xn[e] = v;
+    }
+}
+
 int status(cudaError_t e) { return e == cudaSuccess ? 0 : -4; }
 
 template <class K>
@@ -791,6 +817,15 @@ int loss_grad(const float* X, const float* T, const int* idx, long B, const Pack
     k_loss_grad<<<(unsigned)blocks, THREADS, SMEM_TRAIN, (cudaStream_t)stream>>>(X, T, idx, B, P, part);
     if (cudaGetLastError() != cudaSuccess) return -4;
     k_reduce_grad<<<(NPARAM + 1 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(part, blocks, grad, loss);
+    return status(cudaGetLastError());
+}
+
+int perturb(const float* X, float* Xn, long M, int cols, float sigma, unsigned long long seed, void* stream) {
+    const long total = M * NIN;
+    if (total <= 0) return 0;
+    long blocks = (total + 255) / 256;
+    if (blocks > 32L * sm_count()) blocks = 32L * sm_count();
+    k_perturb<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(X, Xn, total, cols, sigma, seed);
     return status(cudaGetLastError());
 }
 

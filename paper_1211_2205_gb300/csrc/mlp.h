@@ -65,6 +65,9 @@ int loss_grad(const float* X, const float* T, const int* idx, long B, const Pack
 long grad_blocks(long B);
 int adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps, long step,
          void* stream);
+// Xn = X with N(0, sigma^2) noise on the first `cols` of the NIN inputs of
+// each of the M rows (counter-based: the same seed gives the same noise).
+int perturb(const float* X, float* Xn, long M, int cols, float sigma, unsigned long long seed, void* stream);
 template <class T> int samples(const ClosureArgs<T>& A, float* X, float* scale, float* tgt, void* stream);
 // Closure evaluation (features, network, order-8 moments written to G11 and
 // G22); scratch holds closure_scratch_floats(n_x n_y) floats; n_x n_y must

@@ -186,6 +186,16 @@ int starmap_mlp_train_step(starmap_mlp_t* net, const float* X, const float* T, c
     return STARMAP_OK;
 }
 
+int starmap_mlp_perturb_inputs(starmap_mlp_t* net, const float* X, float* Xn, size_t M, int cols, float sigma,
+                               unsigned long long seed) {
+    if (!net) return STARMAP_E_ARG;
+    if (M == 0) return STARMAP_OK;
+    if (!X || !Xn || cols < 0 || cols > mlp::NIN || !(sigma >= 0.f) || !std::isfinite(sigma))
+        return mfail(net, STARMAP_E_ARG, "perturb_inputs needs X, Xn, 0 <= cols <= 38 and a finite sigma >= 0");
+    if (mlp::perturb(X, Xn, (long)M, cols, sigma, seed, net->stream)) MCK(cudaGetLastError(), "perturb");
+    return STARMAP_OK;
+}
+
 long starmap_mlp_steps(const starmap_mlp_t* net) { return net ? net->steps : 0; }
 
 int starmap_mlp_sync(starmap_mlp_t* net) {

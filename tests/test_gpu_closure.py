@@ -358,3 +358,37 @@ def test_tcgen05_closed_run_matches_mma_sync_run():
     plain.run(p.nsteps)
     effect = rel_l2([u.T for u in plain.U], runs[0][:36])
     assert rel_l2(runs[1][:36], runs[0][:36]) <= 0.05 * effect
+
+
+def test_input_noise_is_gaussian_and_reproducible():
+    """Training-input noise: the first 36 inputs get N(0, sigma^2) noise from
+    a counter-based stream (same seed, same noise), the two material inputs
+    are copied exactly; in place gives the same result."""
+    M, sigma = 200000, 0.1
+    rng = np.random.default_rng(7)
+    X = rng.normal(size=(M, C.N_IN)).astype(np.float32)
+    net = capi.Network(_params(3))
+    Xd = _dev(X)
+    A = torch.empty_like(Xd)
+    B = torch.empty_like(Xd)
+    D = torch.empty_like(Xd)
+    torch.cuda.synchronize()
+    net.perturb_inputs(Xd, A, M, 36, sigma, 11)
+    net.perturb_inputs(Xd, B, M, 36, sigma, 11)
+    net.perturb_inputs(Xd, D, M, 36, sigma, 12)
+    net.sync()
+    a, b, d = A.cpu().numpy(), B.cpu().numpy(), D.cpu().numpy()
+    assert np.array_equal(a, b) and not np.array_equal(a, d)
+    assert np.array_equal(a[:, 36:], X[:, 36:])
+    n = (a[:, :36].astype(np.float64) - X[:, :36]) / sigma
+    k = n.size
+    assert abs(n.mean()) < 5 / math.sqrt(k)
+    assert abs(n.std() - 1.0) < 5e-3
+    assert abs(np.mean(np.abs(n) < 1.0) - 0.682689) < 3e-3          # normal, not uniform or clipped
+    assert abs(np.mean(np.abs(n) < 2.0) - 0.954500) < 2e-3
+    assert abs(float(np.corrcoef(n[:, 0], n[:, 1])[0, 1])) < 0.02      # independent across columns
+    net.perturb_inputs(Xd, Xd, M, 36, sigma, 11)                      # in place
+    net.sync()
+    assert np.array_equal(Xd.cpu().numpy(), a)
+    with pytest.raises(capi.StarmapError):
+        net.perturb_inputs(Xd, A, M, 39, sigma, 1)
