@@ -316,7 +316,19 @@ def oracle_all_cores(spec, cells: int, warm: int, steps: int, workers: int = 0):
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    res = [out.get(timeout=1800) for _ in procs]
+    import queue
+    res, waited = [], 0.0
+    while len(res) < workers:
+        try:
+            res.append(out.get(timeout=5))
+        except queue.Empty:
+            waited += 5
+            dead = [pr.exitcode for pr in procs if pr.exitcode not in (None, 0)]
+            if dead or waited > 1800:
+                for pr in procs:
+                    if pr.is_alive():
+                        pr.terminate()
+                raise RuntimeError(f"oracle workers failed (exit codes {dead})" if dead else "oracle workers timed out")
     for pr in procs:
         pr.join(timeout=60)
     errs = [r[2] for r in res if r[2]]
