@@ -158,6 +158,30 @@ int starmap_host_matrices(int system, int N, int ncomp_capacity,
  * |mu| > 1, short out). */
 int starmap_direction_moments(int system, int N, double mu, double phi, double* out, size_t count);
 
+/* The tiled kernel's schedule of one pass, built on the host exactly as
+ * the stepper builds it (no GPU needed; for tests and inspection).  The
+ * pass updates the components of order parity `parity` (1: the odd pass
+ * of eq. solution_operator_full_step, 0: the even pair) from half-grid
+ * differences of the other parity, streaming the inputs by order
+ * (section 5.5, with the reach of Lemma 2).  frozen_top: the order-N
+ * components are not updated (a closure sets them).  Outputs, each may be
+ * NULL, filled up to its capacity (counts always reports the full sizes):
+ *   stages : 4 ints per pipeline stage, global component indices of the
+ *            stage's input R, input I, finalised output R and output I
+ *            (-1 where absent), in consumer order;
+ *   coef   : 16 floats per streamed input: for the four targets in reach
+ *            (order l'-1 with q'-1 and q', order l'+1 with q' and q'+1) the
+ *            coefficient -Mx[target][input]/dx of the input's own kind, then
+ *            -My[target][input]/dy of the other kind, each value twice (one
+ *            per point of an f32x2 pair); zero where a target is absent;
+ *   fin    : per finalising event, the component finalised (-1: no I part);
+ *   counts : {stages, streamed inputs, finalising events}.
+ * Errors: E_ARG (N outside 1..63, parity not 0/1), E_UNSUPPORTED (a
+ * placement the kernel does not cover). */
+int starmap_tiled_schedule(int N, int parity, int frozen_top, double dx, double dy,
+                           int* stages, size_t stage_capacity, float* coef, size_t coef_capacity,
+                           int* fin, size_t fin_capacity, long* counts);
+
 /* E(c) = (exp(c) - 1)/c, section 5.6 (series for |c| <= 2e-4), applied to
  * count values in place.  Host function, for tests. */
 int starmap_host_expm1div(double* c, size_t count);

@@ -81,6 +81,10 @@ def lib():
         "starmap_config_default": (None, [ctypes.POINTER(Config)]),
         "starmap_host_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _ip, _ip, _dp]),
         "starmap_host_expm1div": (ctypes.c_int, [_dp, ctypes.c_size_t]),
+        "starmap_tiled_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                                  ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
+                                                  ctypes.c_void_p]),
         "starmap_direction_moments": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                      _dp, ctypes.c_size_t]),
         "starmap_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(H)]),
@@ -198,6 +202,27 @@ def direction_moments(N: int, mu: float, phi: float) -> np.ndarray:
     if rc != OK:
         raise StarmapError(rc, L.starmap_last_error(None).decode())
     return out
+
+
+def tiled_schedule(N: int, parity: int, frozen_top: bool = False, dx: float = 1.0, dy: float = 1.0):
+    """The tiled kernel's schedule of one pass (host only): stages (S, 4)
+    global components (input R, input I, output R, output I; -1 absent),
+    coefficient rows (R, 16) and the finalised component per event."""
+    L = lib()
+    counts = np.zeros(3, dtype=np.int64)
+    rc = L.starmap_tiled_schedule(int(N), int(parity), int(bool(frozen_top)), float(dx), float(dy),
+                                  None, 0, None, 0, None, 0, counts.ctypes.data)
+    if rc != OK:
+        raise StarmapError(rc, L.starmap_last_error(None).decode())
+    st = np.zeros((int(counts[0]), 4), dtype=np.int32)
+    co = np.zeros((int(counts[1]), 16), dtype=np.float32)
+    fi = np.zeros(int(counts[2]), dtype=np.int32)
+    rc = L.starmap_tiled_schedule(int(N), int(parity), int(bool(frozen_top)), float(dx), float(dy),
+                                  st.ctypes.data, st.shape[0], co.ctypes.data, co.shape[0], fi.ctypes.data,
+                                  fi.size, counts.ctypes.data)
+    if rc != OK:
+        raise StarmapError(rc, L.starmap_last_error(None).decode())
+    return st, co, fi
 
 
 def selftest_bounded_wait() -> int:

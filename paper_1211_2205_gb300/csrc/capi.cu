@@ -526,6 +526,25 @@ int starmap_direction_moments(int system, int N, double mu, double phi, double* 
     return STARMAP_OK;
 }
 
+int starmap_tiled_schedule(int N, int parity, int frozen_top, double dx, double dy,
+                           int* stages, size_t stage_capacity, float* coef, size_t coef_capacity,
+                           int* fin, size_t fin_capacity, long* counts) {
+    std::vector<int> st, fi;
+    std::vector<float> co;
+    std::string err;
+    const int rc = tiled_schedule(N, parity, frozen_top != 0, dx, dy, st, co, fi, err);
+    if (rc) return fail(nullptr, rc == -8 ? STARMAP_E_UNSUPPORTED : STARMAP_E_ARG, err);
+    if (stages) std::copy(st.begin(), st.begin() + std::min(st.size(), stage_capacity * 4), stages);
+    if (coef) std::copy(co.begin(), co.begin() + std::min(co.size(), coef_capacity * 16), coef);
+    if (fin) std::copy(fi.begin(), fi.begin() + std::min(fi.size(), fin_capacity), fin);
+    if (counts) {
+        counts[0] = (long)(st.size() / 4);
+        counts[1] = (long)(co.size() / 16);
+        counts[2] = (long)fi.size();
+    }
+    return STARMAP_OK;
+}
+
 int starmap_host_expm1div(double* c, size_t count) {
     if (!c && count) return STARMAP_E_ARG;
     for (size_t i = 0; i < count; ++i) c[i] = expm1div(c[i]);

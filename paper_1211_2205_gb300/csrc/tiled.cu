@@ -272,6 +272,32 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
 
 }  // namespace
 
+int tiled_schedule(int N, int P, bool frozen_top, double dx, double dy, std::vector<int>& stages,
+                   std::vector<float>& coef, std::vector<int>& fin, std::string& err) {
+    if (N < 1 || N > MAXN || (P != 0 && P != 1)) { err = "schedule needs 1 <= N <= 63 and parity 0 or 1"; return -1; }
+    SystemMatrices sys;
+    if (!build_system(0, N, sys, err)) return -1;
+    TiledPlan plan;
+    plan.N = N;
+    std::vector<int> cls(sys.ncomp, 0);
+    std::vector<char> frozen(sys.ncomp, 0);
+    for (int j = 0; j < sys.ncomp; ++j) frozen[j] = frozen_top && sys.moms[j].l == N;
+    PassTables t;
+    if (!build_pass(&plan, sys, cls, frozen, P, dx, dy, t, err)) return -8;
+    // local indices of the stage slots back to global components
+    std::vector<int> inv(4 * (sys.ncomp + 1), -1);
+    for (int j = 0; j < sys.ncomp; ++j) inv[sys.moms[j].grid * (sys.ncomp + 1) + sys.moms[j].local] = j;
+    const int grid_of_slot[4] = {P == 1 ? 0 : 1, P == 1 ? 3 : 2, P == 1 ? 1 : 0, P == 1 ? 2 : 3};
+    stages.clear();
+    for (const int4& st : t.stages) {
+        const int v[4] = {st.x, st.y, st.z, st.w};
+        for (int k = 0; k < 4; ++k) stages.push_back(v[k] < 0 ? -1 : inv[grid_of_slot[k] * (sys.ncomp + 1) + v[k]]);
+    }
+    coef = t.coef;
+    fin = t.fin_comp;
+    return 0;
+}
+
 bool tiled_supported(int system, int N, int precision) {
     return system == 0 && precision == 1 && N >= 1 && N <= MAXN && encode_fn() != nullptr;
 }

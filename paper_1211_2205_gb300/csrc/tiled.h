@@ -23,6 +23,12 @@ struct TiledGeometry {
 int tiled_default_variant(int N);
 
 bool tiled_supported(int system, int N, int precision);
+// Host only: the stage list of pass P (parity of its outputs) as global
+// components (4 per stage: input R, input I, output R, output I; -1 absent),
+// its coefficient rows (16 floats per input, each value twice) and the
+// component finalised at each finalising event (-1: absent I).
+int tiled_schedule(int N, int P, bool frozen_top, double dx, double dy, std::vector<int>& stages,
+                   std::vector<float>& coef, std::vector<int>& fin, std::string& err);
 int tiled_create(const TiledGeometry& geo, TiledPlan** out);
 // frozen[j] != 0: component j is read but never written (closure moments)
 int tiled_update(TiledPlan* plan, const SystemMatrices& sys, const std::vector<int>& comp_class,
