@@ -456,6 +456,18 @@ int  starmap_batch_step(starmap_batch_t* b, long nsteps);
  * instance (E_TIMEOUT). */
 int  starmap_batch_sync(starmap_batch_t* b);
 
+/* The work-unit plan starmap_batch_create uses, computed on the host (no
+ * GPU; for tests and inspection).  Instance i has tiles_x[i] x tiles_y[i]
+ * tiles of cost[i] pipeline stages each; slots = CTAs the persistent grid
+ * may hold.  items gets 4 ints per item (instance, first tile, tile count,
+ * tile stride: the item covers tiles first + k * stride, k < count, tile t
+ * at column t mod tiles_x, row t / tiles_x); off gets grid + 1 ints (CTA c
+ * runs items off[c] .. off[c + 1] - 1); counts = {grid, items}.  Outputs
+ * may be NULL and are filled up to their capacities.  E_ARG for count or
+ * slots < 1 or a shape with no tiles. */
+int starmap_batch_plan(const int* tiles_x, const int* tiles_y, const int* cost, int count, int slots,
+                       int* items, size_t item_capacity, int* off, size_t off_capacity, long* counts);
+
 /* Inference engine of starmap_mlp_forward (STARMAP_MLP_ENGINE_*). */
 int  starmap_mlp_set_engine(starmap_mlp_t* net, int engine);
 /* Number of Adam steps taken since creation or the last set_params. */

@@ -81,6 +81,9 @@ def lib():
         "starmap_config_default": (None, [ctypes.POINTER(Config)]),
         "starmap_host_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _ip, _ip, _dp]),
         "starmap_host_expm1div": (ctypes.c_int, [_dp, ctypes.c_size_t]),
+        "starmap_batch_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                              ctypes.c_size_t, ctypes.c_void_p]),
         "starmap_tiled_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                   ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                                   ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
@@ -223,6 +226,27 @@ def tiled_schedule(N: int, parity: int, frozen_top: bool = False, dx: float = 1.
     if rc != OK:
         raise StarmapError(rc, L.starmap_last_error(None).decode())
     return st, co, fi
+
+
+def batch_plan(tiles_x, tiles_y, cost, slots: int):
+    """The batch's work-unit plan (host only): (items (I, 4): instance,
+    first tile, tile count, tile stride; off (grid + 1,))."""
+    L = lib()
+    tx = np.ascontiguousarray(tiles_x, dtype=np.int32)
+    ty = np.ascontiguousarray(tiles_y, dtype=np.int32)
+    c = np.ascontiguousarray(cost, dtype=np.int32)
+    counts = np.zeros(2, dtype=np.int64)
+    rc = L.starmap_batch_plan(tx.ctypes.data, ty.ctypes.data, c.ctypes.data, int(tx.size), int(slots),
+                              None, 0, None, 0, counts.ctypes.data)
+    if rc != OK:
+        raise StarmapError(rc, L.starmap_last_error(None).decode())
+    items = np.zeros((int(counts[1]), 4), dtype=np.int32)
+    off = np.zeros(int(counts[0]) + 1, dtype=np.int32)
+    rc = L.starmap_batch_plan(tx.ctypes.data, ty.ctypes.data, c.ctypes.data, int(tx.size), int(slots),
+                              items.ctypes.data, items.shape[0], off.ctypes.data, off.size, counts.ctypes.data)
+    if rc != OK:
+        raise StarmapError(rc, L.starmap_last_error(None).decode())
+    return items, off
 
 
 def selftest_bounded_wait() -> int:

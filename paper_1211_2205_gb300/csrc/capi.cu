@@ -477,9 +477,17 @@ void release(starmap_t* h) {
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
+
 }  // namespace
 
 extern "C" {
+
+namespace {
+// Tile grid of a batch instance and the cost of one of its tiles (pipeline
+// stages of its longer pass), and the work-unit plan of a batch (below).
+struct BatchShape { int tx, ty, cost; };
+int batch_plan(const std::vector<BatchShape>& shapes, int slots, std::vector<int4>& items, std::vector<int>& off);
+}  // namespace
 
 void starmap_config_default(starmap_config* c) {
     if (!c) return;
@@ -542,6 +550,29 @@ int starmap_tiled_schedule(int N, int parity, int frozen_top, double dx, double 
         counts[1] = (long)(co.size() / 16);
         counts[2] = (long)fi.size();
     }
+    return STARMAP_OK;
+}
+
+int starmap_batch_plan(const int* tiles_x, const int* tiles_y, const int* cost, int count, int slots,
+                       int* items, size_t item_capacity, int* off, size_t off_capacity, long* counts) {
+    if (count < 1 || slots < 1 || !tiles_x || !tiles_y || !cost)
+        return fail(nullptr, STARMAP_E_ARG, "batch_plan needs count >= 1, slots >= 1 and the shape arrays");
+    std::vector<BatchShape> shapes(count);
+    for (int i = 0; i < count; ++i) {
+        if (tiles_x[i] < 1 || tiles_y[i] < 1 || cost[i] < 0 || (long long)tiles_x[i] * tiles_y[i] > 0x7fffffffll)
+            return fail(nullptr, STARMAP_E_ARG, "batch_plan: bad shape of instance " + std::to_string(i));
+        shapes[i] = {tiles_x[i], tiles_y[i], cost[i]};
+    }
+    std::vector<int4> it;
+    std::vector<int> of;
+    const int grid = batch_plan(shapes, slots, it, of);
+    if (grid < 1) return fail(nullptr, STARMAP_E_ARG, "too many tiles in one batch");
+    if (items)
+        for (size_t e = 0; e < std::min(it.size(), item_capacity); ++e) {
+            items[4 * e] = it[e].x; items[4 * e + 1] = it[e].y; items[4 * e + 2] = it[e].z; items[4 * e + 3] = it[e].w;
+        }
+    if (off) std::copy(of.begin(), of.begin() + std::min(of.size(), off_capacity), off);
+    if (counts) { counts[0] = grid; counts[1] = (long)it.size(); }
     return STARMAP_OK;
 }
 
@@ -1174,6 +1205,100 @@ int batch_issue(starmap_batch_t* b, long n) {
 }  // namespace
 
 namespace {
+// Work units of all instances (heaviest instance first) form one list
+// dealt to the resident CTAs (below) so that every CTA gets about the same
+// work and at any time the CTAs work on one contiguous band of the list
+// (x-neighbouring units run side by side and share their halo columns in
+// L2).  A unit is
+//  * for short tiles (few stages): a strip of consecutive tiles in y,
+//    about STRIP_STAGES stages long, streamed through one pipeline (the
+//    next tile's halo row is still in L2; setup, fill and drain are paid
+//    once per strip);
+//  * for long tiles: one tile; a CTA's tiles of one instance are then a
+//    single run with stride grid (the band of tiles moves down the grid in
+//    lockstep, so vertical neighbours also share halo rows in L2).
+// Items are (instance, first tile, tile count, tile stride); CTA c runs
+// items[off[c]] .. items[off[c + 1] - 1].  Returns the grid (0 if the
+// lists would not fit 32-bit indices).
+int batch_plan(const std::vector<BatchShape>& shapes, int slots, std::vector<int4>& items, std::vector<int>& off) {
+    const int count = (int)shapes.size();
+    constexpr int STRIP_MAX_STAGES = 48;     // tiles up to this long go in strips
+    // stages per strip: 192, halved while the list would hold fewer than
+    // four units per CTA (a few small instances must still fill the GPU)
+    std::vector<int> strip(count, 1);
+    long long total_units = 0;
+    for (int strip_stages = 192;; strip_stages /= 2) {
+        total_units = 0;
+        for (int i = 0; i < count; ++i) {
+            const int tx = shapes[i].tx, ty = shapes[i].ty;
+            const int c = std::max(1, shapes[i].cost);
+            strip[i] = c <= STRIP_MAX_STAGES ? std::max(1, std::min(ty, (strip_stages + c - 1) / c)) : 1;
+            total_units += strip[i] > 1 ? (long long)tx * ((ty + strip[i] - 1) / strip[i]) : (long long)tx * ty;
+        }
+        if (total_units >= 4LL * slots || strip_stages <= 1) break;
+    }
+    const int grid = (int)std::max(1LL, std::min<long long>(total_units, std::max(1, slots)));
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (double)shapes[a].tx * shapes[a].ty * shapes[a].cost > (double)shapes[c].tx * shapes[c].ty * shapes[c].cost;
+    });
+    // Instances are dealt in that order, each to the CTAs by current load:
+    // the strips of a short-tile instance in chunks of `grid` units, the
+    // heaviest units of a chunk to the least-loaded CTAs; the tiles of a
+    // long-tile instance as one strided run per CTA (residue k: tiles k,
+    // k + grid, ...), the residues with one tile more to the least-loaded
+    // CTAs.  Every CTA still works through the instances in the same order,
+    // so at any time the CTAs share one band of the list.
+    std::vector<std::vector<int4>> per(grid);
+    std::vector<long long> load(grid, 0);
+    std::vector<int> ctas(grid);
+    auto by_load = [&]() {
+        for (int c = 0; c < grid; ++c) ctas[c] = c;
+        std::stable_sort(ctas.begin(), ctas.end(), [&](int a, int c) { return load[a] < load[c]; });
+    };
+    std::vector<int4> units;
+    for (int i : order) {
+        const int tx = shapes[i].tx, ty = shapes[i].ty;
+        const long long c = shapes[i].cost;
+        if (strip[i] > 1) {
+            const int S = strip[i];
+            units.clear();
+            for (int y0 = 0; y0 < ty; y0 += S)
+                for (int x = 0; x < tx; ++x) units.push_back(make_int4(i, y0 * tx + x, std::min(S, ty - y0), tx));
+            for (size_t r = 0; r < units.size(); r += (size_t)grid) {
+                const size_t end = std::min(units.size(), r + (size_t)grid);
+                std::stable_sort(units.begin() + r, units.begin() + end,
+                                 [](const int4& a, const int4& b) { return a.z > b.z; });
+                by_load();
+                for (size_t e = r; e < end; ++e) {
+                    const int cta = ctas[e - r];
+                    per[cta].push_back(units[e]);
+                    load[cta] += (long long)units[e].z * c;
+                }
+            }
+        } else {
+            const int tiles = tx * ty, q = tiles / grid, rem = tiles % grid;
+            by_load();
+            for (int k = 0; k < grid; ++k) {
+                const int n = q + (k < rem ? 1 : 0);
+                if (n == 0) continue;
+                per[ctas[k]].push_back(make_int4(i, k, n, grid));
+                load[ctas[k]] += (long long)n * c;
+            }
+        }
+    }
+    items.clear();
+    off.assign(grid + 1, 0);
+    for (int cta = 0; cta < grid; ++cta) {
+        off[cta] = (int)items.size();
+        items.insert(items.end(), per[cta].begin(), per[cta].end());
+        if (items.size() > 0x7fffffffu) return 0;
+    }
+    off[grid] = (int)items.size();
+    return grid;
+}
+
 // Build a batch whose instances use tile height `variant` (0: 10 rows, 1: 5 rows).
 int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batch_t** out) {
     *out = nullptr;
@@ -1198,8 +1323,7 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
         if (e != cudaSuccess) return bail(bfail(b, STARMAP_E_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
         b->own_stream = true;
     }
-    struct Inst { int tiles, cost; };       // tiles and per-tile cost (stages of the longer parity)
-    std::vector<Inst> shapes;
+    std::vector<BatchShape> shapes;
     b->variant = variant;
     for (int i = 0; i < count; ++i) {
         starmap_config c = cfgs[i];
@@ -1218,79 +1342,17 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
         const int cost = std::max(tiled_stage_count(h->tiled, 0), tiled_stage_count(h->tiled, 1));
         if ((long long)tx * ty * cost > 0x7fffffffll)
             return bail(bfail(b, STARMAP_E_ARG, "batch instance " + std::to_string(i) + ": too many pipeline stages"));
-        shapes.push_back({tx * ty, cost});
+        shapes.push_back({tx, ty, cost});
         b->smem = std::max(b->smem, std::max(tiled_smem_bytes(h->tiled, 0), tiled_smem_bytes(h->tiled, 1)));
     }
-    // Work units of all instances (heaviest instance first) form one list
-    // dealt round robin to the resident CTAs: unit e goes to CTA e mod grid,
-    // so every CTA gets about the same work and at any time the CTAs work on
-    // one contiguous band of the list (x-neighbouring units run side by
-    // side and share their halo columns in L2).  A unit is
-    //  * for short tiles (few stages): a strip of consecutive tiles in y,
-    //    STRIP_STAGES stages long, streamed through one pipeline (the next
-    //    tile's halo row is still in L2; setup, fill and drain are paid once
-    //    per strip);
-    //  * for long tiles: one tile; a CTA's tiles of one instance are then a
-    //    single run with stride grid (the band of tiles moves down the grid
-    //    in lockstep, so vertical neighbours also share halo rows in L2).
-    // Items are (instance, first tile, tile count, tile stride).
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    constexpr int STRIP_MAX_STAGES = 48;     // tiles up to this long go in strips
     const int slots = sms * tiled_ctas_per_sm(b->variant);     // resident CTAs of the persistent grid
-    // stages per strip: 192, halved while the list would hold fewer than
-    // four units per CTA (a few small instances must still fill the GPU)
-    std::vector<int> strip(count, 1);
-    long long total_units = 0;
-    for (int strip_stages = 192;; strip_stages /= 2) {
-        total_units = 0;
-        for (int i = 0; i < count; ++i) {
-            int tx = 0, ty = 0;
-            tiled_tile_grid(b->inst[i]->tiled, &tx, &ty);
-            const int c = std::max(1, shapes[i].cost);
-            strip[i] = c <= STRIP_MAX_STAGES ? std::max(1, std::min(ty, (strip_stages + c - 1) / c)) : 1;
-            total_units += strip[i] > 1 ? (long long)tx * ((ty + strip[i] - 1) / strip[i]) : shapes[i].tiles;
-        }
-        if (total_units >= 4LL * slots || strip_stages <= 1) break;
-    }
-    const int grid = (int)std::max(1LL, std::min<long long>(total_units, slots));
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-        return (double)shapes[a].tiles * shapes[a].cost > (double)shapes[c].tiles * shapes[c].cost;
-    });
-    std::vector<std::vector<int4>> per(grid);
-    long long cum = 0;                        // list position of the instance's first unit
-    for (int i : order) {
-        int tx = 0, ty = 0;
-        tiled_tile_grid(b->inst[i]->tiled, &tx, &ty);
-        if (strip[i] > 1) {
-            const int S = strip[i];
-            long long u = 0;
-            for (int y0 = 0; y0 < ty; y0 += S)
-                for (int x = 0; x < tx; ++x, ++u)
-                    per[(cum + u) % grid].push_back(make_int4(i, y0 * tx + x, std::min(S, ty - y0), tx));
-            cum += u;
-        } else {
-            const int tiles = shapes[i].tiles;
-            for (int cta = 0; cta < grid; ++cta) {
-                const long long first = ((cta - cum) % grid + grid) % grid;
-                if (first >= tiles) continue;
-                const int n = (int)((tiles - 1 - first) / grid) + 1;
-                per[cta].push_back(make_int4(i, (int)first, n, grid));
-            }
-            cum += tiles;
-        }
-    }
     std::vector<int4> it;
-    std::vector<int> off(grid + 1, 0);
-    for (int cta = 0; cta < grid; ++cta) {
-        off[cta] = (int)it.size();
-        it.insert(it.end(), per[cta].begin(), per[cta].end());
-        if (it.size() > 0x7fffffffu) return bail(bfail(b, STARMAP_E_ARG, "too many tiles in one batch"));
-    }
-    off[grid] = (int)it.size();
+    std::vector<int> off;
+    const int grid = batch_plan(shapes, slots, it, off);
+    if (grid < 1) return bail(bfail(b, STARMAP_E_ARG, "too many tiles in one batch"));
     int rc = tiled_batch_prepare(b->smem, b->variant);
     if (rc) return bail(bfail(b, rc, "batch kernel needs more shared memory than the device offers"));
     b->grid = grid;
