@@ -424,7 +424,7 @@ int starmap_mlp_perturb_inputs(starmap_mlp_t* net, const float* X, float* Xn, si
  * starmap_batch_step advances every instance by nsteps of its own dt with
  * one CUDA graph launch: per pass, one persistent kernel walks the tiles of
  * all instances with each instance's own tables (work units of all
- * instances dealt round robin to the CTAs: strips of consecutive tiles in y
+ * instances dealt to the CTAs by load: strips of consecutive tiles in y
  * for short tiles, single tiles for long ones), then one kernel refreshes
  * the boundary copies of every instance; the pass sequence of a step count
  * is captured once and replayed.  The
