@@ -432,7 +432,7 @@ int starmap_mlp_perturb_inputs(starmap_mlp_t* net, const float* X, float* Xn, si
  * must be a non-default stream (graphs are captured on it).  Tile shape:
  * cfgs[0].kernel = STARMAP_KERNEL_TILED_TALL or _TILED_SHORT forces 64 x 10
  * or 64 x 5 tiles; anything else runs the autotuner, which builds the batch
- * with both, times two steps of each on the fresh all-zero state (left
+ * with both, times four steps of each on the fresh all-zero state (left
  * zero; time and step counters are reset) and keeps the faster -- creation
  * then takes both builds and needs twice the state memory meanwhile.
  * Errors: E_UNSUPPORTED for an FP64, slab or closure instance, else as

@@ -1427,15 +1427,16 @@ int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t*
     const int k = cfgs[0].kernel;
     if (k == STARMAP_KERNEL_TILED_TALL || k == STARMAP_KERNEL_TILED_SHORT)
         return batch_build(cfgs, count, k == STARMAP_KERNEL_TILED_SHORT ? 1 : 0, out);
-    // Autotuner: build the batch with each tile height, time two steps of
-    // each on the freshly created (all-zero, source-free, vacuum) state --
-    // which the steps leave zero -- and keep the faster.
+    // Autotuner: build the batch with each tile height, time four steps of
+    // each (one step call: nine passes with the merged schedule) on the
+    // freshly created (all-zero, source-free, vacuum) state -- which the
+    // steps leave zero -- and keep the faster.
     starmap_batch_t* cand[2] = {nullptr, nullptr};
     double ms[2] = {-1.0, -1.0};
     int rc = STARMAP_OK;
     for (int v = 0; v < 2 && rc == STARMAP_OK; ++v) {
         rc = batch_build(cfgs, count, v, &cand[v]);
-        if (rc == STARMAP_OK) rc = batch_time(cand[v], 2, &ms[v]);
+        if (rc == STARMAP_OK) rc = batch_time(cand[v], 4, &ms[v]);
         if (rc != STARMAP_OK && cand[v]) g_batch_create_error = cand[v]->err;
     }
     if (rc != STARMAP_OK) {
