@@ -392,3 +392,23 @@ def test_input_noise_is_gaussian_and_reproducible():
     assert np.array_equal(Xd.cpu().numpy(), a)
     with pytest.raises(capi.StarmapError):
         net.perturb_inputs(Xd, A, M, 39, sigma, 1)
+
+
+@pytest.mark.parametrize("schedule", ["literal", "merged"])
+def test_closed_run_same_on_both_tile_heights(schedule):
+    """The frozen order-8 outputs and the closure's inputs do not depend on
+    the tile shape: a closed run on 64 x 5 tiles equals the one on 64 x 10
+    tiles bit for bit."""
+    p = _closure_problem(precision="fp32", nsteps=4, n=(130, 70), bc=("extrapolation", "periodic"))
+    params = _params(45, scale_out=0.6)
+    runs = []
+    for kernel in ("tiled_tall", "tiled_short"):
+        s = capi.Stepper.from_problem(p, kernel=kernel, closure="mlp8", schedule=schedule)
+        assert s.tile_rows == (10 if kernel == "tiled_tall" else 5)
+        s.set_closure(params)
+        s.step(p.nsteps)
+        s.sync()
+        runs.append(_state(s))
+        s.close()
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
