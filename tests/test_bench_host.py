@@ -86,3 +86,29 @@ def test_closure_summary_matches_lowest_accurate_order():
     none = {"plain": case["plain"], "closure": {"err": 0.001, "ms": 1.0}}
     out = closure.summarize([none], list(errs))
     assert out["matched_N"] is None and out["error_matched_speedup"] is None
+
+
+def test_algorithmic_bytes_are_three_values_per_update_per_step():
+    """The roofline's numerator: a pass reads every input of the other
+    parity once and reads and writes every output once, so the two passes
+    of a merged step move 3 values per moment-cell update (12 B in FP32);
+    at P_39 on 1024^2 the odd pass moves 5.20 GB."""
+    sys.path.insert(0, ROOT)
+    import __graft_entry__
+    __graft_entry__.build()
+    import bench
+    from paper_1211_2205_gb300 import capi
+    N, n = 39, 1024
+    grid = capi.host_matrices(capi.PN2D, N)[2]
+
+    class Fake:
+        ncomp = len(grid)
+
+        def moment_info(self, j):
+            return {"grid": int(grid[j]), "nx": n, "ny": n}
+
+    odd = bench.algorithmic_pass_bytes(Fake(), 1, 4)
+    even = bench.algorithmic_pass_bytes(Fake(), 0, 4)
+    assert odd == (2 * 420 + 400) * n * n * 4
+    assert odd == pytest.approx(5.20e9, rel=2e-3)
+    assert odd + even == 3 * 820 * n * n * 4
