@@ -418,6 +418,9 @@ def run_native(args):
     if args.grid > 0:
         problem = inputs.Problem(**{**problem.__dict__, "n": (args.grid, args.grid)})
         desc += f" (grid overridden to {args.grid}x{args.grid})"
+    if args.precision and args.precision != problem.precision:
+        problem = inputs.Problem(**{**problem.__dict__, "precision": args.precision})
+        desc += f" (precision overridden to {args.precision})"
     esize = 4 if problem.precision == "fp32" else 8
     # a dedicated stream: the legacy default stream has handle 0, which the
     # library would read as "use your own stream"
@@ -486,7 +489,7 @@ def run_native(args):
     achieved = alg_bytes / (pass_times[dom] / 1e3) / 1e9
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
-    traffic = measured_traffic(s.kernel, args.workload, dom) if args.grid <= 0 else None
+    traffic = measured_traffic(s.kernel, args.workload, dom) if args.grid <= 0 and not args.precision else None
 
     # end to end through the C ABI with host buffers: zero the state on the
     # device, upload the initial moments from the host, K steps, read back
@@ -767,6 +770,8 @@ def main():
     ap.add_argument("--grid", type=int, default=0,
                     help="override the cells per axis of a single-instance workload (profiling captures of a "
                          "smaller case of the same kernel)")
+    ap.add_argument("--precision", default="", choices=["", "fp32", "fp64"],
+                    help="override the precision of a single-instance workload (FP64 runs take the gather kernel)")
     ap.add_argument("--instances", type=int, default=0,
                     help="batched_256: keep only the first K instances (profiling captures of a smaller case of "
                          "the same kernel)")
