@@ -555,7 +555,11 @@ def run_native(args):
         line["vs_baseline"] = value / PAPER_UPDATES_PER_S
         line["paper"] = {"updates_per_s": PAPER_UPDATES_PER_S, "seconds_to_t_final": 1.5,
                          "hardware": "2008 Lenovo W500 laptop, Matlab (section 6.3)"}
+    if steps_to_final:
+        # a workload defined by a final time: the steps to reach it at the
+        # measured rate (output interpolated in the last step)
         line["time_to_t_final_ms"] = steps_to_final * ms_max / args.steps
+        line["config"]["t_final"] = problem.t_final
         line["config"]["steps_to_t_final"] = steps_to_final
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cells, nst = {"random_p39": (192, 4), "checkerboard_p13": (256, 8), "gaussian_p5": (64, 100),
