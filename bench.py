@@ -112,18 +112,34 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    INTERVAL_MS = 20
+
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.path = None
+        self.skip = 0
+
+    def _lines(self) -> int:
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
 
     def __enter__(self):
         try:
             self.path = os.path.join("/tmp", f"starmap_clocks_{os.getpid()}.csv")
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            # the region starts once the sampler is live (its first line is
+            # out); lines before that are not counted as in-region samples
+            t0 = time.perf_counter()
+            while self._lines() == 0 and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.skip = self._lines()
         except Exception:
             self.proc = None
         return self
@@ -142,7 +158,10 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = open(self.path).read().splitlines()
+        inside = lines[self.skip:]
+        # a region shorter than the interval: the sample just before it
+        for line in (inside if inside else lines[-1:]):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -157,7 +176,7 @@ class ClockSampler:
         os.remove(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(inside), "interval_ms": self.INTERVAL_MS}
 
 
 def kernel_hash(kind: str) -> str:
