@@ -365,6 +365,53 @@ def test_homogeneous_state_follows_the_relaxation_ode(n, aniso):
         np.testing.assert_allclose(s.U[j], want, rtol=1e-13, atol=1e-15)
 
 
+@pytest.mark.parametrize("bc", ["periodic", "extrapolation"])
+def test_even_then_odd_pass_reach_one_point_of_odd_data(bc):
+    """One full even pass followed by one full odd pass (the two passes of a
+    merged step, which a temporally fused step would run per tile): every
+    odd output at array index (i, j) of either odd grid depends on odd
+    inputs only at indices i-1..i+1, j-1..j+1 (wrapped on a periodic axis,
+    clamped at an extrapolation boundary), so a tile of odd outputs needs one
+    point of odd halo on each side.  The bound is reached."""
+    N = 4
+    Mx, My, order = O.system_matrices("pn2d", N)
+    n = (12, 10)
+    rng = inputs.SplitMix64(77)
+    s = O.StaggeredSolver(Mx, My, order, (0, 1.2, 0, 1.0), n, (bc, bc),
+                          sigma_a=lambda t, x, y: 0.3 + 0 * x, sigma_s0=lambda t, x, y: 0.7 + 0 * x,
+                          ic=_random_ic(len(order), 9))
+    s._evaluate(0.0)
+    base = [u.copy() for u in s.U]
+
+    def even_then_odd(U):
+        s.U = [u.copy() for u in U]
+        dxU, dyU = s._differences(s.odd)
+        s._half_step(s.even, dxU, dyU)
+        s._half_step(s.even, dxU, dyU)
+        dxU, dyU = s._differences(s.even)
+        s._half_step(s.odd, dxU, dyU)
+        s._half_step(s.odd, dxU, dyU)
+        return [s.U[j].copy() for j in s.odd]
+
+    def dist(a, b, d):
+        m = n[d] + (1 if bc == "extrapolation" and d == 0 else 0)
+        return min(abs(a - b), m - abs(a - b)) if bc == "periodic" else abs(a - b)
+
+    ref = even_then_odd(base)
+    reached = 0
+    for k0 in s.odd[::3]:
+        shape = base[k0].shape
+        for (i0, j0) in ((6, 5), (0, 0), (shape[0] - 1, shape[1] - 1)):
+            pert = [u.copy() for u in base]
+            pert[k0][i0, j0] += 1.0 + rng.uniform()
+            out = even_then_odd(pert)
+            for got, want in zip(out, ref):
+                for i, j in zip(*np.nonzero(np.abs(got - want) > 1e-14)):
+                    assert dist(i, i0, 0) <= 1 and dist(j, j0, 1) <= 1, (k0, (i0, j0), (i, j))
+                    reached = max(reached, max(dist(i, i0, 0), dist(j, j0, 1)))
+    assert reached == 1
+
+
 def test_symmetry_of_centred_gaussian():
     p = inputs.gaussian_p5(n=32, nsteps=20)
     s = O.solver_from_problem(p)
