@@ -387,6 +387,19 @@ def test_input_noise_is_gaussian_and_reproducible():
     assert abs(np.mean(np.abs(n) < 1.0) - 0.682689) < 3e-3          # normal, not uniform or clipped
     assert abs(np.mean(np.abs(n) < 2.0) - 0.954500) < 2e-3
     assert abs(float(np.corrcoef(n[:, 0], n[:, 1])[0, 1])) < 0.02      # independent across columns
+    # the definition: SplitMix64's finaliser of seed * golden + element
+    # index, two 32-bit halves, Box-Muller (recomputed here in float64)
+    mask = (1 << 64) - 1
+    for e in (0, 1, 37, 38 * 1000 + 5, 38 * (M - 1) + 35):
+        z = (11 * 0x9E3779B97F4A7C15 + e + 0x9E3779B97F4A7C15) & mask
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        z ^= z >> 31
+        u1 = ((z >> 32) + 0.5) * 2.0 ** -32
+        u2 = ((z & 0xFFFFFFFF) + 0.5) * 2.0 ** -32
+        g = math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+        m, c = divmod(e, C.N_IN)
+        assert abs(float(a[m, c]) - (float(X[m, c]) + sigma * g)) <= 2e-6 * (1 + abs(g)), e
     net.perturb_inputs(Xd, Xd, M, 36, sigma, 11)                      # in place
     net.sync()
     assert np.array_equal(Xd.cpu().numpy(), a)
