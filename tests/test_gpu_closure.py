@@ -399,7 +399,8 @@ def test_input_noise_is_gaussian_and_reproducible():
         u2 = ((z & 0xFFFFFFFF) + 0.5) * 2.0 ** -32
         g = math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
         m, c = divmod(e, C.N_IN)
-        assert abs(float(a[m, c]) - (float(X[m, c]) + sigma * g)) <= 2e-6 * (1 + abs(g)), e
+        want = float(X[m, c]) + (sigma * g if c < 36 else 0.0)       # the material inputs stay exact
+        assert abs(float(a[m, c]) - want) <= 2e-6 * (1 + abs(g)), e
     net.perturb_inputs(Xd, Xd, M, 36, sigma, 11)                      # in place
     net.sync()
     assert np.array_equal(Xd.cpu().numpy(), a)
