@@ -78,3 +78,12 @@ def test_grid_placement_follows_kind_and_parity(capi, N):
         l = order[j]
         want = (0 if l % 2 == 0 else 1) if kinds[j] == "R" else (2 if l % 2 == 1 else 3)
         assert grid[j] == want, j
+
+
+def test_binding_declares_every_header_function(capi):
+    """The binding gives every function of include/starmap.h a ctypes
+    signature, and declares none the header lacks."""
+    import re
+    src = open(os.path.join(ROOT, "paper_1211_2205_gb300", "capi.py")).read()
+    declared = set(re.findall(r'"(starmap_[a-z0-9_]+)": \(', src))
+    assert declared == set(capi.exported_functions())
