@@ -6,7 +6,7 @@ match the FP64 oracle within the FP32 bar."""
 import numpy as np
 import pytest
 
-from helpers import oracle_run, rel_l2
+from helpers import assert_parity, oracle_run, rel_l2
 from paper_1211_2205_gb300 import capi, inputs
 
 pytestmark = pytest.mark.gpu
@@ -64,8 +64,8 @@ def test_batch_subset_matches_oracle():
     for k in (0, 2, 3, 5):
         inst = b.instances[k]
         got = [inst.moments(j) for j in range(inst.ncomp)]
-        _, ref = oracle_run(probs[k], dt=inst.dt, nsteps=6)
-        assert rel_l2(got, ref) <= FP32_TOL, k
+        _, ref = oracle_run(probs[k], inst, nsteps=6)
+        assert_parity(got, ref, FP32_TOL, "fp32", k)
     b.close()
 
 
@@ -108,8 +108,8 @@ def test_full_size_batch_samples():
     small = min(picks, key=lambda k: probs[k].n[0] * (probs[k].N + 1) ** 2)
     inst = b.instances[small]
     got = [inst.moments(j) for j in range(inst.ncomp)]
-    _, ref = oracle_run(probs[small], dt=inst.dt, nsteps=3)
-    assert rel_l2(got, ref) <= FP32_TOL
+    _, ref = oracle_run(probs[small], inst, nsteps=3)
+    assert_parity(got, ref, FP32_TOL, "fp32")
     b.close()
 
 

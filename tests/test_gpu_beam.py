@@ -7,7 +7,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import rel_l2
+from helpers import DT_RTOL, assert_parity
 from oracle import pn_oracle as O
 from paper_1211_2205_gb300 import capi, inputs
 
@@ -20,12 +20,13 @@ def test_beam_matches_oracle_through_the_interface(precision, kernel, tol):
     p = inputs.beam(capi.direction_moments(N, 0.0, inputs.BEAM_ANGLE), n=n, precision=precision)
     po = inputs.beam(O.direction_moments(N, 0.0, inputs.BEAM_ANGLE), n=n, precision="fp64")
     s = capi.Stepper.from_problem(p, kernel=kernel, schedule="merged")
-    nsteps = int(math.ceil(0.5 / s.dt))            # the front passes x = 0.3 at t ~ 0.35
+    o = O.solver_from_problem(po)                  # the oracle's own step size ...
+    assert abs(s.dt - o.dt) <= DT_RTOL * o.dt      # ... equals the library's
+    nsteps = int(math.ceil(0.5 / o.dt))            # the front passes x = 0.3 at t ~ 0.35
     s.step(nsteps)
     got = [s.moments(j) for j in range(s.ncomp)]
-    o = O.solver_from_problem(po, dt=s.dt)
     o.run(nsteps)
-    assert rel_l2(got, [u.T for u in o.U]) <= tol
+    assert_parity(got, [u.T for u in o.U], tol, precision)
 
 
 def test_full_size_beam_p39():

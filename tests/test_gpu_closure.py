@@ -12,7 +12,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import rel_l2
+from helpers import DT_RTOL, assert_parity, check_dt, rel_l2
 from oracle import closure_oracle as C
 from oracle import pn_oracle as O
 from paper_1211_2205_gb300 import capi, inputs
@@ -178,6 +178,15 @@ def _state(s):
     return [s.moments(j) for j in range(s.ncomp)]
 
 
+def _closed_dt(s, p):
+    """The oracle's step size of the closed system (P_8's lambda_max, the
+    rule of section 4.5), checked against the closure handle's."""
+    Mx, _, _ = O.system_matrices("pn2d", C.N_CLOSED)
+    d = O.time_step(Mx, p.ax, p.n, p.cn)
+    assert abs(s.dt - d) <= DT_RTOL * d, (s.dt, d)
+    return d
+
+
 @pytest.mark.parametrize("bc", [("periodic", "periodic"), ("extrapolation", "extrapolation"),
                                 ("periodic", "extrapolation")])
 @pytest.mark.parametrize("precision,kernel", [("fp64", "gather"), ("fp32", "tiled")])
@@ -187,7 +196,7 @@ def test_samples_match_oracle_features_and_targets(bc, precision, kernel):
     p = _closure_problem(bc=bc, precision=precision, N=8, nsteps=2)
     s = capi.Stepper.from_problem(p, kernel=kernel)
     s.step(2)
-    o = O.solver_from_problem(p, dt=s.dt)
+    o = O.solver_from_problem(p, dt=check_dt(s, p))
     o.run(2)
     X0, Y0 = o.coords[(1, 1)]
     Xr, scale_r = C.features(o, p.sigma_a(0, X0, Y0), p.sigma_s0(0, X0, Y0))
@@ -218,9 +227,9 @@ def test_zero_network_is_plain_p7(precision, kernel, tol, schedule):
     s.set_closure(params)
     s.step(p.nsteps)
     got = _state(s)
-    o = O.solver_from_problem(p, dt=s.dt)
+    o = O.solver_from_problem(p, dt=_closed_dt(s, p))
     o.run(p.nsteps)
-    assert rel_l2(got[:36], [u.T for u in o.U]) <= tol
+    assert_parity(got[:36], [u.T for u in o.U], tol, precision)
     for j in range(36, 45):
         assert not got[j].any()
 
@@ -237,7 +246,7 @@ def test_closure_prediction_matches_oracle_hook(bc):
     before = _state(s)
     s.run_pass(1, 0)
     after = _state(s)
-    o = C.closed_solver(p, _oracle_mlp(params), dt=s.dt)
+    o = C.closed_solver(p, _oracle_mlp(params), dt=_closed_dt(s, p))
     for j in range(45):
         o.U[j] = before[j].T.copy()
     o.pre_odd(o)
@@ -258,9 +267,9 @@ def test_closed_run_matches_oracle(precision, kernel, schedule):
     s.set_closure(params)
     s.step(p.nsteps)
     got = _state(s)
-    o = C.closed_solver(p, _oracle_mlp(params), dt=s.dt)
+    o = C.closed_solver(p, _oracle_mlp(params), dt=_closed_dt(s, p))
     o.run(p.nsteps, merged_closure=schedule == "merged")
-    plain = O.solver_from_problem(p, dt=s.dt)
+    plain = O.solver_from_problem(p, dt=_closed_dt(s, p))
     plain.run(p.nsteps)
     ref = [u.T for u in o.U[:36]]
     effect = rel_l2([u.T for u in plain.U], ref)
@@ -335,7 +344,7 @@ def test_tcgen05_closure_prediction_matches_oracle_hook(bc):
     s.run_pass(1, 0)
     after = _state(s)
     s.sync()
-    o = C.closed_solver(p, _oracle_mlp(params), dt=s.dt)
+    o = C.closed_solver(p, _oracle_mlp(params), dt=_closed_dt(s, p))
     for j in range(45):
         o.U[j] = before[j].T.copy()
     o.pre_odd(o)
@@ -354,7 +363,7 @@ def test_tcgen05_closed_run_matches_mma_sync_run():
         s.step(p.nsteps)
         s.sync()
         runs.append(_state(s))
-    plain = O.solver_from_problem(p, dt=s.dt)
+    plain = O.solver_from_problem(p, dt=_closed_dt(s, p))
     plain.run(p.nsteps)
     effect = rel_l2([u.T for u in plain.U], runs[0][:36])
     assert rel_l2(runs[1][:36], runs[0][:36]) <= 0.05 * effect

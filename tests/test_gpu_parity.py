@@ -6,7 +6,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import gpu_run, oracle_run, rel_l2
+from helpers import assert_parity, gpu_run, oracle_run, rel_l2
 from oracle import pn_oracle as O
 from paper_1211_2205_gb300 import capi, inputs
 
@@ -39,9 +39,9 @@ def test_gaussian_p5_fp64_full_config(schedule):
     """P_5, FP64, 64x64 periodic, sigma_s0 = 1, Gaussian pulse, 100 steps."""
     p = inputs.gaussian_p5()
     s, got = gpu_run(p, schedule=schedule, kernel="gather")
-    o, ref = oracle_run(p, dt=s.dt)
+    o, ref = oracle_run(p, s)
     assert abs(s.dt - 0.0167566) < 1e-6
-    assert rel_l2(got, ref) <= FP64_TOL
+    assert_parity(got, ref, FP64_TOL, "fp64")
 
 
 @pytest.mark.parametrize("bc", [("periodic", "periodic"), ("extrapolation", "extrapolation"),
@@ -53,15 +53,15 @@ def test_random_media_fp64_ragged(bc, N):
     p = _random_problem(N, (37, 29), bc, "fp64", 100 + N, 9)
     for sched in ("literal", "merged"):
         s, got = gpu_run(p, schedule=sched, kernel="gather")
-        o, ref = oracle_run(p, dt=s.dt)
-        assert rel_l2(got, ref) <= FP64_TOL, sched
+        o, ref = oracle_run(p, s)
+        assert_parity(got, ref, FP64_TOL, "fp64", sched)
 
 
 def test_anisotropic_scattering_fp64():
     p = _random_problem(5, (24, 30), ("extrapolation", "periodic"), "fp64", 7, 8, aniso=True)
     s, got = gpu_run(p, kernel="gather")
-    o, ref = oracle_run(p, dt=s.dt)
-    assert rel_l2(got, ref) <= FP64_TOL
+    o, ref = oracle_run(p, s)
+    assert_parity(got, ref, FP64_TOL, "fp64")
 
 
 @pytest.mark.parametrize("bc", ["periodic", "extrapolation"])
@@ -69,8 +69,8 @@ def test_slab_fp64(bc):
     N = 7
     p = _random_problem(N, (47, 1), (bc, "periodic"), "fp64", 3, 12, system="slab")
     s, got = gpu_run(p, kernel="gather")
-    o, ref = oracle_run(p, dt=s.dt)
-    assert rel_l2(got, ref) <= FP64_TOL
+    o, ref = oracle_run(p, s)
+    assert_parity(got, ref, FP64_TOL, "fp64")
 
 
 def test_fp32_gather_checkerboard_reduced():
@@ -78,23 +78,23 @@ def test_fp32_gather_checkerboard_reduced():
     FP32 against the FP64 oracle."""
     p = inputs.checkerboard_p13(n=72, t_final=0.8, precision="fp32")
     s, got = gpu_run(p, t_final=0.8, kernel="gather")
-    o, ref = oracle_run(p, dt=s.dt, t_final=0.8)
-    assert rel_l2(got, ref) <= FP32_TOL
+    o, ref = oracle_run(p, s, t_final=0.8)
+    assert_parity(got, ref, FP32_TOL, "fp32")
 
 
 def test_advance_to_interpolates():
     p = inputs.gaussian_p5(n=40)
     t_out = 0.37
     s, got = gpu_run(p, t_final=t_out, kernel="gather")
-    o, ref = oracle_run(p, dt=s.dt, t_final=t_out)
-    assert rel_l2(got, ref) <= FP64_TOL
+    o, ref = oracle_run(p, s, t_final=t_out)
+    assert_parity(got, ref, FP64_TOL, "fp64")
     assert s.time >= t_out and s.time - s.dt < t_out
 
 
 def test_diagnostics_match_oracle():
     p = _random_problem(4, (33, 31), ("periodic", "extrapolation"), "fp64", 21, 6)
     s, got = gpu_run(p, kernel="gather")
-    o, ref = oracle_run(p, dt=s.dt)
+    o, ref = oracle_run(p, s)
     mass, l2, bad = s.diagnostics()
     assert bad == 0
     assert abs(mass - o.mass()) <= 1e-12 * abs(o.l2norm())

@@ -5,7 +5,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import gpu_run, oracle_run, rel_l2
+from helpers import assert_parity, check_dt, gpu_run, oracle_run, rel_l2
 from oracle import pn_oracle as O
 from paper_1211_2205_gb300 import capi, inputs
 from test_gpu_parity import _random_problem
@@ -27,8 +27,8 @@ def test_tiled_vs_oracle_ragged(N, bc, kernel):
     for sched in ("literal", "merged"):
         s, got = gpu_run(p, schedule=sched, kernel=kernel)
         assert s.kernel == "tiled" and s.tile_rows == (10 if kernel == "tiled_tall" else 5)
-        o, ref = oracle_run(p, dt=s.dt)
-        assert rel_l2(got, ref) <= FP32_TOL, sched
+        o, ref = oracle_run(p, s)
+        assert_parity(got, ref, FP32_TOL, "fp32", sched)
 
 
 @pytest.mark.parametrize("N", [3, 9, 22])
@@ -44,8 +44,8 @@ def test_tile_heights_agree(N):
 def test_tiled_anisotropic():
     p = _random_problem(6, (41, 33), ("extrapolation", "periodic"), "fp32", 17, 6, aniso=True)
     s, got = gpu_run(p, kernel="tiled")
-    o, ref = oracle_run(p, dt=s.dt)
-    assert rel_l2(got, ref) <= FP32_TOL
+    o, ref = oracle_run(p, s)
+    assert_parity(got, ref, FP32_TOL, "fp32")
 
 
 def test_tiled_matches_gather():
@@ -59,16 +59,16 @@ def test_tiled_checkerboard_to_time():
     """P_13 checkerboard, 72 x 72, interpolated output at t = 0.8."""
     p = inputs.checkerboard_p13(n=72, t_final=0.8, precision="fp32")
     s, got = gpu_run(p, t_final=0.8, kernel="tiled", schedule="merged")
-    o, ref = oracle_run(p, dt=s.dt, t_final=0.8)
-    assert rel_l2(got, ref) <= FP32_TOL
+    o, ref = oracle_run(p, s, t_final=0.8)
+    assert_parity(got, ref, FP32_TOL, "fp32")
 
 
 def test_tiled_large_order():
     """P_39 on a 40 x 36 periodic grid (all 820 moments, several tiles)."""
     p = _random_problem(39, (40, 36), ("periodic", "periodic"), "fp32", 39, 3)
     s, got = gpu_run(p, kernel="tiled", schedule="merged")
-    o, ref = oracle_run(p, dt=s.dt)
-    assert rel_l2(got, ref) <= FP32_TOL
+    o, ref = oracle_run(p, s)
+    assert_parity(got, ref, FP32_TOL, "fp32")
 
 
 def test_tiled_mass_conservation_fp32():
@@ -83,7 +83,7 @@ def test_tiled_mass_conservation_fp32():
     assert abs(m1 - m0) <= 1e-5 * abs(m0)
 
 
-def _window_problem(p, i0, j0, cells, dt):
+def _window_problem(p, i0, j0, cells):
     """Sub-problem on cells x cells cells starting at cell (i0, j0) of p,
     same spacing and material, periodic wrap (valid in the window interior
     while the wrap error has not travelled in)."""
@@ -105,8 +105,8 @@ def test_full_size_random_p39_sampled(nsteps):
     halo = int(math.ceil(1.5 * nsteps)) + 3
     w = 16
     i0, j0 = 600 - halo, 300 - halo            # window cell origin (includes the Gaussian's tail)
-    sub = _window_problem(p, i0, j0, w + 2 * halo, s.dt)
-    o = O.solver_from_problem(sub, dt=s.dt)
+    sub = _window_problem(p, i0, j0, w + 2 * halo)
+    o = O.solver_from_problem(sub, dt=check_dt(s, p))
     o.run(nsteps)
     got, ref = [], []
     for j in range(s.ncomp):
@@ -114,7 +114,7 @@ def test_full_size_random_p39_sampled(nsteps):
         got.append(s.moments_window(j, i0 + halo, j0 + halo, w, w))
         sub_u = o.U[j].T                       # (ny, nx) on the window grid
         ref.append(sub_u[halo: halo + w, halo: halo + w])
-    assert rel_l2(got, ref) <= FP32_TOL
+    assert_parity(got, ref, FP32_TOL, "fp32")
 
 
 def test_full_size_random_p39_sampled_across_periodic_edge():
@@ -136,10 +136,10 @@ def test_full_size_random_p39_sampled_across_periodic_edge():
         # f at the point of the periodic domain that (x, y) stands for
         return lambda t, x, y: f(t, x0 + np.mod(x - x0, x1 - x0), y0 + np.mod(y - y0, y1 - y0))
 
-    sub = _window_problem(p, i0, j0, w + 2 * halo, s.dt)
+    sub = _window_problem(p, i0, j0, w + 2 * halo)
     sub = inputs.Problem(**{**sub.__dict__, "sigma_a": wrapped(p.sigma_a), "sigma_s0": wrapped(p.sigma_s0),
                             "ic": [(k, wrapped(f)) for k, f in p.ic]})
-    o = O.solver_from_problem(sub, dt=s.dt)
+    o = O.solver_from_problem(sub, dt=check_dt(s, p))
     o.run(nsteps)
     xa = i0 + halo                          # first window column on the full grid
     left = p.n[0] - xa                      # columns before the wrap
@@ -150,7 +150,7 @@ def test_full_size_random_p39_sampled_across_periodic_edge():
         got.append(np.concatenate([a, b], axis=1))
         ref.append(o.U[j].T[halo: halo + w, halo: halo + w])
     assert min(np.abs(r).max() for r in ref[:1]) > 1e-30
-    assert rel_l2(got, ref) <= FP32_TOL
+    assert_parity(got, ref, FP32_TOL, "fp32")
 
 
 def test_state_beyond_32bit_offsets():
@@ -186,16 +186,16 @@ def test_state_beyond_32bit_offsets():
         seen[g] += 1
     assert len(high) >= 60
     s.step(nsteps)
-    sub = _window_problem(p, i0, j0, w + 2 * halo, s.dt)
+    sub = _window_problem(p, i0, j0, w + 2 * halo)
     sub = inputs.Problem(**{**sub.__dict__, "ic": list(p.ic) + bumps})
-    o = O.solver_from_problem(sub, dt=s.dt)
+    o = O.solver_from_problem(sub, dt=check_dt(s, p))
     o.run(nsteps)
     got = [s.moments_window(j, i0 + halo, j0 + halo, w, w) for j in range(s.ncomp)]
     ref = [o.U[j].T[halo: halo + w, halo: halo + w] for j in range(s.ncomp)]
     s.close()
     assert min(float(np.abs(ref[j]).max()) for j in high) > 1e-3
-    assert rel_l2(got, ref) <= FP32_TOL
-    assert rel_l2([got[j] for j in high], [ref[j] for j in high]) <= FP32_TOL
+    assert_parity(got, ref, FP32_TOL, "fp32")
+    assert_parity([got[j] for j in high], [ref[j] for j in high], FP32_TOL, "fp32")
 
 
 def test_full_size_checkerboard_p13_sampled():
@@ -213,8 +213,8 @@ def test_full_size_checkerboard_p13_sampled():
     halo = int(math.ceil(1.5 * nsteps)) + 3
     w = 16
     i0, j0 = 285 - halo, 250 - halo
-    sub = _window_problem(p, i0, j0, w + 2 * halo, s.dt)
-    o = O.solver_from_problem(sub, dt=s.dt)
+    sub = _window_problem(p, i0, j0, w + 2 * halo)
+    o = O.solver_from_problem(sub, dt=check_dt(s, p))
     o.run(nsteps)
     got, ref = [], []
     for j in range(s.ncomp):
@@ -224,7 +224,7 @@ def test_full_size_checkerboard_p13_sampled():
         got.append(s.moments_window(j, xo, yo, w, w))
         ref.append(o.U[j].T[halo: halo + w, halo: halo + w])
     assert np.abs(ref[0]).max() > 1e-3
-    assert rel_l2(got, ref) <= FP32_TOL
+    assert_parity(got, ref, FP32_TOL, "fp32")
 
 
 @pytest.mark.parametrize("kernel", ["auto", "tiled"])
@@ -240,9 +240,8 @@ def test_highest_orders_run_on_short_tiles(kernel):
     assert s.kernel == "tiled" and s.tile_rows == 5
     s.step(2)
     got = [s.moments(j) for j in range(s.ncomp)]
-    o = O.solver_from_problem(p, dt=s.dt)
-    o.run(2)
-    assert rel_l2(got, [u.T for u in o.U]) <= 1e-5
+    o, ref = oracle_run(p, s, nsteps=2)
+    assert_parity(got, ref, FP32_TOL, "fp32")
     with pytest.raises(capi.StarmapError) as e:
         capi.Stepper.from_problem(p, kernel="tiled_tall")
     assert e.value.code == capi.E_UNSUPPORTED

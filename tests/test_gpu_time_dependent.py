@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import rel_l2
+from helpers import assert_parity, check_dt
 from oracle import pn_oracle as O
 from paper_1211_2205_gb300 import capi, inputs
 
@@ -40,9 +40,10 @@ def mms_problem(n, precision="fp64"):
 
 def _run_gpu(p, t_final, kernel="auto"):
     s = capi.Stepper.from_problem(p, kernel=kernel, schedule="literal")
-    nsteps = int(math.ceil(t_final / s.dt - 1e-9))
-    dt = t_final / nsteps                      # the final time on a step
+    d = check_dt(s, p)                         # the library's own step rule equals the oracle's
     s.close()
+    nsteps = int(math.ceil(t_final / d - 1e-9))
+    dt = t_final / nsteps                      # the final time on a step: both sides use this one
     s = capi.Stepper.from_problem(p, kernel=kernel, schedule="literal", dt=dt)
     s.step_time_dependent(p, nsteps)
     out = [s.moments(j) for j in range(s.ncomp)]
@@ -59,7 +60,7 @@ def test_time_dependent_matches_oracle(precision, kernel, tol):
     o = O.solver_from_problem(p, dt=dt)
     o.run(nsteps)
     ref = [u.T for u in o.U]
-    assert rel_l2(got, ref) <= tol
+    assert_parity(got, ref, tol, precision)
 
 
 def test_mms_second_order_on_gpu():
