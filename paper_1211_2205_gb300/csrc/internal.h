@@ -88,6 +88,7 @@ struct ReduceArgs {
     GridDev<T> g[4];
     long pitch;
     double cell;                  // dx * dy
+    int row0 = 1;                 // memory row of y = 0 counted from base (1: ghost row first)
 };
 
 // launchers (kernels_gather.cu)

@@ -157,7 +157,7 @@ __global__ void k_reduce_partials(const ReduceArgs<T> A, double* partials) {
         while (rr >= (long)A.g[g].K * A.g[g].ny) { rr -= (long)A.g[g].K * A.g[g].ny; ++g; }
         const GridDev<T>& G = A.g[g];
         const int k = (int)(rr / G.ny), y = (int)(rr % G.ny);
-        const T* row = G.base + (long)k * G.cstride + (long)(y + 1) * A.pitch;
+        const T* row = G.base + (long)k * G.cstride + (long)(y + A.row0) * A.pitch;
         for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
             const double v = (double)row[x];
             if (!isfinite(v)) { bad += 1.0; continue; }
