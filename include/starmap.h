@@ -57,6 +57,7 @@ extern "C" {
 #define STARMAP_E_TIMEOUT    -6   /* a bounded device wait gave up            */
 #define STARMAP_E_STATE      -7   /* call not valid in the handle's state     */
 #define STARMAP_E_UNSUPPORTED -8  /* configuration not supported by a kernel  */
+#define STARMAP_E_GROWTH     -9   /* health check: the L2 norm grew past its bound */
 
 /* ------------------------------------------------------------------ enums */
 #define STARMAP_PERIODIC       0  /* p = 1 in eq. periodicity_flags */
@@ -246,6 +247,39 @@ int starmap_set_time(starmap_t* h, double t);
 /* Advance nsteps full time steps (eq. solution_operator_full_step) with the
  * configured schedule.  Asynchronous on the handle's stream. */
 int starmap_step(starmap_t* h, long nsteps);
+/* Periodic health check of the stepping (failure detection; the paper has
+ * no counterpart).  With every > 0, starmap_step and starmap_advance_to run
+ * their steps in spans of at most `every` steps; after each span the state
+ * is reduced in FP64 (the reduction of starmap_diagnostics, one host
+ * synchronisation per span) and the span fails if
+ *   - any value is NaN or Inf (STARMAP_E_NONFINITE), or
+ *   - the discrete L2 norm (eq. discrete_L2_norm) exceeds
+ *     growth * (l2_start + t_span * q_l2) (STARMAP_E_GROWTH),
+ *     l2_start the norm at the span's start, t_span the span's time and
+ *     q_l2 the discrete L2 norm of the sources.  The exact solution obeys
+ *     this bound with growth = 1 (absorption and scattering do not increase
+ *     the norm, a source adds at most t_span * q_l2); the scheme keeps its
+ *     norm to a small fraction (section 6.2), so growth = 1.05 only fires
+ *     on a run that diverges, such as a closure network feeding energy in.
+ * On failure the state, time and step count go back to the end of the last
+ * span that passed (or the start of the call), kept in a device copy of the
+ * state that exists while the check is on; the call then returns the
+ * error, and starmap_health reports where it happened.  Spans make the
+ * merged schedule's odd halves split at their ends (equal up to rounding)
+ * and, with the closure, add one network evaluation per span.
+ * every = 0 turns the check off and frees the copy.  E_ARG for every < 0
+ * or growth < 1. */
+int starmap_set_health_check(starmap_t* h, long every, double growth);
+/* State of the health check: steps done at the last span that passed, the
+ * L2 norm there, and the L2 norm found at the failed span's end (NaN if
+ * none failed).  Any output may be NULL. */
+int starmap_health(const starmap_t* h, long* good_steps, double* l2_good, double* l2_failed);
+/* The health check's decision on its own (host only; for tests and for
+ * callers doing their own checks): STARMAP_E_NONFINITE if nonfinite > 0 or
+ * a norm is not finite, STARMAP_E_GROWTH if l2_end > growth * (l2_start +
+ * t_span * q_l2), else STARMAP_OK. */
+int starmap_health_verdict(double l2_start, double l2_end, double t_span, double q_l2, double growth,
+                           long nonfinite);
 /* Run one pass of the step: parity 1 updates the odd components (grids
  * G21, G12) from the even ones, parity 0 the even components (G11, G22) from
  * the odd ones; which = 0 applies the half-step coefficients (tau = dt/2),
@@ -292,16 +326,21 @@ int starmap_diagnostics(starmap_t* h, double* mass, double* l2, long* nonfinite)
  * STARMAP_NOALLOC_MAX_BLOCKS x 3 doubles that every GPU loading the library
  * keeps until process exit; nothing is allocated or freed.  The first call
  * on a device looks up that array's device address (make that first call
- * before any stream capture).  All calls share the array: calls whose work
+ * before any stream capture); a call that finds a different current context
+ * on that device than the lookup saw (after cudaDeviceReset, for instance)
+ * looks it up again.  All calls share the array: calls whose work
  * overlaps on the GPU race and give wrong results; serialise them (one
  * stream, or events).  Every partial a call reads is written by the same
  * call, so no clearing is needed between calls.
- * Errors: E_ARG for null pointers, bad layout, or more than
- * STARMAP_NOALLOC_MAX_ROWS rows (ncomp*ny) or STARMAP_NOALLOC_MAX_ROW_LENGTH
- * points per row; E_CUDA if a launch or the address lookup fails. */
+ * Errors: E_ARG for null pointers, bad layout (pitch < nx, comp_stride <
+ * pitch*ny, origin < 0), more than STARMAP_NOALLOC_MAX_ROWS rows (ncomp*ny),
+ * more than STARMAP_NOALLOC_MAX_ROW_LENGTH points per row or a pitch above
+ * STARMAP_NOALLOC_MAX_PITCH elements; E_CUDA if a launch or the address
+ * lookup fails. */
 #define STARMAP_NOALLOC_MAX_BLOCKS      1024
 #define STARMAP_NOALLOC_MAX_ROWS        (1L << 26)
 #define STARMAP_NOALLOC_MAX_ROW_LENGTH  (1L << 24)
+#define STARMAP_NOALLOC_MAX_PITCH       (1L << 31)
 int starmap_diagnostics_noalloc(const void* data, int precision, int ncomp, int nx, int ny,
                                 long pitch, long comp_stride, long origin, double cell,
                                 double* out_device, void* stream);
