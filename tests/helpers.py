@@ -14,19 +14,22 @@ from oracle import pn_oracle as O
 from paper_1211_2205_gb300 import capi
 
 # The library computes lambda_max by bisection on a Sturm sequence, the
-# oracle with LAPACK's eigenvalue routine: both are accurate to a few units
-# of the last place of a number near 1.
-DT_RTOL = 1e-14
+# oracle with LAPACK's general eigenvalue routine, whose error grows with the
+# matrix size (1.7e-14 relative at N = 39, an 820 x 820 matrix); the CPU
+# tests hold the two lambda_max to 1e-13.
+DT_RTOL = 1e-13
 
 # Unit round-off of the stored precision.
 UNIT_ROUNDOFF = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24}
 
-# Per-component bar: ||g_j - r_j|| <= tol * ||r_j|| + FLOOR_ULPS * u * ||r||,
-# with ||r|| the norm of all components together.  The floor lets a
-# component that is zero (or rounding noise) in exact arithmetic carry the
-# rounding noise its larger neighbours feed it; it is a few units of
-# round-off of the whole state, far below the pooled bar tol * ||r||.
-FLOOR_ULPS = 64.0
+# Per-component bar: ||g_j - r_j|| <= tol * ||r_j|| + FLOOR_ULPS[p] * u * ||r||,
+# with ||r|| the norm of all components together and u the unit round-off.
+# The floor lets a component that is tiny (or zero) in exact arithmetic
+# carry the rounding noise of its larger neighbours.  FP32: 4 units of the
+# whole state's round-off (the parity suite needs at most 0.62).  FP64: the
+# two sides' step sizes agree only to DT_RTOL, which moves every component
+# by up to ~1e-14 of the state: 64 units (the suite needs at most 31).
+FLOOR_ULPS = {"fp32": 4.0, "fp64": 64.0}
 
 
 def gpu_run(problem, nsteps=None, t_final=None, **over):
@@ -79,12 +82,12 @@ def rel_l2(got, ref):
 def component_ratios(got, ref, tol, precision):
     """Per component j: ||g_j - r_j|| / (tol ||r_j|| + FLOOR_ULPS u ||r||);
     every entry must be <= 1."""
-    u = UNIT_ROUNDOFF[precision]
+    u = UNIT_ROUNDOFF[precision] * FLOOR_ULPS[precision]
     err = np.array([math.sqrt(float(np.sum((np.asarray(g, dtype=np.float64) - r) ** 2)))
                     for g, r in zip(got, ref)])
     nrm = np.array([math.sqrt(float(np.sum(np.asarray(r, dtype=np.float64) ** 2))) for r in ref])
     pooled = math.sqrt(float(np.sum(nrm ** 2)))
-    bar = tol * nrm + FLOOR_ULPS * u * pooled
+    bar = tol * nrm + u * pooled
     return np.where(bar > 0, err / np.where(bar > 0, bar, 1.0), np.where(err > 0, np.inf, 0.0))
 
 
