@@ -19,6 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "starmap.h")
 
 OK = 0
 E_ARG, E_CFL, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE, E_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7, -8
+E_GROWTH = -9
 PERIODIC, EXTRAPOLATION = 0, 1
 PN2D, SLAB = 0, 1
 FP64, FP32 = 0, 1
@@ -107,6 +108,10 @@ def lib():
         "starmap_set_time": (ctypes.c_int, [H, ctypes.c_double]),
         "starmap_clear": (ctypes.c_int, [H]),
         "starmap_step": (ctypes.c_int, [H, ctypes.c_long]),
+        "starmap_set_health_check": (ctypes.c_int, [H, ctypes.c_long, ctypes.c_double]),
+        "starmap_health": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_long), _dp, _dp]),
+        "starmap_health_verdict": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_long]),
         "starmap_advance_to": (ctypes.c_int, [H, ctypes.c_double]),
         "starmap_pass": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int]),
         "starmap_output": (ctypes.c_int, [H, ctypes.c_int, _dp, ctypes.c_size_t]),
@@ -252,6 +257,13 @@ def batch_plan(tiles_x, tiles_y, cost, slots: int):
 def selftest_bounded_wait() -> int:
     """Status of the bounded-wait self-test (E_TIMEOUT is the expected outcome)."""
     return lib().starmap_selftest_bounded_wait()
+
+
+def health_verdict(l2_start: float, l2_end: float, t_span: float, q_l2: float, growth: float,
+                   nonfinite: int = 0) -> int:
+    """The library's health-check decision (OK, E_NONFINITE or E_GROWTH)."""
+    return lib().starmap_health_verdict(float(l2_start), float(l2_end), float(t_span), float(q_l2),
+                                        float(growth), int(nonfinite))
 
 
 def host_expm1div(c) -> np.ndarray:
@@ -412,6 +424,20 @@ class Stepper:
     # -- stepping -------------------------------------------------------
     def step(self, n: int = 1):
         self._check(self._L.starmap_step(self._h, int(n)))
+
+    def set_health_check(self, every: int, growth: float = 1.05):
+        """FP64 check after every `every` steps (0 = off); a failing span
+        raises StarmapError (E_NONFINITE / E_GROWTH) with the state reset to
+        the last span that passed."""
+        self._check(self._L.starmap_set_health_check(self._h, int(every), float(growth)))
+
+    def health(self):
+        """(steps at the last span that passed, its L2 norm, the failed
+        span's L2 norm or NaN)."""
+        k = ctypes.c_long()
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.starmap_health(self._h, ctypes.byref(k), ctypes.byref(a), ctypes.byref(b)))
+        return k.value, a.value, b.value
 
     def step_time_dependent(self, problem, n: int = 1):
         """n steps of a problem whose material or sources change in time.

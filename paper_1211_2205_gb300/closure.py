@@ -305,3 +305,53 @@ def summarize(cases: List[Dict], orders: Sequence[int], compare: Optional[Sequen
            "e2e_error_matched_speedup": e2e if e2e is None or math.isfinite(e2e) else None,
            "gain_vs_p7": plain[N_BASE]["err"] / cl["err"] if N_BASE in plain and cl["err"] > 0 else None}
     return out
+
+
+@dataclass
+class FallbackRun:
+    state: List[np.ndarray]       # components of order <= 7 at the final time, [ny, nx] each
+    fell_back: bool               # True if the closed run failed its health check
+    good_steps: int               # closed-run steps that passed the check
+    fallback_N: int
+    detail: str = ""
+
+
+def run_with_fallback(problem: inputs.Problem, params: np.ndarray, dt: float, nsteps: int,
+                      fallback_N: int = 15, every: int = 16, growth: float = 1.05,
+                      closure_schedule: str = "merged") -> FallbackRun:
+    """P_7 with the learned closure, watched by the library's health check
+    (FP64 reduction every `every` steps: NaN/Inf, or L2 growth beyond
+    `growth` times what the sources can add).  If a span fails, the closed
+    state of the last span that passed seeds plain P_{fallback_N} (its
+    moments up to order 8, the higher orders zero) and plain P_N runs the
+    rest of the steps; the result then comes from plain P_N."""
+    q7 = inputs.Problem(**{**problem.__dict__, "N": N_BASE})
+    s = capi.Stepper.from_problem(q7, dt=dt, schedule=closure_schedule, closure="mlp8")
+    try:
+        s.set_closure(params)
+        s.set_health_check(every, growth)
+        try:
+            s.step(nsteps)
+            return FallbackRun(state=[s.moments(j) for j in range(36)], fell_back=False, good_steps=nsteps,
+                               fallback_N=fallback_N)
+        except capi.StarmapError as e:
+            if e.code not in (capi.E_GROWTH, capi.E_NONFINITE):
+                raise
+            detail = str(e)
+        good, _, _ = s.health()
+        seed = [s.moments(j) for j in range(s.ncomp)]        # 45 components of the closed P_8 system
+        t_good = s.time
+    finally:
+        s.close()
+    qN = inputs.Problem(**{**problem.__dict__, "N": fallback_N})
+    f = capi.Stepper.from_problem(qN, dt=dt, schedule="merged")
+    try:
+        f.clear()
+        for j, u in enumerate(seed):       # the first 45 components of P_N are those of P_8
+            f.set_moment(j, u)
+        f.set_time(t_good)
+        f.step(nsteps - good)
+        state = [f.moments(j) for j in range(36)]
+    finally:
+        f.close()
+    return FallbackRun(state=state, fell_back=True, good_steps=good, fallback_N=fallback_N, detail=detail)

@@ -72,6 +72,15 @@ struct starmap_s {
     int engine = mlp::ENGINE_TCGEN05;      // tensor-core path of the closure network
     int* closure_err = nullptr;            // bounded-wait flag of the tcgen05 network
     unsigned long version = 0;             // bumped whenever the tiled pass parameters change
+    // periodic health check (starmap_set_health_check)
+    long health_every = 0;                 // steps per span, 0 = off
+    double health_growth = 1.05;
+    void* snap[4] = {nullptr, nullptr, nullptr, nullptr};   // state at the end of the last span that passed
+    double snap_t = 0.0;
+    long snap_steps = 0;
+    long health_good_steps = 0;
+    double health_l2_good = 0.0, health_l2_failed = std::nan("");
+    std::vector<double> src_sq;            // per component: sum of the squared source values at its grid points
     std::string err;
 };
 
@@ -473,6 +482,7 @@ void release(starmap_t* h) {
     if (h->ctr) cudaFree(h->ctr);
     if (h->lsig) cudaFree(h->lsig);
     if (h->closure_err) cudaFree(h->closure_err);
+    for (int g = 0; g < 4; ++g) if (h->snap[g]) cudaFree(h->snap[g]);
     if (h->tiled) tiled_destroy(h->tiled);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -843,6 +853,7 @@ int starmap_set_source(starmap_t* h, int j, const double* q, size_t count) {
     CK(cudaStreamSynchronize(h->stream), "set_source");
     size_t np = comp_points(h, j);
     if (!q) {
+        if (j < (int)h->src_sq.size()) h->src_sq[j] = 0.0;
         if (h->src_slot[j] >= 0) {
             int s = h->src_slot[j];
             cudaFree(h->src_dev[s]);
@@ -867,6 +878,10 @@ int starmap_set_source(starmap_t* h, int j, const double* q, size_t count) {
         h->src_dev.push_back(d);
     }
     void* d = h->src_dev[h->src_slot[j]];
+    if (h->src_sq.size() != (size_t)h->ncomp) h->src_sq.assign(h->ncomp, 0.0);
+    double sq = 0.0;
+    for (size_t i = 0; i < np; ++i) sq += q[i] * q[i];
+    h->src_sq[j] = sq;
     if (h->fp32) {
         std::vector<float> tmp(q, q + np);
         CK(cudaMemcpy(d, tmp.data(), np * 4, cudaMemcpyHostToDevice), "upload source");
@@ -913,10 +928,125 @@ int starmap_set_time(starmap_t* h, double t) {
     return STARMAP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// FP64 reduction of the whole state, res = {mass, l2, nonfinite}
+// (synchronises the stream).
+int reduce_state(starmap_t* h, double* res) {
+    int rc;
+    if (h->fp32) {
+        ReduceArgs<float> a;
+        for (int g = 0; g < 4; ++g) a.g[g] = grid_dev<float>(h, g);
+        a.pitch = h->pitch; a.cell = h->dx * h->dy;
+        rc = launch_reduce<float>(a, h->partials, h->red_blocks, h->result, h->stream);
+    } else {
+        ReduceArgs<double> a;
+        for (int g = 0; g < 4; ++g) a.g[g] = grid_dev<double>(h, g);
+        a.pitch = h->pitch; a.cell = h->dx * h->dy;
+        rc = launch_reduce<double>(a, h->partials, h->red_blocks, h->result, h->stream);
+    }
+    if (rc) return cuda_fail(h, cudaGetLastError(), "reduction");
+    if ((rc = poll_kernel(h))) return rc;
+    CK(cudaMemcpyAsync(res, h->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reduction read-back");
+    CK(cudaStreamSynchronize(h->stream), "reduction");
+    return STARMAP_OK;
+}
+
+double source_l2(const starmap_t* h) {
+    double s = 0.0;
+    for (double v : h->src_sq) s += v;
+    return std::sqrt(s * h->dx * h->dy);
+}
+
+int health_copy(starmap_t* h, bool save) {
+    for (int g = 0; g < 4; ++g) {
+        if (save) CK(cudaMemcpyAsync(h->snap[g], h->alloc[g], h->grid_bytes[g], cudaMemcpyDeviceToDevice, h->stream), "health copy");
+        else CK(cudaMemcpyAsync(h->alloc[g], h->snap[g], h->grid_bytes[g], cudaMemcpyDeviceToDevice, h->stream), "health restore");
+    }
+    if (save) { h->snap_t = h->t; h->snap_steps = h->steps; }
+    else { h->t = h->snap_t; h->steps = h->snap_steps; h->ghosts_dirty = true; }
+    return STARMAP_OK;
+}
+
+// Steps in spans of health_every with the FP64 check after each span; on
+// failure the state of the last span that passed comes back.
+template <class T>
+int do_steps_checked(starmap_t* h, long n) {
+    if (n <= 0) return STARMAP_OK;
+    for (int g = 0; g < 4; ++g)
+        if (!h->snap[g]) CK(cudaMalloc(&h->snap[g], h->grid_bytes[g]), "cudaMalloc health copy");
+    double res[3];
+    int rc = reduce_state(h, res);
+    if (rc) return rc;
+    h->health_good_steps = h->steps;
+    h->health_l2_good = res[1];
+    h->health_l2_failed = std::nan("");
+    if (starmap_health_verdict(res[1], res[1], 0.0, 0.0, 1.0, (long)res[2]) != STARMAP_OK) {
+        h->health_l2_failed = res[1];
+        return fail(h, STARMAP_E_NONFINITE, "health check: the state holds NaN or Inf before stepping");
+    }
+    if ((rc = health_copy(h, true))) return rc;
+    for (long done = 0; done < n;) {
+        const long k = std::min(h->health_every, n - done);
+        if ((rc = do_steps<T>(h, k))) return rc;
+        if ((rc = reduce_state(h, res))) return rc;
+        const int v = starmap_health_verdict(h->health_l2_good, res[1], k * h->dt, source_l2(h), h->health_growth,
+                                             (long)res[2]);
+        if (v != STARMAP_OK) {
+            h->health_l2_failed = res[1];
+            if ((rc = health_copy(h, false))) return rc;
+            return fail(h, v, v == STARMAP_E_NONFINITE
+                                  ? "health check: NaN or Inf after a span; state reset to the last span that passed"
+                                  : "health check: L2 norm grew past its bound; state reset to the last span that passed");
+        }
+        h->health_good_steps = h->steps;
+        h->health_l2_good = res[1];
+        done += k;
+        if (done < n && (rc = health_copy(h, true))) return rc;
+    }
+    return STARMAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int starmap_health_verdict(double l2_start, double l2_end, double t_span, double q_l2, double growth,
+                           long nonfinite) {
+    if (nonfinite > 0 || !std::isfinite(l2_start) || !std::isfinite(l2_end)) return STARMAP_E_NONFINITE;
+    if (l2_end > growth * (l2_start + t_span * q_l2)) return STARMAP_E_GROWTH;
+    return STARMAP_OK;
+}
+
+int starmap_set_health_check(starmap_t* h, long every, double growth) {
+    if (!h) return STARMAP_E_ARG;
+    if (every < 0 || !(growth >= 1.0) || !std::isfinite(growth))
+        return fail(h, STARMAP_E_ARG, "health check: every must be >= 0 and growth >= 1");
+    h->health_every = every;
+    h->health_growth = growth;
+    if (every == 0) {
+        CK(cudaStreamSynchronize(h->stream), "health check off");
+        for (int g = 0; g < 4; ++g) if (h->snap[g]) { cudaFree(h->snap[g]); h->snap[g] = nullptr; }
+    }
+    return STARMAP_OK;
+}
+
+int starmap_health(const starmap_t* h, long* good_steps, double* l2_good, double* l2_failed) {
+    if (!h) return STARMAP_E_ARG;
+    if (good_steps) *good_steps = h->health_good_steps;
+    if (l2_good) *l2_good = h->health_l2_good;
+    if (l2_failed) *l2_failed = h->health_l2_failed;
+    return STARMAP_OK;
+}
+
 int starmap_step(starmap_t* h, long nsteps) {
     if (!h) return STARMAP_E_ARG;
     if (nsteps < 0) return fail(h, STARMAP_E_ARG, "negative step count");
     h->have_output = false;
+    if (h->health_every > 0)
+        return h->fp32 ? do_steps_checked<float>(h, nsteps) : do_steps_checked<double>(h, nsteps);
     return h->fp32 ? do_steps<float>(h, nsteps) : do_steps<double>(h, nsteps);
 }
 
@@ -1011,23 +1141,9 @@ int starmap_moments_window(starmap_t* h, int j, int i0, int k0, int nx, int ny, 
 
 int starmap_diagnostics(starmap_t* h, double* mass, double* l2, long* nonfinite) {
     if (!h) return STARMAP_E_ARG;
-    int rc;
-    if (h->fp32) {
-        ReduceArgs<float> a;
-        for (int g = 0; g < 4; ++g) a.g[g] = grid_dev<float>(h, g);
-        a.pitch = h->pitch; a.cell = h->dx * h->dy;
-        rc = launch_reduce<float>(a, h->partials, h->red_blocks, h->result, h->stream);
-    } else {
-        ReduceArgs<double> a;
-        for (int g = 0; g < 4; ++g) a.g[g] = grid_dev<double>(h, g);
-        a.pitch = h->pitch; a.cell = h->dx * h->dy;
-        rc = launch_reduce<double>(a, h->partials, h->red_blocks, h->result, h->stream);
-    }
-    if (rc) return cuda_fail(h, cudaGetLastError(), "reduction");
-    if ((rc = poll_kernel(h))) return rc;
     double res[3];
-    CK(cudaMemcpyAsync(res, h->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reduction read-back");
-    CK(cudaStreamSynchronize(h->stream), "reduction");
+    int rc = reduce_state(h, res);
+    if (rc) return rc;
     if (mass) *mass = res[0];
     if (l2) *l2 = res[1];
     if (nonfinite) *nonfinite = (long)res[2];

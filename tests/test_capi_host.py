@@ -87,3 +87,18 @@ def test_binding_declares_every_header_function(capi):
     src = open(os.path.join(ROOT, "paper_1211_2205_gb300", "capi.py")).read()
     declared = set(re.findall(r'"(starmap_[a-z0-9_]+)": \(', src))
     assert declared == set(capi.exported_functions())
+
+
+def test_health_verdict(capi):
+    """The health check's decision: the L2 norm may reach growth * (start +
+    t * |q|) and not beyond; a NaN or Inf anywhere is non-finite."""
+    v = capi.health_verdict
+    assert v(1.0, 1.0, 0.0, 0.0, 1.0) == capi.OK
+    assert v(1.0, 1.05, 0.0, 0.0, 1.05) == capi.OK
+    assert v(1.0, 1.0500001, 0.0, 0.0, 1.05) == capi.E_GROWTH
+    assert v(2.0, 2.0 + 0.5 * 3.0, 0.5, 3.0, 1.0) == capi.OK          # the source's share
+    assert v(2.0, 2.0 + 0.5 * 3.0 + 1e-9, 0.5, 3.0, 1.0) == capi.E_GROWTH
+    assert v(1.0, 0.2, 1.0, 0.0, 1.05) == capi.OK                      # decay is always fine
+    assert v(1.0, float("nan"), 0.1, 0.0, 1.05) == capi.E_NONFINITE
+    assert v(1.0, float("inf"), 0.1, 0.0, 1.05) == capi.E_NONFINITE
+    assert v(1.0, 1.0, 0.1, 0.0, 1.05, 3) == capi.E_NONFINITE
