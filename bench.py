@@ -596,6 +596,87 @@ def run_native(args):
     return 0
 
 
+def run_slab(args):
+    """The workload split in y over the ranks (strong scaling): each rank
+    steps its slab plus a halo and swaps halo rows with its neighbours every
+    --exchange-every steps (NCCL send/recv).  With one process and
+    --emulate R, R ranks' windows run on this GPU with device-to-device
+    exchanges (the split's overhead: halo rows stepped twice, the copies)."""
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1211_2205_gb300 import capi, slab
+
+    problem, desc = workload(args.workload)
+    if isinstance(problem, list):
+        raise SystemExit("--decomp slab splits one instance")
+    if args.grid > 0:
+        problem = inputs.Problem(**{**problem.__dict__, "n": (args.grid, args.grid)})
+    ranks = world if world > 1 else max(1, args.emulate)
+    plan = slab.SlabPlan(problem.n[1], problem.bc[1] == "periodic", ranks, args.exchange_every)
+    lam = capi.host_matrices(capi.PN2D, problem.N)[4]
+    h = min((problem.ax[1] - problem.ax[0]) / problem.n[0], (problem.ax[3] - problem.ax[2]) / problem.n[1])
+    dt = problem.cn * h / lam
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    mine = [rank] if world > 1 else list(range(ranks))
+    engines = [slab.LibraryEngine(plan, r, problem, dt, kernel=args.kernel, stream=stream.cuda_stream) for r in mine]
+    glob = slab.global_samples(problem, [engines[0].s.moment_info(j)["grid"] for j in range(engines[0].s.ncomp)])
+    for e in engines:
+        e.load(glob)
+    if world > 1:
+        exchange = lambda: slab.exchange_dist(plan, rank, engines[0])      # noqa: E731
+    else:
+        exchange = lambda: slab.exchange_local(plan, engines)              # noqa: E731
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    slab.run(plan, engines, args.warmup, exchange)
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        a.record(stream)
+        moved = slab.run(plan, engines, args.steps, exchange)
+        b.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = a.elapsed_time(b)
+    local_updates = sum(e.owned_updates() for e in engines) * args.steps
+    units, ms_max = aggregate(local_updates, ms, world)
+    mass, sq, bad = (sum(v) for v in zip(*(e.owned_sums() for e in engines)))
+    if world > 1:
+        tot = torch.tensor([mass, sq, float(bad)], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tot)
+        mass, sq, bad = tot.tolist()
+    line = {
+        "metric": METRIC, "value": units / (ms_max / 1e3), "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f32" if problem.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc + ", split in y", "N": problem.N,
+                   "grid": list(problem.n), "ranks": ranks, "emulated": world == 1 and ranks > 1,
+                   "exchange_every": plan.k, "halo_rows": plan.H, "window_cells": [plan.window_cells(r) for r in range(ranks)],
+                   "exchanged_bytes_per_step": moved / args.steps, "schedule": "merged",
+                   "l2_flush": "none: state larger than L2" if problem.n[0] * problem.n[1] >= 512 * 512 else "none",
+                   "parallelism": f"slab{ranks}"},
+        "diagnostics": {"l2": math.sqrt(sq * h * h), "nonfinite": int(bad)},
+        "clocks": clk.summary(),
+    }
+    for e in engines:
+        e.s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_batch(args):
     import torch
     world, rank, local = dist_env()
@@ -798,6 +879,11 @@ def main():
     ap.add_argument("--instances", type=int, default=0,
                     help="batched_256: keep only the first K instances (profiling captures of a smaller case of "
                          "the same kernel)")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="N > 1: independent replicas (default) or the workload split in y with halo exchanges")
+    ap.add_argument("--exchange-every", type=int, default=4, help="--decomp slab: steps between halo exchanges")
+    ap.add_argument("--emulate", type=int, default=0,
+                    help="--decomp slab in one process: run this many ranks' windows on one GPU")
     ap.add_argument("--train-steps", type=int, default=48000,
                     help="closure_p7: Adam steps (0: time the untrained network, for profiling captures)")
     args = ap.parse_args()
@@ -809,6 +895,8 @@ def main():
         return run_batch(args)
     if args.workload == "closure_p7":
         return run_closure(args)
+    if args.decomp == "slab":
+        return run_slab(args)
     return run_native(args)
 
 

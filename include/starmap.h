@@ -344,6 +344,18 @@ int starmap_diagnostics(starmap_t* h, double* mass, double* l2, long* nonfinite)
 int starmap_diagnostics_noalloc(const void* data, int precision, int ncomp, int nx, int ny,
                                 long pitch, long comp_stride, long origin, double cell,
                                 double* out_device, void* stream);
+/* Rows of a grid for halo exchanges (a spatial split of the domain over
+ * several GPUs; the paper has no counterpart).  pack copies rows
+ * [y0, y0 + rows) of every component of grid g (in its local order) to buf,
+ * laid out [component][row][x] with nx_g values per row in the run's
+ * precision; unpack copies such a buffer into those rows (and marks the
+ * boundary copies for refresh before the next pass).  bytes must equal
+ * K_g * rows * nx_g * element size.  buf may be host or device memory
+ * (any address the CUDA runtime can copy from); the copy is asynchronous on
+ * the handle's stream (synchronise before reusing a host buffer).  E_ARG if
+ * the rows leave the grid or the size does not match. */
+int starmap_pack_rows(starmap_t* h, int g, int y0, int rows, void* buf, size_t bytes);
+int starmap_unpack_rows(starmap_t* h, int g, int y0, int rows, const void* buf, size_t bytes);
 /* Device pointer of component j (borrowed), with its row pitch in elements
  * and the offset of point (0,0) in elements.  Element (i, k) is at
  * ptr[offset + k*pitch + i]; indices -1 and nx_g / ny_g hold boundary

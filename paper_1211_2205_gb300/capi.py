@@ -125,6 +125,10 @@ def lib():
         "starmap_get_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t]),
         "starmap_set_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t]),
         "starmap_sync": (ctypes.c_int, [H]),
+        "starmap_pack_rows": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_size_t]),
+        "starmap_unpack_rows": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_size_t]),
         "starmap_selftest_bounded_wait": (ctypes.c_int, []),
         "starmap_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                        ctypes.c_int, ctypes.c_long, ctypes.c_long, ctypes.c_long,
@@ -489,6 +493,16 @@ class Stepper:
         pitch, off = ctypes.c_long(), ctypes.c_long()
         self._check(self._L.starmap_device_ptr(self._h, j, ctypes.byref(p), ctypes.byref(pitch), ctypes.byref(off)))
         return p.value, pitch.value, off.value
+
+    def pack_rows(self, g: int, y0: int, rows: int, buf: int, nbytes: int):
+        """Rows [y0, y0 + rows) of every component of grid g into the buffer
+        at address buf ([component][row][x], the run's precision)."""
+        self._check(self._L.starmap_pack_rows(self._h, int(g), int(y0), int(rows), ctypes.c_void_p(buf),
+                                              int(nbytes)))
+
+    def unpack_rows(self, g: int, y0: int, rows: int, buf: int, nbytes: int):
+        self._check(self._L.starmap_unpack_rows(self._h, int(g), int(y0), int(rows), ctypes.c_void_p(buf),
+                                                int(nbytes)))
 
     def state_bytes(self) -> int:
         return self._L.starmap_state_bytes(self._h)

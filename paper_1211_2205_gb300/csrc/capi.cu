@@ -911,6 +911,46 @@ int starmap_set_moment(starmap_t* h, int j, const double* u, size_t count) {
     return STARMAP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Rows [y0, y0 + rows) of every component of grid g <-> a packed buffer
+// [component][row][x] (one 3D copy; buf host or device memory).
+int copy_rows(starmap_t* h, int g, int y0, int rows, void* buf, size_t bytes, bool pack) {
+    if (!h) return STARMAP_E_ARG;
+    if (g < 0 || g > 3) return fail(h, STARMAP_E_ARG, "grid index out of range");
+    if (y0 < 0 || rows < 0 || y0 + rows > h->nyg[g]) return fail(h, STARMAP_E_ARG, "rows leave the grid");
+    const size_t need = (size_t)h->Kg[g] * rows * h->nxg[g] * h->esize;
+    if (bytes != need) return fail(h, STARMAP_E_ARG, "buffer size does not match components x rows x nx of the grid");
+    if (need == 0) return STARMAP_OK;
+    if (!buf) return fail(h, STARMAP_E_ARG, "null buffer");
+    if (int rc = poll_kernel(h)) return rc;
+    char* dev = (char*)h->base[g] + (size_t)(y0 + 1) * h->pitch * h->esize;
+    cudaPitchedPtr state = make_cudaPitchedPtr(dev, h->pitch * h->esize, h->nxg[g] * h->esize, h->rows);
+    cudaPitchedPtr packed = make_cudaPitchedPtr(buf, h->nxg[g] * h->esize, h->nxg[g] * h->esize, rows);
+    cudaMemcpy3DParms p = {};
+    p.srcPtr = pack ? state : packed;
+    p.dstPtr = pack ? packed : state;
+    p.extent = make_cudaExtent(h->nxg[g] * h->esize, rows, h->Kg[g]);
+    p.kind = cudaMemcpyDefault;
+    CK(cudaMemcpy3DAsync(&p, h->stream), pack ? "pack rows" : "unpack rows");
+    if (!pack) { h->ghosts_dirty = true; h->have_output = false; }
+    return STARMAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int starmap_pack_rows(starmap_t* h, int g, int y0, int rows, void* buf, size_t bytes) {
+    return copy_rows(h, g, y0, rows, buf, bytes, true);
+}
+
+int starmap_unpack_rows(starmap_t* h, int g, int y0, int rows, const void* buf, size_t bytes) {
+    return copy_rows(h, g, y0, rows, const_cast<void*>(buf), bytes, false);
+}
+
 int starmap_clear(starmap_t* h) {
     if (!h) return STARMAP_E_ARG;
     for (int g = 0; g < 4; ++g)
