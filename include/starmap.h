@@ -234,6 +234,32 @@ int starmap_set_scattering_factors(starmap_t* h, const double* factor, int count
 /* Source of component j (par.source / par.source_ind), sampled on the grid
  * of j; count = nx*ny of that grid.  NULL clears it. */
 int starmap_set_source(starmap_t* h, int j, const double* q, size_t count);
+/* Time-dependent material and sources (section 5.7): each step freezes
+ * them at its midpoint t + dt/2.  With a callback set, starmap_step (and
+ * starmap_advance_to) asks it before every step for sigma_a and sigma_s0 on
+ * each of the four grids and for the source of every listed component at
+ * t + dt/2, uploads them (starmap_set_material / starmap_set_source: the
+ * decay coefficients are formed in FP64 on the host), and runs that step as
+ * O_1/2 E E O_1/2 (the literal schedule, whatever the handle's schedule).
+ * fn(user, field, t, g, x, y, count, out) fills out[i] with the value of
+ * `field` at time t at the points (x[i], y[i]) of grid g, for
+ *   field = STARMAP_FIELD_SIGMA_A, STARMAP_FIELD_SIGMA_S0, or
+ *   STARMAP_FIELD_SOURCE + j: the source of component j (g is j's grid);
+ * it returns 0, or nonzero to stop the step (the call then returns E_ARG
+ * with the state of the steps done so far).  source_comps lists the
+ * n_sources components with a source; sources of other components are
+ * removed.  The handle keeps fn, user and the list until the next call;
+ * fn = NULL turns the time dependence off (material and sources stay as
+ * last set).  fn runs on the calling thread inside the stepping call.  With
+ * the health check on, it checks after every such step.  Costs a host
+ * evaluation and an upload per step: a correctness path, not a fast one. */
+#define STARMAP_FIELD_SIGMA_A   0
+#define STARMAP_FIELD_SIGMA_S0  1
+#define STARMAP_FIELD_SOURCE    2
+typedef int (*starmap_field_fn)(void* user, int field, double t, int g, const double* x,
+                                const double* y, size_t count, double* out);
+int starmap_set_time_dependence(starmap_t* h, starmap_field_fn fn, void* user,
+                                const int* source_comps, int n_sources);
 /* Set component j (initial condition, par.ic); count = nx*ny of its grid. */
 int starmap_set_moment(starmap_t* h, int j, const double* u, size_t count);
 /* Zero every component (and its boundary copies) on the device and reset

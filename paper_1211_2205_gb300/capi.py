@@ -28,6 +28,7 @@ KERNEL_AUTO, KERNEL_GATHER, KERNEL_TILED, KERNEL_TILED_TALL, KERNEL_TILED_SHORT 
 CLOSURE_NONE, CLOSURE_MLP8 = 0, 1
 ENGINE_MMA_SYNC, ENGINE_TCGEN05 = 0, 1
 MLP_INPUTS, MLP_HIDDEN, MLP_OUTPUTS, MLP_PARAMS = 38, 128, 9, 22665
+FIELD_SIGMA_A, FIELD_SIGMA_S0, FIELD_SOURCE = 0, 1, 2
 
 
 class StarmapError(RuntimeError):
@@ -57,6 +58,10 @@ _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 _fp = ctypes.POINTER(ctypes.c_float)
+# int fn(void* user, int field, double t, int g, const double* x, const double* y, size_t count, double* out)
+FieldFn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
+                           ctypes.POINTER(ctypes.c_double))
 
 
 def exported_functions() -> list:
@@ -109,6 +114,7 @@ def lib():
         "starmap_clear": (ctypes.c_int, [H]),
         "starmap_step": (ctypes.c_int, [H, ctypes.c_long]),
         "starmap_set_health_check": (ctypes.c_int, [H, ctypes.c_long, ctypes.c_double]),
+        "starmap_set_time_dependence": (ctypes.c_int, [H, FieldFn, ctypes.c_void_p, _ip, ctypes.c_int]),
         "starmap_health": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_long), _dp, _dp]),
         "starmap_health_verdict": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                   ctypes.c_double, ctypes.c_double, ctypes.c_long]),
@@ -443,15 +449,51 @@ class Stepper:
         self._check(self._L.starmap_health(self._h, ctypes.byref(k), ctypes.byref(a), ctypes.byref(b)))
         return k.value, a.value, b.value
 
+    def set_time_dependence(self, problem):
+        """Hand the library a callback that evaluates the problem's material
+        and sources at any time (starmap_set_time_dependence): from then on
+        every step samples them at its midpoint t + dt/2 (section 5.7) and
+        runs as O_1/2 E E O_1/2.  None turns it off."""
+        if problem is None:
+            self._check(self._L.starmap_set_time_dependence(self._h, FieldFn(), None, None, 0))
+            self._td = None
+            return
+        zero = lambda t, x, y: 0.0 * x                                  # noqa: E731
+        sa = problem.sigma_a or zero
+        ss = problem.sigma_s0 or zero
+        src = {}
+        for j, q in problem.sources:
+            src.setdefault(j, []).append(q)
+
+        def fn(user, field, t, g, x, y, count, out):
+            try:
+                X = np.ctypeslib.as_array(x, shape=(count,))
+                Y = np.ctypeslib.as_array(y, shape=(count,))
+                dst = np.ctypeslib.as_array(out, shape=(count,))
+                if field == FIELD_SIGMA_A:
+                    dst[:] = np.broadcast_to(sa(t, X, Y), X.shape)
+                elif field == FIELD_SIGMA_S0:
+                    dst[:] = np.broadcast_to(ss(t, X, Y), X.shape)
+                else:
+                    dst[:] = sum(np.broadcast_to(q(t, X, Y), X.shape) for q in src[field - FIELD_SOURCE])
+                return 0
+            except Exception:                   # the library turns this into E_ARG
+                return 1
+
+        cb = FieldFn(fn)
+        comps = np.array(sorted(src), dtype=np.int32)
+        self._check(self._L.starmap_set_time_dependence(self._h, cb, None,
+                                                        comps.ctypes.data_as(_ip) if comps.size else None,
+                                                        int(comps.size)))
+        self._td = (cb, comps)                  # kept alive while the library holds the pointer
+
     def step_time_dependent(self, problem, n: int = 1):
-        """n steps of a problem whose material or sources change in time.
-        The method freezes them at each step's midpoint (section 5.5): before
-        every step they are sampled at t + dt/2 on the host and uploaded (the
-        library recomputes the decay coefficients); one step per call is the
-        literal schedule O_1/2 E E O_1/2 whatever the handle's schedule."""
-        for _ in range(int(n)):
-            self.load_problem(problem, self.time + 0.5 * self.dt, ic=False, factors=False)
-            self.step(1)
+        """n steps of a problem whose material or sources change in time,
+        through the library's time dependence (see set_time_dependence)."""
+        if getattr(self, "_td_problem", None) is not problem:
+            self.set_time_dependence(problem)
+            self._td_problem = problem
+        self.step(n)
 
     def run_pass(self, parity: int, which: int):
         self._check(self._L.starmap_pass(self._h, int(parity), int(which)))

@@ -81,6 +81,11 @@ struct starmap_s {
     long health_good_steps = 0;
     double health_l2_good = 0.0, health_l2_failed = std::nan("");
     std::vector<double> src_sq;            // per component: sum of the squared source values at its grid points
+    // time-dependent material and sources (starmap_set_time_dependence)
+    starmap_field_fn td_fn = nullptr;
+    void* td_user = nullptr;
+    std::vector<int> td_src;               // components with a source
+    std::vector<double> gx[4], gy[4];      // point coordinates of each grid, [y][x]
     std::string err;
 };
 
@@ -1081,10 +1086,99 @@ int starmap_health(const starmap_t* h, long* good_steps, double* l2_good, double
     return STARMAP_OK;
 }
 
+int starmap_set_time_dependence(starmap_t* h, starmap_field_fn fn, void* user, const int* source_comps,
+                                int n_sources) {
+    if (!h) return STARMAP_E_ARG;
+    if (!fn) {
+        h->td_fn = nullptr;
+        h->td_user = nullptr;
+        h->td_src.clear();
+        return STARMAP_OK;
+    }
+    if (n_sources < 0 || (n_sources > 0 && !source_comps)) return fail(h, STARMAP_E_ARG, "bad source list");
+    std::vector<char> seen(h->ncomp, 0);
+    for (int i = 0; i < n_sources; ++i) {
+        const int j = source_comps[i];
+        if (j < 0 || j >= h->ncomp) return fail(h, STARMAP_E_ARG, "source component out of range");
+        if (h->frozen[j]) return fail(h, STARMAP_E_ARG, "the order-8 components of the closure take no source");
+        if (seen[j]++) return fail(h, STARMAP_E_ARG, "source component listed twice");
+    }
+    for (int g = 0; g < 4; ++g) {
+        double x0, y0, dx, dy;
+        int nx, ny;
+        starmap_grid_info(h, g, &nx, &ny, &x0, &y0, &dx, &dy);
+        h->gx[g].resize((size_t)nx * ny);
+        h->gy[g].resize((size_t)nx * ny);
+        for (int k = 0; k < ny; ++k)
+            for (int i = 0; i < nx; ++i) {
+                h->gx[g][(size_t)k * nx + i] = x0 + i * dx;
+                h->gy[g][(size_t)k * nx + i] = y0 + k * dy;
+            }
+    }
+    // components that had a source and are not listed lose it
+    for (int j = 0; j < h->ncomp; ++j)
+        if (!seen[j] && h->src_slot[j] >= 0) {
+            int rc = starmap_set_source(h, j, nullptr, 0);
+            if (rc) return rc;
+        }
+    h->td_fn = fn;
+    h->td_user = user;
+    h->td_src.assign(source_comps, source_comps + n_sources);
+    return STARMAP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Material and sources of a time-dependent problem at time t, through the
+// caller's callback.
+int load_fields_at(starmap_t* h, double t) {
+    std::vector<double> a, s;
+    for (int g = 0; g < 4; ++g) {
+        const size_t np = h->gx[g].size();
+        if (np == 0) continue;
+        a.resize(np);
+        s.resize(np);
+        if (h->td_fn(h->td_user, STARMAP_FIELD_SIGMA_A, t, g, h->gx[g].data(), h->gy[g].data(), np, a.data()) ||
+            h->td_fn(h->td_user, STARMAP_FIELD_SIGMA_S0, t, g, h->gx[g].data(), h->gy[g].data(), np, s.data()))
+            return fail(h, STARMAP_E_ARG, "time-dependence callback failed (material)");
+        int rc = starmap_set_material(h, g, a.data(), s.data(), np);
+        if (rc) return rc;
+    }
+    for (int j : h->td_src) {
+        const int g = h->sys.moms[j].grid;
+        const size_t np = h->gx[g].size();
+        a.resize(np);
+        if (h->td_fn(h->td_user, STARMAP_FIELD_SOURCE + j, t, g, h->gx[g].data(), h->gy[g].data(), np, a.data()))
+            return fail(h, STARMAP_E_ARG, "time-dependence callback failed (source)");
+        int rc = starmap_set_source(h, j, a.data(), np);
+        if (rc) return rc;
+    }
+    return STARMAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int starmap_step(starmap_t* h, long nsteps) {
     if (!h) return STARMAP_E_ARG;
     if (nsteps < 0) return fail(h, STARMAP_E_ARG, "negative step count");
     h->have_output = false;
+    if (h->td_fn) {
+        for (long i = 0; i < nsteps; ++i) {
+            int rc = load_fields_at(h, h->t + 0.5 * h->dt);
+            if (rc) return rc;
+            // one step of the merged schedule is O_1/2 E O_1/2 with the fused even pair: the literal step
+            if (h->health_every > 0)
+                rc = h->fp32 ? do_steps_checked<float>(h, 1) : do_steps_checked<double>(h, 1);
+            else
+                rc = h->fp32 ? do_steps<float>(h, 1) : do_steps<double>(h, 1);
+            if (rc) return rc;
+        }
+        return STARMAP_OK;
+    }
     if (h->health_every > 0)
         return h->fp32 ? do_steps_checked<float>(h, nsteps) : do_steps_checked<double>(h, nsteps);
     return h->fp32 ? do_steps<float>(h, nsteps) : do_steps<double>(h, nsteps);

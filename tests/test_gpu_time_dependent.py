@@ -45,7 +45,8 @@ def _run_gpu(p, t_final, kernel="auto"):
     nsteps = int(math.ceil(t_final / d - 1e-9))
     dt = t_final / nsteps                      # the final time on a step: both sides use this one
     s = capi.Stepper.from_problem(p, kernel=kernel, schedule="literal", dt=dt)
-    s.step_time_dependent(p, nsteps)
+    s.set_time_dependence(p)                   # the library samples at every step's midpoint
+    s.step(nsteps)
     out = [s.moments(j) for j in range(s.ncomp)]
     info = [s.moment_info(j) for j in range(s.ncomp)]
     coords = [s.grid_coords(i["grid"]) for i in info]
@@ -75,3 +76,26 @@ def test_mms_second_order_on_gpu():
     errs = np.array(errs)
     orders = np.log2(errs[:-1] / errs[1:])
     assert np.all(orders > 1.9) and np.all(orders < 2.1), orders
+
+
+def test_time_dependence_callback_errors_and_off():
+    """A failing callback stops the step with E_ARG; with the callback off
+    the material and sources stay as last sampled; a merged-schedule
+    handle steps time-dependent problems as the literal schedule does."""
+    p = mms_problem(16, "fp64")
+    s = capi.Stepper.from_problem(p, kernel="gather", schedule="merged")
+    s.set_time_dependence(p)
+    s.step(3)
+    lit = capi.Stepper.from_problem(p, kernel="gather", schedule="literal")
+    lit.set_time_dependence(p)
+    lit.step(3)
+    for j in range(s.ncomp):
+        assert np.array_equal(s.moments(j), lit.moments(j))
+    bad = inputs.Problem(**{**p.__dict__, "sigma_a": lambda t, x, y: 1 / 0})
+    s.set_time_dependence(bad)
+    with pytest.raises(capi.StarmapError) as e:
+        s.step(1)
+    assert e.value.code == capi.E_ARG and s.steps_done == 3
+    s.set_time_dependence(None)
+    s.step(1)
+    assert s.steps_done == 4
