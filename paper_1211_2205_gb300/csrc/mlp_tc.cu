@@ -299,7 +299,9 @@ __device__ void tc_teardown(TcSmem& S) {
 }
 
 // Fused closure evaluation: four groups per CTA work on their own tiles of
-// 128 cells (tile = 4 * CTA + group, then stepping by 4 * grid).  Each
+// 128 cells (the CTA's contiguous run of tiles, group g taking every fourth
+// from the g-th; the runs of the CTAs differ by at most one tile, so no SM
+// carries a round of tiles more than the others).  Each
 // thread of a group gathers the inputs of its cell (exactly the features
 // of the training sampler) into the group's operand buffer, the group runs
 // the network, and the thread writes s * y: R_8^m straight to G11 (with
@@ -324,7 +326,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_closure_tc(const ClosureArgs<
     const int tiles = (M + TM - 1) / TM;
     const long Pp = A.pitch;
     uint32_t ph = 0;
-    for (int tile = blockIdx.x * GROUPS + c.g; tile < tiles; tile += gridDim.x * GROUPS) {
+    // CTA b takes a contiguous run of tiles/grid or one more tiles (the
+    // runs differ by at most one tile), its groups every GROUPS-th of them
+    const int per = tiles / (int)gridDim.x, extra = tiles % (int)gridDim.x;
+    const int t0 = (int)blockIdx.x * per + min((int)blockIdx.x, extra);
+    const int t1 = t0 + per + ((int)blockIdx.x < extra ? 1 : 0);
+    for (int tile = t0 + c.g; tile < t1; tile += GROUPS) {
         TcGroup& G = S.grp[c.g];
         const int m = tile * TM + c.row;
         const bool ok = m < M;
@@ -379,7 +386,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_forward_tc(const float* __res
     const int t = threadIdx.x % GTHREADS;
     const long tiles = (M + TM - 1) / TM;
     uint32_t ph = 0;
-    for (long tile = (long)blockIdx.x * GROUPS + c.g; tile < tiles; tile += (long)gridDim.x * GROUPS) {
+    const long per = tiles / (long)gridDim.x, extra = tiles % (long)gridDim.x;
+    const long t0 = (long)blockIdx.x * per + min((long)blockIdx.x, extra);
+    const long t1 = t0 + per + ((long)blockIdx.x < extra ? 1 : 0);
+    for (long tile = t0 + c.g; tile < t1; tile += GROUPS) {
         TcGroup& G = S.grp[c.g];
         // FP32 rows -> BF16 canonical (two columns per step)
         for (int i = t; i < TM * (KX_TC / 2); i += GTHREADS) {
