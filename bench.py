@@ -788,8 +788,10 @@ def run_closure(args):
     torch.cuda.set_device(local)
     from paper_1211_2205_gb300 import capi, closure
 
+    media_kind = args.closure_media
+    t_final = 0.5 if media_kind == "periodic" else 3.2
     t0 = time.perf_counter()
-    data = closure.generate(list(range(32)), n=512, N_ref=39, snapshots=16, t_final=0.5)
+    data = closure.generate(list(range(32)), n=512, N_ref=39, snapshots=16, t_final=t_final, media=media_kind)
     t1 = time.perf_counter()
     tr = closure.train(data, steps=args.train_steps, batch=8192, noise=0.05) if args.train_steps > 0 else \
         closure.TrainResult(params=closure.init_params(0), losses=[float("nan")], steps=0)
@@ -798,7 +800,8 @@ def run_closure(args):
     # the headline compares with plain P_7 / P_11 / P_15 (the workload's comparison set); the
     # line also reports the stricter comparison with every odd order 7..15
     with ClockSampler(local) as clk:
-        ev = closure.evaluate(tr.params, [100 + k for k in range(media)], n=512, repeats=2, compare=(7, 11, 15))
+        ev = closure.evaluate(tr.params, [100 + k for k in range(media)], n=512, repeats=2, compare=(7, 11, 15),
+                              t_final=t_final, media=media_kind)
     # cost of one closure evaluation: closure + odd pass minus the same odd pass without closure
     p = inputs.closure_medium(100, n=512, N=7)
     dt = closure.common_dt(p, 39)
@@ -837,7 +840,10 @@ def run_closure(args):
         "config": {"workload": "closure_p7", "description": "P_7 FP32 + per-cell MLP 38-128-128-9 (BF16, FP32 "
                    "accumulation) predicting the order-8 moments, merged closure schedule; trained on P_39 runs "
                    "over 32 seeded 512x512 random media (16 snapshots each), input noise 0.05 in training; held-out "
-                   "media 100.. ; error = rel-L2 of R_0^0 vs P_39",
+                   "media 100.. ; error = rel-L2 of R_0^0 vs P_39; media: " +
+                   ("periodic [-1,1]^2, three pulses, to t = 0.5" if media_kind == "periodic" else
+                    "[0,7]^2, extrapolation, random blocks sigma_a U[0,5] / sigma_s0 U[0,10], Gaussian source, to t = 3.2"),
+                   "media": media_kind, "t_final": t_final,
                    "train_samples": data.count, "train_steps": tr.steps, "final_train_loss": tr.losses[-1],
                    "generate_s": t1 - t0, "train_s": t2 - t1, "compare_orders": ev["compare_orders"],
                    "matched_N": ev["matched_N"], "strict_matched_N": ev["strict_matched_N"],
@@ -884,6 +890,9 @@ def main():
     ap.add_argument("--exchange-every", type=int, default=4, help="--decomp slab: steps between halo exchanges")
     ap.add_argument("--emulate", type=int, default=0,
                     help="--decomp slab in one process: run this many ranks' windows on one GPU")
+    ap.add_argument("--closure-media", default="periodic", choices=["periodic", "c5"],
+                    help="closure_p7: periodic pulses to t = 0.5, or source-driven media on [0,7]^2 with "
+                         "extrapolation boundaries to t = 3.2")
     ap.add_argument("--train-steps", type=int, default=48000,
                     help="closure_p7: Adam steps (0: time the untrained network, for profiling captures)")
     args = ap.parse_args()

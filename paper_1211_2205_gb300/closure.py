@@ -87,8 +87,11 @@ def _set_ic(s: capi.Stepper, problem: inputs.Problem):
         s.set_moment(j, np.broadcast_to(f(0.0, X, Y), X.shape))
 
 
+MEDIA = {"periodic": inputs.closure_medium, "c5": inputs.closure_c5}
+
+
 def generate(seeds: Sequence[int], n: int = 512, N_ref: int = 39, snapshots: int = 8,
-             t_final: float = 0.5, rel_floor: float = 1e-4) -> SampleSet:
+             t_final: float = 0.5, rel_floor: float = 1e-4, media: str = "periodic") -> SampleSet:
     """Training samples from plain P_{N_ref} runs on the media of `seeds`.
     Cells whose moment scale s lies below rel_floor times the largest s of
     their snapshot are left out: there the moments are round-off far from
@@ -102,7 +105,7 @@ def generate(seeds: Sequence[int], n: int = 512, N_ref: int = 39, snapshots: int
     off = 0
     keep = []
     for seed in seeds:
-        p = inputs.closure_medium(seed, n=n, N=N_ref, t_final=t_final)
+        p = MEDIA[media](seed, n=n, N=N_ref, t_final=t_final)
         dt = common_dt(p, N_ref)
         nsteps = int(round(t_final / dt))
         marks = [int(round((k + 1) * nsteps / snapshots)) for k in range(snapshots)]
@@ -256,13 +259,14 @@ def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
 
 def evaluate(params: np.ndarray, seeds: Sequence[int], n: int = 512, orders: Sequence[int] = (7, 9, 11, 13, 15),
              N_ref: int = 39, t_final: float = 0.5, repeats: int = 1,
-             closure_schedules: Sequence[str] = ("merged",), compare: Optional[Sequence[int]] = None) -> Dict:
+             closure_schedules: Sequence[str] = ("merged",), compare: Optional[Sequence[int]] = None,
+             media: str = "periodic") -> Dict:
     """Errors of R_0^0 against P_{N_ref} and device times, per held-out
     medium; the error-matched speedup is taken among the orders `compare`
     (default: all of `orders`) and among all of `orders` ("strict")."""
     cases = []
     for seed in seeds:
-        p = inputs.closure_medium(seed, n=n, N=N_ref, t_final=t_final)
+        p = MEDIA[media](seed, n=n, N=N_ref, t_final=t_final)
         dt = common_dt(p, N_ref)
         nsteps = int(round(t_final / dt))
         ref = run_case(p, N_ref, dt, nsteps)

@@ -256,6 +256,25 @@ def closure_medium(seed: int, n: int = 512, N: int = 39, t_final: float = 0.5,
         precision=precision, sigma_a=sigma_a, sigma_s0=sigma_s0, ic=[(0, ic0)], t_final=t_final)
 
 
+def closure_c5(seed: int, n: int = 512, N: int = 39, t_final: float = 3.2, precision: str = "fp32") -> Problem:
+    """Instance of the learned-closure workload in its source-driven form
+    (seed 2205500 + seed): [0, 7]^2 with n x n cells and extrapolation
+    boundaries, to t = 3.2 (the checkerboard's domain and time), the
+    batched workload's media scaled to the domain: sigma_a iid U[0, 5] and
+    sigma_s0 iid U[0, 10] on 8 x 8 blocks; an isotropic Gaussian source of
+    R_0^0 (std 0.35, unit mass) centred uniformly in [1.75, 5.25]^2; zero
+    initial state."""
+    rng = SplitMix64(2205500 + seed)
+    ax = (0.0, 7.0, 0.0, 7.0)
+    sigma_a = piecewise_blocks(rng, 8, 0.0, 5.0, ax)
+    sigma_s0 = piecewise_blocks(rng, 8, 0.0, 10.0, ax, shift=0.61)
+    c = rng.uniforms(2)
+    src = gaussian_std(1.75 + 3.5 * c[0], 1.75 + 3.5 * c[1], 0.35)
+    return Problem(
+        name=f"closure_c5_{seed}_p{N}_{n}", N=N, ax=ax, n=(n, n), bc=("extrapolation", "extrapolation"), cn=0.5,
+        precision=precision, sigma_a=sigma_a, sigma_s0=sigma_s0, sources=[(0, src)], ic=[], t_final=t_final)
+
+
 BEAM_ANGLE = math.pi / 6
 BEAM_INTERFACE = 0.3
 
