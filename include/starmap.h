@@ -77,6 +77,15 @@ extern "C" {
  * O_1/2 (E O)^(n-1) E O_1/2 inside one starmap_step(n) call. */
 #define STARMAP_SCHEDULE_LITERAL 0
 #define STARMAP_SCHEDULE_MERGED  1
+/* FUSED: the merged schedule with each inner (E O) pair run as one
+ * temporally fused launch: per tile, the full even update and then the full
+ * odd update from the new even values (on chip and in L2), so the inner
+ * steps read and write the state once instead of moving it three times;
+ * results equal MERGED bit for bit.  Needs the tiled kernel (FP32, 2D,
+ * no closure) and a second copy of the state on the device; the step's
+ * inner pairs run two at a time (an odd count runs one of them unfused).
+ * E_UNSUPPORTED where the order's tables leave no room in shared memory. */
+#define STARMAP_SCHEDULE_FUSED   2
 
 /* Kernel selection for the half-step passes. */
 #define STARMAP_KERNEL_AUTO    0  /* tiled kernel where supported (FP32 2D P_N, N <= 63),
@@ -311,7 +320,9 @@ int starmap_health_verdict(double l2_start, double l2_end, double t_span, double
  * the odd ones; which = 0 applies the half-step coefficients (tau = dt/2),
  * which = 1 the full-step ones (tau = dt: the fused even pair, or two merged
  * odd halves).  Time and step count are not advanced.  For profiling and for
- * callers composing their own schedule of eq. solution_operator_full_step. */
+ * callers composing their own schedule of eq. solution_operator_full_step.
+ * With the fused schedule, parity 2 (which = 1) runs two fused inner steps
+ * E_dt O_dt E_dt O_dt (two launches and their boundary refreshes). */
 int starmap_pass(starmap_t* h, int parity, int which);
 /* Step until t_out lies in (t, t + dt] and keep the solution of the last
  * two time levels; starmap_output() then returns the linear interpolation

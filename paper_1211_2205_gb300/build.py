@@ -25,7 +25,8 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2"
 CXX_FLAGS = ["-O2", "-fPIC", "-std=c++17", "-I", CSRC]
 
 SOURCES = ["host_math.cpp", "kernels_gather.cu", "tiled.cu", "capi.cu", "noalloc.cu", "mlp.cu", "mlp_tc.cu", "mlp_capi.cu"]
-HEADERS = ["host_math.h", "internal.h", "tiled.h", "tiled_kernel.cuh", "mlp.h", "closure_features.cuh", "pdl.h"]
+HEADERS = ["host_math.h", "internal.h", "tiled.h", "tiled_kernel.cuh", "fused_kernel.cuh", "mlp.h", "closure_features.cuh",
+           "pdl.h"]
 
 
 def _nvcc() -> str:

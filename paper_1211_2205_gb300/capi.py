@@ -23,7 +23,7 @@ E_GROWTH = -9
 PERIODIC, EXTRAPOLATION = 0, 1
 PN2D, SLAB = 0, 1
 FP64, FP32 = 0, 1
-SCHEDULE_LITERAL, SCHEDULE_MERGED = 0, 1
+SCHEDULE_LITERAL, SCHEDULE_MERGED, SCHEDULE_FUSED = 0, 1, 2
 KERNEL_AUTO, KERNEL_GATHER, KERNEL_TILED, KERNEL_TILED_TALL, KERNEL_TILED_SHORT = 0, 1, 2, 3, 4
 CLOSURE_NONE, CLOSURE_MLP8 = 0, 1
 ENGINE_MMA_SYNC, ENGINE_TCGEN05 = 0, 1
@@ -301,7 +301,7 @@ def make_config(N: int, ax, n, bc=("periodic", "periodic"), cn: float = 0.5, pre
     c.cn = float(cn)
     c.dt = float(dt)
     c.precision = {"fp64": FP64, "fp32": FP32}[precision]
-    c.schedule = {"literal": SCHEDULE_LITERAL, "merged": SCHEDULE_MERGED}[schedule]
+    c.schedule = {"literal": SCHEDULE_LITERAL, "merged": SCHEDULE_MERGED, "fused": SCHEDULE_FUSED}[schedule]
     c.kernel = {"auto": KERNEL_AUTO, "gather": KERNEL_GATHER, "tiled": KERNEL_TILED, "tiled_tall": KERNEL_TILED_TALL,
                 "tiled_short": KERNEL_TILED_SHORT}[kernel]
     c.cuda_stream = stream

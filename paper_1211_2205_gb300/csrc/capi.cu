@@ -34,6 +34,8 @@ struct starmap_s {
     bool fp32 = false;
     void* alloc[4] = {nullptr, nullptr, nullptr, nullptr};
     void* base[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* alloc1[4] = {nullptr, nullptr, nullptr, nullptr};   // second state set (fused schedule)
+    void* base1[4] = {nullptr, nullptr, nullptr, nullptr};
     long cstride[4] = {0, 0, 0, 0};
     size_t grid_bytes[4] = {0, 0, 0, 0};
     void* coef[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -397,13 +399,53 @@ int odd_pass(starmap_t* h, int which) {
     return run_pass<T>(h, true, which);
 }
 
+// Boundary copies of the odd grids of state set `set` (0: base, 1: base1).
+template <class T>
+int refresh_odd(starmap_t* h, int set) {
+    GhostPassArgs<T> ga;
+    const int go[2] = {1, 2};
+    for (int q = 0; q < 2; ++q) {
+        ga.g[q] = grid_dev<T>(h, go[q]);
+        if (set) ga.g[q].base = (T*)h->base1[go[q]];
+        ga.grid[q] = go[q];
+    }
+    ga.pitch = h->pitch;
+    ga.p[0] = h->p[0];
+    ga.p[1] = h->p[1];
+    if (launch_fill_ghosts_pass<T>(ga, h->stream, false)) return cuda_fail(h, cudaGetLastError(), "ghost refresh");
+    return STARMAP_OK;
+}
+
+// The inner steps of the merged schedule, E_dt O_dt each, as fused launches
+// two at a time (set 0 -> set 1 -> set 0); an odd count runs one unfused.
+template <class T>
+int fused_inner_steps(starmap_t* h, long m) {
+    int rc;
+    if (m % 2) {
+        if ((rc = run_pass<T>(h, false, 1)) || (rc = odd_pass<T>(h, 1))) return rc;
+        --m;
+    }
+    for (long i = 0; i < m; ++i) {
+        const int dir = (int)(i & 1);
+        rc = tiled_fused_step(h->tiled, dir, h->stream);
+        if (rc) return fail(h, rc, tiled_error(h->tiled));
+        if ((rc = refresh_odd<T>(h, 1 - dir))) return rc;
+    }
+    return STARMAP_OK;
+}
+
 template <class T>
 int do_steps(starmap_t* h, long n) {
     if (n <= 0) return STARMAP_OK;
     if (h->closure && !h->net_ready) return fail(h, STARMAP_E_STATE, "closure handle stepped before starmap_set_closure");
     if (h->ghosts_dirty) { int rc = fill_ghosts_all<T>(h); if (rc) return rc; }
     int rc;
-    if (h->cfg.schedule == STARMAP_SCHEDULE_MERGED) {
+    if (h->cfg.schedule == STARMAP_SCHEDULE_FUSED) {
+        if ((rc = odd_pass<T>(h, 0))) return rc;
+        if ((rc = fused_inner_steps<T>(h, n - 1))) return rc;
+        if ((rc = run_pass<T>(h, false, 1))) return rc;
+        if ((rc = odd_pass<T>(h, 0))) return rc;
+    } else if (h->cfg.schedule == STARMAP_SCHEDULE_MERGED) {
         if ((rc = odd_pass<T>(h, 0))) return rc;
         for (long i = 0; i < n; ++i) {
             if ((rc = run_pass<T>(h, false, 1))) return rc;
@@ -488,6 +530,7 @@ void release(starmap_t* h) {
     if (h->lsig) cudaFree(h->lsig);
     if (h->closure_err) cudaFree(h->closure_err);
     for (int g = 0; g < 4; ++g) if (h->snap[g]) cudaFree(h->snap[g]);
+    for (int g = 0; g < 4; ++g) if (h->alloc1[g]) cudaFree(h->alloc1[g]);
     if (h->tiled) tiled_destroy(h->tiled);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -611,8 +654,13 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
         if (c.bc[d] != STARMAP_PERIODIC && c.bc[d] != STARMAP_EXTRAPOLATION)
             return fail(nullptr, STARMAP_E_ARG, "unknown boundary condition");
     if (c.precision != STARMAP_FP64 && c.precision != STARMAP_FP32) return fail(nullptr, STARMAP_E_ARG, "unknown precision");
-    if (c.schedule != STARMAP_SCHEDULE_LITERAL && c.schedule != STARMAP_SCHEDULE_MERGED)
+    if (c.schedule != STARMAP_SCHEDULE_LITERAL && c.schedule != STARMAP_SCHEDULE_MERGED &&
+        c.schedule != STARMAP_SCHEDULE_FUSED)
         return fail(nullptr, STARMAP_E_ARG, "unknown schedule");
+    if (c.schedule == STARMAP_SCHEDULE_FUSED &&
+        (c.closure != STARMAP_CLOSURE_NONE || c.system != STARMAP_PN2D || c.precision != STARMAP_FP32 ||
+         c.kernel == STARMAP_KERNEL_GATHER))
+        return fail(nullptr, STARMAP_E_UNSUPPORTED, "the fused schedule needs the tiled kernel: FP32, 2D, no closure");
     if (c.kernel < STARMAP_KERNEL_AUTO || c.kernel > STARMAP_KERNEL_TILED_SHORT) return fail(nullptr, STARMAP_E_ARG, "unknown kernel");
     if (c.closure != STARMAP_CLOSURE_NONE && c.closure != STARMAP_CLOSURE_MLP8)
         return fail(nullptr, STARMAP_E_ARG, "unknown closure");
@@ -757,6 +805,20 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
         rc = rebuild_tables(h);
     }
     if (rc) return bail(rc);
+    if (c.schedule == STARMAP_SCHEDULE_FUSED) {
+        // the second state set the fused steps alternate with
+        if (!h->tiled) return bail(fail(h, STARMAP_E_UNSUPPORTED, "the fused schedule needs the tiled kernel"));
+        for (int g = 0; g < 4; ++g) {
+            e = cudaMalloc(&h->alloc1[g], h->grid_bytes[g]);
+            if (e != cudaSuccess) return bail(fail(h, e == cudaErrorMemoryAllocation ? STARMAP_E_NOMEM : STARMAP_E_CUDA,
+                                                    std::string("cudaMalloc second state: ") + cudaGetErrorString(e)));
+            e = cudaMemsetAsync(h->alloc1[g], 0, h->grid_bytes[g], h->stream);
+            if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMemset second state"));
+            h->base1[g] = (char*)h->alloc1[g] + LEAD * h->esize;
+        }
+        rc = tiled_fused_setup(h->tiled, h->base1);
+        if (rc) return bail(fail(h, rc, tiled_error(h->tiled)));
+    }
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "create"));
     *out = h;
@@ -1186,6 +1248,14 @@ int starmap_step(starmap_t* h, long nsteps) {
 
 int starmap_pass(starmap_t* h, int parity, int which) {
     if (!h) return STARMAP_E_ARG;
+    if (parity == 2) {
+        // two fused inner steps (set 0 -> set 1 -> set 0)
+        if (h->cfg.schedule != STARMAP_SCHEDULE_FUSED || which != 1)
+            return fail(h, STARMAP_E_ARG, "parity 2 (a fused pair) needs the fused schedule and which = 1");
+        h->have_output = false;
+        if (h->ghosts_dirty) { int rc = fill_ghosts_all<float>(h); if (rc) return rc; }
+        return fused_inner_steps<float>(h, 2);
+    }
     if ((parity != 0 && parity != 1) || (which != 0 && which != 1)) return fail(h, STARMAP_E_ARG, "parity and which must be 0 or 1");
     h->have_output = false;
     if (h->closure && parity == 1 && !h->net_ready)

@@ -35,6 +35,22 @@ __device__ __forceinline__ void store_point(T* comp, long pitch, int x, int y, i
     if (gyb != -2) comp[(long)(gyb + 1) * pitch + x] = v;
 }
 
+// Corner boundary copy t (0: (-1,-1), 1: (nx,-1), 2: (-1,ny), 3: (nx,ny)):
+// where both axes keep a copy on that side, the x rule applied to the y
+// copy.  The passes never read corners; the fused step's even update does
+// at the points it adds beyond a periodic edge next to a corner.
+template <class T>
+__device__ __forceinline__ void corner_ghost(T* comp, long pitch, int nx, int ny, bool xnode, bool ynode,
+                                             int px, int py, int t) {
+    const bool hx = px || !xnode, hy = py || !ynode;
+    if (!hx || !hy) return;
+    const bool right = t & 1, top = t & 2;
+    const int gx = right ? nx : -1, gy = top ? ny : -1;
+    const int sx = right ? (px ? 0 : nx - 1) : (px ? nx - 1 : 0);
+    const int sy = top ? (py ? 0 : ny - 1) : (py ? ny - 1 : 0);
+    comp[(long)(gy + 1) * pitch + gx] = comp[(long)(sy + 1) * pitch + sx];
+}
+
 template <class T>
 __global__ void k_gather_pass(const GatherArgs<T> A) {
     const int g = A.out_grid;
@@ -97,6 +113,10 @@ __global__ void k_fill_ghosts(const GhostArgs<T> A) {
         const T v = comp[(long)(y + 1) * A.pitch + x];
         store_point(comp, A.pitch, x, y, G.nx, G.ny, xnode, ynode, A.p[0], A.p[1], v);
     }
+    const long corners = 4L * (A.kend - A.kbegin);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < corners; t += (long)gridDim.x * blockDim.x)
+        corner_ghost(G.base + (long)(A.kbegin + t / 4) * G.cstride, A.pitch, G.nx, G.ny, xnode, ynode, A.p[0], A.p[1],
+                     (int)(t % 4));
 }
 
 // Boundary copies after a pass whose kernel left them out: blockIdx.y runs
@@ -123,6 +143,7 @@ __global__ void k_fill_ghosts_pass(const GhostPassArgs<T> A) {
         const T v = comp[(long)(y + 1) * A.pitch + x];
         store_point(comp, A.pitch, x, y, nx, ny, xnode, ynode, A.p[0], A.p[1], v);
     }
+    if (blockIdx.x == 0 && threadIdx.x < 4) corner_ghost(comp, A.pitch, nx, ny, xnode, ynode, A.p[0], A.p[1], threadIdx.x);
 }
 
 // Batched refresh: block b re-stores the boundary points of component

@@ -22,6 +22,8 @@
 #define STARMAP_TILED_MINB 2
 #define STARMAP_TILED_RW 1
 #include "tiled_kernel.cuh"
+// the temporally fused step (even then odd update per tile, one launch)
+#include "fused_kernel.cuh"
 
 namespace starmap {
 
@@ -128,6 +130,14 @@ struct TiledPlan {
     int nring[2] = {0, 0};                // ring stages per parity
     Params prm[2][2];                     // [P][which]
     bool ready = false;
+    // temporally fused step
+    bool fused = false;
+    void* base1[4] = {nullptr, nullptr, nullptr, nullptr};   // the second buffer set
+    fused::FusedParams fprm[2];           // [dir]: 0 set 0 -> set 1, 1 set 1 -> set 0
+    void* dev_odep = nullptr;
+    int fsmem = 0;
+    int ftiles_x = 0, ftiles_y = 0;
+    bool fready = false;
 };
 
 namespace {
@@ -144,6 +154,9 @@ void free_tables(TiledPlan* pl) {
     }
     if (pl->dev_src) cudaFree(pl->dev_src);
     pl->dev_src = nullptr;
+    if (pl->dev_odep) cudaFree(pl->dev_odep);
+    pl->dev_odep = nullptr;
+    pl->fready = false;
 }
 
 template <class V>
@@ -268,6 +281,136 @@ bool build_pass(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int>
     }
     if (covered != total) { err = "coupling pattern differs from the tiled kernel's structure"; return false; }
     return true;
+}
+
+// Parameters of the fused step, both directions, from the pass tables.
+int build_fused(TiledPlan* pl) {
+    pl->fready = false;
+    if (!pl->fused || !pl->ready) return 0;
+    const PassTables& te = pl->tab[0];
+    const PassTables& to = pl->tab[1];
+    if (te.top != pl->N || to.top != pl->N) { pl->err = "the fused step has no frozen components"; return -8; }
+    // odep: the O stage's even inputs are finalised at these E stages
+    std::vector<int> fin_at[2];
+    for (int k = 0; k < 2; ++k) fin_at[k].assign(pl->geo.K[k == 0 ? 0 : 3] + 1, -1);
+    for (size_t s = 0; s < te.stages.size(); ++s) {
+        if (te.stages[s].z >= 0) fin_at[0][te.stages[s].z] = (int)s;
+        if (te.stages[s].w >= 0) fin_at[1][te.stages[s].w] = (int)s;
+    }
+    std::vector<int> odep(to.stages.size());
+    int run = 0;
+    for (size_t k = 0; k < to.stages.size(); ++k) {
+        const int4 st = to.stages[k];
+        if (st.x >= 0) {
+            if (fin_at[0][st.x] < 0) { pl->err = "fused step: an even input is never finalised"; return -8; }
+            run = std::max(run, fin_at[0][st.x] + 1);
+        }
+        if (st.y >= 0) {
+            if (fin_at[1][st.y] < 0) { pl->err = "fused step: an even input is never finalised"; return -8; }
+            run = std::max(run, fin_at[1][st.y] + 1);
+        }
+        odep[k] = run;
+    }
+    if (pl->dev_odep) cudaFree(pl->dev_odep);
+    pl->dev_odep = nullptr;
+    if (!upload(&pl->dev_odep, odep)) { pl->err = "uploading the fused tables failed"; return -4; }
+    // shared memory: barriers, two rings, both machines' tables, odep, partial sums
+    auto al16 = [](int v) { return (v + 15) & ~15; };
+    int tab = 0;
+    int coef_rel[2][2], fin_rel[2][2], stage_rel[2], part_rel[2];
+    for (int M = 0; M < 2; ++M) {
+        const Params& q = pl->prm[M == 0 ? 0 : 1][1];
+        for (int K = 0; K < 2; ++K) {
+            coef_rel[M][K] = tab;
+            tab = al16(tab + q.nin * 2 * (int)sizeof(float4));
+            fin_rel[M][K] = tab;
+            tab = al16(tab + q.nfin * (int)sizeof(int2));
+        }
+        stage_rel[M] = tab;
+        tab = al16(tab + q.nstages * (int)sizeof(int4));
+    }
+    const int odep_rel = tab;
+    tab = al16(tab + (int)odep.size() * (int)sizeof(int));
+    part_rel[0] = tab;
+    tab += nq_of(pl->N) * fused::E_CONS * 8;
+    part_rel[1] = tab;
+    tab += nq_of(pl->N) * fused::O_CONS * 8;
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int avail = maxsm - fused::RING_OFF - tab;
+    int depth = std::min(8, avail / (fused::E_STAGE + fused::O_STAGE));
+    if (depth < 3) { pl->err = "the fused step needs more shared memory than the device offers at this order"; return -8; }
+    const int ering = fused::RING_OFF, oring = ering + depth * fused::E_STAGE;
+    const int tables = oring + depth * fused::O_STAGE;
+    pl->fsmem = tables + tab;
+    if (cudaFuncSetAttribute(fused::k_fused_step, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->fsmem) != cudaSuccess) {
+        pl->err = "cudaFuncSetAttribute (fused step) failed";
+        return -4;
+    }
+    int nxmax = 0, nymax = 0;
+    for (int g = 0; g < 4; ++g) { nxmax = std::max(nxmax, pl->geo.nx[g]); nymax = std::max(nymax, pl->geo.ny[g]); }
+    pl->ftiles_x = (nxmax + fused::TXO - 1) / fused::TXO;
+    pl->ftiles_y = (nymax + fused::TYO - 1) / fused::TYO;
+    const int geven[2] = {0, 3}, godd[2] = {1, 2};
+    for (int dir = 0; dir < 2; ++dir) {
+        void* cur[4];
+        void* nxt[4];
+        for (int g = 0; g < 4; ++g) {
+            cur[g] = dir == 0 ? pl->geo.base[g] : pl->base1[g];
+            nxt[g] = dir == 0 ? pl->base1[g] : pl->geo.base[g];
+        }
+        fused::FusedParams& fp = pl->fprm[dir];
+        std::memset(&fp, 0, sizeof(fp));
+        const long rows = pl->geo.rows, pitch = pl->geo.pitch;
+        bool ok = true;
+        for (int k = 0; k < 2; ++k) {
+            // E: odd inputs of the current set, old even outputs of the current set
+            ok = ok && encode_grid_map(&fp.m[0].maps[k], cur[godd[k]], pitch, rows, pl->geo.K[godd[k]], fused::BXI, fused::BYI);
+            ok = ok && encode_grid_map(&fp.m[0].maps[2 + k], cur[geven[k]], pitch, rows, pl->geo.K[geven[k]], fused::BXO, fused::TYE);
+            // O: new even inputs of the other set, old odd outputs of the current set
+            ok = ok && encode_grid_map(&fp.m[1].maps[k], nxt[geven[k]], pitch, rows, pl->geo.K[geven[k]], fused::BXI, fused::BYI);
+            ok = ok && encode_grid_map(&fp.m[1].maps[2 + k], cur[godd[k]], pitch, rows, pl->geo.K[godd[k]], fused::BXO, fused::TYO);
+        }
+        if (!ok) { pl->err = "cuTensorMapEncodeTiled failed (fused step)"; return -4; }
+        for (int M = 0; M < 2; ++M) {
+            const int P = M == 0 ? 0 : 1;
+            const Params& q = pl->prm[P][1];
+            fused::Machine& m = fp.m[M];
+            for (int k = 0; k < 2; ++k) {
+                const int g = M == 0 ? geven[k] : godd[k];
+                m.out[k].base = (float*)nxt[g];
+                m.out[k].cstride = pl->geo.cstride[g];
+                m.out[k].coef = (const float*)pl->coef[g];
+                m.out[k].nx = pl->geo.nx[g];
+                m.out[k].ny = pl->geo.ny[g];
+                m.coef[k] = q.coef[k];
+                m.fin[k] = q.fin[k];
+                m.smem_coef_off[k] = tables + coef_rel[M][k];
+                m.smem_fin_off[k] = tables + fin_rel[M][k];
+            }
+            m.nstages = q.nstages;
+            m.nin = q.nin;
+            m.nfin = q.nfin;
+            m.nring = depth;
+            m.stages = q.stages;
+            m.smem_stage_off = tables + stage_rel[M];
+            m.smem_part_off = tables + part_rel[M];
+            m.ring_off = M == 0 ? ering : oring;
+        }
+        fp.odep = (const int*)pl->dev_odep;
+        fp.smem_odep_off = tables + odep_rel;
+        fp.pitch = pitch;
+        fp.p[0] = pl->geo.p[0];
+        fp.p[1] = pl->geo.p[1];
+        fp.tiles_x = pl->ftiles_x;
+        fp.N = pl->N;
+        fp.nclasses = pl->nclasses;
+        fp.srcs = (const float* const*)pl->dev_src;
+        fp.err = pl->err_dev;
+    }
+    pl->fready = true;
+    return 0;
 }
 
 }  // namespace
@@ -483,7 +626,7 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
         }
     }
     pl->ready = true;
-    return 0;
+    return build_fused(pl);
 }
 
 void tiled_set_coef(TiledPlan* pl, int g, void* coef, int nclasses) {
@@ -499,6 +642,42 @@ void tiled_set_coef(TiledPlan* pl, int g, void* coef, int nclasses) {
                 if (gout == g) prm.out[k].coef = (const float*)coef;
             }
         }
+    for (int dir = 0; dir < 2; ++dir) {
+        pl->fprm[dir].nclasses = nclasses;
+        for (int M = 0; M < 2; ++M)
+            for (int k = 0; k < 2; ++k) {
+                const int gout = M == 0 ? (k == 0 ? 0 : 3) : (k == 0 ? 1 : 2);
+                if (gout == g) pl->fprm[dir].m[M].out[k].coef = (const float*)coef;
+            }
+    }
+}
+
+int tiled_fused_setup(TiledPlan* pl, void* const base1[4]) {
+    if (!pl) return -7;
+    if (pl->variant != 0 && pl->variant != 1) return -8;
+    for (int g = 0; g < 4; ++g) pl->base1[g] = base1[g];
+    pl->fused = true;
+    return pl->ready ? build_fused(pl) : 0;
+}
+
+bool tiled_fused_ready(TiledPlan* pl) { return pl && pl->fused && pl->fready; }
+
+int tiled_fused_step(TiledPlan* pl, int dir, void* stream) {
+    if (!pl || !pl->fready) { if (pl) pl->err = "fused step not prepared"; return -7; }
+    const int ntiles = pl->ftiles_x * pl->ftiles_y;
+    if (ntiles <= 0) return 0;
+    const int grid = std::min(ntiles, pl->sms);
+    if ((long long)((ntiles + grid - 1) / grid) * pl->fprm[dir].m[0].nstages > 0x7fffffffll) {
+        pl->err = "too many pipeline stages per CTA for the fused step";
+        return -8;
+    }
+    fused::k_fused_step<<<grid, fused::THREADS, pl->fsmem, (cudaStream_t)stream>>>(pl->fprm[dir & 1], ntiles);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        pl->err = std::string("fused step launch: ") + cudaGetErrorString(e);
+        return -4;
+    }
+    return 0;
 }
 
 // Pipeline stages per CTA below which a pass overlaps its kernel boundaries

@@ -40,6 +40,15 @@ int tiled_pass(TiledPlan* plan, bool odd, int which, void* stream);
 // boundary refresh should be too): only for short passes, where the kernel
 // boundary is a visible share of the pass.
 bool tiled_overlap(TiledPlan* plan, bool odd);
+// Temporally fused step: one launch applies the full even update and then
+// the full odd update, tile by tile (fused_kernel.cuh), reading one buffer
+// set and writing the other.  base1: the second set's grid bases (the same
+// layout as the first).  The fused parameters follow every table rebuild.
+int tiled_fused_setup(TiledPlan* plan, void* const base1[4]);
+bool tiled_fused_ready(TiledPlan* plan);
+// dir 0: set 0 -> set 1; dir 1: set 1 -> set 0.  The caller refreshes the
+// boundary copies of the written odd grids afterwards.
+int tiled_fused_step(TiledPlan* plan, int dir, void* stream);
 // Read and clear the bounded-wait failure flag (synchronises the stream).
 int tiled_poll(TiledPlan* plan, void* stream);
 const char* tiled_error(TiledPlan* plan);
