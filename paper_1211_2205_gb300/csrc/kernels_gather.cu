@@ -51,6 +51,84 @@ __device__ __forceinline__ void corner_ghost(T* comp, long pitch, int nx, int ny
     comp[(long)(gy + 1) * pitch + gx] = comp[(long)(sy + 1) * pitch + sx];
 }
 
+// Boundary copies of one component as independent items.  A column copy
+// lands in a 32-byte sector that holds nothing else of use, so the item
+// that writes it stores the sector whole (fewer partial stores, which make
+// DRAM read the sector first):
+//   items [0, ny)                row y's gap [nx, pitch): the sector holding
+//                                nx (the interior values in it kept, row y's
+//                                right copy at nx, zero padding) and the row's
+//                                last sector (row y + 1's left copy at
+//                                pitch - 1, zero padding)
+//   items [.., + 2 nx)           rows -1 and ny (where the y axis keeps copies)
+//   4 items                      single stores: row 0's left copy and the
+//                                corners (-1,-1), (nx,-1), (nx,ny); the corner
+//                                (-1,ny) is row ny - 1's gap
+// Only padding lies between nx and pitch - 1 (pitch >= nx + 6); the copies
+// follow the rules of store_point, corners those of corner_ghost.
+// (Reading the boundary values costs a 128-byte line each from DRAM: one
+// line per row and side is what bounds this kernel.)
+__device__ __forceinline__ void store_sector(float* dst, const float (&v)[8]) {
+    reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void store_sector(double* dst, const double (&v)[4]) {
+    reinterpret_cast<double2*>(dst)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(dst)[1] = make_double2(v[2], v[3]);
+}
+
+template <class T>
+__host__ __device__ __forceinline__ int ghost_items(int nx, int ny, bool hx, bool hy) {
+    return (hx ? ny : 0) + (hy ? 2 * nx : 0) + 4;
+}
+
+template <class T>
+__device__ __forceinline__ void ghost_item(T* comp, long pitch, int nx, int ny, bool xnode, bool ynode,
+                                           int px, int py, int i) {
+    constexpr int EPS = 32 / (int)sizeof(T);         // elements per 32-byte sector
+    const bool hx = px || !xnode, hy = py || !ynode;
+    const int xl = px ? nx - 1 : 0, xr = px ? 0 : nx - 1;          // sources of the left / right copies
+    const int ylo = py ? ny - 1 : 0, yhi = py ? 0 : ny - 1;        // sources of rows -1 and ny
+    auto at = [&](int x, int y) -> T& { return comp[(long)(y + 1) * pitch + x]; };
+    if (hx) {
+        if (i < ny) {
+            const int y = i;
+            T* row = &at(0, y);
+            const int a0 = nx & ~(EPS - 1), b0 = (int)pitch - EPS;
+            T sa[EPS];
+#pragma unroll
+            for (int e = 0; e < EPS; ++e) {
+                const int x = a0 + e;
+                sa[e] = x < nx ? row[x] : (x == nx ? row[xr] : T(0));
+            }
+            // left copy of row y + 1 (for the last row: the corner (-1, ny))
+            const T left = y + 1 < ny ? at(xl, y + 1) : (hy ? at(xl, yhi) : T(0));
+            if (a0 == b0) {
+                sa[EPS - 1] = left;
+            } else {
+                T sb[EPS];
+#pragma unroll
+                for (int e = 0; e < EPS; ++e) sb[e] = T(0);
+                sb[EPS - 1] = left;
+                store_sector(row + b0, sb);
+            }
+            store_sector(row + a0, sa);
+            return;
+        }
+        i -= ny;
+    }
+    if (hy) {
+        if (i < nx) { at(i, -1) = at(i, ylo); return; }
+        if (i < 2 * nx) { at(i - nx, ny) = at(i - nx, yhi); return; }
+        i -= 2 * nx;
+    }
+    if (i == 0) { if (hx) at(-1, 0) = at(xl, 0); return; }
+    if (!hx || !hy) return;
+    if (i == 1) at(-1, -1) = at(xl, ylo);
+    else if (i == 2) at(nx, -1) = at(xr, ylo);
+    else if (i == 3) at(nx, ny) = at(xr, yhi);
+}
+
 template <class T>
 __global__ void k_gather_pass(const GatherArgs<T> A) {
     const int g = A.out_grid;
@@ -134,16 +212,9 @@ __global__ void k_fill_ghosts_pass(const GhostPassArgs<T> A) {
     const bool xnode = (A.grid[which] & 1) != 0, ynode = (A.grid[which] & 2) != 0;
     T* comp = G.base + (long)k * G.cstride;
     const int nx = G.nx, ny = G.ny;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < 2 * (nx + ny); r += gridDim.x * blockDim.x) {
-        int x, y;
-        if (r < nx) { x = r; y = 0; }
-        else if (r < 2 * nx) { x = r - nx; y = ny - 1; }
-        else if (r < 2 * nx + ny) { x = 0; y = r - 2 * nx; }
-        else { x = nx - 1; y = r - 2 * nx - ny; }
-        const T v = comp[(long)(y + 1) * A.pitch + x];
-        store_point(comp, A.pitch, x, y, nx, ny, xnode, ynode, A.p[0], A.p[1], v);
-    }
-    if (blockIdx.x == 0 && threadIdx.x < 4) corner_ghost(comp, A.pitch, nx, ny, xnode, ynode, A.p[0], A.p[1], threadIdx.x);
+    const int items = ghost_items<T>(nx, ny, A.p[0] || !xnode, A.p[1] || !ynode);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < items; r += gridDim.x * blockDim.x)
+        ghost_item(comp, A.pitch, nx, ny, xnode, ynode, A.p[0], A.p[1], r);
 }
 
 // Batched refresh: block b re-stores the boundary points of component
@@ -152,15 +223,9 @@ __global__ void k_fill_ghosts_jobs(const GhostJob* __restrict__ jobs) {
     const GhostJob J = jobs[blockIdx.x];
     const bool xnode = (J.grid & 1) != 0, ynode = (J.grid & 2) != 0;
     const int nx = J.nx, ny = J.ny;
-    for (int r = threadIdx.x; r < 2 * (nx + ny); r += blockDim.x) {
-        int x, y;
-        if (r < nx) { x = r; y = 0; }
-        else if (r < 2 * nx) { x = r - nx; y = ny - 1; }
-        else if (r < 2 * nx + ny) { x = 0; y = r - 2 * nx; }
-        else { x = nx - 1; y = r - 2 * nx - ny; }
-        const float v = J.comp[(long)(y + 1) * J.pitch + x];
-        store_point(J.comp, J.pitch, x, y, nx, ny, xnode, ynode, J.px, J.py, v);
-    }
+    const int items = ghost_items<float>(nx, ny, J.px || !xnode, J.py || !ynode);
+    for (int r = threadIdx.x; r < items; r += blockDim.x)
+        ghost_item(J.comp, J.pitch, nx, ny, xnode, ynode, J.px, J.py, r);
 }
 
 // Deterministic FP64 reduction: per-block partials (mass, sum of squares,
@@ -252,7 +317,7 @@ template <class T>
 int launch_fill_ghosts_pass(const GhostPassArgs<T>& a, void* stream, bool overlap) {
     const int K = a.g[0].K + a.g[1].K;
     if (K <= 0) return 0;
-    const int len = 2 * std::max(a.g[0].nx + a.g[0].ny, a.g[1].nx + a.g[1].ny);
+    const int len = std::max(ghost_items<T>(a.g[0].nx, a.g[0].ny, true, true), ghost_items<T>(a.g[1].nx, a.g[1].ny, true, true));
     const dim3 grid((len + 255) / 256, K);
     const cudaError_t e = launch_pdl(k_fill_ghosts_pass<T>, grid, dim3(256), 0, (cudaStream_t)stream, overlap, a);
     return status_of(e != cudaSuccess ? e : cudaGetLastError());
