@@ -105,8 +105,72 @@ def aggregate(local_units: float, local_ms: float, world: int):
     return local_units, local_ms
 
 
+class NvmlSampler:
+    """Reads the SM clock and the clock-event reasons through NVML (queries
+    only) every INTERVAL_MS in a thread during a region; None if NVML cannot
+    be loaded."""
+
+    INTERVAL_MS = 2
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    @classmethod
+    def create(cls, index: int):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            dev = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(dev)) != 0:
+                return None
+            reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            s = cls()
+            s.lib, s.dev, s.reasons_fn, s.ct = lib, dev, reasons, ctypes
+            smax = ctypes.c_uint()
+            s.max_mhz = float(smax.value) if lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(smax)) == 0 else None
+            return s
+        except Exception:
+            return None
+
+    def __enter__(self):
+        import threading
+        self.samples = []
+        self.stop = threading.Event()
+
+        def run():
+            clk = self.ct.c_uint()
+            rs = self.ct.c_ulonglong()
+            while not self.stop.is_set():
+                if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, self.ct.byref(clk)) == 0 and \
+                        self.reasons_fn(self.dev, self.ct.byref(rs)) == 0:
+                    self.samples.append((float(clk.value), int(rs.value)))
+                self.stop.wait(self.INTERVAL_MS / 1e3)
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < 1.0:
+            time.sleep(0.001)
+        self.skip = len(self.samples)
+        return self
+
+    def __exit__(self, *exc):
+        self.stop.set()
+        self.thread.join(timeout=2)
+
+    def summary(self):
+        inside = self.samples[self.skip:] or self.samples[-1:]
+        reasons = sorted({nm for _, r in inside for bit, nm in self.REASONS.items() if r & bit})
+        sm = [c for c, _ in inside]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples) - self.skip, "interval_ms": self.INTERVAL_MS,
+                "source": "nvml"}
+
+
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons during a region."""
+    """Samples clocks and throttle reasons during a region: through NVML
+    every 2 ms where it loads, else nvidia-smi every 20 ms."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -116,6 +180,7 @@ class ClockSampler:
 
     def __init__(self, index: int):
         self.index = index
+        self.nvml = None
         self.proc = None
         self.path = None
         self.skip = 0
@@ -128,6 +193,10 @@ class ClockSampler:
             return 0
 
     def __enter__(self):
+        self.nvml = NvmlSampler.create(self.index)
+        if self.nvml is not None:
+            self.nvml.__enter__()
+            return self
         try:
             self.path = os.path.join("/tmp", f"starmap_clocks_{os.getpid()}.csv")
             self.fh = open(self.path, "w")
@@ -145,6 +214,9 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
+        if self.nvml is not None:
+            self.nvml.__exit__(*exc)
+            return
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -154,6 +226,8 @@ class ClockSampler:
             self.fh.close()
 
     def summary(self):
+        if self.nvml is not None:
+            return self.nvml.summary()
         if self.proc is None or not self.path or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, smax, reasons = [], [], set()

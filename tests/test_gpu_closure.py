@@ -274,7 +274,9 @@ def test_closed_run_matches_oracle(precision, kernel, schedule):
     ref = [u.T for u in o.U[:36]]
     effect = rel_l2([u.T for u in plain.U], ref)
     assert effect > 1e-6
-    assert rel_l2(got[:36], ref) <= 0.05 * effect
+    # the BF16 activations of the GPU network against the oracle's FP64 ones:
+    # measured 0.8 % (literal) and 1.0 % (merged) of the closure's effect
+    assert rel_l2(got[:36], ref) <= 0.02 * effect
 
 
 def test_closure_errors():
