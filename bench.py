@@ -847,6 +847,7 @@ def run_batch(args):
                    "updates_per_step": updates_per_step, "state_bytes": state_bytes, "schedule": "merged",
                    "kernel": "tiled_batch (persistent, CUDA graph)",
                    "tile_rows_autotuned": b.tile_rows()[0],
+                   "strip_stages_autotuned": b.tuning()[1], "tuning_from_cache": b.tuning()[2],
                    "autotune_ms_per_step": {"rows10": b.tile_rows()[1], "rows5": b.tile_rows()[2]},
                    "l2_flush": "none: state larger than L2", "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

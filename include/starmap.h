@@ -537,6 +537,17 @@ starmap_t* starmap_batch_instance(starmap_batch_t* b, int i);
 /* Rows of the tiles the batch uses (10 or 5) and the autotuner's ms per
  * step for each (-1 where it did not time them).  Outputs may be NULL. */
 int  starmap_batch_tile_rows(const starmap_batch_t* b, double* ms_tall, double* ms_short);
+/* The autotuner's choice: tile rows (10 or 5), stages per strip of short
+ * tiles (96, 192 or 384), and whether it came from the tuning cache (1) or
+ * from timing (0).  The autotuner (kernel AUTO) builds the batch with each
+ * tile height, plans its work units with each strip length, times four
+ * steps of every candidate and keeps the fastest; it caches the choice in a
+ * text file keyed by the device and every instance's system, order, cells,
+ * boundaries and schedule, so a later batch of the same shapes skips the
+ * timing.  The file is $STARMAP_TUNE_CACHE, else
+ * $HOME/.cache/starmap/batch_tune.txt; STARMAP_TUNE_CACHE=off disables it.
+ * A file that cannot be read or written only means no cache. */
+int  starmap_batch_tuning(const starmap_batch_t* b, int* tile_rows, int* strip_stages, int* from_cache);
 /* Kernel launches of one starmap_batch_step(b, nsteps) (inside its graph). */
 long starmap_batch_launches(const starmap_batch_t* b, long nsteps);
 int  starmap_batch_step(starmap_batch_t* b, long nsteps);

@@ -165,6 +165,7 @@ def lib():
         "starmap_batch_launches": (ctypes.c_long, [H, ctypes.c_long]),
         "starmap_batch_step": (ctypes.c_int, [H, ctypes.c_long]),
         "starmap_batch_tile_rows": (ctypes.c_int, [H, _dp, _dp]),
+        "starmap_batch_tuning": (ctypes.c_int, [H, _ip, _ip, _ip]),
         "starmap_batch_sync": (ctypes.c_int, [H]),
         "starmap_mlp_sync": (ctypes.c_int, [H]),
     }
@@ -761,6 +762,12 @@ class Batch:
         a, b = ctypes.c_double(), ctypes.c_double()
         rows = self._L.starmap_batch_tile_rows(self._h, ctypes.byref(a), ctypes.byref(b))
         return rows, a.value, b.value
+
+    def tuning(self):
+        """(tile rows, stages per strip, from the tuning cache)."""
+        r, s, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self._L.starmap_batch_tuning(self._h, ctypes.byref(r), ctypes.byref(s), ctypes.byref(c)))
+        return r.value, s.value, bool(c.value)
 
     def launches(self, nsteps: int) -> int:
         return self._L.starmap_batch_launches(self._h, int(nsteps))

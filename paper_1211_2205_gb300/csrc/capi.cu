@@ -4,9 +4,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
+
+#include <sys/stat.h>
 
 #include "host_math.h"
 #include "internal.h"
@@ -18,6 +22,9 @@ using namespace starmap;
 
 namespace {
 thread_local std::string g_create_error;
+// Tile grid of a batch instance and the cost of one of its tiles (pipeline
+// stages of its longer pass).
+struct BatchShape { int tx, ty, cost; };
 }
 
 struct starmap_s {
@@ -97,6 +104,10 @@ struct starmap_batch_s {
     int schedule = STARMAP_SCHEDULE_MERGED;
     int variant = 1;                       // tile height of every instance (see starmap_batch_create)
     double tuned_ms[2] = {-1.0, -1.0};     // autotuner: ms per step with 10-row / 5-row tiles (-1: not timed)
+    int strip = 192;                       // stages per strip of short tiles (batch_plan)
+    bool from_cache = false;               // the tuning came from the cache file
+    std::vector<BatchShape> shapes;        // per instance: tiles and stages (for re-planning)
+    int slots = 0;                         // resident CTA slots of the persistent grid
     std::vector<starmap_t*> inst;
     std::vector<unsigned long> uploaded;   // parameter version of each instance on the device
     std::vector<char> staging;             // host copy of the parameter blocks
@@ -541,10 +552,9 @@ void release(starmap_t* h) {
 extern "C" {
 
 namespace {
-// Tile grid of a batch instance and the cost of one of its tiles (pipeline
-// stages of its longer pass), and the work-unit plan of a batch (below).
-struct BatchShape { int tx, ty, cost; };
-int batch_plan(const std::vector<BatchShape>& shapes, int slots, std::vector<int4>& items, std::vector<int>& off);
+// The work-unit plan of a batch (below).
+int batch_plan(const std::vector<BatchShape>& shapes, int slots, std::vector<int4>& items, std::vector<int>& off,
+               int strip_stages = 192);
 }  // namespace
 
 void starmap_config_default(starmap_config* c) {
@@ -1540,14 +1550,16 @@ namespace {
 // Items are (instance, first tile, tile count, tile stride); CTA c runs
 // items[off[c]] .. items[off[c + 1] - 1].  Returns the grid (0 if the
 // lists would not fit 32-bit indices).
-int batch_plan(const std::vector<BatchShape>& shapes, int slots, std::vector<int4>& items, std::vector<int>& off) {
+int batch_plan(const std::vector<BatchShape>& shapes, int slots, std::vector<int4>& items, std::vector<int>& off,
+               int strip_stages_max) {
     const int count = (int)shapes.size();
     constexpr int STRIP_MAX_STAGES = 48;     // tiles up to this long go in strips
-    // stages per strip: 192, halved while the list would hold fewer than
-    // four units per CTA (a few small instances must still fill the GPU)
+    // stages per strip: strip_stages_max (192 unless the batch autotuner
+    // chose 96 or 384), halved while the list would hold fewer than four
+    // units per CTA (a few small instances must still fill the GPU)
     std::vector<int> strip(count, 1);
     long long total_units = 0;
-    for (int strip_stages = 192;; strip_stages /= 2) {
+    for (int strip_stages = std::max(1, strip_stages_max);; strip_stages /= 2) {
         total_units = 0;
         for (int i = 0; i < count; ++i) {
             const int tx = shapes[i].tx, ty = shapes[i].ty;
@@ -1619,6 +1631,32 @@ int batch_plan(const std::vector<BatchShape>& shapes, int slots, std::vector<int
     return grid;
 }
 
+// (Re)plan the work units with strips of about `strip` stages, upload the
+// lists and drop the captured step graphs (they hold the old lists).
+int batch_replan(starmap_batch_t* b, int strip) {
+    std::vector<int4> it;
+    std::vector<int> off;
+    const int grid = batch_plan(b->shapes, b->slots, it, off, strip);
+    if (grid < 1) return bfail(b, STARMAP_E_ARG, "too many tiles in one batch");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    for (auto& gx : b->graphs) cudaGraphExecDestroy(gx.second);
+    b->graphs.clear();
+    if (b->dev_items) { cudaFree(b->dev_items); b->dev_items = nullptr; }
+    if (b->dev_off) { cudaFree(b->dev_off); b->dev_off = nullptr; }
+    if (e == cudaSuccess) e = cudaMalloc(&b->dev_off, off.size() * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dev_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int4));
+    if (e == cudaSuccess && !it.empty())
+        e = cudaMemcpyAsync(b->dev_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, e == cudaErrorMemoryAllocation ? STARMAP_E_NOMEM : STARMAP_E_CUDA,
+                                       std::string("batch plan upload: ") + cudaGetErrorString(e));
+    b->grid = grid;
+    b->strip = strip;
+    return STARMAP_OK;
+}
+
 // Build a batch whose instances use tile height `variant` (0: 10 rows, 1: 5 rows).
 int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batch_t** out) {
     *out = nullptr;
@@ -1668,14 +1706,10 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int slots = sms * tiled_ctas_per_sm(b->variant);     // resident CTAs of the persistent grid
-    std::vector<int4> it;
-    std::vector<int> off;
-    const int grid = batch_plan(shapes, slots, it, off);
-    if (grid < 1) return bail(bfail(b, STARMAP_E_ARG, "too many tiles in one batch"));
+    b->slots = sms * tiled_ctas_per_sm(b->variant);     // resident CTAs of the persistent grid
+    b->shapes = shapes;
     int rc = tiled_batch_prepare(b->smem, b->variant);
     if (rc) return bail(bfail(b, rc, "batch kernel needs more shared memory than the device offers"));
-    b->grid = grid;
     b->staging.assign((size_t)count * 4 * tiled_params_bytes(), 0);
     b->uploaded.assign(count, ~0ul);
     // Boundary refresh after a pass of parity P: every component of its two
@@ -1688,12 +1722,6 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
                     jobs[P].push_back(GhostJob{(float*)h->base[g] + (long)k * h->cstride[g], h->pitch, h->nxg[g],
                                                h->nyg[g], g, h->p[0], h->p[1], 0});
     e = cudaMalloc(&b->dev_params, b->staging.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->dev_off, off.size() * sizeof(int));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->dev_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int4));
-    if (e == cudaSuccess && !it.empty())
-        e = cudaMemcpyAsync(b->dev_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
     for (int P = 0; P < 2 && e == cudaSuccess; ++P) {
         if (jobs[P].size() > 0x7fffffffu) return bail(bfail(b, STARMAP_E_ARG, "too many components in one batch"));
         b->nghosts[P] = (int)jobs[P].size();
@@ -1706,6 +1734,8 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
     if (e != cudaSuccess) return bail(bfail(b, e == cudaErrorMemoryAllocation ? STARMAP_E_NOMEM : STARMAP_E_CUDA,
                                             std::string("batch setup: ") + cudaGetErrorString(e)));
     rc = batch_sync_params(b);
+    if (rc) return bail(rc);
+    rc = batch_replan(b, b->strip);
     if (rc) return bail(rc);
     *out = b;
     return STARMAP_OK;
@@ -1740,6 +1770,78 @@ void batch_reset_clock(starmap_batch_t* b) {
 }
 }  // namespace
 
+}  // extern "C"
+
+namespace {
+
+// The autotuner's cache: one line per batch signature, "signature rows
+// strip ms" (the last line of a signature wins).
+std::string tune_cache_path() {
+    const char* env = std::getenv("STARMAP_TUNE_CACHE");
+    if (env) return std::string(env) == "off" ? std::string() : std::string(env);
+    const char* home = std::getenv("HOME");
+    return home ? std::string(home) + "/.cache/starmap/batch_tune.txt" : std::string();
+}
+
+// FNV-1a over the device (name, SM count) and every instance's system,
+// order, cells, boundaries and schedule.
+std::string batch_signature(const starmap_config* cfgs, int count) {
+    unsigned long long hsh = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) { hsh ^= c[i]; hsh *= 1099511628211ull; }
+    };
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+        mix(prop.name, std::strlen(prop.name));
+        mix(&prop.multiProcessorCount, sizeof(int));
+    }
+    mix(&count, sizeof(int));
+    for (int i = 0; i < count; ++i) {
+        const starmap_config& c = cfgs[i];
+        const int v[7] = {c.system, c.N, c.n[0], c.n[1], c.bc[0], c.bc[1], c.schedule};
+        mix(v, sizeof(v));
+    }
+    char buf[32];
+    std::snprintf(buf, sizeof(buf), "%016llx", hsh);
+    return buf;
+}
+
+bool tune_cache_get(const std::string& sig, int* rows, int* strip) {
+    const std::string path = tune_cache_path();
+    if (path.empty()) return false;
+    FILE* fp = std::fopen(path.c_str(), "r");
+    if (!fp) return false;
+    char s[64];
+    int r, st;
+    double ms;
+    bool found = false;
+    while (std::fscanf(fp, "%63s %d %d %lf", s, &r, &st, &ms) == 4)
+        if (sig == s && (r == 10 || r == 5) && st >= 1 && st <= 4096) { *rows = r; *strip = st; found = true; }
+    std::fclose(fp);
+    return found;
+}
+
+void tune_cache_put(const std::string& sig, int rows, int strip, double ms) {
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos && slash > 0) {
+        std::string dir = path.substr(0, slash);
+        for (size_t p = 1; p <= dir.size(); ++p)                  // mkdir -p
+            if (p == dir.size() || dir[p] == '/') mkdir(dir.substr(0, p).c_str(), 0755);
+    }
+    FILE* fp = std::fopen(path.c_str(), "a");
+    if (!fp) return;
+    std::fprintf(fp, "%s %d %d %.6f\n", sig.c_str(), rows, strip, ms);
+    std::fclose(fp);
+}
+
+}  // namespace
+
+extern "C" {
+
 int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t** out) {
     if (!out) return bfail(nullptr, STARMAP_E_ARG, "out is NULL");
     *out = nullptr;
@@ -1747,16 +1849,40 @@ int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t*
     const int k = cfgs[0].kernel;
     if (k == STARMAP_KERNEL_TILED_TALL || k == STARMAP_KERNEL_TILED_SHORT)
         return batch_build(cfgs, count, k == STARMAP_KERNEL_TILED_SHORT ? 1 : 0, out);
-    // Autotuner: build the batch with each tile height, time four steps of
-    // each (one step call: nine passes with the merged schedule) on the
-    // freshly created (all-zero, source-free, vacuum) state -- which the
-    // steps leave zero -- and keep the faster.
+    const std::string sig = batch_signature(cfgs, count);
+    int rows = 0, strip = 0;
+    if (tune_cache_get(sig, &rows, &strip)) {
+        starmap_batch_t* b = nullptr;
+        int rc = batch_build(cfgs, count, rows == 5 ? 1 : 0, &b);
+        if (rc == STARMAP_OK && strip != b->strip) rc = batch_replan(b, strip);
+        if (rc != STARMAP_OK) {
+            if (b) g_batch_create_error = b->err;
+            starmap_batch_destroy(b);
+            return rc;
+        }
+        b->from_cache = true;
+        *out = b;
+        return STARMAP_OK;
+    }
+    // Autotuner: build the batch with each tile height and, for each, plan
+    // the work units with strips of 96, 192 and 384 stages; time four steps
+    // of every candidate (one step call: nine passes with the merged
+    // schedule) on the freshly created (all-zero, source-free, vacuum) state
+    // -- which the steps leave zero -- keep the fastest and cache the choice.
+    static const int kStrips[3] = {192, 96, 384};
     starmap_batch_t* cand[2] = {nullptr, nullptr};
     double ms[2] = {-1.0, -1.0};
+    int best_strip[2] = {192, 192};
     int rc = STARMAP_OK;
     for (int v = 0; v < 2 && rc == STARMAP_OK; ++v) {
         rc = batch_build(cfgs, count, v, &cand[v]);
-        if (rc == STARMAP_OK) rc = batch_time(cand[v], 4, &ms[v]);
+        for (int s = 0; s < 3 && rc == STARMAP_OK; ++s) {
+            if (cand[v]->strip != kStrips[s]) rc = batch_replan(cand[v], kStrips[s]);
+            double t = 0.0;
+            if (rc == STARMAP_OK) rc = batch_time(cand[v], 4, &t);
+            if (rc == STARMAP_OK && (ms[v] < 0 || t < ms[v])) { ms[v] = t; best_strip[v] = kStrips[s]; }
+        }
+        if (rc == STARMAP_OK && cand[v]->strip != best_strip[v]) rc = batch_replan(cand[v], best_strip[v]);
         if (rc != STARMAP_OK && cand[v]) g_batch_create_error = cand[v]->err;
     }
     if (rc != STARMAP_OK) {
@@ -1769,7 +1895,16 @@ int starmap_batch_create(const starmap_config* cfgs, int count, starmap_batch_t*
     b->tuned_ms[0] = ms[0];
     b->tuned_ms[1] = ms[1];
     batch_reset_clock(b);
+    tune_cache_put(sig, best ? 5 : 10, b->strip, ms[best]);
     *out = b;
+    return STARMAP_OK;
+}
+
+int starmap_batch_tuning(const starmap_batch_t* b, int* tile_rows, int* strip_stages, int* from_cache) {
+    if (!b) return STARMAP_E_ARG;
+    if (tile_rows) *tile_rows = b->variant ? 5 : 10;
+    if (strip_stages) *strip_stages = b->strip;
+    if (from_cache) *from_cache = b->from_cache ? 1 : 0;
     return STARMAP_OK;
 }
 

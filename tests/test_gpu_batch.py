@@ -126,12 +126,15 @@ def test_batch_rejects_unsupported_instances():
     assert e.value.code == capi.E_UNSUPPORTED
 
 
-def test_autotuner_times_both_tile_heights_and_leaves_state_zero():
+def test_autotuner_times_both_tile_heights_and_leaves_state_zero(monkeypatch):
+    monkeypatch.setenv("STARMAP_TUNE_CACHE", "off")
     probs = [_instance(k) for k in range(6)]
     b = capi.Batch.from_problems(probs)                  # kernel "auto": tuned
     rows, tall, short = b.tile_rows()
     assert rows in (5, 10) and tall > 0 and short > 0
     assert (rows == 5) == (short < tall)
+    r, strip, cached = b.tuning()
+    assert r == rows and strip in (96, 192, 384) and not cached
     for inst in b.instances:
         assert inst.steps_done == 0 and inst.time == 0.0
     # the tuning steps left the state as loaded (zero before the problem data)
@@ -165,3 +168,26 @@ def test_batch_mixing_long_and_short_tiles():
             for j in range(0, inst.ncomp, max(1, inst.ncomp // 8)):
                 assert np.array_equal(inst.moments(j), alone.moments(j)), (kernel, k, j)
         b.close()
+
+
+def test_autotuner_cache(tmp_path, monkeypatch):
+    """The tuned choice is written to the cache file; a batch of the same
+    shapes takes it from there (no timing) and steps the same way."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("STARMAP_TUNE_CACHE", str(path))
+    probs = [_instance(k, nsteps=3) for k in range(3)]
+    a = capi.Batch.from_problems(probs)
+    rows, strip, cached = a.tuning()
+    assert not cached and path.exists() and len(path.read_text().splitlines()) == 1
+    b = capi.Batch.from_problems(probs)
+    assert b.tuning() == (rows, strip, True)
+    assert b.tile_rows() == (rows, -1.0, -1.0)
+    for batch in (a, b):
+        batch.step(3)
+        batch.sync()
+    for k in range(3):
+        for j in range(a.instances[k].ncomp):
+            assert np.array_equal(a.instances[k].moments(j), b.instances[k].moments(j)), (k, j)
+    other = capi.Batch.from_problems(probs[:2])          # another signature: tuned again
+    assert not other.tuning()[2]
+    assert len(path.read_text().splitlines()) == 2
