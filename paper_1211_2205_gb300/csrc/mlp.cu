@@ -727,14 +727,21 @@ __global__ void k_closure_nodes(const ClosureArgs<T> A, const float* __restrict_
             int cx0 = kx + A.p[0] - 1, cx1 = kx + A.p[0];
             if (A.p[0]) { cx0 = cx0 < 0 ? nx - 1 : cx0; cx1 = cx1 == nx ? 0 : cx1; }
             else { cx0 = max(cx0, 0); cx1 = min(cx1, nx - 1); }
+            // every load before the first store, so the loads of all outputs are in flight at once
+            float v[NOUT];
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) {
+                v[o] = 0.f;
+                if (A.slot[NMOM + o].x != 3) continue;
+                const float* c = ctr + (long)o * M;
+                v[o] = 0.25f * ((c[(long)cy0 * nx + cx0] + c[(long)cy0 * nx + cx1]) +
+                                (c[(long)cy1 * nx + cx0] + c[(long)cy1 * nx + cx1]));
+            }
 #pragma unroll
             for (int o = 0; o < NOUT; ++o) {
                 if (A.slot[NMOM + o].x != 3) continue;
-                const float* c = ctr + (long)o * M;
-                const float v = 0.25f * ((c[(long)cy0 * nx + cx0] + c[(long)cy0 * nx + cx1]) +
-                                         (c[(long)cy1 * nx + cx0] + c[(long)cy1 * nx + cx1]));
                 T* d = G.base + (long)A.slot[NMOM + o].y * G.cstride;
-                const T tv = (T)v;
+                const T tv = (T)v[o];
                 d[(long)(ky + 1) * Pp + kx] = tv;
                 if (A.p[0]) {
                     if (kx == G.nx - 1) d[(long)(ky + 1) * Pp - 1] = tv;
@@ -868,7 +875,7 @@ int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine
     float* sc = scratch + Mpad * LDX / 2;
     float* ctr = sc + Mpad;
     if (engine == ENGINE_TCGEN05) {
-        if (closure_tc<T>(A, P, ctr, err, stream)) return -4;
+        if (closure_tc<T>(A, P, ctr, sc, err, stream)) return -4;
     } else {
         long fb = (Mpad + 255) / 256;      // the features kernel covers the padded rows too
         if (fb > 32L * sm_count()) fb = 32L * sm_count();

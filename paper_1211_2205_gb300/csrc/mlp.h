@@ -82,9 +82,10 @@ int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine
 // tcgen05 network (mlp_tc.cu)
 size_t tc_smem_bytes();
 int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void* stream);
-// fused features + network + order-8 output on tcgen05 (I_8 centre values to ctr)
+// fused features + network + order-8 output on tcgen05 (I_8 centre values to
+// ctr; scl: n_x n_y floats for the cells' feature scales)
 template <class T>
-int closure_tc(const ClosureArgs<T>& A, const Packed* P, float* ctr, int* err, void* stream);
+int closure_tc(const ClosureArgs<T>& A, const Packed* P, float* ctr, float* scl, int* err, void* stream);
 
 }  // namespace mlp
 }  // namespace starmap

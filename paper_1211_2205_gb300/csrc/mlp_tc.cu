@@ -1,20 +1,29 @@
 // The closure network on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// One CTA per SM: four independent groups of 4 warps, each owning a tile of
-// 128 samples at a time (its own TMEM columns, operand buffers, mbarrier and
-// named barrier; the weights are shared).  Operands live in shared
-// memory in the canonical K-major layout without swizzle: 8-row x 16-byte
-// core matrices; an M x K (or N x K) operand stores element (r, k) at
+// Operands live in shared memory in the canonical K-major layout without
+// swizzle: 8-row x 16-byte core matrices; an M x K (or N x K) operand stores
+// element (r, k) at
 //     (k / 8) * LBO + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2  bytes,
 // LBO = (rows / 8) * 128 (core matrices adjacent along M/N are 128 bytes
-// apart = SBO, along K LBO apart).  One elected thread issues the layer's
-// tcgen05.mma (M = 128, K = 16 per instruction, BF16 x BF16 -> FP32) into the
-// group's 128-column TMEM accumulator and commits it to the group's
-// mbarrier; the group's 4 warps then read the accumulator with tcgen05.ld
-// (thread = row = TMEM lane), add the bias, apply the shared activation
-// (tanh.approx.bf16x2 of the BF16-rounded pre-activation) and write the
-// next layer's operand back to shared memory.  Layers: 38(48) -> 128
-// (3 MMAs), 128 -> 128 (8 MMAs), 128 -> 16 (9 used, 8 MMAs with N = 16).
+// apart = SBO, along K LBO apart).  A tile is 128 samples.  One elected
+// thread of a 4-warp group issues the layer's tcgen05.mma (M = 128, K = 16
+// per instruction, BF16 x BF16 -> FP32) into the group's 128-column TMEM
+// accumulator and commits it to the group's mbarrier; the group's 4 warps
+// then read the accumulator with tcgen05.ld (thread = row = TMEM lane), add
+// the bias, apply the shared activation (tanh.approx.bf16x2 of the
+// BF16-rounded pre-activation) and write the next layer's operand back to
+// shared memory.  Layers: 38(48) -> 128 (3 MMAs), 128 -> 128 (8 MMAs),
+// 128 -> 16 (9 used, 8 MMAs with N = 16).
+//
+// Two kernels, one CTA per SM each:
+//  - k_forward_tc (inference on given input rows): five groups, each staging
+//    its own tiles, sharing four TMEM accumulators (a group loading its
+//    inputs holds none);
+//  - k_closure_tc (the fused closure): one producer group gathers each
+//    tile's cell features from the moment grids into the input buffer of the
+//    consumer group that runs the tile's network; full / empty mbarriers
+//    hand the buffers back and forth, so the gather's memory latency hides
+//    behind the other tiles' tensor and activation work.
 // Every wait is bounded; on expiry the kernel raises the error flag, skips
 // the rest, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -33,7 +42,8 @@ namespace mlp {
 namespace {
 
 constexpr int TM = 128;                  // samples per tile (MMA M)
-constexpr int GROUPS = 4;                // independent 4-warp groups per CTA, one tile each
+constexpr int GROUPS = 5;                // independent 4-warp groups per CTA, one tile each
+constexpr int SLOTS = 4;                 // 128-column TMEM accumulators, shared by the groups
 constexpr int GWARPS = 4;
 constexpr int GTHREADS = GWARPS * 32;    // one thread per tile row (= TMEM lane)
 constexpr int TC_THREADS = GROUPS * GTHREADS;
@@ -43,11 +53,18 @@ constexpr int W1_BYTES = (KX_TC / 8) * (HID / 8) * 128;      // 12288
 constexpr int W2_BYTES = (HID / 8) * (HID / 8) * 128;        // 32768
 constexpr int W3_BYTES = (HID / 8) * (OUTP / 8) * 128;       // 4096
 constexpr int H_BYTES = (HID / 8) * (TM / 8) * 128;          // 32768
-constexpr int TMEM_COLS = 512;           // 128 accumulator columns per group
+constexpr int TMEM_COLS = SLOTS * 128;   // one 128-column accumulator per slot
+constexpr int CONSUMERS = 4;             // closure kernel: network groups (one accumulator each)
+constexpr int PRODUCERS = 2;             // closure kernel: feature-gathering groups
+constexpr int CL_THREADS = (CONSUMERS + PRODUCERS) * GTHREADS;
+static_assert(CONSUMERS % PRODUCERS == 0, "each consumer is fed by one producer");
+static_assert(CONSUMERS * 128 <= TMEM_COLS, "one accumulator per consumer group");
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
+static_assert(XC_BYTES <= H_BYTES, "the input operand fits in the hidden operand's buffer");
 
+// A group's operand buffer: the layer-0 input (canonical, K = 48) at its
+// start, overwritten by the hidden activations once layer 0's MMAs are done.
 struct TcGroup {
-    alignas(128) unsigned char x[XC_BYTES];
     alignas(128) unsigned char h[H_BYTES];
 };
 struct TcSmem {
@@ -55,12 +72,38 @@ struct TcSmem {
     alignas(128) unsigned char w2[W2_BYTES];
     alignas(128) unsigned char w3[W3_BYTES];
     TcGroup grp[GROUPS];
-    float b1[HID], b2[HID], b3[OUTP];
+    alignas(16) float b1[HID];
+    alignas(16) float b2[HID];
+    alignas(16) float b3[OUTP];
     alignas(8) uint64_t mbar[GROUPS];
     uint32_t tmem;
     int abort[GROUPS];
+    int slot[GROUPS];                    // TMEM slot a group holds from its first MMA to its output
+    int free_slots;                      // bit s: slot s is free
 };
-static_assert(sizeof(TcSmem) <= 227 * 1024, "tile groups must fit in shared memory");
+static_assert(sizeof(TcSmem) <= 227 * 1024, "forward kernel shared memory");
+
+// Closure kernel: per consumer group its hidden operand h and its input
+// buffer x (written by the producer group); full[c] completes when the
+// producer has written consumer c's next tile (one arrival per producer
+// thread), empty[c] when consumer c's layer-0 MMAs have read it.
+struct ClSmem {
+    alignas(128) unsigned char w1[W1_BYTES];
+    alignas(128) unsigned char w2[W2_BYTES];
+    alignas(128) unsigned char w3[W3_BYTES];
+    alignas(128) unsigned char h[CONSUMERS][H_BYTES];
+    alignas(128) unsigned char x[CONSUMERS][XC_BYTES];
+    alignas(16) float b1[HID];
+    alignas(16) float b2[HID];
+    alignas(16) float b3[OUTP];
+    alignas(8) uint64_t mma[CONSUMERS];
+    alignas(8) uint64_t full[CONSUMERS];
+    alignas(8) uint64_t empty[CONSUMERS];
+    uint32_t tmem;
+    int abort;                           // a wait expired: every role stops at its next wait
+    int stop[CONSUMERS];                 // a consumer group's verdict, set by its leader
+};
+static_assert(sizeof(ClSmem) + 64 * sizeof(void*) <= 227 * 1024, "closure kernel shared memory");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -104,22 +147,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
         : "r"(taddr));
 }
-// 64 consecutive columns of this warp's 32 lanes in one load
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+// 32 consecutive columns of this warp's 32 lanes in one load
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
           "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
-          "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
-          "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
-          "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
-          "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -129,11 +166,13 @@ __device__ __forceinline__ unsigned long long gtime() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// The waiting thread is suspended until the phase completes or about 0.1 ms
+// pass, so a wait issues a handful of instructions rather than a busy loop.
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok) : "r"(su32(bar)), "r"(parity) : "memory");
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(su32(bar)), "r"(parity), "r"(100000u) : "memory");
     return ok != 0;
 }
 // bounded wait for the MMA commit of the given phase; false on expiry
@@ -159,6 +198,17 @@ __device__ __forceinline__ uint32_t act2_tc(float lo, float hi) {
     asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
     return y;
 }
+// accumulator pair + bias pair in one packed FP32 add (each half rounded
+// exactly as a scalar add), then the activation
+__device__ __forceinline__ uint32_t bias_act2_tc(uint32_t a_lo, uint32_t a_hi, float b_lo, float b_hi) {
+    unsigned long long a, b, s;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "r"(a_lo), "r"(a_hi));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(b_lo), "f"(b_hi));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s) : "l"(a), "l"(b));
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(s));
+    return act2_tc(lo, hi);
+}
 
 __device__ __forceinline__ void cp_async16_tc(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
@@ -166,17 +216,19 @@ __device__ __forceinline__ void cp_async16_tc(uint32_t dst, const void* src) {
 
 // Weights (row-major padded BF16 of Packed) into the canonical layouts,
 // 16-byte pieces by cp.async (no register round trip); the caller waits.
-__device__ void load_weights_tc(TcSmem& S, const Packed* P) {
+template <class Sm>
+__device__ void load_weights_tc(Sm& S, const Packed* P) {
     const uint32_t w1 = su32(S.w1), w2 = su32(S.w2), w3 = su32(S.w3);
-    for (int i = threadIdx.x; i < HID * (KX_TC / 8); i += TC_THREADS) {         // W1: 128 rows x 6 chunks
+    const int nt = (int)blockDim.x;
+    for (int i = threadIdx.x; i < HID * (KX_TC / 8); i += nt) {         // W1: 128 rows x 6 chunks
         const int n = i / (KX_TC / 8), c = i % (KX_TC / 8);
         cp_async16_tc(w1 + canon(n, 8 * c, HID), P->W1 + n * LDX + 8 * c);
     }
-    for (int i = threadIdx.x; i < HID * (HID / 8); i += TC_THREADS) {           // W2: 128 rows x 16 chunks
+    for (int i = threadIdx.x; i < HID * (HID / 8); i += nt) {           // W2: 128 rows x 16 chunks
         const int n = i / (HID / 8), c = i % (HID / 8);
         cp_async16_tc(w2 + canon(n, 8 * c, HID), P->W2 + n * LDH + 8 * c);
     }
-    for (int i = threadIdx.x; i < OUTP * (HID / 8); i += TC_THREADS) {          // W3: 16 rows x 16 chunks
+    for (int i = threadIdx.x; i < OUTP * (HID / 8); i += nt) {          // W3: 16 rows x 16 chunks
         const int n = i / (HID / 8), c = i % (HID / 8);
         cp_async16_tc(w3 + canon(n, 8 * c, OUTP), P->W3 + n * LDH + 8 * c);
     }
@@ -185,10 +237,11 @@ __device__ void load_weights_tc(TcSmem& S, const Packed* P) {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Per-thread view of its group: group g, row (TMEM lane) and TMEM base.
+// Per-thread view of its group: group g, row (TMEM lane) and the lane
+// quarter's TMEM address (column 0; the group's slot adds 128 per slot).
 struct GroupCtx {
     int g, row;
-    uint32_t tacc;                      // this thread's lane quarter, the group's columns
+    uint32_t tlane;
     bool leader;
 };
 
@@ -197,34 +250,84 @@ __device__ __forceinline__ GroupCtx group_ctx(const TcSmem& S) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     c.g = warp / GWARPS;
     c.row = 32 * (warp % GWARPS) + lane;
-    c.tacc = S.tmem + ((uint32_t)(32 * (warp % GWARPS)) << 16) + (uint32_t)(128 * c.g);
+    c.tlane = S.tmem + ((uint32_t)(32 * (warp % GWARPS)) << 16);
     c.leader = (threadIdx.x % GTHREADS) == 0;
     return c;
 }
 
-// The three layers of the group's tile (inputs in its x buffer); on return
-// the output accumulator (columns 0..15 of the group) is in TMEM.  Returns
-// false if a wait expired.
+// The leader takes a free TMEM slot (bounded spin: a slot is released by a
+// group that holds it, which never waits for another group); false and the
+// error flag on expiry.
+__device__ bool slot_take(TcSmem& S, int g, int* err) {
+    volatile int* mask = &S.free_slots;
+    const unsigned long long t0 = gtime();
+    for (;;) {
+        const int m = *mask;
+        if (m != 0) {
+            const int s = __ffs(m) - 1;
+            if (atomicCAS(&S.free_slots, m, m & ~(1 << s)) == m) {
+                __threadfence_block();          // acquire: the last holder's reads are done
+                S.slot[g] = s;
+                return true;
+            }
+            continue;
+        }
+        if (gtime() - t0 > TC_WAIT_NS) {
+            atomicExch(err, 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+// One layer's MMAs of a tile: A (canonical; K = 48 for layer 0, else 128)
+// at shared address a0, the layer's weights as B, into the accumulator at
+// TMEM address dcol (lane 0, the accumulator's first column).
+template <class Sm>
+__device__ __forceinline__ void issue_layer(const Sm& S, int layer, uint32_t dcol, uint32_t a0) {
+    const uint32_t id = layer == 2 ? idesc(TM, OUTP) : idesc(TM, HID);
+    const int nb = layer == 2 ? OUTP : HID, ksteps = layer == 0 ? KX_TC / 16 : HID / 16;
+    const uint32_t b0 = su32(layer == 0 ? S.w1 : layer == 1 ? S.w2 : S.w3);
+    for (int kk = 0; kk < ksteps; ++kk)
+        mma_f16(dcol, sdesc(a0 + kk * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
+                sdesc(b0 + kk * 2 * (nb / 8) * 128, (nb / 8) * 128, 128), id, kk > 0);
+}
+
+// Bias + activation of a hidden layer for the thread's row: accumulator
+// (tacc: the thread's lane, first column) -> row `row` of the next layer's
+// A operand h.
+__device__ __forceinline__ void epilogue_layer(unsigned char* h, uint32_t tacc, const float* bias, int row) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t v[32];
+        tmem_ld32(tacc + (uint32_t)(32 * q), v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int cb = 0; cb < 32; cb += 16) {
+            uint32_t w[8];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                const float4 b = *reinterpret_cast<const float4*>(bias + 32 * q + cb + 2 * e);
+                w[e] = bias_act2_tc(v[cb + 2 * e], v[cb + 2 * e + 1], b.x, b.y);
+                w[e + 1] = bias_act2_tc(v[cb + 2 * e + 2], v[cb + 2 * e + 3], b.z, b.w);
+            }
+            *reinterpret_cast<uint4*>(h + canon(row, 32 * q + cb, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(h + canon(row, 32 * q + cb + 8, TM)) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+    }
+}
+
+// The three layers of the group's tile (inputs at the start of its operand
+// buffer); the leader first takes a TMEM slot, which the group keeps until
+// slot_give.  On return the output accumulator (columns 0..15 of the slot)
+// is in TMEM.  Returns false if a wait expired.
 __device__ bool tile_network(TcSmem& S, const GroupCtx& c, uint32_t& ph, int* err) {
     TcGroup& G = S.grp[c.g];
-    const uint32_t dcol = S.tmem + (uint32_t)(128 * c.g);     // lane 0 of the group's accumulator
-    const uint32_t id128 = idesc(TM, HID), id16 = idesc(TM, OUTP);
+    if (c.leader && !slot_take(S, c.g, err)) S.abort[c.g] = 1;
     for (int layer = 0; layer < 3; ++layer) {
-        if (c.leader) {
+        if (c.leader && !S.abort[c.g]) {
             fence_after();
-            if (layer == 0) {
-                const uint32_t a0 = su32(G.x), b0 = su32(S.w1);
-                for (int kk = 0; kk < KX_TC / 16; ++kk)
-                    mma_f16(dcol, sdesc(a0 + kk * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
-                            sdesc(b0 + kk * 2 * (HID / 8) * 128, (HID / 8) * 128, 128), id128, kk > 0);
-            } else {
-                const uint32_t a0 = su32(G.h), b0 = su32(layer == 1 ? S.w2 : S.w3);
-                const int nb = layer == 1 ? HID : OUTP;
-                for (int kk = 0; kk < HID / 16; ++kk)
-                    mma_f16(dcol, sdesc(a0 + kk * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
-                            sdesc(b0 + kk * 2 * (nb / 8) * 128, (nb / 8) * 128, 128), layer == 1 ? id128 : id16,
-                            kk > 0);
-            }
+            issue_layer(S, layer, S.tmem + (uint32_t)(128 * S.slot[c.g]), su32(G.h));
             mma_commit(&S.mbar[c.g]);
             if (!mbar_wait(&S.mbar[c.g], ph & 1, err)) S.abort[c.g] = 1;
         }
@@ -233,26 +336,7 @@ __device__ bool tile_network(TcSmem& S, const GroupCtx& c, uint32_t& ph, int* er
         if (S.abort[c.g]) return false;
         fence_after();
         if (layer == 2) return true;
-        // bias + activation: accumulator -> next layer's A operand in G.h
-        const float* bias = layer == 0 ? S.b1 : S.b2;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            uint32_t v[64];
-            tmem_ld64(c.tacc + (uint32_t)(64 * half), v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int cb = 0; cb < 64; cb += 16) {
-                uint32_t w[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int col = 64 * half + cb + 2 * e;
-                    w[e] = act2_tc(__uint_as_float(v[cb + 2 * e]) + bias[col],
-                                   __uint_as_float(v[cb + 2 * e + 1]) + bias[col + 1]);
-                }
-                *reinterpret_cast<uint4*>(G.h + canon(c.row, 64 * half + cb, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4*>(G.h + canon(c.row, 64 * half + cb + 8, TM)) = make_uint4(w[4], w[5], w[6], w[7]);
-            }
-        }
+        epilogue_layer(G.h, c.tlane + (uint32_t)(128 * S.slot[c.g]), layer == 0 ? S.b1 : S.b2, c.row);
         fence_async_smem();
         fence_before();
         group_sync(c.g);
@@ -263,10 +347,20 @@ __device__ bool tile_network(TcSmem& S, const GroupCtx& c, uint32_t& ph, int* er
 // Output of the group's tile (thread = row): y[0..15] from TMEM + b3.
 __device__ __forceinline__ void tile_output(const TcSmem& S, const GroupCtx& c, float (&y)[16]) {
     uint32_t v[16];
-    tmem_ld16(c.tacc, v);
+    tmem_ld16(c.tlane + (uint32_t)(128 * S.slot[c.g]), v);
     tmem_wait_ld();
 #pragma unroll
     for (int o = 0; o < 16; ++o) y[o] = __uint_as_float(v[o]) + S.b3[o];
+}
+
+// After the group's last TMEM read of a tile: the slot goes back to the pool.
+__device__ __forceinline__ void slot_give(TcSmem& S, const GroupCtx& c) {
+    fence_before();
+    group_sync(c.g);
+    if (c.leader) {
+        __threadfence_block();              // release: the group's TMEM reads precede the hand-back
+        atomicOr(&S.free_slots, 1 << S.slot[c.g]);
+    }
 }
 
 __device__ void tc_setup(TcSmem& S, const Packed* P) {
@@ -274,7 +368,9 @@ __device__ void tc_setup(TcSmem& S, const Packed* P) {
     if (threadIdx.x < GROUPS) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.mbar[threadIdx.x])) : "memory");
         S.abort[threadIdx.x] = 0;
+        S.slot[threadIdx.x] = 0;
     }
+    if (threadIdx.x == 0) S.free_slots = (1 << SLOTS) - 1;
     if (threadIdx.x == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem)),
@@ -298,47 +394,97 @@ __device__ void tc_teardown(TcSmem& S) {
     }
 }
 
-// Fused closure evaluation: four groups per CTA work on their own tiles of
-// 128 cells (the CTA's contiguous run of tiles, group g taking every fourth
-// from the g-th; the runs of the CTAs differ by at most one tile, so no SM
-// carries a round of tiles more than the others).  Each
-// thread of a group gathers the inputs of its cell (exactly the features
-// of the training sampler) into the group's operand buffer, the group runs
-// the network, and the thread writes s * y: R_8^m straight to G11 (with
-// their ghost copies), the centre values of I_8^m to ctr[o][M] for the node
-// averaging.  While one group gathers or waits for its MMAs, the others
-// run their epilogues, so load, tensor and MUFU latencies overlap.
+__device__ __forceinline__ void mbar_arrive_tc(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+// Bounded wait on a phase of a closure-kernel barrier: false (and the error
+// flag) on expiry, or as soon as another role of the CTA has given up.
+__device__ bool cl_wait(ClSmem& S, uint64_t* bar, uint32_t parity, int* err) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    volatile int* abort = &S.abort;
+    while (!mbar_test(bar, parity)) {
+        if (*abort) return false;
+        if (gtime() - t0 > TC_WAIT_NS) {
+            *abort = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ void cl_setup(ClSmem& S, const Packed* P) {
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x < CONSUMERS) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.mma[threadIdx.x])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&S.full[threadIdx.x])), "r"(GTHREADS)
+                     : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.empty[threadIdx.x])) : "memory");
+        S.stop[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) {
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem)),
+                     "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    load_weights_tc(S, P);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+}
+
+// Fused closure evaluation.  CTA b takes a contiguous run of the 128-cell
+// tiles (tiles / grid or one more: the runs differ by at most one tile, so
+// no SM carries a round of tiles more than the others); the k-th tile of
+// the run belongs to consumer group k mod 4 and producer group k mod 2.  A
+// producer group (one thread per cell) gathers its tiles in turn: the
+// inputs of its cell, exactly the features of the training sampler, into
+// the consumer's input buffer as BF16, and the feature scale s to scl[m],
+// once the consumer has released the buffer.  A consumer group runs the
+// network on its tiles and writes s * y: R_8^m straight to G11 (with their
+// ghost copies), the centre values of I_8^m to ctr[o][M] for the node
+// averaging.  Every consumer's tiles come from one producer in order, so
+// each barrier phase is waited on at most one phase ahead.
 template <class T>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_closure_tc(const ClosureArgs<T> A, const Packed* __restrict__ P,
-                                                              float* __restrict__ ctr, int* __restrict__ err) {
+__global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<T> A, const Packed* __restrict__ P,
+                                                              float* __restrict__ ctr, float* __restrict__ scl,
+                                                              int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char raw[];
-    TcSmem& S = *reinterpret_cast<TcSmem*>(raw);
+    ClSmem& S = *reinterpret_cast<ClSmem*>(raw);
     __shared__ const T* colp[NMOM];
     column_table(A, colp, NMOM);
-    tc_setup(S, P);                         // ends with a CTA barrier: colp is visible
+    cl_setup(S, P);                         // ends with a CTA barrier: colp is visible
     // weights, TMEM and the column table come from host-written data; the
     // state is read below, after the previous kernel of the stream is done
     pdl_trigger();
     pdl_wait();
-    const GroupCtx c = group_ctx(S);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = warp / GWARPS, row = 32 * (warp % GWARPS) + lane;
     const int nx = A.nx, ny = A.ny;
     const int M = nx * ny;
     const int tiles = (M + TM - 1) / TM;
     const long Pp = A.pitch;
-    uint32_t ph = 0;
-    // CTA b takes a contiguous run of tiles/grid or one more tiles (the
-    // runs differ by at most one tile), its groups every GROUPS-th of them
     const int per = tiles / (int)gridDim.x, extra = tiles % (int)gridDim.x;
     const int t0 = (int)blockIdx.x * per + min((int)blockIdx.x, extra);
-    const int t1 = t0 + per + ((int)blockIdx.x < extra ? 1 : 0);
-    for (int tile = t0 + c.g; tile < t1; tile += GROUPS) {
-        TcGroup& G = S.grp[c.g];
-        const int m = tile * TM + c.row;
-        const bool ok = m < M;
-        const int ix = ok ? m % nx : 0, iy = ok ? m / nx : 0;
-        float f[NMOM], s, inv;
-        features36<T>(colp, stencil(ix, iy, nx, ny, A.p[0], A.p[1], Pp), ok, f, s, inv);
-        {
+    const int n = per + ((int)blockIdx.x < extra ? 1 : 0);
+    if (g >= CONSUMERS) {
+        // producer p: tiles p, p + PRODUCERS, ... of the run, tile k into consumer k mod 4's buffer
+        for (int k = g - CONSUMERS; k < n; k += PRODUCERS) {
+            const int c = k % CONSUMERS, use = k / CONSUMERS;
+            if (use > 0 && !cl_wait(S, &S.empty[c], (uint32_t)(use - 1) & 1, err)) break;
+            const int m = (t0 + k) * TM + row;
+            const bool ok = m < M;
+            const int ix = ok ? m % nx : 0, iy = ok ? m / nx : 0;
+            float f[NMOM], s, inv;
+            features36<T>(colp, stencil(ix, iy, nx, ny, A.p[0], A.p[1], Pp), ok, f, s, inv);
             const float la = ok ? A.lsa[m] : 0.f, ls = ok ? A.lss[m] : 0.f;
             uint32_t w[KX_TC / 2];
 #pragma unroll
@@ -348,32 +494,74 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_closure_tc(const ClosureArgs<
             for (int q = NMOM / 2 + 1; q < KX_TC / 2; ++q) w[q] = 0u;
 #pragma unroll
             for (int q = 0; q < KX_TC / 8; ++q)
-                *reinterpret_cast<uint4*>(G.x + canon(c.row, 8 * q, TM)) =
+                *reinterpret_cast<uint4*>(S.x[c] + canon(row, 8 * q, TM)) =
                     make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            if (ok) scl[m] = s;
+            fence_async_smem();             // the rows are read by the tensor cores (async proxy)
+            mbar_arrive_tc(&S.full[c]);
         }
-        fence_async_smem();
-        group_sync(c.g);
-        if (!tile_network(S, c, ph, err)) break;
-        float y[16];
-        tile_output(S, c, y);
-        if (ok) {
-#pragma unroll
-            for (int o = 0; o < NOUT; ++o) {
-                const float val = s * y[o];
-                if (A.slot[NMOM + o].x != 0) { ctr[(long)o * M + m] = val; continue; }
-                T* cc = A.g[0].base + (long)A.slot[NMOM + o].y * A.g[0].cstride;
-                const T tv = (T)val;
-                cc[(long)(iy + 1) * Pp + ix] = tv;
-                if (ix == (A.p[0] ? nx - 1 : 0)) cc[(long)(iy + 1) * Pp - 1] = tv;
-                if (ix == (A.p[0] ? 0 : nx - 1)) cc[(long)(iy + 1) * Pp + nx] = tv;
-                if (iy == (A.p[1] ? ny - 1 : 0)) cc[ix] = tv;
-                if (iy == (A.p[1] ? 0 : ny - 1)) cc[(long)(ny + 1) * Pp + ix] = tv;
+    } else {
+        // consumer g: tiles g, g + 4, ... of the run
+        const bool leader = (threadIdx.x % GTHREADS) == 0;
+        const uint32_t dcol = S.tmem + (uint32_t)(128 * g);
+        const uint32_t tacc = dcol + ((uint32_t)(32 * (warp % GWARPS)) << 16);
+        uint32_t ph = 0;
+        for (int k = g, use = 0; k < n; k += CONSUMERS, ++use) {
+            const int m = (t0 + k) * TM + row;
+            float s = 0.f;                  // the cell's feature scale, loaded once the tile is produced
+            for (int layer = 0; layer < 3; ++layer) {
+                if (leader) {
+                    bool ok = layer > 0 || cl_wait(S, &S.full[g], (uint32_t)use & 1, err);
+                    if (ok) {
+                        fence_after();
+                        issue_layer(S, layer, dcol, su32(layer == 0 ? S.x[g] : S.h[g]));
+                        mma_commit(&S.mma[g]);
+                        ok = cl_wait(S, &S.mma[g], ph & 1, err);
+                        if (ok && layer == 0) mbar_arrive_tc(&S.empty[g]);   // the input buffer is read
+                    }
+                    if (!ok) S.stop[g] = 1;
+                }
+                ++ph;
+                group_sync(g);
+                if (S.stop[g]) break;
+                fence_after();
+                if (layer == 0 && m < M) s = scl[m];
+                if (layer == 2) break;
+                epilogue_layer(S.h[g], tacc, layer == 0 ? S.b1 : S.b2, row);
+                fence_async_smem();
+                fence_before();
+                group_sync(g);
             }
+            if (S.stop[g]) break;
+            // output: s * (y + b3), y from the accumulator's first 16 columns
+            uint32_t v[16];
+            tmem_ld16(tacc, v);
+            tmem_wait_ld();
+            if (m < M) {
+                const int ix = m % nx, iy = m / nx;
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    const float val = s * (__uint_as_float(v[o]) + S.b3[o]);
+                    if (A.slot[NMOM + o].x != 0) { ctr[(long)o * M + m] = val; continue; }
+                    T* cc = A.g[0].base + (long)A.slot[NMOM + o].y * A.g[0].cstride;
+                    const T tv = (T)val;
+                    cc[(long)(iy + 1) * Pp + ix] = tv;
+                    if (ix == (A.p[0] ? nx - 1 : 0)) cc[(long)(iy + 1) * Pp - 1] = tv;
+                    if (ix == (A.p[0] ? 0 : nx - 1)) cc[(long)(iy + 1) * Pp + nx] = tv;
+                    if (iy == (A.p[1] ? ny - 1 : 0)) cc[ix] = tv;
+                    if (iy == (A.p[1] ? 0 : ny - 1)) cc[(long)(ny + 1) * Pp + ix] = tv;
+                }
+            }
+            fence_before();                 // the accumulator is read before the next tile's MMAs
+            group_sync(g);
         }
-        fence_before();
-        group_sync(c.g);
     }
-    tc_teardown(S);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(TMEM_COLS) : "memory");
+    }
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_forward_tc(const float* __restrict__ X, long M,
@@ -397,7 +585,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_forward_tc(const float* __res
             const long m = tile * TM + r;
             float a = 0.f, b = 0.f;
             if (m < M && col < NIN) { a = X[m * NIN + col]; b = X[m * NIN + col + 1]; }
-            *reinterpret_cast<uint32_t*>(G.x + canon(r, col, TM)) = pack_bf16_tc(a, b);
+            *reinterpret_cast<uint32_t*>(G.h + canon(r, col, TM)) = pack_bf16_tc(a, b);
         }
         fence_async_smem();
         group_sync(c.g);
@@ -408,8 +596,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_forward_tc(const float* __res
         if (m < M)
 #pragma unroll
             for (int o = 0; o < NOUT; ++o) Y[m * NOUT + o] = y[o];
-        fence_before();
-        group_sync(c.g);
+        slot_give(S, c);
     }
     tc_teardown(S);
 }
@@ -448,20 +635,25 @@ int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void
 }
 
 template <class T>
-int closure_tc(const ClosureArgs<T>& A, const Packed* P, float* ctr, int* err, void* stream) {
+int closure_tc(const ClosureArgs<T>& A, const Packed* P, float* ctr, float* scl, int* err, void* stream) {
     static bool attr = false;
-    if (smem_attr(k_closure_tc<T>, attr)) return -4;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_closure_tc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ClSmem)) !=
+            cudaSuccess)
+            return -4;
+        attr = true;
+    }
     const long M = (long)A.nx * A.ny;
     if (M <= 0) return 0;
-    long blocks = (M + TM * GROUPS - 1) / (TM * GROUPS);
+    long blocks = (M + TM * CONSUMERS - 1) / (TM * CONSUMERS);
     if (blocks > sms_tc()) blocks = sms_tc();
-    const cudaError_t e = launch_pdl(k_closure_tc<T>, dim3((unsigned)blocks), dim3(TC_THREADS), sizeof(TcSmem),
-                                     (cudaStream_t)stream, true, A, P, ctr, err);
+    const cudaError_t e = launch_pdl(k_closure_tc<T>, dim3((unsigned)blocks), dim3(CL_THREADS), sizeof(ClSmem),
+                                     (cudaStream_t)stream, true, A, P, ctr, scl, err);
     return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
-template int closure_tc<float>(const ClosureArgs<float>&, const Packed*, float*, int*, void*);
-template int closure_tc<double>(const ClosureArgs<double>&, const Packed*, float*, int*, void*);
+template int closure_tc<float>(const ClosureArgs<float>&, const Packed*, float*, float*, int*, void*);
+template int closure_tc<double>(const ClosureArgs<double>&, const Packed*, float*, float*, int*, void*);
 
 }  // namespace mlp
 }  // namespace starmap
