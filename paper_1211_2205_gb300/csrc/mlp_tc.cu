@@ -48,6 +48,8 @@ constexpr int GWARPS = 4;
 constexpr int GTHREADS = GWARPS * 32;    // one thread per tile row (= TMEM lane)
 constexpr int TC_THREADS = GROUPS * GTHREADS;
 constexpr int KX_TC = 48;                // input width padded to the MMA K step
+constexpr int BIAS_COL = NIN;            // first of the three input columns carrying layer 0's bias
+static_assert(BIAS_COL + 3 <= KX_TC, "the bias columns fit in the padding");
 constexpr int XC_BYTES = (KX_TC / 8) * (TM / 8) * 128;       // 12288
 constexpr int W1_BYTES = (KX_TC / 8) * (HID / 8) * 128;      // 12288
 constexpr int W2_BYTES = (HID / 8) * (HID / 8) * 128;        // 32768
@@ -120,7 +122,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 }
 
 // instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major
-__device__ __forceinline__ uint32_t idesc(int m, int n) {
+__host__ __device__ constexpr uint32_t idesc(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
@@ -216,13 +218,35 @@ __device__ __forceinline__ void cp_async16_tc(uint32_t dst, const void* src) {
 
 // Weights (row-major padded BF16 of Packed) into the canonical layouts,
 // 16-byte pieces by cp.async (no register round trip); the caller waits.
+//
+// Layer 0's bias rides in the MMA: input columns BIAS_COL .. BIAS_COL + 2
+// (padding beyond the NIN features) hold 1.0, and W1's row n holds there the
+// three BF16 parts hi + mid + lo of b1[n] (each part the BF16 rounding of
+// what the previous parts leave, so their sum is b1[n] to FP32 precision).
 template <class Sm>
 __device__ void load_weights_tc(Sm& S, const Packed* P) {
     const uint32_t w1 = su32(S.w1), w2 = su32(S.w2), w3 = su32(S.w3);
     const int nt = (int)blockDim.x;
     for (int i = threadIdx.x; i < HID * (KX_TC / 8); i += nt) {         // W1: 128 rows x 6 chunks
         const int n = i / (KX_TC / 8), c = i % (KX_TC / 8);
-        cp_async16_tc(w1 + canon(n, 8 * c, HID), P->W1 + n * LDX + 8 * c);
+        if (8 * c + 8 <= BIAS_COL) {
+            cp_async16_tc(w1 + canon(n, 8 * c, HID), P->W1 + n * LDX + 8 * c);
+            continue;
+        }
+        __nv_bfloat16 e[8];
+        const float b = P->b1[n];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+        const float r1 = b - __bfloat162float(hi);
+        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int col = 8 * c + j;
+            e[j] = col < BIAS_COL ? P->W1[n * LDX + col]
+                 : col == BIAS_COL ? hi : col == BIAS_COL + 1 ? mid : col == BIAS_COL + 2 ? lo
+                 : __float2bfloat16_rn(0.f);
+        }
+        *reinterpret_cast<uint4*>(S.w1 + canon(n, 8 * c, HID)) = *reinterpret_cast<const uint4*>(e);
     }
     for (int i = threadIdx.x; i < HID * (HID / 8); i += nt) {           // W2: 128 rows x 16 chunks
         const int n = i / (HID / 8), c = i % (HID / 8);
@@ -232,8 +256,8 @@ __device__ void load_weights_tc(Sm& S, const Packed* P) {
         const int n = i / (HID / 8), c = i % (HID / 8);
         cp_async16_tc(w3 + canon(n, 8 * c, OUTP), P->W3 + n * LDH + 8 * c);
     }
-    for (int i = threadIdx.x; i < HID; i += TC_THREADS) { S.b1[i] = P->b1[i]; S.b2[i] = P->b2[i]; }
-    for (int i = threadIdx.x; i < OUTP; i += TC_THREADS) S.b3[i] = P->b3[i];
+    for (int i = threadIdx.x; i < HID; i += nt) { S.b1[i] = P->b1[i]; S.b2[i] = P->b2[i]; }
+    for (int i = threadIdx.x; i < OUTP; i += nt) S.b3[i] = P->b3[i];
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
@@ -282,20 +306,36 @@ __device__ bool slot_take(TcSmem& S, int g, int* err) {
 
 // One layer's MMAs of a tile: A (canonical; K = 48 for layer 0, else 128)
 // at shared address a0, the layer's weights as B, into the accumulator at
-// TMEM address dcol (lane 0, the accumulator's first column).
+// TMEM address dcol (lane 0, the accumulator's first column).  The K steps
+// advance both descriptors' start address (bits 0-13, in 16-byte units) by
+// the bytes of two core-matrix columns; shared memory is below 2^18 bytes,
+// so the field does not carry.
 template <class Sm>
 __device__ __forceinline__ void issue_layer(const Sm& S, int layer, uint32_t dcol, uint32_t a0) {
-    const uint32_t id = layer == 2 ? idesc(TM, OUTP) : idesc(TM, HID);
-    const int nb = layer == 2 ? OUTP : HID, ksteps = layer == 0 ? KX_TC / 16 : HID / 16;
-    const uint32_t b0 = su32(layer == 0 ? S.w1 : layer == 1 ? S.w2 : S.w3);
-    for (int kk = 0; kk < ksteps; ++kk)
-        mma_f16(dcol, sdesc(a0 + kk * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
-                sdesc(b0 + kk * 2 * (nb / 8) * 128, (nb / 8) * 128, 128), id, kk > 0);
+    const uint64_t ad = sdesc(a0, (TM / 8) * 128, 128);
+    constexpr uint64_t ASTEP = (2 * (TM / 8) * 128) >> 4;
+    if (layer == 0) {
+        const uint64_t bd = sdesc(su32(S.w1), (HID / 8) * 128, 128);
+#pragma unroll
+        for (int kk = 0; kk < KX_TC / 16; ++kk)
+            mma_f16(dcol, ad + kk * ASTEP, bd + kk * ((2 * (HID / 8) * 128) >> 4), idesc(TM, HID), kk > 0);
+    } else if (layer == 1) {
+        const uint64_t bd = sdesc(su32(S.w2), (HID / 8) * 128, 128);
+#pragma unroll
+        for (int kk = 0; kk < HID / 16; ++kk)
+            mma_f16(dcol, ad + kk * ASTEP, bd + kk * ((2 * (HID / 8) * 128) >> 4), idesc(TM, HID), kk > 0);
+    } else {
+        const uint64_t bd = sdesc(su32(S.w3), (OUTP / 8) * 128, 128);
+#pragma unroll
+        for (int kk = 0; kk < HID / 16; ++kk)
+            mma_f16(dcol, ad + kk * ASTEP, bd + kk * ((2 * (OUTP / 8) * 128) >> 4), idesc(TM, OUTP), kk > 0);
+    }
 }
 
 // Bias + activation of a hidden layer for the thread's row: accumulator
 // (tacc: the thread's lane, first column) -> row `row` of the next layer's
 // A operand h.
+// bias == nullptr: the bias is already in the accumulator (layer 0).
 __device__ __forceinline__ void epilogue_layer(unsigned char* h, uint32_t tacc, const float* bias, int row) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -305,11 +345,17 @@ __device__ __forceinline__ void epilogue_layer(unsigned char* h, uint32_t tacc, 
 #pragma unroll
         for (int cb = 0; cb < 32; cb += 16) {
             uint32_t w[8];
+            if (bias) {
 #pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                const float4 b = *reinterpret_cast<const float4*>(bias + 32 * q + cb + 2 * e);
-                w[e] = bias_act2_tc(v[cb + 2 * e], v[cb + 2 * e + 1], b.x, b.y);
-                w[e + 1] = bias_act2_tc(v[cb + 2 * e + 2], v[cb + 2 * e + 3], b.z, b.w);
+                for (int e = 0; e < 8; e += 2) {
+                    const float4 b = *reinterpret_cast<const float4*>(bias + 32 * q + cb + 2 * e);
+                    w[e] = bias_act2_tc(v[cb + 2 * e], v[cb + 2 * e + 1], b.x, b.y);
+                    w[e + 1] = bias_act2_tc(v[cb + 2 * e + 2], v[cb + 2 * e + 3], b.z, b.w);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    w[e] = act2_tc(__uint_as_float(v[cb + 2 * e]), __uint_as_float(v[cb + 2 * e + 1]));
             }
             *reinterpret_cast<uint4*>(h + canon(row, 32 * q + cb, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
             *reinterpret_cast<uint4*>(h + canon(row, 32 * q + cb + 8, TM)) = make_uint4(w[4], w[5], w[6], w[7]);
@@ -336,7 +382,7 @@ __device__ bool tile_network(TcSmem& S, const GroupCtx& c, uint32_t& ph, int* er
         if (S.abort[c.g]) return false;
         fence_after();
         if (layer == 2) return true;
-        epilogue_layer(G.h, c.tlane + (uint32_t)(128 * S.slot[c.g]), layer == 0 ? S.b1 : S.b2, c.row);
+        epilogue_layer(G.h, c.tlane + (uint32_t)(128 * S.slot[c.g]), layer == 0 ? nullptr : S.b2, c.row);
         fence_async_smem();
         fence_before();
         group_sync(c.g);
@@ -492,6 +538,8 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<
             w[NMOM / 2] = pack_bf16_tc(la, ls);
 #pragma unroll
             for (int q = NMOM / 2 + 1; q < KX_TC / 2; ++q) w[q] = 0u;
+            w[BIAS_COL / 2] = pack_bf16_tc(1.f, 1.f);         // the bias columns
+            w[BIAS_COL / 2 + 1] = pack_bf16_tc(1.f, 0.f);
 #pragma unroll
             for (int q = 0; q < KX_TC / 8; ++q)
                 *reinterpret_cast<uint4*>(S.x[c] + canon(row, 8 * q, TM)) =
@@ -527,7 +575,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<
                 fence_after();
                 if (layer == 0 && m < M) s = scl[m];
                 if (layer == 2) break;
-                epilogue_layer(S.h[g], tacc, layer == 0 ? S.b1 : S.b2, row);
+                epilogue_layer(S.h[g], tacc, layer == 0 ? nullptr : S.b2, row);
                 fence_async_smem();
                 fence_before();
                 group_sync(g);
@@ -585,6 +633,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_forward_tc(const float* __res
             const long m = tile * TM + r;
             float a = 0.f, b = 0.f;
             if (m < M && col < NIN) { a = X[m * NIN + col]; b = X[m * NIN + col + 1]; }
+            if (col == BIAS_COL) a = b = 1.f;              // the bias columns
+            if (col == BIAS_COL + 2) a = 1.f;
             *reinterpret_cast<uint32_t*>(G.h + canon(r, col, TM)) = pack_bf16_tc(a, b);
         }
         fence_async_smem();
