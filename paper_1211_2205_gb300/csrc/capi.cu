@@ -377,8 +377,10 @@ mlp::ClosureArgs<T> closure_args(const starmap_t* h) {
     a.p[1] = h->p[1];
     a.nx = h->nxg[0];
     a.ny = h->nyg[0];
-    for (int j = 0; j < mlp::NMOM + mlp::NOUT; ++j)
+    for (int j = 0; j < mlp::NMOM + mlp::NOUT; ++j) {
         a.slot[j] = j < h->ncomp ? make_int2(h->sys.moms[j].grid, h->sys.moms[j].local) : make_int2(0, 0);
+        a.col[j] = a.g[a.slot[j].x].base + (long)a.slot[j].y * a.g[a.slot[j].x].cstride;
+    }
     const size_t M = (size_t)a.nx * a.ny;
     a.lsa = h->lsig;
     a.lss = h->lsig + M;

@@ -50,15 +50,6 @@ __device__ __forceinline__ void gather8(const T* const* colp, const Stencil& o, 
     ((f[J] = centre<T, grid_of(NMOM + J)>(colp[NMOM + J], o)), ...);
 }
 
-// Base pointers of components 0..count-1 (grid, local from the slot table).
-template <class T>
-__device__ __forceinline__ void column_table(const ClosureArgs<T>& A, const T** colp, int count) {
-    if (threadIdx.x < count) {
-        const int gg = A.slot[threadIdx.x].x;
-        colp[threadIdx.x] = A.g[gg].base + (long)A.slot[threadIdx.x].y * A.g[gg].cstride;
-    }
-}
-
 // The 36 moment features of a cell (order <= 7 averaged to the centre and
 // divided by their RMS s), s and 1/s.  A cell whose largest moment
 // magnitude is at most EMPTY counts as empty: features 0, s = 0, 1/s = 0.

@@ -572,16 +572,13 @@ __global__ void k_pack(const float* __restrict__ params, Packed* __restrict__ P)
 template <class T>
 __global__ void __launch_bounds__(256) k_samples(const ClosureArgs<T> A, float* __restrict__ X,
                                                  float* __restrict__ scale, float* __restrict__ tgt) {
-    __shared__ const T* colp[NMOM + NOUT];
-    column_table(A, colp, tgt ? NMOM + NOUT : NMOM);
-    __syncthreads();
     const int nx = A.nx, ny = A.ny;
     const long M = (long)nx * ny;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
         const int ix = (int)(m % nx), iy = (int)(m / nx);
         const Stencil o = stencil(ix, iy, nx, ny, A.p[0], A.p[1], A.pitch);
         float f[NMOM], s, inv;
-        features36<T>(colp, o, true, f, s, inv);
+        features36<T>(A.col, o, true, f, s, inv);
 #pragma unroll
         for (int c = 0; c < NMOM; ++c) X[m * NIN + c] = f[c];
         X[m * NIN + NMOM] = A.lsa[m];
@@ -589,7 +586,7 @@ __global__ void __launch_bounds__(256) k_samples(const ClosureArgs<T> A, float* 
         scale[m] = s;
         if (tgt) {
             float t[NOUT];
-            gather8<T>(colp, o, t, std::make_integer_sequence<int, NOUT>{});
+            gather8<T>(A.col, o, t, std::make_integer_sequence<int, NOUT>{});
 #pragma unroll
             for (int k = 0; k < NOUT; ++k) tgt[m * NOUT + k] = t[k] * inv;
         }
@@ -605,9 +602,6 @@ constexpr int PAD_ROWS_F = 128;         // input rows are written up to a whole 
 template <class T>
 __global__ void __launch_bounds__(256) k_closure_features(const ClosureArgs<T> A, __nv_bfloat16* __restrict__ xg,
                                                           float* __restrict__ sc) {
-    __shared__ const T* colp[NMOM];
-    column_table(A, colp, NMOM);
-    __syncthreads();
     const int nx = A.nx, ny = A.ny;
     const int M = nx * ny;
     const int Mpad = (M + PAD_ROWS_F - 1) / PAD_ROWS_F * PAD_ROWS_F;
@@ -616,7 +610,7 @@ __global__ void __launch_bounds__(256) k_closure_features(const ClosureArgs<T> A
         const int ix = ok ? m % nx : 0, iy = ok ? m / nx : 0;
         const Stencil o = stencil(ix, iy, nx, ny, A.p[0], A.p[1], A.pitch);
         float f[NMOM], scale, inv;
-        features36<T>(colp, o, ok, f, scale, inv);
+        features36<T>(A.col, o, ok, f, scale, inv);
         uint32_t w[LDX / 2];
 #pragma unroll
         for (int c = 0; c < NMOM / 2; ++c) w[c] = pack_bf16(f[2 * c], f[2 * c + 1]);

@@ -51,6 +51,8 @@ struct ClosureArgs {
     int p[2];
     int nx, ny;                   // cells (points of G11)
     int2 slot[NMOM + NOUT];       // (grid, local) of components 0..44 of P_8
+    const T* col[NMOM + NOUT];    // point (0, 0) of each of those components (kernel parameters:
+                                  // the same for every thread, read without a shared-memory table)
     const float* lsa;             // log(1 + sigma_a) at the cell centres [ny][nx]
     const float* lss;             // log(1 + sigma_s0)
 };

@@ -105,7 +105,7 @@ struct ClSmem {
     int abort;                           // a wait expired: every role stops at its next wait
     int stop[CONSUMERS];                 // a consumer group's verdict, set by its leader
 };
-static_assert(sizeof(ClSmem) + 64 * sizeof(void*) <= 227 * 1024, "closure kernel shared memory");
+static_assert(sizeof(ClSmem) <= 227 * 1024, "closure kernel shared memory");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -505,9 +505,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<
                                                               int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char raw[];
     ClSmem& S = *reinterpret_cast<ClSmem*>(raw);
-    __shared__ const T* colp[NMOM];
-    column_table(A, colp, NMOM);
-    cl_setup(S, P);                         // ends with a CTA barrier: colp is visible
+    cl_setup(S, P);
     // weights, TMEM and the column table come from host-written data; the
     // state is read below, after the previous kernel of the stream is done
     pdl_trigger();
@@ -530,7 +528,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<
             const bool ok = m < M;
             const int ix = ok ? m % nx : 0, iy = ok ? m / nx : 0;
             float f[NMOM], s, inv;
-            features36<T>(colp, stencil(ix, iy, nx, ny, A.p[0], A.p[1], Pp), ok, f, s, inv);
+            features36<T>(A.col, stencil(ix, iy, nx, ny, A.p[0], A.p[1], Pp), ok, f, s, inv);
             const float la = ok ? A.lsa[m] : 0.f, ls = ok ? A.lss[m] : 0.f;
             uint32_t w[KX_TC / 2];
 #pragma unroll
