@@ -334,9 +334,16 @@ def test_tcgen05_forward_matches_oracle_and_mma_sync(M):
     assert _rel(yt, ym) <= 2e-3
 
 
-@pytest.mark.parametrize("bc", [("periodic", "periodic"), ("extrapolation", "periodic")])
-def test_tcgen05_closure_prediction_matches_oracle_hook(bc):
-    p = _closure_problem(bc=bc, nsteps=3, n=(150, 90))
+@pytest.mark.parametrize("bc,n", [(("periodic", "periodic"), (150, 90)), (("extrapolation", "periodic"), (150, 90)),
+                                  # one partial tile; exactly 32 whole tiles; 469 tiles over 118 CTAs (3-4 each,
+                                  # so consumers and producers run uneven counts)
+                                  (("periodic", "extrapolation"), (10, 7)), (("periodic", "periodic"), (64, 64)),
+                                  (("extrapolation", "extrapolation"), (200, 300))])
+def test_tcgen05_closure_prediction_matches_oracle_hook(bc, n):
+    """The fused closure kernel's prediction of the order-8 moments against
+    the oracle's hook on the same state: tile counts from one partial tile to
+    several per CTA, each consumer group fed by its producer group."""
+    p = _closure_problem(bc=bc, nsteps=3, n=n)
     params = _params(43, scale_out=0.6)
     s = capi.Stepper.from_problem(p, kernel="gather", closure="mlp8")
     s.set_closure(params)
