@@ -1419,10 +1419,13 @@ int starmap_set_state(starmap_t* h, const void* buf, size_t bytes) {
 }
 
 int starmap_selftest_bounded_wait(void) {
-    int gave_up = 0;
-    if (tiled_wait_selftest(&gave_up)) return fail(nullptr, STARMAP_E_CUDA, "bounded-wait self-test could not run");
+    int gave_up = 0, tc_gave_up = 0;
+    if (tiled_wait_selftest(&gave_up) || mlp::tc_wait_selftest(&tc_gave_up))
+        return fail(nullptr, STARMAP_E_CUDA, "bounded-wait self-test could not run");
     if (!gave_up) return fail(nullptr, STARMAP_E_STATE, "bounded wait did not give up on a barrier nothing arrives at");
-    return fail(nullptr, STARMAP_E_TIMEOUT, "bounded wait gave up as expected");
+    if (!tc_gave_up)
+        return fail(nullptr, STARMAP_E_STATE, "a network kernel's bounded wait did not give up as it must");
+    return fail(nullptr, STARMAP_E_TIMEOUT, "bounded waits gave up as expected");
 }
 
 int starmap_sync(starmap_t* h) {

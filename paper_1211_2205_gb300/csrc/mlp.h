@@ -83,6 +83,10 @@ int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine
 
 // tcgen05 network (mlp_tc.cu)
 size_t tc_smem_bytes();
+// Self-test of the network kernels' bounded waits (an mbarrier phase nothing
+// completes, a TMEM slot request with every slot held): *gave_up = 1 when
+// both waits expired and raised the flag as they must.
+int tc_wait_selftest(int* gave_up);
 int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void* stream);
 // fused features + network + order-8 output on tcgen05 (I_8 centre values to
 // ctr; scl: n_x n_y floats for the cells' feature scales)

@@ -282,16 +282,16 @@ __device__ __forceinline__ GroupCtx group_ctx(const TcSmem& S) {
 // The leader takes a free TMEM slot (bounded spin: a slot is released by a
 // group that holds it, which never waits for another group); false and the
 // error flag on expiry.
-__device__ bool slot_take(TcSmem& S, int g, int* err) {
-    volatile int* mask = &S.free_slots;
+__device__ bool slot_take(int* free_slots, int* slot, int* err) {
+    volatile int* mask = free_slots;
     const unsigned long long t0 = gtime();
     for (;;) {
         const int m = *mask;
         if (m != 0) {
             const int s = __ffs(m) - 1;
-            if (atomicCAS(&S.free_slots, m, m & ~(1 << s)) == m) {
+            if (atomicCAS(free_slots, m, m & ~(1 << s)) == m) {
                 __threadfence_block();          // acquire: the last holder's reads are done
-                S.slot[g] = s;
+                *slot = s;
                 return true;
             }
             continue;
@@ -369,7 +369,7 @@ __device__ __forceinline__ void epilogue_layer(unsigned char* h, uint32_t tacc, 
 // is in TMEM.  Returns false if a wait expired.
 __device__ bool tile_network(TcSmem& S, const GroupCtx& c, uint32_t& ph, int* err) {
     TcGroup& G = S.grp[c.g];
-    if (c.leader && !slot_take(S, c.g, err)) S.abort[c.g] = 1;
+    if (c.leader && !slot_take(&S.free_slots, &S.slot[c.g], err)) S.abort[c.g] = 1;
     for (int layer = 0; layer < 3; ++layer) {
         if (c.leader && !S.abort[c.g]) {
             fence_after();
@@ -446,10 +446,10 @@ __device__ __forceinline__ void mbar_arrive_tc(uint64_t* bar) {
 
 // Bounded wait on a phase of a closure-kernel barrier: false (and the error
 // flag) on expiry, or as soon as another role of the CTA has given up.
-__device__ bool cl_wait(ClSmem& S, uint64_t* bar, uint32_t parity, int* err) {
+__device__ bool cl_wait(int* abort_flag, uint64_t* bar, uint32_t parity, int* err) {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = gtime();
-    volatile int* abort = &S.abort;
+    volatile int* abort = abort_flag;
     while (!mbar_test(bar, parity)) {
         if (*abort) return false;
         if (gtime() - t0 > TC_WAIT_NS) {
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<
         // producer p: tiles p, p + PRODUCERS, ... of the run, tile k into consumer k mod 4's buffer
         for (int k = g - CONSUMERS; k < n; k += PRODUCERS) {
             const int c = k % CONSUMERS, use = k / CONSUMERS;
-            if (use > 0 && !cl_wait(S, &S.empty[c], (uint32_t)(use - 1) & 1, err)) break;
+            if (use > 0 && !cl_wait(&S.abort, &S.empty[c], (uint32_t)(use - 1) & 1, err)) break;
             const int m = (t0 + k) * TM + row;
             const bool ok = m < M;
             const int ix = ok ? m % nx : 0, iy = ok ? m / nx : 0;
@@ -557,12 +557,12 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<
             float s = 0.f;                  // the cell's feature scale, loaded once the tile is produced
             for (int layer = 0; layer < 3; ++layer) {
                 if (leader) {
-                    bool ok = layer > 0 || cl_wait(S, &S.full[g], (uint32_t)use & 1, err);
+                    bool ok = layer > 0 || cl_wait(&S.abort, &S.full[g], (uint32_t)use & 1, err);
                     if (ok) {
                         fence_after();
                         issue_layer(S, layer, dcol, su32(layer == 0 ? S.x[g] : S.h[g]));
                         mma_commit(&S.mma[g]);
-                        ok = cl_wait(S, &S.mma[g], ph & 1, err);
+                        ok = cl_wait(&S.abort, &S.mma[g], ph & 1, err);
                         if (ok && layer == 0) mbar_arrive_tc(&S.empty[g]);   // the input buffer is read
                     }
                     if (!ok) S.stop[g] = 1;
@@ -649,6 +649,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_forward_tc(const float* __res
     tc_teardown(S);
 }
 
+// Self-test of the network kernels' bounded waits, with no tensor work: a
+// wait for an mbarrier phase that nothing completes, and a request for a
+// TMEM slot while every slot is held.  Both must give up and raise the flag.
+__global__ void k_tc_wait_selftest(int* err, int* result) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag, free_slots, slot;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+        free_slots = 0;
+        slot = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool waited = cl_wait(&abort_flag, &bar, 0, err);
+        const bool took = slot_take(&free_slots, &slot, err);
+        result[0] = waited ? 1 : 0;
+        result[1] = took ? 1 : 0;
+        result[2] = abort_flag;
+    }
+}
+
 int sms_tc() {
     static int n = 0;
     if (n == 0) {
@@ -671,6 +694,22 @@ int smem_attr(K kernel, bool& done) {
 }  // namespace
 
 size_t tc_smem_bytes() { return sizeof(TcSmem); }
+
+int tc_wait_selftest(int* gave_up) {
+    int* d = nullptr;
+    if (cudaMalloc(&d, 4 * sizeof(int)) != cudaSuccess) return -4;
+    int h[4] = {0, -1, -1, -1};
+    cudaError_t e = cudaMemcpy(d, h, 4 * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_tc_wait_selftest<<<1, 32>>>(d, d + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, 4 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return -4;
+    *gave_up = (h[0] == 1 && h[1] == 0 && h[2] == 0 && h[3] == 1) ? 1 : 0;
+    return 0;
+}
 
 int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void* stream) {
     if (M <= 0) return 0;
