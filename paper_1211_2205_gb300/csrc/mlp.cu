@@ -704,47 +704,54 @@ __global__ void __launch_bounds__(ITHREADS, 1) k_closure_mlp(const ClosureArgs<T
 // Node k of an axis lies between cells k + p - 1 and k + p (wrapped when
 // periodic, clamped to the boundary cell for extrapolation); ghost copies
 // only on periodic axes (extrapolation node axes are never read outside).
-// Rows of G22 by blockIdx.y, points along x by threads.
+// One thread per node; the outputs on G22 come as a list (their centre
+// values and their point (0, 0)), all loads before the first store.
 template <class T>
-__global__ void k_closure_nodes(const ClosureArgs<T> A, const float* __restrict__ ctr) {
+struct NodeJobs {
+    int count;
+    const float* src[NOUT];     // centre values of the output, [ny][nx]
+    T* dst[NOUT];               // its component on G22
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) k_closure_nodes(const ClosureArgs<T> A, const NodeJobs<T> J) {
     pdl_trigger();
     pdl_wait();                         // the centre values are written
-    const GridDev<T>& G = A.g[3];
+    const int gnx = A.g[3].nx, gny = A.g[3].ny;
     const int nx = A.nx, ny = A.ny;
-    const long M = (long)nx * ny;
     const long Pp = A.pitch;
-    for (int ky = blockIdx.y; ky < G.ny; ky += gridDim.y) {
+    // (cells below 2^31, checked by the caller, so nodes below 2^32)
+    const unsigned nodes = (unsigned)gnx * (unsigned)gny;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += gridDim.x * blockDim.x) {
+        const int ky = (int)(i / (unsigned)gnx), kx = (int)(i - (unsigned)ky * (unsigned)gnx);
         int cy0 = ky + A.p[1] - 1, cy1 = ky + A.p[1];
         if (A.p[1]) { cy0 = cy0 < 0 ? ny - 1 : cy0; cy1 = cy1 == ny ? 0 : cy1; }
         else { cy0 = max(cy0, 0); cy1 = min(cy1, ny - 1); }
-        for (int kx = blockIdx.x * blockDim.x + threadIdx.x; kx < G.nx; kx += gridDim.x * blockDim.x) {
-            int cx0 = kx + A.p[0] - 1, cx1 = kx + A.p[0];
-            if (A.p[0]) { cx0 = cx0 < 0 ? nx - 1 : cx0; cx1 = cx1 == nx ? 0 : cx1; }
-            else { cx0 = max(cx0, 0); cx1 = min(cx1, nx - 1); }
-            // every load before the first store, so the loads of all outputs are in flight at once
-            float v[NOUT];
+        int cx0 = kx + A.p[0] - 1, cx1 = kx + A.p[0];
+        if (A.p[0]) { cx0 = cx0 < 0 ? nx - 1 : cx0; cx1 = cx1 == nx ? 0 : cx1; }
+        else { cx0 = max(cx0, 0); cx1 = min(cx1, nx - 1); }
+        const int a = cy0 * nx + cx0, b = cy0 * nx + cx1, c = cy1 * nx + cx0, d = cy1 * nx + cx1;
+        float v[NOUT];
 #pragma unroll
-            for (int o = 0; o < NOUT; ++o) {
-                v[o] = 0.f;
-                if (A.slot[NMOM + o].x != 3) continue;
-                const float* c = ctr + (long)o * M;
-                v[o] = 0.25f * ((c[(long)cy0 * nx + cx0] + c[(long)cy0 * nx + cx1]) +
-                                (c[(long)cy1 * nx + cx0] + c[(long)cy1 * nx + cx1]));
+        for (int j = 0; j < NOUT; ++j) {
+            if (j >= J.count) break;
+            const float* s = J.src[j];
+            v[j] = 0.25f * ((s[a] + s[b]) + (s[c] + s[d]));
+        }
+        const long row = (long)(ky + 1) * Pp;
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) {
+            if (j >= J.count) break;
+            T* dd = J.dst[j];
+            const T tv = (T)v[j];
+            dd[row + kx] = tv;
+            if (A.p[0]) {
+                if (kx == gnx - 1) dd[row - 1] = tv;
+                if (kx == 0) dd[row + gnx] = tv;
             }
-#pragma unroll
-            for (int o = 0; o < NOUT; ++o) {
-                if (A.slot[NMOM + o].x != 3) continue;
-                T* d = G.base + (long)A.slot[NMOM + o].y * G.cstride;
-                const T tv = (T)v[o];
-                d[(long)(ky + 1) * Pp + kx] = tv;
-                if (A.p[0]) {
-                    if (kx == G.nx - 1) d[(long)(ky + 1) * Pp - 1] = tv;
-                    if (kx == 0) d[(long)(ky + 1) * Pp + G.nx] = tv;
-                }
-                if (A.p[1]) {
-                    if (ky == G.ny - 1) d[kx] = tv;
-                    if (ky == 0) d[(long)(G.ny + 1) * Pp + kx] = tv;
-                }
+            if (A.p[1]) {
+                if (ky == gny - 1) dd[kx] = tv;
+                if (ky == 0) dd[(long)(gny + 1) * Pp + kx] = tv;
             }
         }
     }
@@ -881,9 +888,19 @@ int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine
         if (cudaGetLastError() != cudaSuccess) return -4;
     }
     if (A.g[3].nx > 0 && A.g[3].ny > 0) {
-        const dim3 grid((A.g[3].nx + 255) / 256, A.g[3].ny < 65535 ? A.g[3].ny : 65535);
-        if (launch_pdl(k_closure_nodes<T>, grid, dim3(256), 0, (cudaStream_t)stream, true, A, (const float*)ctr) !=
-            cudaSuccess)
+        NodeJobs<T> J;
+        J.count = 0;
+        for (int o = 0; o < NOUT; ++o)
+            if (A.slot[NMOM + o].x == 3) {
+                J.src[J.count] = ctr + (long)o * M;
+                J.dst[J.count] = A.g[3].base + (long)A.slot[NMOM + o].y * A.g[3].cstride;
+                ++J.count;
+            }
+        const long nodes = (long)A.g[3].nx * A.g[3].ny;
+        long blocks = (nodes + 255) / 256;
+        if (blocks > 64L * sm_count()) blocks = 64L * sm_count();
+        if (J.count > 0 && launch_pdl(k_closure_nodes<T>, dim3((unsigned)blocks), dim3(256), 0, (cudaStream_t)stream,
+                                      true, A, J) != cudaSuccess)
             return -4;
     }
     return status(cudaGetLastError());
