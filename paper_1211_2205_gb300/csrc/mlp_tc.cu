@@ -584,18 +584,21 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<
             tmem_ld16(tacc, v);
             tmem_wait_ld();
             if (m < M) {
-                const int ix = m % nx, iy = m / nx;
+                const int iy = m / nx, ix = m - iy * nx;
+                const long at = (long)(iy + 1) * Pp + ix;     // the cell on G11, ghost row/column offsets below
+                const bool gw = ix == (A.p[0] ? nx - 1 : 0), ge = ix == (A.p[0] ? 0 : nx - 1);
+                const bool gs = iy == (A.p[1] ? ny - 1 : 0), gn = iy == (A.p[1] ? 0 : ny - 1);
 #pragma unroll
                 for (int o = 0; o < NOUT; ++o) {
                     const float val = s * (__uint_as_float(v[o]) + S.b3[o]);
                     if (A.slot[NMOM + o].x != 0) { ctr[(long)o * M + m] = val; continue; }
-                    T* cc = A.g[0].base + (long)A.slot[NMOM + o].y * A.g[0].cstride;
+                    T* cc = const_cast<T*>(A.col[NMOM + o]);
                     const T tv = (T)val;
-                    cc[(long)(iy + 1) * Pp + ix] = tv;
-                    if (ix == (A.p[0] ? nx - 1 : 0)) cc[(long)(iy + 1) * Pp - 1] = tv;
-                    if (ix == (A.p[0] ? 0 : nx - 1)) cc[(long)(iy + 1) * Pp + nx] = tv;
-                    if (iy == (A.p[1] ? ny - 1 : 0)) cc[ix] = tv;
-                    if (iy == (A.p[1] ? 0 : ny - 1)) cc[(long)(ny + 1) * Pp + ix] = tv;
+                    cc[at] = tv;
+                    if (gw) cc[at - 1 - ix] = tv;
+                    if (ge) cc[at - ix + nx] = tv;
+                    if (gs) cc[ix] = tv;
+                    if (gn) cc[(long)(ny + 1) * Pp + ix] = tv;
                 }
             }
             fence_before();                 // the accumulator is read before the next tile's MMAs
