@@ -506,6 +506,17 @@ int starmap_mlp_train_step(starmap_mlp_t* net, const float* X, const float* T, c
  * outside [0, 38] or a negative or non-finite sigma. */
 int starmap_mlp_perturb_inputs(starmap_mlp_t* net, const float* X, float* Xn, size_t M, int cols, float sigma,
                                unsigned long long seed);
+/* Sample order for a training epoch (not in the paper): out[i] =
+ * index[perm(i)] for i < count (index NULL: out[i] = perm(i)), where perm is
+ * a pseudo-random permutation of [0, count) determined by seed (a four-round
+ * Feistel network on the smallest even number of bits covering count,
+ * restricted to [0, count) by cycle walking), so the order is drawn on the
+ * device with no host work and the same seed gives the same order.  index
+ * (count int32, may be NULL) and out (count int32) are caller-owned device
+ * pointers, distinct; queued on the network's stream.  E_ARG for a NULL out
+ * or count >= 2^31. */
+int starmap_mlp_shuffle(starmap_mlp_t* net, const int32_t* index, size_t count, unsigned long long seed,
+                        int32_t* out);
 /* ------------------------------------------------------------- batches
  * Not in the paper: many independent problems advanced together.  A batch
  * holds `count` FP32 2D P_N instances (any grid size, N up to the order at

@@ -154,6 +154,8 @@ def lib():
                                                   ctypes.c_size_t, ctypes.c_float, ctypes.c_void_p]),
         "starmap_mlp_perturb_inputs": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                                       ctypes.c_int, ctypes.c_float, ctypes.c_ulonglong]),
+        "starmap_mlp_shuffle": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_ulonglong,
+                                               ctypes.c_void_p]),
         "starmap_mlp_steps": (ctypes.c_long, [H]),
         "starmap_mlp_set_engine": (ctypes.c_int, [H, ctypes.c_int]),
         "starmap_set_closure_engine": (ctypes.c_int, [H, ctypes.c_int]),
@@ -677,6 +679,12 @@ class Network:
         """Xn = X plus N(0, sigma^2) noise on the first cols inputs of each row."""
         self._check(self._L.starmap_mlp_perturb_inputs(self._h, _addr(X), _addr(Xn), int(M), int(cols),
                                                        float(sigma), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    def shuffle(self, index, count: int, seed: int, out):
+        """out[i] = index[perm(i)] on the device (index None: perm(i)), perm a
+        seeded pseudo-random permutation of range(count)."""
+        self._check(self._L.starmap_mlp_shuffle(self._h, _addr(index), int(count),
+                                                int(seed) & 0xFFFFFFFFFFFFFFFF, _addr(out)))
 
     def sync(self):
         self._check(self._L.starmap_mlp_sync(self._h))

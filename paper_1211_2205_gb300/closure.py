@@ -144,17 +144,18 @@ def train(data: SampleSet, steps: int = 48000, batch: int = 8192, lr0: float = 2
     tolerate them)."""
     torch = _torch()
     net = capi.Network(init_params(seed))
-    rng = np.random.default_rng(seed)
     loss = torch.zeros(1, device="cuda")
     res = TrainResult(params=np.empty(0))
-    idx = None
+    # the kept samples on the device once; each epoch's order is drawn there
+    index = torch.from_numpy(np.ascontiguousarray(data.index, dtype=np.int32)).cuda()
+    idx = torch.empty_like(index)
     pos = data.count
     X = torch.empty_like(data.X) if noise > 0 else data.X
     epoch = 0
     torch.cuda.synchronize()
     for it in range(steps):
         if pos + batch > data.count:
-            idx = torch.from_numpy(data.index[rng.permutation(data.count)]).cuda()
+            net.shuffle(index, data.count, (seed << 20) + epoch, idx)
             if noise > 0:
                 net.perturb_inputs(data.X, X, data.X.shape[0], capi.MLP_INPUTS - 2, noise,
                                    (seed << 20) + epoch)

@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(256) k_closure_nodes(const ClosureArgs<T> A, c
 // counter-based stream: the SplitMix64 finaliser (Steele, Lea & Flood 2014)
 // of seed * golden + counter gives two 32-bit uniforms in (0, 1), turned
 // into one normal by the Box-Muller transform (Box & Muller 1958).
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
     z += 0x9e3779b97f4a7c15ull;
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
@@ -780,6 +780,36 @@ __global__ void k_perturb(const float* X, float* Xn, long total, int cols, float
             v += sigma * sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
         }
         Xn[e] = v;
+    }
+}
+
+// Sample order for an epoch: out[i] = index[perm(i)] (index NULL: perm(i))
+// for a keyed pseudo-random permutation of [0, count).  perm is a balanced
+// four-round Feistel network on the smallest even number of bits 2h with
+// 2^(2h) >= count (round function: the SplitMix64 finaliser of the key, the
+// round and the right half, keeping h bits), restricted to [0, count) by
+// cycle walking — applying it again until the value falls inside, which
+// stays a bijection and ends within the cycle through i (Black & Rogaway
+// 2002, "Ciphers with arbitrary finite domains"); with 2^(2h) < 4 count a
+// walk takes fewer than four rounds of the network on average.
+__device__ __forceinline__ unsigned long long feistel(unsigned long long x, int h, unsigned long long key) {
+    const unsigned long long mask = (1ull << h) - 1;
+    unsigned long long L = x >> h, R = x & mask;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const unsigned long long F = splitmix64(key ^ ((unsigned long long)(r + 1) * 0xd1b54a32d192ed03ull) ^ R) & mask;
+        const unsigned long long nl = R;
+        R = L ^ F;
+        L = nl;
+    }
+    return (L << h) | R;
+}
+
+__global__ void k_shuffle(const int* __restrict__ index, long count, int h, unsigned long long key, int* __restrict__ out) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+        unsigned long long x = (unsigned long long)i;
+        do x = feistel(x, h, key); while (x >= (unsigned long long)count);
+        out[i] = index ? index[x] : (int)x;
     }
 }
 
@@ -825,6 +855,16 @@ int loss_grad(const float* X, const float* T, const int* idx, long B, const Pack
     k_loss_grad<<<(unsigned)blocks, THREADS, SMEM_TRAIN, (cudaStream_t)stream>>>(X, T, idx, B, P, part);
     if (cudaGetLastError() != cudaSuccess) return -4;
     k_reduce_grad<<<(NPARAM + 1 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(part, blocks, grad, loss);
+    return status(cudaGetLastError());
+}
+
+int shuffle(const int* index, long count, unsigned long long seed, int* out, void* stream) {
+    if (count <= 0) return 0;
+    int h = 1;
+    while ((1ll << (2 * h)) < count) ++h;
+    long blocks = (count + 255) / 256;
+    if (blocks > 32L * sm_count()) blocks = 32L * sm_count();
+    k_shuffle<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(index, count, h, splitmix64(seed), out);
     return status(cudaGetLastError());
 }
 

@@ -70,6 +70,9 @@ int adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1
 // Xn = X with N(0, sigma^2) noise on the first `cols` of the NIN inputs of
 // each of the M rows (counter-based: the same seed gives the same noise).
 int perturb(const float* X, float* Xn, long M, int cols, float sigma, unsigned long long seed, void* stream);
+// out[i] = index[perm(i)] (index NULL: perm(i)), perm a keyed pseudo-random
+// permutation of [0, count) (count < 2^31); the same seed, the same order.
+int shuffle(const int* index, long count, unsigned long long seed, int* out, void* stream);
 template <class T> int samples(const ClosureArgs<T>& A, float* X, float* scale, float* tgt, void* stream);
 // Closure evaluation (features, network, order-8 moments written to G11 and
 // G22); scratch holds closure_scratch_floats(n_x n_y) floats; n_x n_y must

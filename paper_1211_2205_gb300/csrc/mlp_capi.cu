@@ -196,6 +196,15 @@ int starmap_mlp_perturb_inputs(starmap_mlp_t* net, const float* X, float* Xn, si
     return STARMAP_OK;
 }
 
+int starmap_mlp_shuffle(starmap_mlp_t* net, const int32_t* index, size_t count, unsigned long long seed,
+                        int32_t* out) {
+    if (!net) return STARMAP_E_ARG;
+    if (count == 0) return STARMAP_OK;
+    if (!out || count > 0x7fffffffu) return mfail(net, STARMAP_E_ARG, "shuffle needs an output and fewer than 2^31 samples");
+    if (mlp::shuffle(index, (long)count, seed, out, net->stream)) MCK(cudaGetLastError(), "shuffle");
+    return STARMAP_OK;
+}
+
 long starmap_mlp_steps(const starmap_mlp_t* net) { return net ? net->steps : 0; }
 
 int starmap_mlp_sync(starmap_mlp_t* net) {

@@ -444,3 +444,39 @@ def test_closed_run_same_on_both_tile_heights(schedule):
         s.close()
     for a, b in zip(*runs):
         assert np.array_equal(a, b)
+
+
+def test_epoch_shuffle_is_a_seeded_permutation():
+    """The device-side epoch order: a permutation of range(count) (also for
+    counts just above and below a power of four, where the cycle walk is
+    longest or absent), the same for the same seed, another for another
+    seed, and index[perm] when an index is given."""
+    net = capi.Network(_params(3))
+    for count in (1, 2, 3, 1000, 4096, 4097, 65535, 1 << 20):
+        out = torch.empty(count, dtype=torch.int32, device="cuda")
+        net.shuffle(None, count, 7, out)
+        net.sync()
+        a = out.cpu().numpy()
+        assert np.array_equal(np.sort(a), np.arange(count)), count
+        if count >= 1000:
+            assert not np.array_equal(a, np.arange(count))
+            # no long runs of neighbours: the order is scrambled
+            assert np.mean(np.abs(np.diff(a.astype(np.int64))) == 1) < 0.01
+    count = 1 << 16
+    outs = []
+    for seed in (5, 5, 6):
+        out = torch.empty(count, dtype=torch.int32, device="cuda")
+        net.shuffle(None, count, seed, out)
+        net.sync()
+        outs.append(out.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.mean(outs[0] == outs[2]) < 0.01
+    index = torch.from_numpy(np.random.default_rng(1).permutation(10 * count)[:count].astype(np.int32)).cuda()
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    net.shuffle(index, count, 5, out)
+    net.sync()
+    assert np.array_equal(out.cpu().numpy(), index.cpu().numpy()[outs[0]])
+    with pytest.raises(capi.StarmapError) as e:
+        net.shuffle(None, 10, 1, None)
+    assert e.value.code == capi.E_ARG
+    net.close()
