@@ -421,6 +421,14 @@ int starmap_sync(starmap_t* h);
  * could not run.  Synchronous (legacy default stream), about 6 s. */
 int starmap_selftest_bounded_wait(void);
 
+/* Host-side fault injection for tests (no counterpart in the paper): the
+ * n-th device allocation the library makes from now on (in any handle,
+ * network or batch of the process) fails as if the device were out of
+ * memory, once; n = 0 disables it.  The failing call returns its error
+ * status (E_NOMEM or E_CUDA) and must leave the process usable.  E_ARG for
+ * n < 0.  Not thread-safe against concurrent creation calls. */
+int starmap_debug_fail_allocation(int n);
+
 /* ------------------------------------------------------ learned closure
  * Not in the paper.  The network maps 38 inputs to the 9 order-8 moments:
  *   inputs  x = (u_0 .. u_35) / s, log(1 + sigma_a), log(1 + sigma_s0), the

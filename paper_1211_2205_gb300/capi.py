@@ -154,6 +154,7 @@ def lib():
                                                   ctypes.c_size_t, ctypes.c_float, ctypes.c_void_p]),
         "starmap_mlp_perturb_inputs": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                                       ctypes.c_int, ctypes.c_float, ctypes.c_ulonglong]),
+        "starmap_debug_fail_allocation": (ctypes.c_int, [ctypes.c_int]),
         "starmap_mlp_shuffle": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_ulonglong,
                                                ctypes.c_void_p]),
         "starmap_mlp_steps": (ctypes.c_long, [H]),
@@ -265,6 +266,11 @@ def batch_plan(tiles_x, tiles_y, cost, slots: int):
     if rc != OK:
         raise StarmapError(rc, L.starmap_last_error(None).decode())
     return items, off
+
+
+def debug_fail_allocation(n: int) -> int:
+    """Make the n-th following device allocation of the library fail (0: off)."""
+    return lib().starmap_debug_fail_allocation(int(n))
 
 
 def selftest_bounded_wait() -> int:

@@ -18,6 +18,13 @@
 #include "tiled.h"
 #include "../../include/starmap.h"
 
+namespace starmap {
+std::atomic<int>& alloc_fail_countdown() {
+    static std::atomic<int> countdown{0};
+    return countdown;
+}
+}  // namespace starmap
+
 using namespace starmap;
 
 namespace {
@@ -213,8 +220,8 @@ int build_tables(starmap_t* h) {
     }
     if (h->outs_dev) { cudaFree(h->outs_dev); h->outs_dev = nullptr; }
     if (h->coefs_dev) { cudaFree(h->coefs_dev); h->coefs_dev = nullptr; }
-    CK(cudaMalloc(&h->outs_dev, std::max<size_t>(1, outs.size()) * sizeof(GatherOut)), "cudaMalloc tables");
-    CK(cudaMalloc(&h->coefs_dev, std::max<size_t>(1, coefs.size()) * sizeof(GatherCoef<T>)), "cudaMalloc tables");
+    CK(dev_alloc(&h->outs_dev, std::max<size_t>(1, outs.size()) * sizeof(GatherOut)), "cudaMalloc tables");
+    CK(dev_alloc(&h->coefs_dev, std::max<size_t>(1, coefs.size()) * sizeof(GatherCoef<T>)), "cudaMalloc tables");
     if (!outs.empty()) {
         CK(cudaMemcpy(h->outs_dev, outs.data(), outs.size() * sizeof(GatherOut), cudaMemcpyHostToDevice), "upload tables");
         CK(cudaMemcpy(h->coefs_dev, coefs.data(), coefs.size() * sizeof(GatherCoef<T>), cudaMemcpyHostToDevice), "upload tables");
@@ -222,7 +229,7 @@ int build_tables(starmap_t* h) {
     // source pointer array
     std::vector<void*> ptrs(h->src_dev.begin(), h->src_dev.end());
     if (h->src_ptrs_dev) { cudaFree(h->src_ptrs_dev); h->src_ptrs_dev = nullptr; }
-    CK(cudaMalloc(&h->src_ptrs_dev, std::max<size_t>(1, ptrs.size()) * sizeof(void*)), "cudaMalloc sources");
+    CK(dev_alloc(&h->src_ptrs_dev, std::max<size_t>(1, ptrs.size()) * sizeof(void*)), "cudaMalloc sources");
     if (!ptrs.empty())
         CK(cudaMemcpy(h->src_ptrs_dev, ptrs.data(), ptrs.size() * sizeof(void*), cudaMemcpyHostToDevice), "upload sources");
     if (h->tiled) {
@@ -271,7 +278,7 @@ int ensure_coef_alloc(starmap_t* h) {
     for (int g = 0; g < 4; ++g) {
         if (h->coef[g]) { cudaFree(h->coef[g]); h->coef[g] = nullptr; }
         size_t bytes = std::max<size_t>(1, (size_t)h->nclasses * 4 * h->nxg[g] * h->nyg[g]) * h->esize;
-        CK(cudaMalloc(&h->coef[g], bytes), "cudaMalloc coefficients");
+        CK(dev_alloc(&h->coef[g], bytes), "cudaMalloc coefficients");
     }
     h->ncls_alloc = h->nclasses;
     return STARMAP_OK;
@@ -354,7 +361,7 @@ bool closure_layout_ok(const starmap_t* h) {
 // log(1 + sigma) of grid G11's material, FP32 on the device (network inputs).
 int ensure_lsig(starmap_t* h) {
     const size_t M = (size_t)h->nxg[0] * h->nyg[0];
-    if (!h->lsig) CK(cudaMalloc(&h->lsig, std::max<size_t>(1, 2 * M) * sizeof(float)), "cudaMalloc closure inputs");
+    if (!h->lsig) CK(dev_alloc(&h->lsig, std::max<size_t>(1, 2 * M) * sizeof(float)), "cudaMalloc closure inputs");
     if (!h->lsig_dirty) return STARMAP_OK;
     std::vector<float> buf(2 * M);
     for (size_t i = 0; i < M; ++i) {
@@ -394,10 +401,10 @@ int run_closure(starmap_t* h) {
     int rc = ensure_lsig(h);
     if (rc) return rc;
     const size_t M = (size_t)h->nxg[0] * h->nyg[0];
-    if (!h->ctr) CK(cudaMalloc(&h->ctr, std::max<size_t>(1, (size_t)mlp::closure_scratch_floats((long)M)) * sizeof(float)),
+    if (!h->ctr) CK(dev_alloc(&h->ctr, std::max<size_t>(1, (size_t)mlp::closure_scratch_floats((long)M)) * sizeof(float)),
                     "cudaMalloc closure scratch");
     if (!h->closure_err) {
-        CK(cudaMalloc(&h->closure_err, sizeof(int)), "cudaMalloc closure flag");
+        CK(dev_alloc(&h->closure_err, sizeof(int)), "cudaMalloc closure flag");
         CK(cudaMemsetAsync(h->closure_err, 0, sizeof(int), h->stream), "closure flag");
     }
     if (mlp::closure<T>(closure_args<T>(h), h->net, h->ctr, h->engine, h->closure_err, h->stream))
@@ -761,16 +768,16 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
         h->cstride[g] = h->rows * h->pitch;
         size_t elems = LEAD + (size_t)std::max(1, h->Kg[g]) * h->cstride[g] + h->pitch;
         h->grid_bytes[g] = elems * h->esize;
-        e = cudaMalloc(&h->alloc[g], h->grid_bytes[g]);
+        e = dev_alloc(&h->alloc[g], h->grid_bytes[g]);
         if (e != cudaSuccess) return bail(fail(h, e == cudaErrorMemoryAllocation ? STARMAP_E_NOMEM : STARMAP_E_CUDA,
                                                 std::string("cudaMalloc state: ") + cudaGetErrorString(e)));
         e = cudaMemsetAsync(h->alloc[g], 0, h->grid_bytes[g], h->stream);
         if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMemset state"));
         h->base[g] = (char*)h->alloc[g] + LEAD * h->esize;
     }
-    e = cudaMalloc(&h->partials, (size_t)h->red_blocks * 3 * sizeof(double));
+    e = dev_alloc(&h->partials, (size_t)h->red_blocks * 3 * sizeof(double));
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc reduction"));
-    e = cudaMalloc(&h->result, 4 * sizeof(double));
+    e = dev_alloc(&h->result, 4 * sizeof(double));
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc reduction"));
     if (h->kernel_used != STARMAP_KERNEL_GATHER) {
         TiledGeometry geo;
@@ -821,7 +828,7 @@ int starmap_create(const starmap_config* cfg, starmap_t** out) {
         // the second state set the fused steps alternate with
         if (!h->tiled) return bail(fail(h, STARMAP_E_UNSUPPORTED, "the fused schedule needs the tiled kernel"));
         for (int g = 0; g < 4; ++g) {
-            e = cudaMalloc(&h->alloc1[g], h->grid_bytes[g]);
+            e = dev_alloc(&h->alloc1[g], h->grid_bytes[g]);
             if (e != cudaSuccess) return bail(fail(h, e == cudaErrorMemoryAllocation ? STARMAP_E_NOMEM : STARMAP_E_CUDA,
                                                     std::string("cudaMalloc second state: ") + cudaGetErrorString(e)));
             e = cudaMemsetAsync(h->alloc1[g], 0, h->grid_bytes[g], h->stream);
@@ -952,7 +959,7 @@ int starmap_set_source(starmap_t* h, int j, const double* q, size_t count) {
     const bool new_slot = h->src_slot[j] < 0;
     if (new_slot) {
         void* d = nullptr;
-        CK(cudaMalloc(&d, np * h->esize), "cudaMalloc source");
+        CK(dev_alloc(&d, np * h->esize), "cudaMalloc source");
         h->src_slot[j] = (int)h->src_dev.size();
         h->src_dev.push_back(d);
     }
@@ -1095,7 +1102,7 @@ template <class T>
 int do_steps_checked(starmap_t* h, long n) {
     if (n <= 0) return STARMAP_OK;
     for (int g = 0; g < 4; ++g)
-        if (!h->snap[g]) CK(cudaMalloc(&h->snap[g], h->grid_bytes[g]), "cudaMalloc health copy");
+        if (!h->snap[g]) CK(dev_alloc(&h->snap[g], h->grid_bytes[g]), "cudaMalloc health copy");
     double res[3];
     int rc = reduce_state(h, res);
     if (rc) return rc;
@@ -1285,7 +1292,7 @@ int starmap_advance_to(starmap_t* h, double t_out) {
     const double eps = 1e-12 * std::max(1.0, std::fabs(t_out));
     if (t_out < h->t - eps) return fail(h, STARMAP_E_ARG, "t_out lies before the current time");
     for (int g = 0; g < 4; ++g) {
-        if (!h->prev[g]) CK(cudaMalloc(&h->prev[g], h->grid_bytes[g]), "cudaMalloc output level");
+        if (!h->prev[g]) CK(dev_alloc(&h->prev[g], h->grid_bytes[g]), "cudaMalloc output level");
     }
     if (t_out <= h->t + eps) {
         for (int g = 0; g < 4; ++g)
@@ -1418,6 +1425,12 @@ int starmap_set_state(starmap_t* h, const void* buf, size_t bytes) {
     return STARMAP_OK;
 }
 
+int starmap_debug_fail_allocation(int n) {
+    if (n < 0) return fail(nullptr, STARMAP_E_ARG, "the allocation to fail is counted from 1 (0 disables)");
+    starmap::alloc_fail_countdown().store(n);
+    return STARMAP_OK;
+}
+
 int starmap_selftest_bounded_wait(void) {
     int gave_up = 0, tc_gave_up = 0;
     if (tiled_wait_selftest(&gave_up) || mlp::tc_wait_selftest(&tc_gave_up))
@@ -1440,8 +1453,8 @@ int starmap_set_closure(starmap_t* h, const float* params, size_t count) {
     if (!params || count != (size_t)mlp::NPARAM) return fail(h, STARMAP_E_ARG, "closure needs STARMAP_MLP_PARAMS floats");
     for (size_t i = 0; i < count; ++i)
         if (!std::isfinite(params[i])) return fail(h, STARMAP_E_NONFINITE, "closure parameters contain NaN or Inf");
-    if (!h->net_params) CK(cudaMalloc(&h->net_params, (size_t)mlp::NPARAM * sizeof(float)), "cudaMalloc closure");
-    if (!h->net) CK(cudaMalloc(&h->net, sizeof(mlp::Packed)), "cudaMalloc closure");
+    if (!h->net_params) CK(dev_alloc(&h->net_params, (size_t)mlp::NPARAM * sizeof(float)), "cudaMalloc closure");
+    if (!h->net) CK(dev_alloc(&h->net, sizeof(mlp::Packed)), "cudaMalloc closure");
     CK(cudaMemcpyAsync(h->net_params, params, count * sizeof(float), cudaMemcpyHostToDevice, h->stream), "upload closure");
     if (mlp::pack(h->net_params, h->net, h->stream)) return cuda_fail(h, cudaGetLastError(), "pack closure");
     CK(cudaStreamSynchronize(h->stream), "set_closure");
@@ -1648,10 +1661,10 @@ int batch_replan(starmap_batch_t* b, int strip) {
     b->graphs.clear();
     if (b->dev_items) { cudaFree(b->dev_items); b->dev_items = nullptr; }
     if (b->dev_off) { cudaFree(b->dev_off); b->dev_off = nullptr; }
-    if (e == cudaSuccess) e = cudaMalloc(&b->dev_off, off.size() * sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc(&b->dev_off, off.size() * sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->dev_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int4));
+    if (e == cudaSuccess) e = dev_alloc(&b->dev_items, std::max<size_t>(1, it.size()) * sizeof(int4));
     if (e == cudaSuccess && !it.empty())
         e = cudaMemcpyAsync(b->dev_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1726,11 +1739,11 @@ int batch_build(const starmap_config* cfgs, int count, int variant, starmap_batc
                 for (int k = 0; k < h->Kg[g]; ++k)
                     jobs[P].push_back(GhostJob{(float*)h->base[g] + (long)k * h->cstride[g], h->pitch, h->nxg[g],
                                                h->nyg[g], g, h->p[0], h->p[1], 0});
-    e = cudaMalloc(&b->dev_params, b->staging.size());
+    e = dev_alloc(&b->dev_params, b->staging.size());
     for (int P = 0; P < 2 && e == cudaSuccess; ++P) {
         if (jobs[P].size() > 0x7fffffffu) return bail(bfail(b, STARMAP_E_ARG, "too many components in one batch"));
         b->nghosts[P] = (int)jobs[P].size();
-        e = cudaMalloc(&b->dev_ghosts[P], std::max<size_t>(1, jobs[P].size()) * sizeof(GhostJob));
+        e = dev_alloc(&b->dev_ghosts[P], std::max<size_t>(1, jobs[P].size()) * sizeof(GhostJob));
         if (e == cudaSuccess && !jobs[P].empty())
             e = cudaMemcpyAsync(b->dev_ghosts[P], jobs[P].data(), jobs[P].size() * sizeof(GhostJob),
                                 cudaMemcpyHostToDevice, b->stream);

@@ -16,10 +16,31 @@
 // so that every half-grid difference (eq. central_differences) reads two
 // plain neighbours.
 #pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
 namespace starmap {
+
+// Every device allocation of the library goes through dev_alloc, so that a
+// test can make the n-th following one fail (starmap_debug_fail_allocation)
+// and check that each error path returns a status and leaves the process
+// usable.  The countdown is process-wide.
+std::atomic<int>& alloc_fail_countdown();
+template <class T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+    std::atomic<int>& c = alloc_fail_countdown();
+    int n = c.load();
+    while (n > 0 && !c.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 
 constexpr int LEAD = 32;          // elements before base_g
 constexpr int MAXC = 4;           // couplings per direction per row (Lemma 2)

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <string>
 
+#include "internal.h"
 #include "mlp.h"
 #include "../../include/starmap.h"
 
@@ -83,7 +84,7 @@ int ensure_part(starmap_mlp_t* net, long tiles) {
         net->part = nullptr;
         net->part_tiles = 0;
     }
-    MCK(cudaMalloc(&net->part, (size_t)tiles * (mlp::NPARAM + 1) * sizeof(float)), "cudaMalloc gradient scratch");
+    MCK(dev_alloc(&net->part, (size_t)tiles * (mlp::NPARAM + 1) * sizeof(float)), "cudaMalloc gradient scratch");
     net->part_tiles = tiles;
     return STARMAP_OK;
 }
@@ -116,12 +117,12 @@ int starmap_mlp_create(const float* params, size_t count, void* cuda_stream, sta
     const size_t pb = (size_t)mlp::NPARAM * sizeof(float);
     float** bufs[4] = {&net->params, &net->m, &net->v, &net->grad};
     for (float** b : bufs) {
-        e = cudaMalloc(b, pb);
+        e = dev_alloc(b, pb);
         if (e != cudaSuccess) return bail(mfail(net, STARMAP_E_NOMEM, "cudaMalloc parameters"));
     }
-    e = cudaMalloc(&net->packed, sizeof(mlp::Packed));
+    e = dev_alloc(&net->packed, sizeof(mlp::Packed));
     if (e != cudaSuccess) return bail(mfail(net, STARMAP_E_NOMEM, "cudaMalloc packed weights"));
-    e = cudaMalloc(&net->flag, sizeof(int));
+    e = dev_alloc(&net->flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(net->flag, 0, sizeof(int));
     if (e != cudaSuccess) return bail(mfail(net, STARMAP_E_NOMEM, "cudaMalloc error flag"));
     if (int rc = load(net, params)) return bail(rc);

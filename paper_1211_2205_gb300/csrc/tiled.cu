@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "internal.h"
 #include "tiled.h"
 // the kernels, once per tile height (namespaces tiled: 10 rows, two per
 // consumer warp; tiled5: 5 rows, one per consumer warp)
@@ -162,7 +163,7 @@ void free_tables(TiledPlan* pl) {
 template <class V>
 bool upload(void** dst, const std::vector<V>& v) {
     size_t bytes = std::max<size_t>(1, v.size()) * sizeof(V);
-    if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
+    if (dev_alloc(dst, bytes) != cudaSuccess) return false;
     if (!v.empty() && cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice) != cudaSuccess) return false;
     return true;
 }
@@ -470,7 +471,7 @@ int tiled_create(const TiledGeometry& geo, TiledPlan** out) {
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || pl->sms < 1) pl->sms = 1;
     }
-    if (cudaMalloc(&pl->err_dev, sizeof(int)) != cudaSuccess || cudaMemset(pl->err_dev, 0, sizeof(int)) != cudaSuccess) {
+    if (dev_alloc(&pl->err_dev, sizeof(int)) != cudaSuccess || cudaMemset(pl->err_dev, 0, sizeof(int)) != cudaSuccess) {
         pl->err = "cudaMalloc error flag failed";
         return -4;
     }
@@ -781,7 +782,7 @@ __global__ void k_wait_selftest(int* err, int* result) {
 
 int tiled_wait_selftest(int* gave_up) {
     int *d = nullptr;
-    if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return -4;
+    if (dev_alloc(&d, 2 * sizeof(int)) != cudaSuccess) return -4;
     int h[2] = {0, -1};
     cudaError_t e = cudaMemcpy(d, h, 2 * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
