@@ -150,7 +150,7 @@ __global__ void k_gather_pass(const GatherArgs<T> A) {
     const T* Xb = A.g[xg].base;
     const T* Yb = A.g[yg].base;
     const long cxs = A.g[xg].cstride, cys = A.g[yg].cstride;
-    for (int t = A.begin; t < A.end; ++t) {
+    for (int t = A.begin + (int)blockIdx.z; t < A.end; t += (int)gridDim.z) {
         const GatherOut o = A.outs[t];
         const GatherCoef<T> c = A.coefs[t];
         T w = T(0);
@@ -293,12 +293,30 @@ int status_of(cudaError_t e) { return e == cudaSuccess ? 0 : -4; }
 
 }  // namespace
 
+static int sm_count_gather() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
 template <class T>
 int launch_gather_pass(const GatherArgs<T>& a, void* stream) {
     const GridDev<T>& G = a.g[a.out_grid];
     if (a.end <= a.begin || G.nx == 0 || G.ny == 0) return 0;
     dim3 block(128);
-    dim3 grid((G.nx + 127) / 128, G.ny);
+    // one thread per point walks the grid's outputs; on a small grid the
+    // outputs are dealt over blockIdx.z as well (output t to slice (t - begin)
+    // mod z), so that about two waves of threads fill the GPU
+    const long threads = (long)((G.nx + 127) / 128) * 128 * G.ny;
+    const long want = 2L * 2048 * sm_count_gather();
+    long z = threads >= want ? 1 : (want + threads - 1) / threads;
+    if (z > a.end - a.begin) z = a.end - a.begin;
+    if (z > 64) z = 64;
+    dim3 grid((G.nx + 127) / 128, G.ny, (unsigned)z);
     k_gather_pass<T><<<grid, block, 0, (cudaStream_t)stream>>>(a);
     return status_of(cudaGetLastError());
 }
