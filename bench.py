@@ -66,20 +66,13 @@ KERNEL_SOURCES = {
 
 
 def workload(name: str):
-    if name == "random_p39":
-        return inputs.random_p39(), "2D P_39 FP32 1024x1024 periodic, smooth random sigma_s0, Gaussian pulse"
-    if name == "checkerboard_p13":
-        return inputs.checkerboard_p13(), "2D P_13 FP32 512x512 checkerboard, extrapolation, source"
-    if name == "gaussian_p5":
-        return inputs.gaussian_p5(), "2D P_5 FP64 64x64 periodic Gaussian"
-    if name == "paper_p5":
-        return (inputs.checkerboard_p13(n=100, N=5, precision="fp64"),
-                "the run the paper times (section 6.3): 2D P_5 FP64 100x100 checkerboard, extrapolation, to t = 3.2")
-    if name == "batched_256":
-        return ([inputs.batched_instance(k) for k in range(256)],
-                "256 independent 2D P_N FP32 instances, grids 64^2-512^2, N in {3..15}, piecewise-constant media, "
-                "Gaussian sources, one graph launch per step call")
-    raise SystemExit(f"unknown workload {name}")
+    """The named workload from configs/<name>.json: one Problem, or the list
+    of a batch."""
+    try:
+        problems, description = inputs.load_config(name)
+    except FileNotFoundError:
+        raise SystemExit(f"unknown workload {name}")
+    return (problems if len(problems) > 1 else problems[0]), description
 
 
 def dist_env():

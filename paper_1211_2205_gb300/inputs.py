@@ -32,7 +32,9 @@ needed):
 from __future__ import annotations
 
 import dataclasses
+import json
 import math
+import os
 from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
@@ -339,3 +341,28 @@ def fourier_mode_ic(count: int, seed: int):
     re = rng.uniforms(count) * 2 - 1
     im = rng.uniforms(count) * 2 - 1
     return re + 1j * im
+
+
+# ---------------------------------------------------------------- config files
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "configs")
+_GENERATORS = {"gaussian_p5": gaussian_p5, "checkerboard_p13": checkerboard_p13, "random_p39": random_p39,
+               "batched_instance": batched_instance, "closure_medium": closure_medium, "closure_c5": closure_c5}
+
+
+def load_config(name_or_path: str):
+    """A run described by a JSON file (configs/<name>.json, or a path): the
+    generator of this module it names with its keyword arguments, called
+    once, once per instance k ("instances": count, k passed as the first
+    argument) or once per seed ("seeds").  Returns (problems, description)."""
+    path = name_or_path if name_or_path.endswith(".json") else os.path.join(CONFIG_DIR, name_or_path + ".json")
+    with open(path) as f:
+        c = json.load(f)
+    gen = _GENERATORS[c["generator"]]
+    kw = dict(c.get("kwargs", {}))
+    if "instances" in c:
+        problems = [gen(k, **kw) for k in range(int(c["instances"]))]
+    elif "seeds" in c:
+        problems = [gen(int(s), **kw) for s in c["seeds"]]
+    else:
+        problems = [gen(**kw)]
+    return problems, c.get("description", c.get("name", ""))
