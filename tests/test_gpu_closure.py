@@ -361,6 +361,30 @@ def test_tcgen05_closure_prediction_matches_oracle_hook(bc, n):
     assert rel_l2(after[36:], ref) <= 2 * BF16_TOL
 
 
+def test_tcgen05_closure_prediction_full_size():
+    """The closure workload's own size and launch configuration: one medium
+    of the benchmark's closure runs (512 x 512, P_8 state after a few plain
+    closed steps), the tcgen05 prediction of all nine order-8 moments on every
+    cell against the oracle's hook on the same state."""
+    p = inputs.closure_medium(100, n=512, N=7)
+    p = inputs.Problem(**{**p.__dict__, "nsteps": 3})
+    params = _params(45, scale_out=0.6)
+    s = capi.Stepper.from_problem(p, kernel="tiled", closure="mlp8", schedule="merged")
+    s.set_closure(params)
+    s.set_closure_engine("tcgen05")
+    s.step(3)
+    before = _state(s)
+    s.run_pass(1, 0)
+    after = _state(s)
+    s.sync()
+    o = C.closed_solver(p, _oracle_mlp(params), dt=_closed_dt(s, p))
+    for j in range(45):
+        o.U[j] = before[j].T.astype(np.float64)
+    o.pre_odd(o)
+    ref = [o.U[j].T for j in range(36, 45)]
+    assert rel_l2(after[36:], ref) <= 2 * BF16_TOL
+
+
 def test_tcgen05_closed_run_matches_mma_sync_run():
     p = _closure_problem(precision="fp32", nsteps=6, n=(130, 70))
     params = _params(44, scale_out=0.6)
