@@ -1521,6 +1521,9 @@ int batch_sync_params(starmap_batch_t* b) {
         if (b->uploaded[i] == h->version) continue;
         if (tiled_export_params(h->tiled, b->staging.data() + i * pb))
             return bfail(b, STARMAP_E_STATE, "instance tables not built");
+        // the batch kernel runs with the shared memory sized at creation
+        if (std::max(tiled_smem_bytes(h->tiled, 0), tiled_smem_bytes(h->tiled, 1)) > b->smem)
+            return bfail(b, STARMAP_E_STATE, "instance " + std::to_string(i) + " outgrew the batch's shared memory");
         b->uploaded[i] = h->version;
         any = true;
     }
