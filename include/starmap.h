@@ -588,7 +588,12 @@ int  starmap_batch_sync(starmap_batch_t* b);
 int starmap_batch_plan(const int* tiles_x, const int* tiles_y, const int* cost, int count, int slots,
                        int* items, size_t item_capacity, int* off, size_t off_capacity, long* counts);
 
-/* Inference engine of starmap_mlp_forward (STARMAP_MLP_ENGINE_*). */
+/* Engine (STARMAP_MLP_ENGINE_*) of starmap_mlp_forward and of the loss and
+ * gradient of starmap_mlp_loss_grad / starmap_mlp_train_step: MMA_SYNC
+ * (mma.sync tiles, the default) or TCGEN05 (tcgen05.mma with TMEM
+ * accumulators; the backward contractions read the activations MN-major).
+ * Both give the same gradients up to FP32 summation order.  E_ARG for an
+ * unknown engine. */
 int  starmap_mlp_set_engine(starmap_mlp_t* net, int engine);
 /* Number of Adam steps taken since creation or the last set_params. */
 long starmap_mlp_steps(const starmap_mlp_t* net);

@@ -666,7 +666,7 @@ class Network:
         return self._L.starmap_mlp_steps(self._h)
 
     def set_engine(self, engine: str):
-        """"mma_sync" or "tcgen05" for forward()."""
+        """"mma_sync" or "tcgen05" for forward(), loss_grad() and train_step()."""
         self._check(self._L.starmap_mlp_set_engine(self._h, {"mma_sync": ENGINE_MMA_SYNC,
                                                              "tcgen05": ENGINE_TCGEN05}[engine]))
 

@@ -136,14 +136,16 @@ class TrainResult:
 
 
 def train(data: SampleSet, steps: int = 48000, batch: int = 8192, lr0: float = 2e-3, lr1: float = 2e-5,
-          seed: int = 0, log_every: int = 200, noise: float = 0.05) -> TrainResult:
+          seed: int = 0, log_every: int = 200, noise: float = 0.05, engine: str = "tcgen05") -> TrainResult:
     """Minibatch Adam with cosine decay from lr0 to lr1.  noise: standard
     deviation of Gaussian noise added to the 36 normalised moment inputs,
     drawn afresh for every pass over the samples (the closed run feeds the
     network states with errors of its own; noise in training makes it
-    tolerate them)."""
+    tolerate them).  engine: kernels of the loss gradient ("tcgen05" or
+    "mma_sync")."""
     torch = _torch()
     net = capi.Network(init_params(seed))
+    net.set_engine(engine)
     loss = torch.zeros(1, device="cuda")
     res = TrainResult(params=np.empty(0))
     # the kept samples on the device once; each epoch's order is drawn there

@@ -847,13 +847,17 @@ int forward(const float* X, long M, const Packed* P, float* Y, void* stream) {
 }
 
 int loss_grad(const float* X, const float* T, const int* idx, long B, const Packed* P, float* part, float* grad,
-              float* loss, void* stream) {
+              float* loss, int engine, int* err, void* stream) {
     if (B <= 0) return 0;
-    static bool attr = false;
-    if (set_smem(k_loss_grad, SMEM_TRAIN, attr)) return -4;
     const long blocks = grad_blocks(B);
-    k_loss_grad<<<(unsigned)blocks, THREADS, SMEM_TRAIN, (cudaStream_t)stream>>>(X, T, idx, B, P, part);
-    if (cudaGetLastError() != cudaSuccess) return -4;
+    if (engine == ENGINE_TCGEN05) {
+        if (loss_grad_tc(X, T, idx, B, P, part, err, stream)) return -4;
+    } else {
+        static bool attr = false;
+        if (set_smem(k_loss_grad, SMEM_TRAIN, attr)) return -4;
+        k_loss_grad<<<(unsigned)blocks, THREADS, SMEM_TRAIN, (cudaStream_t)stream>>>(X, T, idx, B, P, part);
+        if (cudaGetLastError() != cudaSuccess) return -4;
+    }
     k_reduce_grad<<<(NPARAM + 1 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(part, blocks, grad, loss);
     return status(cudaGetLastError());
 }

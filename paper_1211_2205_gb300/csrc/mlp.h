@@ -62,8 +62,10 @@ int forward(const float* X, long M, const Packed* P, float* Y, void* stream);
 // Per-CTA partial gradients (and losses) of the mean squared error over the
 // B samples idx[0..B) (idx NULL: samples 0..B); part holds
 // blocks(B) x (NPARAM + 1) floats, reduced into grad[NPARAM], loss[1].
+// engine: ENGINE_MMA_SYNC (mma.sync tiles) or ENGINE_TCGEN05 (tcgen05 tiles;
+// err: device flag raised by a bounded wait).
 int loss_grad(const float* X, const float* T, const int* idx, long B, const Packed* P, float* part, float* grad,
-              float* loss, void* stream);
+              float* loss, int engine, int* err, void* stream);
 long grad_blocks(long B);
 int adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps, long step,
          void* stream);
@@ -91,6 +93,9 @@ size_t tc_smem_bytes();
 // both waits expired and raised the flag as they must.
 int tc_wait_selftest(int* gave_up);
 int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void* stream);
+// per-tile partial loss and gradients of loss_grad on tcgen05 (same layout of part)
+int loss_grad_tc(const float* X, const float* T, const int* idx, long B, const Packed* P, float* part, int* err,
+                 void* stream);
 // fused features + network + order-8 output on tcgen05 (I_8 centre values to
 // ctr; scl: n_x n_y floats for the cells' feature scales)
 template <class T>

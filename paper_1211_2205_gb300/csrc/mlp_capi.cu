@@ -170,7 +170,8 @@ int starmap_mlp_loss_grad(starmap_mlp_t* net, const float* X, const float* T, co
     if (!net) return STARMAP_E_ARG;
     if (B == 0 || !X || !T || !grad) return mfail(net, STARMAP_E_ARG, "loss_grad needs B > 0 and X, T, grad");
     if (int rc = ensure_part(net, mlp::grad_blocks((long)B))) return rc;
-    if (mlp::loss_grad(X, T, idx, (long)B, net->packed, net->part, grad, loss, net->stream)) MCK(cudaGetLastError(), "loss_grad");
+    if (mlp::loss_grad(X, T, idx, (long)B, net->packed, net->part, grad, loss, net->engine, net->flag, net->stream))
+        MCK(cudaGetLastError(), "loss_grad");
     return STARMAP_OK;
 }
 

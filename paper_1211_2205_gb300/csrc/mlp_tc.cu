@@ -15,7 +15,7 @@
 // shared memory.  Layers: 38(48) -> 128 (3 MMAs), 128 -> 128 (8 MMAs),
 // 128 -> 16 (9 used, 8 MMAs with N = 16).
 //
-// Two kernels, one CTA per SM each:
+// Three kernels, one CTA per SM each:
 //  - k_forward_tc (inference on given input rows): five groups, each staging
 //    its own tiles, sharing four TMEM accumulators (a group loading its
 //    inputs holds none);
@@ -23,7 +23,10 @@
 //    tile's cell features from the moment grids into the input buffer of the
 //    consumer group that runs the tile's network; full / empty mbarriers
 //    hand the buffers back and forth, so the gather's memory latency hides
-//    behind the other tiles' tensor and activation work.
+//    behind the other tiles' tensor and activation work;
+//  - k_loss_grad_tc (training): the loss and every parameter gradient of a
+//    tile of samples, the backward contractions reading the same natural
+//    buffers MN-major (see the training section below).
 // Every wait is bounded; on expiry the kernel raises the error flag, skips
 // the rest, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -675,6 +678,371 @@ __global__ void k_tc_wait_selftest(int* err, int* result) {
     }
 }
 
+// ------------------------------------------------------------------ training
+// One CTA per tile of 128 samples computes the loss and every parameter
+// gradient with tcgen05: forward (3 layers), dH2 = dY W3, dH1 = dZ2 W2 and
+// the weight gradients dW3^T = H2^T dY, dW2 = dZ2^T H1, dW1 = dZ1^T X, which
+// contract over the samples.  Every operand stays in its natural layout (one
+// sample per row, as the forward layers and the epilogues write it); where a
+// contraction needs it the other way round, the MMA reads it as an MN-major
+// operand (transpose bit of the instruction descriptor).  The bias gradients
+// b1 and b2 come out of the same MMAs: X and H1 carry a column of ones, so
+// dW1 and dW2 gain a column sum_s dZ[s][o].
+constexpr int TR_THREADS = 256;          // two warps per TMEM lane quarter, each one half of the columns
+constexpr int H1K = HID + 16;            // H1 columns: the hidden values, a ones column, zeros
+constexpr int H1_BYTES = (H1K / 8) * (TM / 8) * 128;        // 36864
+constexpr int DY_BYTES = (OUTP / 8) * (TM / 8) * 128;       // 4096
+constexpr int ONES_X = NIN;              // X column holding 1: b1's gradient in dW1's column NIN
+constexpr int ONES_H = HID;              // H1 column holding 1: b2's gradient in dW2's column HID
+constexpr uint32_t TC_ACC = 0;           // TMEM: forward accumulators, then dH2, then dH1 (128 columns)
+constexpr uint32_t TC_DW3 = 128;         // dW3^T (16 columns)
+constexpr uint32_t TC_DW2 = 256;         // dW2 and b2's gradient (144 columns)
+constexpr uint32_t TC_DW1 = 400;         // dW1 and b1's gradient (48 columns)
+static_assert(TC_DW1 + KX_TC <= TMEM_COLS, "the training accumulators fit in TMEM");
+// Layout order matters for nothing but keeps every operand's MN-major
+// reading inside the CTA's allocation: the buffers read that way (W3, dY,
+// X, H1, H2) are followed by at least 32 KB of the others.
+struct TrSmem {
+    alignas(128) unsigned char w1[W1_BYTES];    // W1 [o][i], K = 48
+    alignas(128) unsigned char w2[W2_BYTES];    // W2 [o][i]
+    alignas(128) unsigned char w3[W3_BYTES];    // W3 [o (16)][i]
+    alignas(128) unsigned char dy[DY_BYTES];    // dY [s][o (16)]
+    alignas(128) unsigned char x[XC_BYTES];     // X [s][48]
+    alignas(128) unsigned char h1[H1_BYTES];    // H1 [s][144], later dZ1 in its first 128 columns
+    alignas(128) unsigned char h2[H_BYTES];     // H2 [s][128], later dZ2
+    alignas(16) float b1[HID];
+    alignas(16) float b2[HID];
+    alignas(16) float b3[OUTP];
+    float wloss[TR_THREADS / 32];
+    float wb3[GWARPS][OUTP];
+    alignas(8) uint64_t bar;
+    uint32_t tmem;
+    int stop;
+};
+static_assert(sizeof(TrSmem) <= 227 * 1024, "training kernel shared memory");
+
+// instruction descriptor with the operands' majorness: ta / tb = 1 reads A / B MN-major
+__host__ __device__ constexpr uint32_t idesc_t(int m, int n, int ta, int tb) {
+    return idesc(m, n) | ((uint32_t)ta << 15) | ((uint32_t)tb << 16);
+}
+// K-major reading of a natural buffer of `rows` rows: core matrices 128 bytes
+// apart along the rows, (rows / 8) * 128 apart along K; a K step of 16 is
+// two of the latter
+__device__ __forceinline__ uint64_t kdesc(uint32_t a, int rows) { return sdesc(a, (rows / 8) * 128, 128); }
+__device__ __forceinline__ uint64_t kstep(int rows) { return (uint64_t)((2 * (rows / 8) * 128) >> 4); }
+// MN-major reading of the same buffer (the contraction runs over its rows):
+// along K (the rows) core matrices are 128 bytes apart, along M/N (the
+// buffer's columns) (rows / 8) * 128; a K step of 16 rows advances 256 bytes
+__device__ __forceinline__ uint64_t mdesc(uint32_t a, int rows) { return sdesc(a, 128, (rows / 8) * 128); }
+constexpr uint64_t MSTEP = 256 >> 4;
+
+__device__ __forceinline__ void mma_k(uint32_t d, uint64_t a, uint64_t as, uint64_t b, uint64_t bs, uint32_t id,
+                                      int ksteps) {
+    for (int kk = 0; kk < ksteps; ++kk) mma_f16(d, a + kk * as, b + kk * bs, id, kk > 0);
+}
+
+// Thread 0 commits the MMAs it issued and waits for them; every thread then
+// learns whether to stop.  Returns false if a wait expired.
+__device__ __forceinline__ bool tr_sync_mma(TrSmem& S, uint32_t& ph, int* err) {
+    if (threadIdx.x == 0) {
+        mma_commit(&S.bar);
+        if (!mbar_wait(&S.bar, ph & 1, err)) S.stop = 1;
+    }
+    ++ph;
+    __syncthreads();
+    fence_after();
+    return S.stop == 0;
+}
+// Before the next MMAs read what the threads wrote: generic -> async proxy,
+// TMEM reads ordered before the MMAs that overwrite the columns.
+__device__ __forceinline__ void tr_publish() {
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+}
+
+// dZ = dH * (1 - H^2) for the thread's row and 64 columns starting at c0:
+// dH from TMEM, H (BF16) read from and dZ written over the natural buffer
+__device__ __forceinline__ void tanh_backward(unsigned char* buf, uint32_t tacc, int row, int c0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        uint32_t v[32];
+        tmem_ld32(tacc + (uint32_t)(c0 + 32 * q), v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int cb = 0; cb < 32; cb += 8) {
+            uint4* at = reinterpret_cast<uint4*>(buf + canon(row, c0 + 32 * q + cb, TM));
+            const uint4 hv = *at;
+            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&hw[e]);
+                const float h0 = __low2float(h), h1 = __high2float(h);
+                w[e] = pack_bf16_tc(__uint_as_float(v[cb + 2 * e]) * (1.f - h0 * h0),
+                                    __uint_as_float(v[cb + 2 * e + 1]) * (1.f - h1 * h1));
+            }
+            *at = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TR_THREADS, 1) k_loss_grad_tc(const float* __restrict__ X, const float* __restrict__ T,
+                                                                const int* __restrict__ idx, long B,
+                                                                const Packed* __restrict__ P, float* __restrict__ part,
+                                                                int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char raw[];
+    TrSmem& S = *reinterpret_cast<TrSmem*>(raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp % GWARPS, half = warp / GWARPS;
+    const int row = 32 * quarter + lane;                 // TMEM lane: a sample, or an output / input index
+    const long row0 = (long)blockIdx.x * TM;
+    float* out = part + (long)blockIdx.x * (NPARAM + 1);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.stop = 0;
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem)),
+                     "r"(TMEM_COLS) : "memory");
+    // weights (natural layouts; Packed's padding columns are zero)
+    {
+        const uint32_t w1 = su32(S.w1), w2 = su32(S.w2), w3 = su32(S.w3);
+        for (int i = threadIdx.x; i < HID * (KX_TC / 8); i += TR_THREADS) {
+            const int n = i / (KX_TC / 8), c = i % (KX_TC / 8);
+            cp_async16_tc(w1 + canon(n, 8 * c, HID), P->W1 + n * LDX + 8 * c);
+        }
+        for (int i = threadIdx.x; i < HID * (HID / 8); i += TR_THREADS) {
+            const int n = i / (HID / 8), c = i % (HID / 8);
+            cp_async16_tc(w2 + canon(n, 8 * c, HID), P->W2 + n * LDH + 8 * c);
+        }
+        for (int i = threadIdx.x; i < OUTP * (HID / 8); i += TR_THREADS) {
+            const int n = i / (HID / 8), c = i % (HID / 8);
+            cp_async16_tc(w3 + canon(n, 8 * c, OUTP), P->W3 + n * LDH + 8 * c);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int i = threadIdx.x; i < HID; i += TR_THREADS) { S.b1[i] = P->b1[i]; S.b2[i] = P->b2[i]; }
+        if (threadIdx.x < OUTP) S.b3[threadIdx.x] = P->b3[threadIdx.x];
+    }
+    // inputs: sample rows (gathered through idx), a ones column, zeros; H1's
+    // ones column and zeros behind it
+    {
+        const int r = threadIdx.x % TM, part_ = threadIdx.x / TM;       // half a row each
+        const long m = row0 + r;
+        const bool ok = m < B;
+        const float* xs = X + (ok ? (idx ? (long)idx[m] : m) : 0) * NIN;
+#pragma unroll
+        for (int c = 3 * part_; c < 3 * part_ + 3; ++c) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float v[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int col = 8 * c + 2 * e + h;
+                    v[h] = col < NIN ? (ok ? xs[col] : 0.f) : col == ONES_X ? 1.f : 0.f;
+                }
+                w[e] = pack_bf16_tc(v[0], v[1]);
+            }
+            *reinterpret_cast<uint4*>(S.x + canon(r, 8 * c, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        const uint32_t one = pack_bf16_tc(1.f, 0.f);
+        *reinterpret_cast<uint4*>(S.h1 + canon(r, HID + 8 * part_, TM)) =
+            part_ == 0 ? make_uint4(one, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    // the targets of the thread's sample (rows of the output epilogue), loaded
+    // now so that their latency hides behind the forward layers
+    float tgt[NOUT];
+    {
+        const long m = row0 + row;
+        const bool valid = half == 0 && m < B;
+        const float* ts = T + (valid ? (idx ? (long)idx[m] : m) : 0) * NOUT;
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) tgt[o] = valid ? ts[o] : 0.f;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    fence_before();
+    tr_publish();
+    const uint32_t tm = S.tmem;
+    const uint32_t tl = tm + ((uint32_t)(32 * quarter) << 16);      // this warp's lane quarter, column 0
+    uint32_t ph = 0;
+    bool ok = true;
+    // ---- forward: Z1 = X W1^T, H1 = tanh(Z1 + b1)
+    if (threadIdx.x == 0) mma_k(tm + TC_ACC, kdesc(su32(S.x), TM), kstep(TM), kdesc(su32(S.w1), HID), kstep(HID),
+                                idesc(TM, HID), KX_TC / 16);
+    ok = tr_sync_mma(S, ph, err);
+    if (ok) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c0 = 64 * half + 32 * q;
+            uint32_t v[32];
+            tmem_ld32(tl + TC_ACC + (uint32_t)c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int cb = 0; cb < 32; cb += 8) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    w[e] = bias_act2_tc(v[cb + 2 * e], v[cb + 2 * e + 1], S.b1[c0 + cb + 2 * e], S.b1[c0 + cb + 2 * e + 1]);
+                *reinterpret_cast<uint4*>(S.h1 + canon(row, c0 + cb, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        tr_publish();
+        // Z2 = H1 W2^T, H2 = tanh(Z2 + b2)
+        if (threadIdx.x == 0) mma_k(tm + TC_ACC, kdesc(su32(S.h1), TM), kstep(TM), kdesc(su32(S.w2), HID), kstep(HID),
+                                    idesc(TM, HID), HID / 16);
+        ok = tr_sync_mma(S, ph, err);
+    }
+    if (ok) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c0 = 64 * half + 32 * q;
+            uint32_t v[32];
+            tmem_ld32(tl + TC_ACC + (uint32_t)c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int cb = 0; cb < 32; cb += 8) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    w[e] = bias_act2_tc(v[cb + 2 * e], v[cb + 2 * e + 1], S.b2[c0 + cb + 2 * e], S.b2[c0 + cb + 2 * e + 1]);
+                *reinterpret_cast<uint4*>(S.h2 + canon(row, c0 + cb, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        tr_publish();
+        // Y = H2 W3^T (+ b3 below)
+        if (threadIdx.x == 0) mma_k(tm + TC_ACC, kdesc(su32(S.h2), TM), kstep(TM), kdesc(su32(S.w3), OUTP), kstep(OUTP),
+                                    idesc(TM, OUTP), HID / 16);
+        ok = tr_sync_mma(S, ph, err);
+    }
+    if (ok) {
+        // dY = 2 (y - t) / (B 9) on the tile's samples and the 9 outputs, else 0;
+        // the loss and b3's gradient (column sums of the BF16 dY) per warp
+        const float inv = 2.f / (float)(B * NOUT);
+        if (half == 0) {
+            uint32_t v[16];
+            tmem_ld16(tl + TC_ACC, v);
+            tmem_wait_ld();
+            const bool valid = row0 + row < B;
+            float lsum = 0.f, d[OUTP];
+#pragma unroll
+            for (int o = 0; o < OUTP; ++o) {
+                d[o] = 0.f;
+                if (valid && o < NOUT) {
+                    const float rr = __uint_as_float(v[o]) + S.b3[o] - tgt[o];
+                    lsum += rr * rr;
+                    d[o] = inv * rr;
+                }
+            }
+            uint32_t w[OUTP / 2];
+#pragma unroll
+            for (int e = 0; e < OUTP / 2; ++e) w[e] = pack_bf16_tc(d[2 * e], d[2 * e + 1]);
+            *reinterpret_cast<uint4*>(S.dy + canon(row, 0, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(S.dy + canon(row, 8, TM)) = make_uint4(w[4], w[5], w[6], w[7]);
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) {
+                const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162*>(&w[o / 2]);
+                float c = (o & 1) ? __high2float(pr) : __low2float(pr);
+#pragma unroll
+                for (int sh = 16; sh > 0; sh >>= 1) c += __shfl_xor_sync(0xffffffffu, c, sh);
+                if (lane == 0) S.wb3[quarter][o] = c;
+            }
+#pragma unroll
+            for (int sh = 16; sh > 0; sh >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, sh);
+            if (lane == 0) S.wloss[quarter] = lsum / (float)(B * NOUT);
+        }
+        tr_publish();
+        // dH2 = dY W3 (K = 16 outputs; W3 read MN-major) and dW3^T = H2^T dY
+        // (M = inputs, N = outputs, K = samples; both read MN-major)
+        if (threadIdx.x == 0) {
+            mma_k(tm + TC_ACC, kdesc(su32(S.dy), TM), kstep(TM), mdesc(su32(S.w3), OUTP), MSTEP, idesc_t(TM, HID, 0, 1), 1);
+            mma_k(tm + TC_DW3, mdesc(su32(S.h2), TM), MSTEP, mdesc(su32(S.dy), TM), MSTEP, idesc_t(HID, OUTP, 1, 1),
+                  TM / 16);
+        }
+        ok = tr_sync_mma(S, ph, err);
+    }
+    if (ok) {
+        // dZ2 = dH2 (1 - H2^2) over H2; dW3 from its transpose (lane = input)
+        tanh_backward(S.h2, tl + TC_ACC, row, 64 * half);
+        if (half == 1) {
+            uint32_t v[16];
+            tmem_ld16(tl + TC_DW3, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) out[OFF_W3 + o * HID + row] = __uint_as_float(v[o]);
+        }
+        tr_publish();
+        // dH1 = dZ2 W2 (W2 read MN-major) and dW2 = dZ2^T [H1 | 1]
+        // (M = outputs, N = inputs and the ones column, K = samples)
+        if (threadIdx.x == 0) {
+            mma_k(tm + TC_ACC, kdesc(su32(S.h2), TM), kstep(TM), mdesc(su32(S.w2), HID), MSTEP, idesc_t(TM, HID, 0, 1),
+                  HID / 16);
+            mma_k(tm + TC_DW2, mdesc(su32(S.h2), TM), MSTEP, mdesc(su32(S.h1), TM), MSTEP, idesc_t(HID, H1K, 1, 1),
+                  TM / 16);
+        }
+        ok = tr_sync_mma(S, ph, err);
+    }
+    if (ok) {
+        // dZ1 = dH1 (1 - H1^2) over H1's first 128 columns; dW2 and b2's gradient
+        tanh_backward(S.h1, tl + TC_ACC, row, 64 * half);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c0 = 64 * half + 32 * q;
+            uint32_t v[32];
+            tmem_ld32(tl + TC_DW2 + (uint32_t)c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) out[OFF_W2 + row * HID + c0 + e] = __uint_as_float(v[e]);
+        }
+        if (half == 0) {
+            uint32_t v[16];
+            tmem_ld16(tl + TC_DW2 + (uint32_t)ONES_H, v);
+            tmem_wait_ld();
+            out[OFF_B2 + row] = __uint_as_float(v[0]);
+        }
+        tr_publish();
+        // dW1 = dZ1^T [X | 1] (M = outputs, N = the 48 input columns, K = samples)
+        if (threadIdx.x == 0)
+            mma_k(tm + TC_DW1, mdesc(su32(S.h1), TM), MSTEP, mdesc(su32(S.x), TM), MSTEP, idesc_t(HID, KX_TC, 1, 1),
+                  TM / 16);
+        ok = tr_sync_mma(S, ph, err);
+    }
+    if (ok) {
+        if (half == 0) {
+            uint32_t v[32];
+            tmem_ld32(tl + TC_DW1, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) out[OFF_W1 + row * NIN + e] = __uint_as_float(v[e]);
+        } else {
+            uint32_t v[16];
+            tmem_ld16(tl + TC_DW1 + 32u, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < NIN - 32; ++e) out[OFF_W1 + row * NIN + 32 + e] = __uint_as_float(v[e]);
+            out[OFF_B1 + row] = __uint_as_float(v[ONES_X - 32]);
+        }
+        if (threadIdx.x < NOUT) {
+            float c = 0.f;
+            for (int q = 0; q < GWARPS; ++q) c += S.wb3[q][threadIdx.x];
+            out[OFF_B3 + threadIdx.x] = c;
+        }
+        if (threadIdx.x == 0) {
+            float l = 0.f;
+            for (int q = 0; q < GWARPS; ++q) l += S.wloss[q];
+            out[NPARAM] = l;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
 int sms_tc() {
     static int n = 0;
     if (n == 0) {
@@ -712,6 +1080,20 @@ int tc_wait_selftest(int* gave_up) {
     if (e != cudaSuccess) return -4;
     *gave_up = (h[0] == 1 && h[1] == 0 && h[2] == 0 && h[3] == 1) ? 1 : 0;
     return 0;
+}
+
+int loss_grad_tc(const float* X, const float* T, const int* idx, long B, const Packed* P, float* part, int* err,
+                 void* stream) {
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_loss_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrSmem)) !=
+            cudaSuccess)
+            return -4;
+        attr = true;
+    }
+    const long blocks = (B + TM - 1) / TM;
+    k_loss_grad_tc<<<(unsigned)blocks, TR_THREADS, sizeof(TrSmem), (cudaStream_t)stream>>>(X, T, idx, B, P, part, err);
+    return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
 int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void* stream) {

@@ -72,17 +72,25 @@ def test_forward_matches_oracle(M):
     assert np.max(np.abs(Y - ref)) <= 3 * BF16_TOL * np.max(np.abs(ref))
 
 
-def test_gradients_match_oracle():
+ENGINES = ["mma_sync", "tcgen05"]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("Mall,B", [(1000, 700), (300, 128), (300, 129), (50, 1)])
+def test_gradients_match_oracle(engine, Mall, B):
     """Loss and gradient of a minibatch given by an index list (700 of 1000
-    samples: five full tiles and a ragged one) against the oracle's
-    backward with the same BF16 weights and inputs."""
-    rng = np.random.default_rng(11)
-    Mall, B = 1000, 700
+    samples: five full tiles and a ragged one; one whole tile; a tile and
+    one sample; a single sample) against the oracle's backward with the
+    same BF16 weights and inputs, on both engines (the tcgen05 kernel reads
+    the activations MN-major for the weight gradients and takes the bias
+    gradients from ones columns)."""
+    rng = np.random.default_rng(11 + B)
     X = rng.normal(size=(Mall, C.N_IN)).astype(np.float32)
     T = rng.normal(size=(Mall, C.N_OUT)).astype(np.float32)
     idx = rng.permutation(Mall)[:B].astype(np.int32)
     params = _params(5, scale_out=0.7)
     net = capi.Network(params)
+    net.set_engine(engine)
     g = torch.zeros(capi.MLP_PARAMS, device="cuda")
     loss = torch.zeros(1, device="cuda")
     Xd, Td, Id = _dev(X), _dev(T), _dev(idx)
@@ -96,11 +104,39 @@ def test_gradients_match_oracle():
         assert _rel(got[k], ref[k]) <= BF16_TOL, k
 
 
-def test_gradient_is_deterministic():
+def test_engines_give_the_same_gradient():
+    """The tcgen05 and mma.sync training kernels compute the same products of
+    the same BF16 operands; only the FP32 summation order differs."""
+    rng = np.random.default_rng(15)
+    M = 3000
+    X = _dev(rng.normal(size=(M, C.N_IN)).astype(np.float32))
+    T = _dev(rng.normal(size=(M, C.N_OUT)).astype(np.float32))
+    params = _params(8, scale_out=0.5)
+    got = {}
+    for engine in ENGINES:
+        net = capi.Network(params)
+        net.set_engine(engine)
+        g = torch.zeros(capi.MLP_PARAMS, device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        torch.cuda.synchronize()
+        net.loss_grad(X, T, M, g, loss)
+        net.sync()
+        got[engine] = (g.cpu().numpy().astype(np.float64), float(loss.item()))
+        net.close()
+    (ga, la), (gb, lb) = got["mma_sync"], got["tcgen05"]
+    assert abs(la - lb) <= 1e-4 * abs(la)
+    da, db = capi.params_to_dict(ga), capi.params_to_dict(gb)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert _rel(db[k], da[k]) <= 2e-3, k
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_gradient_is_deterministic(engine):
     rng = np.random.default_rng(12)
     X = rng.normal(size=(900, C.N_IN)).astype(np.float32)
     T = rng.normal(size=(900, C.N_OUT)).astype(np.float32)
     net = capi.Network(_params(6))
+    net.set_engine(engine)
     Xd, Td = _dev(X), _dev(T)
     g1 = torch.zeros(capi.MLP_PARAMS, device="cuda")
     g2 = torch.zeros(capi.MLP_PARAMS, device="cuda")
@@ -111,7 +147,8 @@ def test_gradient_is_deterministic():
     assert torch.equal(g1, g2)
 
 
-def test_adam_steps_match_oracle_optimizer():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_adam_steps_match_oracle_optimizer(engine):
     """Three Adam steps on the GPU against the oracle's Adam fed with the
     GPU's own gradients (the optimiser arithmetic in isolation)."""
     rng = np.random.default_rng(13)
@@ -119,6 +156,7 @@ def test_adam_steps_match_oracle_optimizer():
     T = rng.normal(size=(512, C.N_OUT)).astype(np.float32)
     params = _params(7)
     net = capi.Network(params)
+    net.set_engine(engine)
     ref = capi.params_to_dict(params)
     opt = C.Adam(ref, lr=2e-3)
     Xd, Td = _dev(X), _dev(T)
@@ -135,7 +173,8 @@ def test_adam_steps_match_oracle_optimizer():
     np.testing.assert_allclose(net.params, capi.params_from_dict(ref), rtol=0, atol=2e-6)
 
 
-def test_training_fits_a_teacher_network():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_training_fits_a_teacher_network(engine):
     """Minibatch Adam on the GPU learns the map of another network."""
     rng = np.random.default_rng(14)
     M = 8192
@@ -143,6 +182,7 @@ def test_training_fits_a_teacher_network():
     teacher = C.MLP(capi.params_to_dict(_params(21, scale_out=1.0)))
     T = teacher.forward(X.astype(np.float64))[0].astype(np.float32)
     net = capi.Network(_params(22, scale_out=0.1))
+    net.set_engine(engine)
     Xd, Td = _dev(X), _dev(T)
     loss = torch.zeros(1, device="cuda")
     torch.cuda.synchronize()
