@@ -165,6 +165,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 consecutive columns of this warp's 32 lanes in one store
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+        ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+          "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+          "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+          "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned long long gtime() {
     unsigned long long t;
@@ -314,7 +327,7 @@ __device__ bool slot_take(int* free_slots, int* slot, int* err) {
 // the bytes of two core-matrix columns; shared memory is below 2^18 bytes,
 // so the field does not carry.
 template <class Sm>
-__device__ __forceinline__ void issue_layer(const Sm& S, int layer, uint32_t dcol, uint32_t a0) {
+__device__ __forceinline__ void issue_layer(const Sm& S, int layer, uint32_t dcol, uint32_t a0, bool onto = false) {
     const uint64_t ad = sdesc(a0, (TM / 8) * 128, 128);
     constexpr uint64_t ASTEP = (2 * (TM / 8) * 128) >> 4;
     if (layer == 0) {
@@ -326,7 +339,7 @@ __device__ __forceinline__ void issue_layer(const Sm& S, int layer, uint32_t dco
         const uint64_t bd = sdesc(su32(S.w2), (HID / 8) * 128, 128);
 #pragma unroll
         for (int kk = 0; kk < HID / 16; ++kk)
-            mma_f16(dcol, ad + kk * ASTEP, bd + kk * ((2 * (HID / 8) * 128) >> 4), idesc(TM, HID), kk > 0);
+            mma_f16(dcol, ad + kk * ASTEP, bd + kk * ((2 * (HID / 8) * 128) >> 4), idesc(TM, HID), onto || kk > 0);
     } else {
         const uint64_t bd = sdesc(su32(S.w3), (OUTP / 8) * 128, 128);
 #pragma unroll
@@ -339,7 +352,10 @@ __device__ __forceinline__ void issue_layer(const Sm& S, int layer, uint32_t dco
 // (tacc: the thread's lane, first column) -> row `row` of the next layer's
 // A operand h.
 // bias == nullptr: the bias is already in the accumulator (layer 0).
-__device__ __forceinline__ void epilogue_layer(unsigned char* h, uint32_t tacc, const float* bias, int row) {
+// prefill != nullptr: once a 32-column block is read, it is overwritten with
+// prefill (the next layer's bias; that layer's MMAs then accumulate onto it)
+__device__ __forceinline__ void epilogue_layer(unsigned char* h, uint32_t tacc, const float* bias, int row,
+                                               const float* prefill = nullptr) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         uint32_t v[32];
@@ -363,7 +379,17 @@ __device__ __forceinline__ void epilogue_layer(unsigned char* h, uint32_t tacc, 
             *reinterpret_cast<uint4*>(h + canon(row, 32 * q + cb, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
             *reinterpret_cast<uint4*>(h + canon(row, 32 * q + cb + 8, TM)) = make_uint4(w[4], w[5], w[6], w[7]);
         }
+        if (prefill) {
+            uint32_t b[32];
+#pragma unroll
+            for (int e = 0; e < 32; e += 4) {
+                const uint4 t = *reinterpret_cast<const uint4*>(prefill + 32 * q + e);
+                b[e] = t.x; b[e + 1] = t.y; b[e + 2] = t.z; b[e + 3] = t.w;
+            }
+            tmem_st32(tacc + (uint32_t)(32 * q), b);
+        }
     }
+    if (prefill) tmem_wait_st();
 }
 
 // The three layers of the group's tile (inputs at the start of its operand
@@ -563,7 +589,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<
                     bool ok = layer > 0 || cl_wait(&S.abort, &S.full[g], (uint32_t)use & 1, err);
                     if (ok) {
                         fence_after();
-                        issue_layer(S, layer, dcol, su32(layer == 0 ? S.x[g] : S.h[g]));
+                        issue_layer(S, layer, dcol, su32(layer == 0 ? S.x[g] : S.h[g]), layer == 1);
                         mma_commit(&S.mma[g]);
                         ok = cl_wait(&S.abort, &S.mma[g], ph & 1, err);
                         if (ok && layer == 0) mbar_arrive_tc(&S.empty[g]);   // the input buffer is read
@@ -576,7 +602,8 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_closure_tc(const ClosureArgs<
                 fence_after();
                 if (layer == 0 && m < M) s = scl[m];
                 if (layer == 2) break;
-                epilogue_layer(S.h[g], tacc, layer == 0 ? nullptr : S.b2, row);
+                // layer 0's epilogue leaves b2 in the accumulator for layer 1 to add onto
+                epilogue_layer(S.h[g], tacc, nullptr, row, layer == 0 ? S.b2 : nullptr);
                 fence_async_smem();
                 fence_before();
                 group_sync(g);
