@@ -413,12 +413,13 @@ int starmap_sync(starmap_t* h);
 /* Failure-detection self-test (no counterpart in the paper).  Runs one CTA
  * that waits, with the same bounded wait the pass kernels use (2 s limit),
  * for an mbarrier phase that nothing completes, and one that runs the
- * closure network kernels' two waits (2 s each) on an mbarrier phase that
- * nothing completes and on a TMEM slot pool with every slot held.  Each wait
- * must give up, raise the error flag and return; the call then returns
- * STARMAP_E_TIMEOUT (the expected outcome; the CUDA context stays usable).
- * STARMAP_E_STATE if a wait did not give up, STARMAP_E_CUDA if a kernel
- * could not run.  Synchronous (legacy default stream), about 6 s. */
+ * network kernels' three waits (2 s each): the closure kernel's and the
+ * forward / training kernels' waits on an mbarrier phase that nothing
+ * completes, and the wait for a TMEM slot of a pool with every slot held.
+ * Each wait must give up, raise the error flag and return; the call then
+ * returns STARMAP_E_TIMEOUT (the expected outcome; the CUDA context stays
+ * usable).  STARMAP_E_STATE if a wait did not give up, STARMAP_E_CUDA if a
+ * kernel could not run.  Synchronous (legacy default stream), about 8 s. */
 int starmap_selftest_bounded_wait(void);
 
 /* Host-side fault injection for tests (no counterpart in the paper): the

@@ -88,9 +88,10 @@ int closure(const ClosureArgs<T>& A, const Packed* P, float* scratch, int engine
 
 // tcgen05 network (mlp_tc.cu)
 size_t tc_smem_bytes();
-// Self-test of the network kernels' bounded waits (an mbarrier phase nothing
+// Self-test of the network kernels' bounded waits (the closure kernel's and
+// the forward / training kernels' waits on an mbarrier phase nothing
 // completes, a TMEM slot request with every slot held): *gave_up = 1 when
-// both waits expired and raised the flag as they must.
+// every wait expired and raised the flag as it must.
 int tc_wait_selftest(int* gave_up);
 int forward_tc(const float* X, long M, const Packed* P, float* Y, int* err, void* stream);
 // per-tile partial loss and gradients of loss_grad on tcgen05 (same layout of part)

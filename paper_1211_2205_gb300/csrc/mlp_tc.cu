@@ -682,9 +682,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_forward_tc(const float* __res
     tc_teardown(S);
 }
 
-// Self-test of the network kernels' bounded waits, with no tensor work: a
-// wait for an mbarrier phase that nothing completes, and a request for a
-// TMEM slot while every slot is held.  Both must give up and raise the flag.
+// Self-test of the network kernels' bounded waits, with no tensor work: the
+// closure kernel's wait and the forward / training kernels' wait for an
+// mbarrier phase that nothing completes, and a request for a TMEM slot while
+// every slot is held.  All must give up and raise the flag.
 __global__ void k_tc_wait_selftest(int* err, int* result) {
     __shared__ uint64_t bar;
     __shared__ int abort_flag, free_slots, slot;
@@ -699,9 +700,11 @@ __global__ void k_tc_wait_selftest(int* err, int* result) {
     if (threadIdx.x == 0) {
         const bool waited = cl_wait(&abort_flag, &bar, 0, err);
         const bool took = slot_take(&free_slots, &slot, err);
+        const bool plain = mbar_wait(&bar, 0, err);
         result[0] = waited ? 1 : 0;
         result[1] = took ? 1 : 0;
         result[2] = abort_flag;
+        result[3] = plain ? 1 : 0;
     }
 }
 
@@ -1095,17 +1098,17 @@ size_t tc_smem_bytes() { return sizeof(TcSmem); }
 
 int tc_wait_selftest(int* gave_up) {
     int* d = nullptr;
-    if (cudaMalloc(&d, 4 * sizeof(int)) != cudaSuccess) return -4;
-    int h[4] = {0, -1, -1, -1};
-    cudaError_t e = cudaMemcpy(d, h, 4 * sizeof(int), cudaMemcpyHostToDevice);
+    if (cudaMalloc(&d, 5 * sizeof(int)) != cudaSuccess) return -4;
+    int h[5] = {0, -1, -1, -1, -1};
+    cudaError_t e = cudaMemcpy(d, h, 5 * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_tc_wait_selftest<<<1, 32>>>(d, d + 1);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpy(h, d, 4 * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, 5 * sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return -4;
-    *gave_up = (h[0] == 1 && h[1] == 0 && h[2] == 0 && h[3] == 1) ? 1 : 0;
+    *gave_up = (h[0] == 1 && h[1] == 0 && h[2] == 0 && h[3] == 1 && h[4] == 0) ? 1 : 0;
     return 0;
 }
 
