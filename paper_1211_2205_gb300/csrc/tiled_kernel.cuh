@@ -330,7 +330,9 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
         int k = pw, tl = 0, r = pw, u = 0;
         while (k >= nst && nst > 0) { k -= nst; ++tl; }
         int tile_at = -1, bx = 0, by = 0;
+        bool entered = false;   // this warp has just issued its first stage of tile tl
         for (int G = pw; G < total; G += PRODUCER_WARPS) {
+            entered = tl != tile_at;
             if (tl != tile_at) {
                 // box origin of this lane's slot in tile tl (tensor coordinates x' = x + VEC, row = y + 1)
                 tile_at = tl;
@@ -355,6 +357,22 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             if (mine != 0u) tma_load_3d(ring + r * STAGE_BYTES + slot_off(slot), map, bx, by, comp, &full[r]);
+            if (entered && tl > 0 && pw == 0 && prm.nclasses == 2) {
+                // the decay pairs of this tile (not the first: there the consumers
+                // load them at once) into L2 while the consumers finish the previous
+                // tiles; lane = (kind, class, plane a / b, half row of 32)
+                const int tile = t0 + tl * tstride;
+                const int x0 = (tile % prm.tiles_x) * TX, y0 = (tile / prm.tiles_x) * TY;
+                const int kind = lane >> 4, c = (lane >> 3) & 1, ab = (lane >> 2) & 1, hx = lane & 1;
+                const OutGrid& Gk = prm.out[kind];
+                const int x = x0 + 32 * hx;
+                if (Gk.coef != nullptr && x < Gk.nx && ((lane >> 1) & 1) == 0) {
+                    const long plane = (long)Gk.nx * Gk.ny;
+                    const float* base = Gk.coef + ((long)c * 4 + 2 * prm.which + ab) * plane + x;
+                    for (int y = y0; y < y0 + TY && y < Gk.ny; ++y)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (long)y * Gk.nx));
+                }
+            }
             last = G;
             k += PRODUCER_WARPS;
             while (k >= nst) { k -= nst; ++tl; }
