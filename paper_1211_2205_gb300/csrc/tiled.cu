@@ -624,6 +624,16 @@ int tiled_update(TiledPlan* pl, const SystemMatrices& sys, const std::vector<int
             prm.err = pl->err_dev;
             prm.smem_part_off = part_off;
             prm.smem_stage_off = stage_off;
+            for (int K = 0; K < 2; ++K) {
+                int slot = -1;
+                bool one = true;
+                for (const int2& f : fk[K])
+                    if (f.y >= 0) {
+                        if (slot >= 0 && f.y != slot) one = false;
+                        slot = f.y;
+                    }
+                prm.pf_src[K] = slot >= 0 && one ? (const float*)src_dev[slot] : nullptr;
+            }
         }
     }
     pl->ready = true;

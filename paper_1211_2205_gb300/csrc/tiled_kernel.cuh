@@ -119,6 +119,8 @@ struct Params {
     const float* const* srcs;   // source arrays by slot
     int* err;                   // bounded-wait failure flag
     int smem_coef_off[2], smem_fin_off[2], smem_part_off, smem_stage_off;   // byte offsets in dynamic smem
+    const float* pf_src[2];     // per output kind: the source array its finalisations read, if it
+                                // has exactly one (prefetched into L2 with the decay pairs), else null
 };
 
 __host__ __device__ constexpr int nq_of(int l) { return l < 0 ? 0 : l / 2 + 1; }
@@ -358,19 +360,23 @@ __device__ __forceinline__ void tiled_tiles(const Params& prm, const CUtensorMap
             if (!ok) break;
             if (mine != 0u) tma_load_3d(ring + r * STAGE_BYTES + slot_off(slot), map, bx, by, comp, &full[r]);
             if (entered && tl > 0 && pw == 0 && prm.nclasses == 2) {
-                // the decay pairs of this tile (not the first: there the consumers
-                // load them at once) into L2 while the consumers finish the previous
-                // tiles; lane = (kind, class, plane a / b, half row of 32)
+                // the decay pairs (and the source) of this tile (not the first: there
+                // the consumers load them at once) into L2 while the consumers finish
+                // the previous tiles; lane = (kind, class, plane a / b, half row of 32)
                 const int tile = t0 + tl * tstride;
                 const int x0 = (tile % prm.tiles_x) * TX, y0 = (tile / prm.tiles_x) * TY;
                 const int kind = lane >> 4, c = (lane >> 3) & 1, ab = (lane >> 2) & 1, hx = lane & 1;
                 const OutGrid& Gk = prm.out[kind];
                 const int x = x0 + 32 * hx;
-                if (Gk.coef != nullptr && x < Gk.nx && ((lane >> 1) & 1) == 0) {
+                if (x < Gk.nx) {
                     const long plane = (long)Gk.nx * Gk.ny;
-                    const float* base = Gk.coef + ((long)c * 4 + 2 * prm.which + ab) * plane + x;
-                    for (int y = y0; y < y0 + TY && y < Gk.ny; ++y)
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (long)y * Gk.nx));
+                    // lanes with bit 1 clear: decay pairs; lanes 2 + 16 kind (+1): the kind's source
+                    const float* base = ((lane >> 1) & 1) == 0
+                        ? (Gk.coef != nullptr ? Gk.coef + ((long)c * 4 + 2 * prm.which + ab) * plane + x : nullptr)
+                        : ((lane & 12) == 0 && prm.pf_src[kind] != nullptr ? prm.pf_src[kind] + x : nullptr);
+                    if (base != nullptr)
+                        for (int y = y0; y < y0 + TY && y < Gk.ny; ++y)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (long)y * Gk.nx));
                 }
             }
             last = G;
