@@ -859,12 +859,12 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_loss_grad_tc(const float* __r
     // inputs: sample rows (gathered through idx), a ones column, zeros; H1's
     // ones column and zeros behind it
     {
-        const int r = threadIdx.x % TM, part_ = threadIdx.x / TM;       // half a row each
+        const int r = threadIdx.x % TM, side = threadIdx.x / TM;        // half a row each
         const long m = row0 + r;
         const bool ok = m < B;
         const float* xs = X + (ok ? (idx ? (long)idx[m] : m) : 0) * NIN;
 #pragma unroll
-        for (int c = 3 * part_; c < 3 * part_ + 3; ++c) {
+        for (int c = 3 * side; c < 3 * side + 3; ++c) {
             uint32_t w[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -879,8 +879,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_loss_grad_tc(const float* __r
             *reinterpret_cast<uint4*>(S.x + canon(r, 8 * c, TM)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         const uint32_t one = pack_bf16_tc(1.f, 0.f);
-        *reinterpret_cast<uint4*>(S.h1 + canon(r, HID + 8 * part_, TM)) =
-            part_ == 0 ? make_uint4(one, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(S.h1 + canon(r, HID + 8 * side, TM)) =
+            side == 0 ? make_uint4(one, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
     }
     // the targets of the thread's sample (rows of the output epilogue), loaded
     // now so that their latency hides behind the forward layers
