@@ -1,5 +1,6 @@
-"""The ncu summaries under profiles/: plain text only, and every ncu command
-they give runs with the GPU clocks left alone (--clock-control none)."""
+"""The ncu summaries under profiles/: plain text only, every ncu command
+they give runs with the GPU clocks left alone (--clock-control none), and the
+commands run committed files only (no scratch scripts)."""
 import os
 import re
 
@@ -42,3 +43,14 @@ def test_every_ncu_command_leaves_the_clocks_alone():
                         seen += 1
                         assert "--clock-control none" in part, f"{name}: {part.strip()[:80]}"
     assert seen >= 5
+
+
+def test_commands_run_committed_files_only():
+    for name in sorted(os.listdir(PROFILES)):
+        if not name.endswith(".md"):
+            continue
+        with open(os.path.join(PROFILES, name)) as f:
+            for cmd in _commands(f.read()):
+                assert "_work" not in cmd, f"{name}: {cmd.strip()[:80]}"
+                for script in re.findall(r"python3? (\S+\.py)", cmd):
+                    assert os.path.exists(os.path.join(ROOT, script)), f"{name}: {script}"
